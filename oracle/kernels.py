@@ -1,0 +1,100 @@
+"""Oracle: Green's functions, the system matrix and proxy surfaces.
+
+Test infrastructure (see the package header).
+
+Green's functions (Sec. 2, Example 1 and 2; Sec. 6.1.2):
+  laplace2d    G = -(1/2 pi) log|x - y|          (eq. 2d-laplace)
+  laplace3d    G = 1 / (4 pi |x - y|)             (eq. 3d-laplace)
+  helmholtz2d  G = (i/4) H0^(1)(k |x - y|)        (eq. 2d-helmholtz)
+System matrix: A = I + w K with K_ij = G(x_i, x_j) for i != j and K_ii = 0
+(punctured trapezoid / one-point rule, the configuration the workloads
+state; w = h for curves, 4 pi / N on the sphere).
+
+Proxy surfaces (Sec. 3.2, Fig. proxy-comp; count per Sec. 6 opening):
+  2D  n_p points on a circle of radius ratio * (sqrt(2)/2) * s around the box
+      centre (s = box side, so ratio times the box circumradius), angles
+      2 pi j / n_p;
+  3D  a g x g grid of cell centres on each of the 6 faces of a cube of
+      half-width ratio * s / 2 (6 g^2 = n_p points), faces in the order
+      -x, +x, -y, +y, -z, +z.
+H0^(1) is taken from scipy.special.hankel1, a library primitive.
+
+Pins: tests/test_oracle_solver.py checks the Laplace 2D kernel through the
+closed-form spectrum of A on the unit circle (eigenvalue 1 - ln(N)/N for the
+constant mode, and its continuum limit 1 + 1/(2m)); the Helmholtz kernel
+through the continuum limit 1 + (i pi / 2) J_m(k) H_m^(1)(k) on the circle;
+the 3D kernel through the single-layer eigenvalue 1 + 1/(2l+1) of the
+spherical harmonics on the sphere.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import hankel1
+
+KINDS = ("laplace2d", "helmholtz2d", "laplace3d")
+
+
+def is_complex(kind: str) -> bool:
+    return kind == "helmholtz2d"
+
+
+def green(kind: str, X: np.ndarray, Y: np.ndarray, kwave: float = 0.0) -> np.ndarray:
+    """G(x_i, y_j) for targets X (dim, m) and sources Y (dim, n); r > 0 assumed."""
+    diff = X[:, :, None] - Y[:, None, :]
+    r = np.sqrt(np.sum(diff * diff, axis=0))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        if kind == "laplace2d":
+            return -np.log(r) / (2.0 * np.pi)
+        if kind == "laplace3d":
+            return 1.0 / (4.0 * np.pi * r)
+        if kind == "helmholtz2d":
+            return 0.25j * hankel1(0, kwave * r)
+    raise ValueError(kind)
+
+
+def system_block(kind, pts, I, J, w, kwave=0.0) -> np.ndarray:
+    """A(I, J) = delta_ij + w G(x_i, x_j), with the diagonal term K_ii = 0."""
+    I = np.asarray(I)
+    J = np.asarray(J)
+    G = green(kind, pts[:, I], pts[:, J], kwave)
+    same = I[:, None] == J[None, :]
+    G[same] = 0.0
+    A = w * G
+    A[same] = 1.0
+    return A
+
+
+def offdiag_block(kind, pts, I, J, w, kwave=0.0) -> np.ndarray:
+    """w G(x_i, x_j) between two disjoint point sets."""
+    return w * green(kind, pts[:, np.asarray(I)], pts[:, np.asarray(J)], kwave)
+
+
+def proxy_points(dim: int, center: np.ndarray, side: float, nproxy: int,
+                 ratio: float = 1.5) -> np.ndarray:
+    """Proxy surface points, shape (dim, nproxy)."""
+    if dim == 2:
+        rho = ratio * (np.sqrt(2.0) / 2.0) * side
+        th = 2.0 * np.pi * np.arange(nproxy) / nproxy
+        return center[:, None] + rho * np.vstack([np.cos(th), np.sin(th)])
+    g = int(round(np.sqrt(nproxy / 6.0)))
+    if 6 * g * g != nproxy:
+        raise ValueError("3D proxy count must be 6 g^2")
+    h = ratio * side / 2.0
+    u = -h + (2.0 * np.arange(g) + 1.0) * h / g
+    ua, ub = np.meshgrid(u, u, indexing="ij")
+    ua = ua.ravel()
+    ub = ub.ravel()
+    faces = []
+    for axis in range(3):
+        others = [a for a in range(3) if a != axis]
+        for sign in (-1.0, 1.0):
+            f = np.zeros((3, g * g))
+            f[axis] = sign * h
+            f[others[0]] = ua
+            f[others[1]] = ub
+            faces.append(f)
+    return center[:, None] + np.hstack(faces)
+
+
+def proxy_radius_2d(side: float, ratio: float = 1.5) -> float:
+    return ratio * (np.sqrt(2.0) / 2.0) * side

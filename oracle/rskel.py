@@ -1,0 +1,287 @@
+"""Oracle: recursive skeletonization -- compression, inverse, solve, apply.
+
+Test infrastructure (see the package header).  Symmetric kernels only (all
+three Green's functions give A = A^T), so each box needs a single ID whose
+projection P serves as both R_i = P and L_i = P^T (Sec. 3.1 with identical
+row and column skeletons; complex symmetric Helmholtz uses the transpose,
+not the conjugate transpose).
+
+Build, level by level from the leaves (Sec. 3.1, the two-step multilevel
+procedure; depth L of the tree is compression level 1, depth 1 is level
+lambda, depth 0 the root):
+  active set of a box: its points at the leaves, otherwise the skeletons of
+  its children in child order (regrouping, Fig. multi-comp);
+  proxy compression (Sec. 3.2): rows = all active points of the colleague
+  boxes (the near neighbours) plus the proxy surface, each scaled by w;
+  2D Laplace adds one constant row when |log rho| < 0.1 (the single layer on
+  a circle of radius 1 cannot make constants);
+  ID of that matrix (interp.interp_decomp) -> skeletons, P;
+  diagonal block D_i: at the leaves A(I_i, I_i); above, the children's
+  Lambda on the diagonal and w G between skeletons of different children
+  (S^(l-1) regrouped, with Lambda^(l-1) added: the system S z = y of eq.
+  sparse-embedding expanded again, eq. multilevel-embedding);
+  block elimination (eq. compressed-inverse):
+    Lambda = (R D^-1 L)^-1,  calD = D^-1 - D^-1 L Lambda R D^-1,
+    calL = D^-1 L Lambda,    calR = Lambda R D^-1;
+root: calS = the root's diagonal block built the same way; solved by dense
+LU with partial pivoting (numpy.linalg.solve, a library primitive).
+
+Solve (eq. multilevel-inverse applied right to left, Sec. 4.3):
+  upward   u_i = calD_i b_i, c_i = calR_i b_i -> parent's active slots
+  root     x = calS^-1 c
+  downward x_i = u_i + calL_i x_parent[slots of i]
+Forward apply of the compressed matrix (eq. multilevel-compression, Sec. 3.3):
+  upward   z -> P z (column projections), D^(l) z kept per box, where D^(l)
+           is A(I_i, I_i) at the leaves and the sibling blocks (zero blocks
+           on the children) above
+  top      S z on the root's active set (sibling blocks of the depth-1 boxes)
+  downward y_i = D^(l)_i z_i + P_i^T y_parent[slots of i]
+
+Pins (tests/test_oracle_solver.py): ||A - A_RS|| / ||A|| <= 10 eps against the
+dense matrix; the solve equals dense Gaussian elimination on A_RS to rounding
+and on A within 10 eps; closed-form circulant spectrum on the unit circle
+(Laplace and Helmholtz); sphere harmonics eigenvalues (3D, loose).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from .interp import interp_decomp, projection
+from .kernels import green, is_complex, offdiag_block, proxy_points, proxy_radius_2d, system_block
+from .tree import Tree
+
+
+@dataclasses.dataclass
+class Params:
+    kind: str = "laplace2d"
+    w: float = 1.0            # quadrature weight in A = I + w K
+    eps: float = 1e-9
+    leaf: int = 64
+    nproxy: int = 64
+    ratio: float = 1.5
+    kwave: float = 0.0
+
+
+@dataclasses.dataclass
+class BoxFactor:
+    I: np.ndarray            # active point ids (tree order positions)
+    sk_loc: np.ndarray       # skeleton positions within I (pivot order)
+    rd_loc: np.ndarray       # redundant positions within I
+    T: np.ndarray            # k x (n - k) interpolation matrix
+    P: np.ndarray            # k x n projection (R_i = P, L_i = P^T)
+    D: np.ndarray            # n x n diagonal block of the inverse recursion
+    Lam: np.ndarray          # k x k
+    calD: np.ndarray         # n x n
+    calL: np.ndarray         # n x k
+    calR: np.ndarray         # k x n
+    m: int = 0               # rows of the compressed matrix
+
+    @property
+    def sk(self):
+        return self.I[self.sk_loc]
+
+    @property
+    def n(self):
+        return len(self.I)
+
+    @property
+    def k(self):
+        return len(self.sk_loc)
+
+
+class Factorization:
+    def __init__(self, tree: Tree, params: Params):
+        self.tree = tree
+        self.params = params
+        self.boxes = {}       # depth -> list[BoxFactor] for depths L..1
+        self.root_I = None    # active set of the root
+        self.calS = None      # root diagonal block (dense)
+        self.fwd_blocks = {}  # depth -> list of forward D^(l) blocks (0..L), root at 0
+
+    # ------------------------------------------------------------------ helpers
+    def _dtype(self):
+        return np.complex128 if is_complex(self.params.kind) else np.float64
+
+    def _blocks_from_children(self, depth, b, with_lambda: bool):
+        """Diagonal block of box b (depth < L) from its children at depth+1."""
+        tr, pr = self.tree, self.params
+        lv = tr.levels[depth]
+        kids = range(lv.child_begin[b], lv.child_end[b])
+        cf = [self.boxes[depth + 1][c] for c in kids]
+        sizes = [f.k for f in cf]
+        offs = np.concatenate([[0], np.cumsum(sizes)])
+        n = int(offs[-1])
+        D = np.zeros((n, n), dtype=self._dtype())
+        for a, fa in enumerate(cf):
+            for c, fc in enumerate(cf):
+                ra = slice(offs[a], offs[a + 1])
+                rc = slice(offs[c], offs[c + 1])
+                if a == c:
+                    if with_lambda:
+                        D[ra, rc] = fa.Lam
+                else:
+                    D[ra, rc] = offdiag_block(pr.kind, tr.points, fa.sk, fc.sk, pr.w, pr.kwave)
+        return D
+
+    def _active(self, depth, b):
+        tr = self.tree
+        lv = tr.levels[depth]
+        if depth == tr.L:
+            return np.arange(lv.begin[b], lv.end[b])
+        kids = range(lv.child_begin[b], lv.child_end[b])
+        return np.concatenate([self.boxes[depth + 1][c].sk for c in kids])
+
+    def _compress_matrix(self, depth, b, I, active_of):
+        """Rows: near-neighbour active points and proxy points (Sec. 3.2)."""
+        tr, pr = self.tree, self.params
+        lv = tr.levels[depth]
+        near = [active_of[c] for c in lv.colleagues[b]]
+        near = np.concatenate(near) if near else np.zeros(0, dtype=np.int64)
+        center = tr.box_center(depth, b)
+        side = tr.box_side(depth)
+        prox = proxy_points(tr.dim, center, side, pr.nproxy, pr.ratio)
+        rows = [offdiag_block(pr.kind, tr.points, near, I, pr.w, pr.kwave)]
+        rows.append(pr.w * green(pr.kind, prox, tr.points[:, I], pr.kwave))
+        if pr.kind == "laplace2d" and abs(np.log(proxy_radius_2d(side, pr.ratio))) < 0.1:
+            rows.append(pr.w * np.ones((1, len(I))))
+        return np.vstack(rows)
+
+    # -------------------------------------------------------------------- build
+    def build(self):
+        tr, pr = self.tree, self.params
+        for depth in range(tr.L, 0, -1):
+            lv = tr.levels[depth]
+            active_of = [self._active(depth, b) for b in range(lv.nbox)]
+            facs, fwd = [], []
+            for b in range(lv.nbox):
+                I = active_of[b]
+                M = self._compress_matrix(depth, b, I, active_of)
+                sk_loc, rd_loc, T = interp_decomp(M, pr.eps)
+                P = projection(sk_loc, rd_loc, T, len(I)).astype(self._dtype())
+                if depth == tr.L:
+                    D = system_block(pr.kind, tr.points, I, I, pr.w, pr.kwave)
+                    Dfwd = D
+                else:
+                    D = self._blocks_from_children(depth, b, with_lambda=True)
+                    Dfwd = self._blocks_from_children(depth, b, with_lambda=False)
+                # block elimination, eq. compressed-inverse (L = P^T, R = P)
+                DinvL = np.linalg.solve(D, P.T)              # D^-1 L
+                RDinv = np.linalg.solve(D.T, P.T).T          # R D^-1
+                Lam = np.linalg.inv(P @ DinvL)               # (R D^-1 L)^-1
+                Dinv = np.linalg.inv(D)
+                calD = Dinv - DinvL @ Lam @ RDinv
+                calL = DinvL @ Lam
+                calR = Lam @ RDinv
+                facs.append(BoxFactor(I, sk_loc, rd_loc, T, P, D, Lam, calD, calL, calR,
+                                      m=M.shape[0]))
+                fwd.append(Dfwd)
+            self.boxes[depth] = facs
+            self.fwd_blocks[depth] = fwd
+        # root (depth 0)
+        self.root_I = self._active(0, 0)
+        if tr.L == 0:
+            self.calS = system_block(pr.kind, tr.points, self.root_I, self.root_I, pr.w, pr.kwave)
+            self.fwd_blocks[0] = [self.calS]
+        else:
+            self.calS = self._blocks_from_children(0, 0, with_lambda=True)
+            self.fwd_blocks[0] = [self._blocks_from_children(0, 0, with_lambda=False)]
+        return self
+
+    # ------------------------------------------------------------ structure info
+    def ranks(self):
+        """Per depth (L..1): list of (n_i, k_i)."""
+        return {d: [(f.n, f.k) for f in fs] for d, fs in self.boxes.items()}
+
+    def skeleton_count(self):
+        return len(self.root_I)
+
+    def storage_scalars(self):
+        tot = len(self.root_I) ** 2
+        for fs in self.boxes.values():
+            for f in fs:
+                tot += f.n * f.n + 2 * f.n * f.k
+        return tot
+
+    def _child_slots(self, depth, b):
+        """Slots of box b (depth) within its parent's active vector."""
+        tr = self.tree
+        p = tr.levels[depth].parent[b]
+        up = tr.levels[depth - 1]
+        off = 0
+        for c in range(up.child_begin[p], b):
+            off += self.boxes[depth][c].k
+        return p, slice(off, off + self.boxes[depth][b].k)
+
+    # -------------------------------------------------------------------- solve
+    def solve(self, B: np.ndarray) -> np.ndarray:
+        """x = A_RS^{-1} b for each column of B (original point order)."""
+        tr = self.tree
+        B2 = np.asarray(B).reshape(tr.N, -1)
+        dt = np.result_type(B2.dtype, self._dtype())
+        bt = B2[tr.perm].astype(dt)
+        if tr.L == 0:
+            xt = np.linalg.solve(self.calS, bt)
+        else:
+            lvL = tr.levels[tr.L]
+            vec = [bt[lvL.begin[b]:lvL.end[b]] for b in range(lvL.nbox)]
+            u = {}
+            for depth in range(tr.L, 0, -1):
+                fs = self.boxes[depth]
+                u[depth] = [f.calD @ v for f, v in zip(fs, vec)]
+                c = [f.calR @ v for f, v in zip(fs, vec)]
+                up = tr.levels[depth - 1]
+                vec = [np.concatenate([c[i] for i in range(up.child_begin[p], up.child_end[p])])
+                       for p in range(up.nbox)]
+            xs = [np.linalg.solve(self.calS, vec[0])]
+            for depth in range(1, tr.L + 1):
+                fs = self.boxes[depth]
+                nxt = []
+                for b, f in enumerate(fs):
+                    p, sl = self._child_slots(depth, b)
+                    nxt.append(u[depth][b] + f.calL @ xs[p][sl])
+                xs = nxt
+            xt = np.concatenate(xs)
+        X = np.empty_like(xt)
+        X[tr.perm] = xt
+        return X.reshape(np.shape(B)) if np.ndim(B) == 1 else X
+
+    # ------------------------------------------------------------ forward apply
+    def apply(self, X: np.ndarray) -> np.ndarray:
+        """y = A_RS x (telescoping forward operator, Sec. 3.3)."""
+        tr = self.tree
+        X2 = np.asarray(X).reshape(tr.N, -1)
+        dt = np.result_type(X2.dtype, self._dtype())
+        xt = X2[tr.perm].astype(dt)
+        if tr.L == 0:
+            yt = self.fwd_blocks[0][0] @ xt
+        else:
+            lvL = tr.levels[tr.L]
+            z = [xt[lvL.begin[b]:lvL.end[b]] for b in range(lvL.nbox)]
+            yD = {}
+            for depth in range(tr.L, 0, -1):
+                fs = self.boxes[depth]
+                yD[depth] = [Df @ v for Df, v in zip(self.fwd_blocks[depth], z)]
+                c = [f.P @ v for f, v in zip(fs, z)]
+                up = tr.levels[depth - 1]
+                z = [np.concatenate([c[i] for i in range(up.child_begin[p], up.child_end[p])])
+                     for p in range(up.nbox)]
+            ys = [self.fwd_blocks[0][0] @ z[0]]
+            for depth in range(1, tr.L + 1):
+                fs = self.boxes[depth]
+                nxt = []
+                for b, f in enumerate(fs):
+                    p, sl = self._child_slots(depth, b)
+                    nxt.append(yD[depth][b] + f.P.T @ ys[p][sl])
+                ys = nxt
+            yt = np.concatenate(ys)
+        Y = np.empty_like(yt)
+        Y[tr.perm] = yt
+        return Y.reshape(np.shape(X)) if np.ndim(X) == 1 else Y
+
+
+def build(points: np.ndarray, params: Params) -> Factorization:
+    """Tree + compression + factorization of A = I + w K on `points` (dim x N)."""
+    tree = Tree(points, params.leaf)
+    return Factorization(tree, params).build()

@@ -1,0 +1,124 @@
+"""Oracle compression, inverse and solve pinned by closed forms and brute force.
+
+Pins: Sec. 5 error bound (||A - A_RS|| / ||A|| within 10 eps for a
+second-kind operator), Sec. 4.3 (the telescoping inverse is one ordering of
+Gaussian elimination on the compressed matrix), and closed-form spectra of
+A = I + h K on the unit circle (circulant) and the sphere.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.special import hankel1, jv
+
+import rs_inputs as ri
+from oracle import dense, rskel
+
+
+def _build(kind, pts, w, eps, leaf, nproxy, kwave=0.0):
+    return rskel.build(pts, rskel.Params(kind=kind, w=w, eps=eps, leaf=leaf, nproxy=nproxy, kwave=kwave))
+
+
+CASES = [
+    # kind, geometry, N, eps, leaf, nproxy
+    ("laplace2d", "circle", 2048, 1e-9, 64, 64),
+    ("laplace2d", "starfish", 2048, 1e-10, 64, 64),
+    ("helmholtz2d", "starfish", 1024, 1e-9, 64, 64),
+    ("laplace3d", "sphere", 1500, 1e-6, 128, 216),
+]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: f"{c[0]}-{c[1]}-{c[2]}")
+def case(request):
+    kind, geom, n, eps, leaf, nproxy = request.param
+    pts, w = ri.geometry(geom, n)
+    kw = 10.0 if kind == "helmholtz2d" else 0.0
+    F = _build(kind, pts, w, eps, leaf, nproxy, kw)
+    A = dense.dense_matrix(kind, pts, w, kw)
+    dt = np.complex128 if kind == "helmholtz2d" else np.float64
+    ARS = F.apply(np.eye(n, dtype=dt))
+    return dict(kind=kind, n=n, eps=eps, F=F, A=A, ARS=ARS, dt=dt)
+
+
+def test_compression_error_within_10eps(case):
+    rel = dense.norm2_est(case["A"] - case["ARS"]) / dense.norm2_est(case["A"])
+    assert rel <= 10 * case["eps"], rel
+
+
+def test_solve_equals_dense_elimination(case):
+    n = case["n"]
+    B = ri.rhs(n, 3, seed=11, complex_=case["dt"] == np.complex128)
+    X = case["F"].solve(B)
+    Xd = np.linalg.solve(case["ARS"], B)
+    assert np.linalg.norm(X - Xd) / np.linalg.norm(Xd) < 1e-12
+    Xa = np.linalg.solve(case["A"], B)
+    assert np.linalg.norm(X - Xa) / np.linalg.norm(Xa) <= 10 * case["eps"]
+
+
+def test_forward_apply_consistent_with_solve(case):
+    n = case["n"]
+    x = ri.rhs(n, 1, seed=4, complex_=case["dt"] == np.complex128)[:, 0]
+    y = case["F"].apply(x)
+    assert np.linalg.norm(case["F"].solve(y) - x) / np.linalg.norm(x) < 1e-12
+
+
+def test_tree_leaf_and_rank_structure(case):
+    F = case["F"]
+    for d, fs in F.boxes.items():
+        for f in fs:
+            assert 0 < f.k <= f.n
+            assert f.calD.shape == (f.n, f.n) and f.calL.shape == (f.n, f.k) and f.calR.shape == (f.k, f.n)
+    assert F.skeleton_count() == F.calS.shape[0]
+
+
+def _circle_laplace_eig(n, m):
+    """lambda_m = 1 - (1/N) sum_j ln(2 sin(pi j/N)) cos(2 pi m j / N), exact sum."""
+    s = math.fsum(math.log(2 * math.sin(math.pi * j / n)) * math.cos(2 * math.pi * m * j / n)
+                  for j in range(1, n))
+    return 1.0 - s / n
+
+
+def test_circle_laplace_closed_form():
+    n, eps = 4096, 1e-9
+    pts, h = ri.circle(n)
+    F = _build("laplace2d", pts, h, eps, 64, 64)
+    th = 2 * np.pi * np.arange(n) / n
+    # constant mode: prod_j 2 sin(pi j / N) = N gives lambda_0 = 1 - ln(N)/N exactly
+    assert abs(_circle_laplace_eig(n, 0) - (1 - math.log(n) / n)) < 1e-14
+    for m in (0, 1, 5, 17):
+        lam = _circle_laplace_eig(n, m)
+        b = np.cos(m * th)
+        x = F.solve(b)
+        assert np.linalg.norm(x - b / lam) / np.linalg.norm(b / lam) <= 10 * eps
+        if m > 0:
+            # continuum single layer on the unit circle: S cos(m t) = cos(m t) / (2m)
+            assert abs(lam - (1 + 1 / (2 * m))) < 5 * (2 * np.pi / n) * math.log(n)
+
+
+def test_circle_helmholtz_closed_form():
+    n, eps, k = 2048, 1e-9, 10.0
+    pts, h = ri.circle(n)
+    F = _build("helmholtz2d", pts, h, eps, 64, 64, k)
+    th = 2 * np.pi * np.arange(n) / n
+    j = np.arange(1, n)
+    row = h * 0.25j * hankel1(0, k * 2 * np.sin(np.pi * j / n))
+    for m in (0, 3, 11):
+        lam = 1 + np.sum(row * np.cos(2 * np.pi * m * j / n))
+        b = np.cos(m * th)
+        x = F.solve(b)
+        assert np.linalg.norm(x - b / lam) / np.linalg.norm(b / lam) <= 10 * eps
+        # continuum: 1 + (i pi / 2) J_m(k) H_m^(1)(k)
+        cont = 1 + 0.5j * np.pi * jv(m, k) * hankel1(m, k)
+        assert abs(lam - cont) < 2e-2
+
+
+def test_sphere_single_layer_eigenvalue():
+    n = 3000
+    pts, w = ri.fibonacci_sphere(n)
+    F = _build("laplace3d", pts, w, 1e-6, 128, 216)
+    for l, Y in ((0, np.ones(n)), (1, pts[2].copy())):
+        x = F.solve(Y)
+        lam = float(Y @ Y / (Y @ x))          # Rayleigh quotient of A^-1
+        # S Y_l = Y_l / (2l + 1) on the unit sphere; the punctured rule drops
+        # about 1/sqrt(N) of the self cell
+        assert abs(lam - (1 + 1 / (2 * l + 1))) < 2.0 / np.sqrt(n)
