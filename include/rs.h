@@ -1,0 +1,158 @@
+/*
+ * rs.h -- C ABI of the GB300 recursive-skeletonization fast direct solver.
+ *
+ * The library builds a compressed inverse of a dense matrix A = I + w K,
+ * K_ij = G(x_i, x_j) (i != j), K_ii = 0, for points x_1..x_N on a curve or
+ * surface, following Ho & Greengard, "A fast direct solver for structured
+ * linear systems by recursive skeletonization" (arXiv 1110.3105):
+ *   - tree: uniform quadtree / octree with contiguous index blocks
+ *     (Sec. 2.1, Example 1; Sec. 6, first paragraph);
+ *   - compression: interpolative decomposition (Sec. 2.2, Def. 2.3) of each
+ *     box against its near neighbours and a proxy surface (Sec. 3.1-3.2),
+ *     level by level (eq. multilevel-compression);
+ *   - factorization: block elimination of the sparse embedding
+ *     (eq. compressed-inverse, eq. multilevel-inverse, Sec. 3.4);
+ *   - solve: the telescoping inverse applied level by level (Sec. 4.3).
+ * Green's functions: eq. 2d-laplace, eq. 3d-laplace, eq. 2d-helmholtz.
+ *
+ * Conventions (all entry points):
+ *   - Return value: RS_OK (0) or a negative RS_ERR_* code.  On error no
+ *     output handle is created and rs_last_error() gives a message for the
+ *     calling thread (valid until its next library call).
+ *   - Pointers may be host or device memory; the library detects which.
+ *     The caller owns every buffer it passes; the library copies what it
+ *     keeps.  A handle owns all device memory it allocates until rs_free.
+ *   - Vectors are N x nrhs, column-major with leading dimension ld >= N, in
+ *     the caller's original point order.  Real kernels use double, the
+ *     Helmholtz kernel interleaved double complex (re, im).
+ *   - stream: a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     stream-ordered; a call returns after its results are complete and, for
+ *     host outputs, copied back.
+ *   - A handle is not thread-safe: calls on one handle must be serialised.
+ *   - Everything runs on the current CUDA device.
+ */
+#ifndef RS_H_
+#define RS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum rs_status {
+  RS_OK = 0,
+  RS_ERR_ARG = -1,      /* invalid argument */
+  RS_ERR_OOM = -2,      /* device or host allocation failed */
+  RS_ERR_CUDA = -3,     /* CUDA runtime error */
+  RS_ERR_SINGULAR = -4, /* a diagonal block or Lambda was numerically singular */
+  RS_ERR_TIMEOUT = -5,  /* a bounded wait ran out */
+  RS_ERR_NAN = -6,      /* non-finite input or result */
+  RS_ERR_STATE = -7     /* call not valid in the handle's current state */
+};
+
+enum rs_kernel {
+  RS_LAPLACE2D = 0,   /* G = -(1/2 pi) log r          (eq. 2d-laplace)   */
+  RS_HELMHOLTZ2D = 1, /* G = (i/4) H0^(1)(k r)         (eq. 2d-helmholtz) */
+  RS_LAPLACE3D = 2    /* G = 1 / (4 pi r)              (eq. 3d-laplace)   */
+};
+
+enum rs_precision {
+  RS_PREC_FP64 = 0,   /* stored factors and arithmetic in double (complex double) */
+  RS_PREC_FP32 = 1    /* float (complex float) copies of the factors */
+};
+
+typedef struct rs_handle_s* rs_handle;
+
+/* Build parameters.  proxy_n: points on the proxy surface (2D: a circle of
+ * radius proxy_ratio * box circumradius; 3D: 6 g^2 cell centres on a cube of
+ * half-width proxy_ratio * box half-width, Sec. 3.2).  weight: w in A. */
+typedef struct {
+  int kernel_id;      /* enum rs_kernel */
+  double k_wave;      /* Helmholtz wavenumber k (ignored otherwise) */
+  double weight;      /* w > 0 */
+  int proxy_n;        /* > 0; 3D needs 6 g^2 */
+  double proxy_ratio; /* > 1 */
+} rs_params;
+
+/* Summary of a built handle (Table solve-lap-2d fields plus timings). */
+typedef struct {
+  int64_t n;              /* matrix dimension N */
+  int dim;                /* 2 or 3 */
+  int depth;              /* tree depth L (root = 0) */
+  int64_t top_skeletons;  /* skeletons left at the root (K at the top) */
+  int64_t factor_bytes;   /* FP64 factor storage read by one solve */
+  int64_t factor_scalars; /* stored scalars of calD, calL, calR and the root */
+  double build_ms;        /* wall time of rs_build on the device timeline */
+  int max_box_n;          /* largest active set of any box */
+  int max_box_m;          /* largest compressed matrix row count */
+  int max_rank;           /* largest skeleton count of any box */
+} rs_stats_t;
+
+/* Build the compressed inverse.
+ *   pts    dim x N column-major (point i at pts[i*dim .. i*dim+dim-1]), host
+ *          or device; N >= 1; dim 2 or 3 (3 only with RS_LAPLACE3D).
+ *   eps    relative ID precision (Sec. 2.2), 0 < eps < 1.
+ *   leaf   maximum points per leaf box, >= 1.
+ * Errors: RS_ERR_ARG (bad sizes, parameters), RS_ERR_NAN (non-finite point),
+ *         RS_ERR_SINGULAR, RS_ERR_OOM, RS_ERR_CUDA. */
+int rs_build(const double* pts, int64_t n, int dim, const rs_params* params,
+             double eps, int leaf, void* stream, rs_handle* out);
+
+/* X = A_RS^{-1} B (eq. multilevel-inverse), nrhs >= 1, in the given precision.
+ * RS_PREC_FP32 takes and returns double data but computes with the float
+ * factors.  B and X may alias only if ldb == ldx. */
+int rs_solve(rs_handle h, int precision, const void* B, int64_t ldb, int nrhs,
+             void* X, int64_t ldx, void* stream);
+
+/* Mixed-precision solve with iterative refinement: x0 = FP32 solve of b;
+ * repeat r = b - A_RS x in FP64 (forward operator of eq.
+ * multilevel-compression with its kernel blocks evaluated on the fly from the
+ * coordinates), x += FP32 solve of r, until every column has
+ * ||r|| <= tol ||b|| or max_it corrections were applied.
+ *   its_out     (host, may be NULL) corrections applied
+ *   relres_out  (host, may be NULL, nrhs entries) final ||r||/||b|| per column
+ * Returns RS_OK even when tol was not met; check relres_out. */
+int rs_solve_refined(rs_handle h, const void* B, int64_t ldb, int nrhs, void* X,
+                     int64_t ldx, double tol, int max_it, int* its_out,
+                     double* relres_out, void* stream);
+
+/* Y = A_RS X in FP64 (Sec. 3.3: upward pass with R^(l), kernel blocks
+ * D^(l) and S from the coordinates, downward pass with L^(l)). */
+int rs_matvec(rs_handle h, const void* X, int64_t ldx, int nrhs, void* Y,
+              int64_t ldy, void* stream);
+
+/* Fill *out with the handle's summary. */
+int rs_stats(rs_handle h, rs_stats_t* out);
+
+/* Tree export for bit-exact comparison (host buffers, caller allocated).
+ * rs_tree_level(h, l, ...) for l = 0..depth:
+ *   nbox_out   number of boxes at depth l
+ *   begin      (nbox) first point of each box in tree order, or NULL
+ *   parent     (nbox) parent box index at depth l-1 (-1 at the root), or NULL
+ *   ncoll      (nbox) colleague count, or NULL
+ *   coll       (nbox * 27) colleague box indices ascending, -1 padded, or NULL
+ * rs_tree_perm(h, perm): perm[i] = original index of the point at tree
+ * position i (int64, N entries). */
+int rs_tree_perm(rs_handle h, int64_t* perm);
+int rs_tree_level(rs_handle h, int level, int* nbox_out, int64_t* begin,
+                  int* parent, int* ncoll, int* coll);
+
+/* Per-box ranks at depth l (1..depth): n (active size) and k (skeletons),
+ * host arrays of nbox entries, either may be NULL. */
+int rs_box_ranks(rs_handle h, int level, int* n, int* k);
+
+/* Release every resource of the handle.  NULL is accepted. */
+int rs_free(rs_handle h);
+
+/* Message of the calling thread's last error ("" if none). */
+const char* rs_last_error(void);
+
+/* Library version string. */
+const char* rs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RS_H_ */

@@ -1,0 +1,10 @@
+"""GB300 recursive-skeletonization fast direct solver (Ho & Greengard, 1110.3105).
+
+The compute path is librs.so (CUDA, sm_103a) behind the C ABI of
+include/rs.h; this package only binds it (``_lib``) and builds it
+(``build``).  Importing the package does not load the library; the first
+call of any binding does, and raises if the library is missing.
+"""
+from ._lib import (RS_HELMHOLTZ2D, RS_LAPLACE2D, RS_LAPLACE3D, RS_PREC_FP32,  # noqa: F401
+                   RS_PREC_FP64, Handle, RSError, load, rs_box_ranks, rs_build, rs_free,
+                   rs_matvec, rs_solve, rs_solve_refined, rs_tree_level, rs_tree_perm, rs_version)

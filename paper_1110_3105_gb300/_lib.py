@@ -1,0 +1,215 @@
+"""ctypes binding of librs.so: argument marshalling only.
+
+Every function maps one-to-one onto an entry point of include/rs.h.  Arrays
+may be numpy arrays (host) or torch tensors (host or CUDA); the library
+detects device pointers itself.  Nothing here computes any part of the
+method: a missing or unloadable library raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librs.so")
+
+RS_LAPLACE2D, RS_HELMHOLTZ2D, RS_LAPLACE3D = 0, 1, 2
+RS_PREC_FP64, RS_PREC_FP32 = 0, 1
+KERNELS = {"laplace2d": RS_LAPLACE2D, "helmholtz2d": RS_HELMHOLTZ2D, "laplace3d": RS_LAPLACE3D}
+STATUS = {0: "RS_OK", -1: "RS_ERR_ARG", -2: "RS_ERR_OOM", -3: "RS_ERR_CUDA", -4: "RS_ERR_SINGULAR",
+          -5: "RS_ERR_TIMEOUT", -6: "RS_ERR_NAN", -7: "RS_ERR_STATE"}
+
+
+class RSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class rs_params(ctypes.Structure):
+    _fields_ = [("kernel_id", ctypes.c_int), ("k_wave", ctypes.c_double), ("weight", ctypes.c_double),
+                ("proxy_n", ctypes.c_int), ("proxy_ratio", ctypes.c_double)]
+
+
+class rs_stats_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("dim", ctypes.c_int), ("depth", ctypes.c_int),
+                ("top_skeletons", ctypes.c_int64), ("factor_bytes", ctypes.c_int64),
+                ("factor_scalars", ctypes.c_int64), ("build_ms", ctypes.c_double),
+                ("max_box_n", ctypes.c_int), ("max_box_m", ctypes.c_int), ("max_rank", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_PROTOS = {
+    "rs_build": (ctypes.c_int, [_P, _I64, ctypes.c_int, ctypes.POINTER(rs_params), ctypes.c_double,
+                                ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "rs_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, ctypes.c_int, _P, _I64, _P]),
+    "rs_solve_refined": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, ctypes.c_double, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), _P, _P]),
+    "rs_matvec": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, _P]),
+    "rs_stats": (ctypes.c_int, [_P, ctypes.POINTER(rs_stats_t)]),
+    "rs_tree_perm": (ctypes.c_int, [_P, _P]),
+    "rs_tree_level": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P, _P, _P, _P]),
+    "rs_box_ranks": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "rs_free": (ctypes.c_int, [_P]),
+    "rs_last_error": (ctypes.c_char_p, []),
+    "rs_version": (ctypes.c_char_p, []),
+}
+EXPORTED = tuple(_PROTOS)
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librs.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"librs.so not built at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _PROTOS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise RSError(rc, _lib.rs_last_error().decode())
+
+
+def _ptr(a):
+    """Data pointer and (rows, cols, ld, element size) of a 1D/2D column-major array."""
+    if hasattr(a, "data_ptr"):   # torch tensor
+        if a.dim() == 1:
+            return a.data_ptr(), a.shape[0], 1, a.shape[0], a.element_size()
+        if a.stride(0) != 1:
+            raise ValueError("torch tensor must be column-major (stride(0) == 1)")
+        return a.data_ptr(), a.shape[0], a.shape[1], a.stride(1), a.element_size()
+    a = np.asarray(a)
+    if a.ndim == 1:
+        return a.ctypes.data, a.shape[0], 1, a.shape[0], a.itemsize
+    if not a.flags["F_CONTIGUOUS"]:
+        raise ValueError("numpy array must be Fortran (column-major) ordered")
+    return a.ctypes.data, a.shape[0], a.shape[1], a.shape[0], a.itemsize
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Handle:
+    """Owns one rs_handle (compressed inverse on the current device)."""
+
+    def __init__(self, ptr, n, complex_):
+        self._h = ptr
+        self.n = n
+        self.complex = complex_
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            _lib.rs_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        s = rs_stats_t()
+        _check(_lib.rs_stats(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in rs_stats_t._fields_}
+
+
+def rs_build(points, kernel: str, weight: float, eps: float, leaf: int, proxy_n: int,
+             proxy_ratio: float = 1.5, k_wave: float = 0.0, stream=None) -> Handle:
+    """points: (dim, N) array (any order numpy, or a column-major torch tensor)."""
+    load()
+    if hasattr(points, "data_ptr"):
+        dim, n = points.shape
+        pts = points.t().contiguous() if points.stride(1) != dim else points   # point-major
+        ptr = pts.data_ptr()
+        keep = pts
+    else:
+        pts = np.asfortranarray(np.asarray(points, dtype=np.float64))
+        dim, n = pts.shape
+        ptr = pts.ctypes.data
+        keep = pts
+    p = rs_params(KERNELS[kernel], float(k_wave), float(weight), int(proxy_n), float(proxy_ratio))
+    out = ctypes.c_void_p()
+    rc = _lib.rs_build(ptr, n, dim, ctypes.byref(p), float(eps), int(leaf), _stream(stream), ctypes.byref(out))
+    del keep
+    _check(rc)
+    return Handle(out.value, n, kernel == "helmholtz2d")
+
+
+def rs_solve(h: Handle, B, X, precision: int = RS_PREC_FP64, stream=None):
+    pb, nb, rb, ldb, _ = _ptr(B)
+    px, nx, rx, ldx, _ = _ptr(X)
+    _check(_lib.rs_solve(h.ptr, precision, pb, ldb, rb, px, ldx, _stream(stream)))
+    return X
+
+
+def rs_solve_refined(h: Handle, B, X, tol: float = 1e-10, max_it: int = 10, stream=None):
+    pb, nb, rb, ldb, _ = _ptr(B)
+    px, nx, rx, ldx, _ = _ptr(X)
+    its = ctypes.c_int(0)
+    rel = np.zeros(rb)
+    _check(_lib.rs_solve_refined(h.ptr, pb, ldb, rb, px, ldx, float(tol), int(max_it), ctypes.byref(its),
+                                 rel.ctypes.data, _stream(stream)))
+    return its.value, rel
+
+
+def rs_matvec(h: Handle, X, Y, stream=None):
+    px, nx, rx, ldx, _ = _ptr(X)
+    py, ny, ry, ldy, _ = _ptr(Y)
+    _check(_lib.rs_matvec(h.ptr, px, ldx, rx, py, ldy, _stream(stream)))
+    return Y
+
+
+def rs_tree_perm(h: Handle) -> np.ndarray:
+    out = np.zeros(h.n, dtype=np.int64)
+    _check(_lib.rs_tree_perm(h.ptr, out.ctypes.data))
+    return out
+
+
+def rs_tree_level(h: Handle, level: int):
+    nbox = ctypes.c_int(0)
+    _check(_lib.rs_tree_level(h.ptr, level, ctypes.byref(nbox), None, None, None, None))
+    nb = nbox.value
+    begin = np.zeros(nb, dtype=np.int64)
+    parent = np.zeros(nb, dtype=np.int32)
+    ncoll = np.zeros(nb, dtype=np.int32)
+    coll = np.zeros(nb * 27, dtype=np.int32)
+    _check(_lib.rs_tree_level(h.ptr, level, ctypes.byref(nbox), begin.ctypes.data, parent.ctypes.data,
+                              ncoll.ctypes.data, coll.ctypes.data))
+    coll = coll.reshape(nb, 27)
+    return dict(begin=begin, parent=parent, colleagues=[coll[b, :ncoll[b]].copy() for b in range(nb)])
+
+
+def rs_box_ranks(h: Handle, level: int, nbox: int):
+    n = np.zeros(nbox, dtype=np.int32)
+    k = np.zeros(nbox, dtype=np.int32)
+    _check(_lib.rs_box_ranks(h.ptr, level, n.ctypes.data, k.ctypes.data))
+    return n, k
+
+
+def rs_free(h: Handle):
+    h.free()
+
+
+def rs_version() -> str:
+    return load().rs_version().decode()

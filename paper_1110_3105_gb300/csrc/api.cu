@@ -1,0 +1,381 @@
+// C ABI entry points and the host-side orchestration of build and solve.
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "rs_internal.h"
+
+// The opaque handle type of the C ABI is the runtime's Handle.
+struct rs_handle_s : public rs::Handle {};
+
+namespace rs {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+int fail(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int dalloc(Handle* h, void** p, size_t bytes) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? RS_ERR_OOM : RS_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
+                cudaGetErrorString(e));
+  }
+  h->allocs.push_back(*p);
+  return RS_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static void destroy(rs_handle_s* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (void* p : h->allocs) cudaFree(p);
+  for (auto& w : h->work) {
+    for (void* p : w.v) if (p) cudaFree(p);
+    for (void* p : w.u) if (p) cudaFree(p);
+    if (w.vin) cudaFree(w.vin);
+  }
+  for (void* p : h->fz) if (p) cudaFree(p);
+  for (void* p : h->fy) if (p) cudaFree(p);
+  for (void* p : {h->r64, h->x64, h->b64}) if (p) cudaFree(p);
+  if (h->colnorm) cudaFree(h->colnorm);
+  delete h;
+}
+
+// Staging of caller buffers: device pointers are used as they are, host
+// buffers go through a device copy (N x nrhs, ld = N).
+struct Staged {
+  void* d = nullptr;
+  int64_t ld = 0;
+  bool owned = false;
+};
+
+static int stage_in(const void* p, int64_t ld, int64_t N, int nrhs, size_t sb, cudaStream_t st, Staged* s) {
+  if (is_device_ptr(p)) {
+    s->d = const_cast<void*>(p);
+    s->ld = ld;
+    return RS_OK;
+  }
+  RS_CUDA(cudaMallocAsync(&s->d, sb * (size_t)N * nrhs, st));
+  s->owned = true;
+  s->ld = N;
+  RS_CUDA(cudaMemcpy2DAsync(s->d, sb * N, p, sb * ld, sb * N, nrhs, cudaMemcpyHostToDevice, st));
+  return RS_OK;
+}
+
+static int stage_out_alloc(void* p, int64_t ld, int64_t N, int nrhs, size_t sb, cudaStream_t st, Staged* s) {
+  if (is_device_ptr(p)) {
+    s->d = p;
+    s->ld = ld;
+    return RS_OK;
+  }
+  RS_CUDA(cudaMallocAsync(&s->d, sb * (size_t)N * nrhs, st));
+  s->owned = true;
+  s->ld = N;
+  return RS_OK;
+}
+
+static int stage_out_finish(void* p, int64_t ld, int64_t N, int nrhs, size_t sb, cudaStream_t st, Staged* s) {
+  if (s->owned) {
+    RS_CUDA(cudaMemcpy2DAsync(p, sb * ld, s->d, sb * N, sb * N, nrhs, cudaMemcpyDeviceToHost, st));
+  }
+  return RS_OK;
+}
+
+static void release(Staged* s, cudaStream_t st) {
+  if (s->owned && s->d) cudaFreeAsync(s->d, st);
+  s->d = nullptr;
+}
+
+static int check_handle(rs_handle h) {
+  if (!h) return fail(RS_ERR_ARG, "null handle");
+  return RS_OK;
+}
+
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" {
+
+const char* rs_last_error(void) { return rs::g_err.c_str(); }
+
+const char* rs_version(void) { return "rs-gb300 0.1 (sm_103a)"; }
+
+int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, double eps, int leaf, void* stream,
+             rs_handle* out) {
+  rs::g_err.clear();
+  if (!out) return fail(RS_ERR_ARG, "rs_build: out is null");
+  *out = nullptr;
+  if (!pts || !params) return fail(RS_ERR_ARG, "rs_build: null pointer argument");
+  if (n < 1 || n > (int64_t)1 << 30) return fail(RS_ERR_ARG, "rs_build: N=%lld out of range", (long long)n);
+  if (dim != 2 && dim != 3) return fail(RS_ERR_ARG, "rs_build: dim must be 2 or 3");
+  if (params->kernel_id < RS_LAPLACE2D || params->kernel_id > RS_LAPLACE3D)
+    return fail(RS_ERR_ARG, "rs_build: unknown kernel_id %d", params->kernel_id);
+  if ((params->kernel_id == RS_LAPLACE3D) != (dim == 3))
+    return fail(RS_ERR_ARG, "rs_build: kernel %d does not match dim %d", params->kernel_id, dim);
+  if (!(eps > 0.0 && eps < 1.0)) return fail(RS_ERR_ARG, "rs_build: eps must be in (0, 1)");
+  if (leaf < 1) return fail(RS_ERR_ARG, "rs_build: leaf must be >= 1");
+  if (!(params->weight > 0.0) || !std::isfinite(params->weight)) return fail(RS_ERR_ARG, "rs_build: weight must be > 0");
+  if (params->proxy_n < 1) return fail(RS_ERR_ARG, "rs_build: proxy_n must be >= 1");
+  if (!(params->proxy_ratio > 1.0)) return fail(RS_ERR_ARG, "rs_build: proxy_ratio must be > 1");
+  if (dim == 3) {
+    int g = (int)std::lround(std::sqrt(params->proxy_n / 6.0));
+    if (6 * g * g != params->proxy_n) return fail(RS_ERR_ARG, "rs_build: 3D proxy_n must be 6 g^2");
+  }
+  if (params->kernel_id == RS_HELMHOLTZ2D && !(params->k_wave > 0.0))
+    return fail(RS_ERR_ARG, "rs_build: Helmholtz needs k_wave > 0");
+
+  cudaStream_t st = (cudaStream_t)stream;
+  rs_handle_s* h = new rs_handle_s();
+  h->dim = dim;
+  h->N = n;
+  h->kp.kind = params->kernel_id;
+  h->kp.w = params->weight;
+  h->kp.kwave = params->k_wave;
+  h->cplx = params->kernel_id == RS_HELMHOLTZ2D;
+  h->nproxy = params->proxy_n;
+  h->ratio = params->proxy_ratio;
+  h->eps = eps;
+  h->leaf = leaf;
+
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  int rc = RS_OK;
+  do {
+    if ((rc = dalloc_t(h, &h->status, 4)) != RS_OK) break;
+    if (cudaMemsetAsync(h->status, 0, sizeof(int) * 4, st) != cudaSuccess) { rc = fail(RS_ERR_CUDA, "memset"); break; }
+    const double* dp = pts;
+    double* tmp = nullptr;
+    if (!is_device_ptr(pts)) {
+      if ((rc = dalloc_t(h, &tmp, (size_t)n * dim)) != RS_OK) break;
+      if (cudaMemcpyAsync(tmp, pts, sizeof(double) * n * dim, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        rc = fail(RS_ERR_CUDA, "copy of points failed");
+        break;
+      }
+      dp = tmp;
+    }
+    if ((rc = build_tree(h, dp, st)) != RS_OK) break;
+    for (int d = h->L; d >= 1 && rc == RS_OK; --d) rc = skeletonize_level(h, d, st);
+    if (rc != RS_OK) break;
+    if ((rc = factor_root(h, st)) != RS_OK) break;
+    if ((rc = make_fp32_copies(h, st)) != RS_OK) break;
+  } while (0);
+  cudaEventRecord(e1, st);
+  cudaError_t se = cudaStreamSynchronize(st);
+  if (rc == RS_OK && se != cudaSuccess) rc = fail(RS_ERR_CUDA, "rs_build: %s", cudaGetErrorString(se));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != RS_OK) {
+    std::string keep = rs::g_err;
+    destroy(h);
+    rs::g_err = keep;
+    return rc;
+  }
+  h->build_ms = ms;
+  *out = h;
+  return RS_OK;
+}
+
+int rs_solve(rs_handle h, int precision, const void* B, int64_t ldb, int nrhs, void* X, int64_t ldx, void* stream) {
+  rs::g_err.clear();
+  RS_TRY(check_handle(h));
+  if (!B || !X) return fail(RS_ERR_ARG, "rs_solve: null buffer");
+  if (nrhs < 1 || ldb < h->N || ldx < h->N) return fail(RS_ERR_ARG, "rs_solve: bad nrhs or leading dimension");
+  if (precision != RS_PREC_FP64 && precision != RS_PREC_FP32) return fail(RS_ERR_ARG, "rs_solve: bad precision");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t sb = h->cplx ? sizeof(c128) : sizeof(double);
+  Staged sB, sX;
+  int rc = stage_in(B, ldb, h->N, nrhs, sb, st, &sB);
+  if (rc == RS_OK) rc = stage_out_alloc(X, ldx, h->N, nrhs, sb, st, &sX);
+  if (rc == RS_OK) rc = solve_device(h, precision, sB.d, sB.ld, nrhs, sX.d, sX.ld, st);
+  if (rc == RS_OK) rc = stage_out_finish(X, ldx, h->N, nrhs, sb, st, &sX);
+  cudaError_t e = cudaStreamSynchronize(st);
+  release(&sB, st);
+  release(&sX, st);
+  if (rc == RS_OK && e != cudaSuccess) rc = fail(RS_ERR_CUDA, "rs_solve: %s", cudaGetErrorString(e));
+  return rc;
+}
+
+int rs_matvec(rs_handle h, const void* X, int64_t ldx, int nrhs, void* Y, int64_t ldy, void* stream) {
+  rs::g_err.clear();
+  RS_TRY(check_handle(h));
+  if (!X || !Y) return fail(RS_ERR_ARG, "rs_matvec: null buffer");
+  if (nrhs < 1 || ldx < h->N || ldy < h->N) return fail(RS_ERR_ARG, "rs_matvec: bad nrhs or leading dimension");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t sb = h->cplx ? sizeof(c128) : sizeof(double);
+  Staged sX, sY;
+  int rc = stage_in(X, ldx, h->N, nrhs, sb, st, &sX);
+  if (rc == RS_OK) rc = stage_out_alloc(Y, ldy, h->N, nrhs, sb, st, &sY);
+  if (rc == RS_OK) rc = matvec_device(h, sX.d, sX.ld, nrhs, sY.d, sY.ld, st);
+  if (rc == RS_OK) rc = stage_out_finish(Y, ldy, h->N, nrhs, sb, st, &sY);
+  cudaError_t e = cudaStreamSynchronize(st);
+  release(&sX, st);
+  release(&sY, st);
+  if (rc == RS_OK && e != cudaSuccess) rc = fail(RS_ERR_CUDA, "rs_matvec: %s", cudaGetErrorString(e));
+  return rc;
+}
+
+int rs_solve_refined(rs_handle h, const void* B, int64_t ldb, int nrhs, void* X, int64_t ldx, double tol,
+                     int max_it, int* its_out, double* relres_out, void* stream) {
+  rs::g_err.clear();
+  RS_TRY(check_handle(h));
+  if (!B || !X) return fail(RS_ERR_ARG, "rs_solve_refined: null buffer");
+  if (nrhs < 1 || ldb < h->N || ldx < h->N) return fail(RS_ERR_ARG, "rs_solve_refined: bad nrhs or ld");
+  if (!(tol > 0.0) || max_it < 0) return fail(RS_ERR_ARG, "rs_solve_refined: bad tol or max_it");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t N = h->N;
+  size_t sb = h->cplx ? sizeof(c128) : sizeof(double);
+  Staged sB, sX;
+  int rc = stage_in(B, ldb, N, nrhs, sb, st, &sB);
+  if (rc != RS_OK) return rc;
+  // contiguous copies b (ld N), x, r, d
+  void *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr;
+  double* nrm = nullptr;
+  size_t bytes = sb * (size_t)N * nrhs;
+  std::vector<double> hb(nrhs), hr(nrhs);
+  int its = 0;
+  do {
+    if (cudaMallocAsync(&b, bytes, st) || cudaMallocAsync(&x, bytes, st) || cudaMallocAsync(&r, bytes, st) ||
+        cudaMallocAsync(&d, bytes, st) || cudaMallocAsync((void**)&nrm, sizeof(double) * 2 * nrhs, st)) {
+      rc = fail(RS_ERR_OOM, "rs_solve_refined: workspace allocation failed");
+      break;
+    }
+    if (cudaMemcpy2DAsync(b, sb * N, sB.d, sb * sB.ld, sb * N, nrhs, cudaMemcpyDeviceToDevice, st)) {
+      rc = fail(RS_ERR_CUDA, "copy");
+      break;
+    }
+    if ((rc = colnorm2_device(h, b, nrhs, nrm + nrhs, st)) != RS_OK) break;
+    if ((rc = solve_device(h, RS_PREC_FP32, b, N, nrhs, x, N, st)) != RS_OK) break;
+    cudaMemcpyAsync(hb.data(), nrm + nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
+    for (;;) {
+      if ((rc = residual_device(h, b, x, r, nrhs, nrm, st)) != RS_OK) break;
+      cudaMemcpyAsync(hr.data(), nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      bool done = true;
+      for (int c = 0; c < nrhs; ++c) {
+        double rel = hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : std::sqrt(hr[c]);
+        if (!std::isfinite(rel)) { rc = fail(RS_ERR_NAN, "rs_solve_refined: non-finite residual"); break; }
+        if (relres_out) relres_out[c] = rel;
+        if (rel > tol) done = false;
+      }
+      if (rc != RS_OK || done || its >= max_it) break;
+      if ((rc = solve_device(h, RS_PREC_FP32, r, N, nrhs, d, N, st)) != RS_OK) break;
+      if ((rc = axpy_lowp_device(h, x, d, nrhs, st)) != RS_OK) break;
+      ++its;
+    }
+    if (rc != RS_OK) break;
+    if ((rc = stage_out_alloc(X, ldx, N, nrhs, sb, st, &sX)) != RS_OK) break;
+    if (cudaMemcpy2DAsync(sX.d, sb * sX.ld, x, sb * N, sb * N, nrhs, cudaMemcpyDeviceToDevice, st)) {
+      rc = fail(RS_ERR_CUDA, "copy");
+      break;
+    }
+    rc = stage_out_finish(X, ldx, N, nrhs, sb, st, &sX);
+  } while (0);
+  cudaError_t e = cudaStreamSynchronize(st);
+  for (void* p : {b, x, r, d, (void*)nrm}) if (p) cudaFreeAsync(p, st);
+  release(&sB, st);
+  release(&sX, st);
+  cudaStreamSynchronize(st);
+  if (rc == RS_OK && e != cudaSuccess) rc = fail(RS_ERR_CUDA, "rs_solve_refined: %s", cudaGetErrorString(e));
+  if (its_out) *its_out = its;
+  return rc;
+}
+
+int rs_stats(rs_handle h, rs_stats_t* out) {
+  RS_TRY(check_handle(h));
+  if (!out) return fail(RS_ERR_ARG, "rs_stats: null output");
+  out->n = h->N;
+  out->dim = h->dim;
+  out->depth = h->L;
+  out->top_skeletons = h->lv[0].ntot;
+  out->factor_scalars = h->factor_scalars;
+  out->factor_bytes = h->factor_scalars * (int64_t)(h->cplx ? sizeof(c128) : sizeof(double));
+  out->build_ms = h->build_ms;
+  int mn = 0, mm = 0, mk = 0;
+  for (auto& lv : h->lv) {
+    mn = std::max(mn, lv.maxn);
+    mm = std::max(mm, lv.maxm);
+    mk = std::max(mk, lv.maxk);
+  }
+  out->max_box_n = mn;
+  out->max_box_m = mm;
+  out->max_rank = mk;
+  return RS_OK;
+}
+
+int rs_tree_perm(rs_handle h, int64_t* perm) {
+  RS_TRY(check_handle(h));
+  if (!perm) return fail(RS_ERR_ARG, "rs_tree_perm: null output");
+  std::vector<int> p(h->N);
+  RS_CUDA(cudaMemcpy(p.data(), h->perm, sizeof(int) * h->N, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < h->N; ++i) perm[i] = p[i];
+  return RS_OK;
+}
+
+int rs_tree_level(rs_handle h, int level, int* nbox_out, int64_t* begin, int* parent, int* ncoll, int* coll) {
+  RS_TRY(check_handle(h));
+  if (level < 0 || level > h->L) return fail(RS_ERR_ARG, "rs_tree_level: level %d out of range", level);
+  const Level& lv = h->lv[level];
+  if (nbox_out) *nbox_out = lv.nbox;
+  for (int b = 0; b < lv.nbox; ++b) {
+    if (begin) begin[b] = lv.h_begin[b];
+    if (parent) parent[b] = lv.h_parent[b];
+    if (ncoll) ncoll[b] = lv.h_ncoll[b];
+  }
+  if (coll) std::copy(lv.h_coll.begin(), lv.h_coll.end(), coll);
+  return RS_OK;
+}
+
+int rs_box_ranks(rs_handle h, int level, int* n, int* k) {
+  RS_TRY(check_handle(h));
+  if (level < 1 || level > h->L) return fail(RS_ERR_ARG, "rs_box_ranks: level %d out of range", level);
+  const Level& lv = h->lv[level];
+  for (int b = 0; b < lv.nbox; ++b) {
+    if (n) n[b] = lv.h_n[b];
+    if (k) k[b] = lv.h_k[b];
+  }
+  return RS_OK;
+}
+
+int rs_free(rs_handle h) {
+  if (h) destroy(h);
+  return RS_OK;
+}
+
+}  // extern "C"

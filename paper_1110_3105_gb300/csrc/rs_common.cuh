@@ -1,0 +1,155 @@
+// Shared device/host definitions for the recursive-skeletonization library.
+//
+// Scalar types: the real kernels (2D/3D Laplace) run in double (build) and
+// float (mixed-precision solve); the Helmholtz kernel in complex<double> and
+// complex<float>.  The complex type is a plain two-field struct with the
+// operators the kernels need, interleaved (re, im) like C99 double complex.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+#include <string>
+
+#include "../../include/rs.h"
+
+namespace rs {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+int fail(int code, const char* fmt, ...);
+
+#define RS_CUDA(call)                                                          \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess)                                                     \
+      return ::rs::fail(RS_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, \
+                        cudaGetErrorString(e_));                               \
+  } while (0)
+
+#define RS_CHECK_LAUNCH() RS_CUDA(cudaGetLastError())
+
+#define RS_TRY(expr)            \
+  do {                          \
+    int rc_ = (expr);           \
+    if (rc_ != RS_OK) return rc_; \
+  } while (0)
+
+// ------------------------------------------------------------ complex type
+template <class R>
+struct cplx {
+  R re, im;
+  cplx() = default;
+  __host__ __device__ cplx(R r) : re(r), im(0) {}
+  __host__ __device__ cplx(R r, R i) : re(r), im(i) {}
+  template <class Q>
+  __host__ __device__ explicit cplx(const cplx<Q>& o) : re((R)o.re), im((R)o.im) {}
+};
+template <class R> __host__ __device__ inline cplx<R> operator+(cplx<R> a, cplx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R> __host__ __device__ inline cplx<R> operator-(cplx<R> a, cplx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R> __host__ __device__ inline cplx<R> operator-(cplx<R> a) { return {-a.re, -a.im}; }
+template <class R> __host__ __device__ inline cplx<R> operator*(cplx<R> a, cplx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class R> __host__ __device__ inline cplx<R> operator*(R s, cplx<R> a) { return {s * a.re, s * a.im}; }
+template <class R> __host__ __device__ inline cplx<R>& operator+=(cplx<R>& a, cplx<R> b) { a.re += b.re; a.im += b.im; return a; }
+template <class R> __host__ __device__ inline cplx<R>& operator-=(cplx<R>& a, cplx<R> b) { a.re -= b.re; a.im -= b.im; return a; }
+template <class R> __host__ __device__ inline cplx<R> operator/(cplx<R> a, cplx<R> b) {
+  R d = b.re * b.re + b.im * b.im;
+  return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+template <class R> __host__ __device__ inline bool operator==(cplx<R> a, cplx<R> b) { return a.re == b.re && a.im == b.im; }
+
+using c64 = cplx<float>;
+using c128 = cplx<double>;
+
+// Generic scalar helpers -----------------------------------------------------
+__host__ __device__ inline double abs2(double x) { return x * x; }
+__host__ __device__ inline float abs2(float x) { return x * x; }
+template <class R> __host__ __device__ inline R abs2(cplx<R> z) { return z.re * z.re + z.im * z.im; }
+__host__ __device__ inline double conj_(double x) { return x; }
+__host__ __device__ inline float conj_(float x) { return x; }
+template <class R> __host__ __device__ inline cplx<R> conj_(cplx<R> z) { return {z.re, -z.im}; }
+__host__ __device__ inline double real_(double x) { return x; }
+template <class R> __host__ __device__ inline R real_(cplx<R> z) { return z.re; }
+
+template <class S> struct real_of { using type = S; };
+template <class R> struct real_of<cplx<R>> { using type = R; };
+template <class S> struct lowp { using type = float; };
+template <> struct lowp<c128> { using type = c64; };
+template <class S> struct is_cplx { static constexpr bool value = false; };
+template <class R> struct is_cplx<cplx<R>> { static constexpr bool value = true; };
+
+template <class S> __device__ inline S shfl_xor(S v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+template <class R> __device__ inline cplx<R> shfl_xor(cplx<R> v, int m) {
+  return {__shfl_xor_sync(0xffffffffu, v.re, m), __shfl_xor_sync(0xffffffffu, v.im, m)};
+}
+template <class S> __device__ inline S shfl(S v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+template <class R> __device__ inline cplx<R> shfl(cplx<R> v, int src) {
+  return {__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+}
+template <class S> __device__ inline S warp_sum(S v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
+  return v;
+}
+
+// ----------------------------------------------------------- point clouds
+// Points are stored per axis (structure of arrays) in tree order.
+struct Pts {
+  const double* x;
+  const double* y;
+  const double* z;  // null in 2D
+};
+
+__device__ inline double dist(const Pts& p, int i, int j) {
+  double dx = p.x[i] - p.x[j], dy = p.y[i] - p.y[j];
+  double s = dx * dx + dy * dy;
+  if (p.z) { double dz = p.z[i] - p.z[j]; s += dz * dz; }
+  return sqrt(s);
+}
+
+// Kernel parameters shared by every device routine.
+struct KParams {
+  int kind;       // RS_LAPLACE2D / RS_HELMHOLTZ2D / RS_LAPLACE3D
+  double w;       // quadrature weight in A = I + w K
+  double kwave;   // Helmholtz wavenumber
+};
+
+// Green's functions: eq. 2d-laplace, eq. 3d-laplace, eq. 2d-helmholtz.
+// H0^(1) = J0 + i Y0 from CUDA's math library.
+__device__ inline double green_real(int kind, double r) {
+  if (kind == RS_LAPLACE3D) return 1.0 / (4.0 * M_PI * r);
+  return -log(r) * (1.0 / (2.0 * M_PI));
+}
+__device__ inline c128 green_cplx(double kwave, double r) {
+  double kr = kwave * r;
+  return c128(-0.25 * y0(kr), 0.25 * j0(kr));   // (i/4)(J0 + i Y0)
+}
+// w G(x_i, x_j) for distinct points.
+template <class S> __device__ inline S offdiag_entry(const KParams& kp, const Pts& p, int i, int j);
+template <> __device__ inline double offdiag_entry<double>(const KParams& kp, const Pts& p, int i, int j) {
+  return kp.w * green_real(kp.kind, dist(p, i, j));
+}
+template <> __device__ inline c128 offdiag_entry<c128>(const KParams& kp, const Pts& p, int i, int j) {
+  c128 g = green_cplx(kp.kwave, dist(p, i, j));
+  return c128(kp.w * g.re, kp.w * g.im);
+}
+// A_ij = delta_ij + w G(x_i, x_j) with K_ii = 0.
+template <class S> __device__ inline S system_entry(const KParams& kp, const Pts& p, int i, int j) {
+  if (i == j) return S(1.0);
+  return offdiag_entry<S>(kp, p, i, j);
+}
+
+// Green's function between an arbitrary location and a point.
+template <class S> __device__ inline S green_at(const KParams& kp, double r);
+template <> __device__ inline double green_at<double>(const KParams& kp, double r) { return kp.w * green_real(kp.kind, r); }
+template <> __device__ inline c128 green_at<c128>(const KParams& kp, double r) {
+  c128 g = green_cplx(kp.kwave, r);
+  return c128(kp.w * g.re, kp.w * g.im);
+}
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace rs

@@ -1,0 +1,151 @@
+// Internal runtime structures of the recursive-skeletonization library.
+//
+// Device data layout (one handle):
+//   pts      coordinates per axis in tree order (x, y[, z]), N doubles each
+//   perm     tree position -> caller's point index
+//   per tree depth d = 0..L (Level):
+//     box tables from the tree (begin, parent, child range, colleagues)
+//     active set of each box: ids of points (tree positions) in `act`,
+//       box b at act[off[b] .. off[b] + n[b]); at the leaves act = identity;
+//       above, the concatenated skeletons of the children (child order)
+//     owner[pos]: the child box (depth d+1) a position of depth d came from
+//     ID output: k[b], lperm (per box a permutation of 0..n-1: first k =
+//       skeletons in pivot order, then the redundant ones), T (k x (n-k)
+//       column-major at toff[b])
+//     skoff[b]: where box b's skeletons start in the depth d-1 active vector
+//     factors (eq. compressed-inverse), column-major:
+//       U   at uoff[b]: (n+k) x n = [calD ; calR]
+//       Lf  at loff[b]: n x k     = calL
+//       Lam at lamoff[b]: k x k   = Lambda (read by the parent's assembly)
+//     float copies U32 / Lf32 for the mixed-precision solve
+//   the root is depth 0 with k = 0, so its U holds calS^{-1}.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "rs_common.cuh"
+
+namespace rs {
+
+// ------------------------------------------------------------ primitives
+// Exclusive scan of n int64 values; *total (host) receives the sum.
+int scan_i64(const int64_t* d_in, int64_t* d_out, int64_t n, int64_t* total, cudaStream_t st);
+// Exclusive scan of int32 values into int64 offsets.
+int scan_i32_to_i64(const int* d_in, int64_t* d_out, int64_t n, int64_t* total, cudaStream_t st);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` key bits.
+int radix_sort_pairs(uint64_t* keys, int* vals, uint64_t* keys_tmp, int* vals_tmp, int n, int bits,
+                     cudaStream_t st);
+// Max / sum of an int array (host result).
+int reduce_max_i32(const int* d_in, int n, int* out, cudaStream_t st);
+
+// Device buffer owned by a handle.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Level {
+  int depth = 0;
+  int nbox = 0;
+  // tree
+  int* begin = nullptr;        // first point (tree order) of each box
+  int* parent = nullptr;       // parent box at depth-1
+  int* child_begin = nullptr;  // children at depth+1 are [child_begin, child_end)
+  int* child_end = nullptr;
+  int* ncoll = nullptr;
+  int* coll = nullptr;         // 27 per box, ascending, -1 padded
+  int* coords = nullptr;       // dim per box
+  uint64_t* keys = nullptr;
+  // active sets
+  int64_t ntot = 0;            // sum of n over boxes
+  int* n = nullptr;
+  int64_t* off = nullptr;
+  int* act = nullptr;
+  int* owner = nullptr;        // child box of each active position (depth < L)
+  // skeletonization
+  int* k = nullptr;
+  int64_t* skoff = nullptr;
+  int* lperm = nullptr;        // ntot entries
+  int64_t* toff = nullptr;
+  int64_t* uoff = nullptr;
+  int64_t* loff = nullptr;
+  int64_t* lamoff = nullptr;
+  void* T = nullptr;
+  void* U = nullptr;
+  void* Lf = nullptr;
+  void* Lam = nullptr;
+  void* U32 = nullptr;
+  void* Lf32 = nullptr;
+  int64_t ksum = 0;            // sum of k (size of depth-1 active vector)
+  int64_t usz = 0, lsz = 0, lamsz = 0, tsz = 0;  // scalars in the pools
+  int maxn = 0, maxm = 0, maxk = 0;
+  // host copies (for sizes and the inspection API)
+  std::vector<int> h_n, h_k, h_begin, h_parent, h_ncoll, h_coll;
+};
+
+struct Handle {
+  int dim = 2;
+  int64_t N = 0;
+  KParams kp{};
+  int nproxy = 64;
+  double ratio = 1.5;
+  double eps = 1e-9;
+  int leaf = 64;
+  bool cplx = false;
+  int L = 0;
+  double center[3] = {0, 0, 0};
+  double half = 1.0;           // root half-width a
+  double* pts = nullptr;       // 3 * N (x, y, z blocks)
+  int* perm = nullptr;
+  std::vector<Level> lv;       // index = depth
+  std::vector<void*> allocs;   // everything to cudaFree
+  double build_ms = 0;
+  int64_t factor_scalars = 0;
+  int* status = nullptr;       // device status word (singularity etc.)
+  // solve workspaces (grown on demand)
+  struct Work {
+    int R = 0;
+    int prec = -1;
+    void* vin = nullptr;        // caller-order staging (double / c128), N*R
+    std::vector<void*> v;       // per depth: input vector of the upward pass
+    std::vector<void*> u;       // per depth: calD b, then x in the downward pass
+    size_t bytes = 0;
+  };
+  Work work[2];                 // [0] = FP64 solve, [1] = FP32 solve
+  // refinement / matvec workspaces
+  void* r64 = nullptr; void* x64 = nullptr; void* b64 = nullptr;
+  std::vector<void*> fz, fy;    // forward operator vectors per depth
+  int fR = 0;
+  double* colnorm = nullptr;    // 2 * R
+  int ncolnorm = 0;
+};
+
+// allocation helper: records in h->allocs
+int dalloc(Handle* h, void** p, size_t bytes);
+template <class T> int dalloc_t(Handle* h, T** p, size_t count) {
+  return dalloc(h, (void**)p, count * sizeof(T));
+}
+
+// Tree construction (tree.cu).
+int build_tree(Handle* h, const double* d_pts_in, cudaStream_t st);
+
+// Skeletonization + factorization of one depth (skel.cu).
+int skeletonize_level(Handle* h, int depth, cudaStream_t st);
+int factor_root(Handle* h, cudaStream_t st);
+int make_fp32_copies(Handle* h, cudaStream_t st);
+
+// Solve / forward operator (solve.cu).
+int solve_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, void* d_X, int64_t ldx,
+                 cudaStream_t st);
+int matvec_device(Handle* h, const void* d_X, int64_t ldx, int nrhs, void* d_Y, int64_t ldy,
+                  cudaStream_t st);
+// r = b - A_RS x (all device, caller order, ld = N); colnorm: per column ||r||^2 (device, R doubles)
+int residual_device(Handle* h, const void* d_b, const void* d_x, void* d_r, int nrhs, double* d_rnorm2,
+                    cudaStream_t st);
+int colnorm2_device(Handle* h, const void* d_v, int nrhs, double* d_out, cudaStream_t st);
+int axpy_lowp_device(Handle* h, void* d_x, const void* d_d, int nrhs, cudaStream_t st);
+
+}  // namespace rs

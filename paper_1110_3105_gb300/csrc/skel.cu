@@ -1,0 +1,776 @@
+// Per-level skeletonization and factorization (the build's hot path).
+//
+// For every box of one tree depth, one CTA:
+//   k_id      fills the proxy-compressed matrix
+//               M = [ w G(near, I) ; w G(proxy, I) (; w 1) ]      (Sec. 3.2)
+//             (near = active points of the colleague boxes, proxy surface as
+//             in the header rs.h describes) and computes its interpolative
+//             decomposition (Sec. 2.2, Def. 2.3) by Householder QR with column
+//             pivoting: pivot = largest trailing column norm (norms recomputed
+//             every step, lowest index on ties, warp-level argmax), rank k =
+//             first j with |R_jj| <= eps |R_00|, T = R11^-1 R12.
+//   k_factor  assembles the diagonal block D (leaf: A(I, I); above: the
+//             children's Lambda on the diagonal, w G between skeletons of
+//             different children -- S^(l-1) regrouped plus Lambda^(l-1), eqs.
+//             sparse-embedding / multilevel-embedding) and eliminates it
+//             (eq. compressed-inverse) with P = [I T] Pi, L = P^T, R = P:
+//               X = D^-1 P^T,  Lambda = (P X)^-1,  calL = X Lambda,
+//               calR = Lambda X^T (D symmetric: P D^-1 = X^T),
+//               calD = D^-1 - calL X^T.
+// Everything is double (complex double for Helmholtz); the rank decision and
+// every LU stay in FP64.  Dense inverses use Gauss-Jordan elimination with
+// partial pivoting on [D | I].
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "rs_internal.h"
+
+namespace rs {
+
+namespace {
+
+constexpr int ID_NT = 256;
+constexpr int FA_NT = 256;
+
+template <class S> __device__ inline S scal(S a, double s);
+template <> __device__ inline double scal<double>(double a, double s) { return a * s; }
+template <> __device__ inline c128 scal<c128>(c128 a, double s) { return c128(a.re * s, a.im * s); }
+
+struct Geo {
+  double lower[3];
+  double side;      // box side at this depth
+  int dim;
+  int nproxy;
+  double ratio;
+  int constrow;     // 1: append a constant row (2D Laplace with |log rho| < 0.1)
+};
+
+// Coordinates of proxy point j of a box with the given integer coordinates.
+__device__ inline void proxy_point(const Geo& g, const int* coords, int j, double* out) {
+  double c[3];
+  for (int d = 0; d < g.dim; ++d) c[d] = g.lower[d] + ((double)coords[d] + 0.5) * g.side;
+  if (g.dim == 2) {
+    double rho = g.ratio * (0.70710678118654752440) * g.side;
+    double th = 2.0 * M_PI * (double)j / (double)g.nproxy;
+    out[0] = c[0] + rho * cos(th);
+    out[1] = c[1] + rho * sin(th);
+    out[2] = 0.0;
+    return;
+  }
+  int gg = (int)lrint(sqrt((double)g.nproxy / 6.0));
+  double h = g.ratio * g.side * 0.5;
+  int face = j / (gg * gg), rem = j % (gg * gg);
+  int ia = rem / gg, ib = rem % gg;
+  int axis = face / 2;
+  double sign = (face % 2) ? 1.0 : -1.0;
+  double ua = -h + (2.0 * ia + 1.0) * h / gg;
+  double ub = -h + (2.0 * ib + 1.0) * h / gg;
+  double p[3];
+  p[axis] = sign * h;
+  int o0 = axis == 0 ? 1 : 0;
+  int o1 = axis == 2 ? 1 : 2;
+  p[o0] = ua;
+  p[o1] = ub;
+  for (int d = 0; d < 3; ++d) out[d] = c[d] + p[d];
+}
+
+__device__ inline double dist_to(const Pts& p, int i, const double* q) {
+  double dx = p.x[i] - q[0], dy = p.y[i] - q[1];
+  double s = dx * dx + dy * dy;
+  if (p.z) { double dz = p.z[i] - q[2]; s += dz * dz; }
+  return sqrt(s);
+}
+
+// Column-pivoted Householder QR of M (m x n, column-major, leading dim ld),
+// stopped at relative precision eps.  On return piv holds the column order,
+// M[0:k, 0:n] the triangular factor; returns k.
+template <class S, int NT>
+__device__ int cpqr(S* M, int m, int n, int ld, double eps, int* piv, double* nrm, S* u) {
+  __shared__ int s_p, s_stop;
+  __shared__ double s_rjj, s_r00;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NT / 32;
+  for (int c = tid; c < n; c += NT) piv[c] = c;
+  const int kmax = min(m, n);
+  int j = 0;
+  __syncthreads();
+  for (; j < kmax; ++j) {
+    for (int c = j + warp; c < n; c += NW) {
+      const S* col = M + (size_t)c * ld;
+      double s = 0.0;
+      for (int r = j + lane; r < m; r += 32) s += abs2(col[r]);
+      s = warp_sum(s);
+      if (lane == 0) nrm[c] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = n;
+      for (int c = j + lane; c < n; c += 32) {
+        double v = nrm[c];
+        if (v > best) { best = v; bi = c; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        double rjj = sqrt(best);
+        int stop = 0;
+        if (j == 0) {
+          s_r00 = rjj;
+          if (!(rjj > 0.0)) stop = 1;
+        } else if (rjj <= eps * s_r00) {
+          stop = 1;
+        }
+        s_p = bi;
+        s_rjj = rjj;
+        s_stop = stop;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_p;
+    const double rjj = s_rjj;
+    if (p != j) {
+      for (int r = tid; r < m; r += NT) {
+        S t = M[r + (size_t)j * ld];
+        M[r + (size_t)j * ld] = M[r + (size_t)p * ld];
+        M[r + (size_t)p * ld] = t;
+      }
+      if (tid == 0) { int t = piv[j]; piv[j] = piv[p]; piv[p] = t; }
+    }
+    __syncthreads();
+    // Householder reflector H = I - f u u^H mapping column j onto beta e_1,
+    // beta = -phase(alpha) ||x||, u = x - beta e_1, f = 2 / (u^H u).
+    const S alpha = M[j + (size_t)j * ld];
+    const double aa = sqrt(abs2(alpha));
+    const S phase = aa > 0.0 ? scal(alpha, 1.0 / aa) : S(1.0);
+    const S beta = scal(phase, -rjj);
+    for (int r = j + tid; r < m; r += NT) u[r - j] = (r == j) ? alpha - beta : M[r + (size_t)j * ld];
+    const double f = 1.0 / (rjj * (rjj + aa));
+    __syncthreads();
+    for (int c = j + 1 + warp; c < n; c += NW) {
+      S* col = M + (size_t)c * ld;
+      S s = S(0.0);
+      for (int r = j + lane; r < m; r += 32) s += conj_(u[r - j]) * col[r];
+      s = warp_sum(s);
+      s = shfl(s, 0);
+      const S fs = scal(s, f);
+      for (int r = j + lane; r < m; r += 32) col[r] -= u[r - j] * fs;
+    }
+    if (tid == 0) M[j + (size_t)j * ld] = beta;
+    __syncthreads();
+  }
+  return j;
+}
+
+// T = R11^-1 R12 in place in M[0:k, k:n]; one warp per column.
+template <class S, int NT>
+__device__ void back_substitute(S* M, int k, int n, int ld) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  for (int c = k + warp; c < n; c += NW) {
+    S* col = M + (size_t)c * ld;
+    for (int i = k - 1; i >= 0; --i) {
+      S ti = S(0.0);
+      if (lane == 0) {
+        ti = col[i] / M[i + (size_t)i * ld];
+        col[i] = ti;
+      }
+      ti = shfl(ti, 0);
+      for (int r = lane; r < i; r += 32) col[r] -= M[r + (size_t)i * ld] * ti;
+      __syncwarp();
+    }
+  }
+}
+
+struct IdArgs {
+  KParams kp;
+  Pts pts;
+  Geo geo;
+  double eps;
+  const int* n;          // per box active size
+  const int64_t* off;    // per box active offset
+  const int* act;        // active point ids
+  const int* ncoll;
+  const int* coll;
+  const int* coords;
+  const int* mrows;      // per box total rows
+  const int64_t* moff;   // per box workspace offset (global path)
+  const int64_t* toff;
+  int* kout;
+  int* lperm;
+  int smem_path;         // 1: M in shared memory
+  int mmax, nmax;
+};
+
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int cstart[28];
+  const int b = blockIdx.x;
+  const int n = a.n[b];
+  const int m = a.mrows[b];
+  const int64_t off = a.off[b];
+  // shared layout: [M (smem path)] | u[mmax] | nrm[nmax] | piv[nmax] | rowid[mmax]
+  S* Ms = reinterpret_cast<S*>(smem);
+  size_t msz = a.smem_path ? (size_t)a.mmax * a.nmax : 0;
+  S* u = Ms + msz;
+  double* nrm = reinterpret_cast<double*>(u + a.mmax);
+  int* piv = reinterpret_cast<int*>(nrm + a.nmax);
+  int* rowid = piv + a.nmax;
+  S* M = a.smem_path ? Ms : Mws + a.moff[b];
+  const int ld = m;
+  const int nc = a.ncoll[b];
+
+  // near-field rows: colleagues' active sets in ascending box order
+  if (threadIdx.x == 0) {
+    int r = 0;
+    for (int j = 0; j < nc; ++j) {
+      cstart[j] = r;
+      r += a.n[a.coll[b * 27 + j]];
+    }
+    cstart[nc] = r;
+  }
+  __syncthreads();
+  const int nnear = cstart[nc];
+  for (int r = threadIdx.x; r < nnear; r += NT) {
+    int j = 0;
+    while (cstart[j + 1] <= r) ++j;
+    int c = a.coll[b * 27 + j];
+    rowid[r] = a.act[a.off[c] + (r - cstart[j])];
+  }
+  __syncthreads();
+
+  // fill M column-major: rows = near | proxy | (constant)
+  const int* bc = a.coords + (size_t)b * a.geo.dim;
+  const int64_t total = (int64_t)m * n;
+  for (int64_t e = threadIdx.x; e < total; e += NT) {
+    int r = (int)(e % m), c = (int)(e / m);
+    int pc = a.act[off + c];
+    S v;
+    if (r < nnear) {
+      v = offdiag_entry<S>(a.kp, a.pts, rowid[r], pc);
+    } else if (r < nnear + a.geo.nproxy) {
+      double q[3];
+      proxy_point(a.geo, bc, r - nnear, q);
+      v = green_at<S>(a.kp, dist_to(a.pts, pc, q));
+    } else {
+      v = S(a.kp.w);
+    }
+    M[r + (size_t)c * ld] = v;
+  }
+  __syncthreads();
+
+  const int k = cpqr<S, NT>(M, m, n, ld, a.eps, piv, nrm, u);
+  __syncthreads();
+  back_substitute<S, NT>(M, k, n, ld);
+  __syncthreads();
+  S* T = Tpool + a.toff[b];
+  const int nr = n - k;
+  for (int e = threadIdx.x; e < k * nr; e += NT) {
+    int r = e % k, c = e / k;
+    T[r + (size_t)c * k] = M[r + (size_t)(k + c) * ld];
+  }
+  for (int c = threadIdx.x; c < n; c += NT) a.lperm[off + c] = piv[c];
+  if (threadIdx.x == 0) a.kout[b] = k;
+}
+
+// Gauss-Jordan with partial pivoting on the augmented n x 2n matrix [A | I]
+// (column-major, ld = n); leaves A^-1 in the right half.  Sets *bad on a zero
+// or non-finite pivot.
+template <class S, int NT>
+__device__ void gauss_jordan(S* A, int n, S* mult, int* bad) {
+  __shared__ int s_p;
+  __shared__ double s_best;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ld = n, w = 2 * n;
+  for (int j = 0; j < n; ++j) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = j;
+      for (int r = j + lane; r < n; r += 32) {
+        double v = abs2(A[r + (size_t)j * ld]);
+        if (v > best) { best = v; bi = r; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { s_p = bi; s_best = best; }
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (!(s_best > 0.0) || !isfinite(s_best)) {
+      if (tid == 0) atomicOr(bad, 1);
+      __syncthreads();
+      continue;
+    }
+    if (p != j)
+      for (int c = tid; c < w; c += NT) {
+        S t = A[j + (size_t)c * ld];
+        A[j + (size_t)c * ld] = A[p + (size_t)c * ld];
+        A[p + (size_t)c * ld] = t;
+      }
+    __syncthreads();
+    const S inv = S(1.0) / A[j + (size_t)j * ld];
+    __syncthreads();
+    for (int c = j + tid; c < w; c += NT) A[j + (size_t)c * ld] = A[j + (size_t)c * ld] * inv;
+    for (int r = tid; r < n; r += NT) mult[r] = A[r + (size_t)j * ld];
+    __syncthreads();
+    const int64_t cnt = (int64_t)(w - j - 1) * n;
+    for (int64_t e = tid; e < cnt; e += NT) {
+      int r = (int)(e % n);
+      int c = j + 1 + (int)(e / n);
+      if (r != j) A[r + (size_t)c * ld] -= mult[r] * A[j + (size_t)c * ld];
+    }
+    __syncthreads();
+  }
+}
+
+struct FaArgs {
+  KParams kp;
+  Pts pts;
+  int leaf_level;         // 1: D = A(I, I)
+  const int* n;
+  const int* k;
+  const int64_t* off;
+  const int* act;
+  const int* owner;       // child box of each active position (upper levels)
+  const int64_t* cskoff;  // children's skeleton offsets (depth + 1)
+  const int* ck;          // children's ranks
+  const int64_t* clamoff; // children's Lambda offsets
+  const int* lperm;
+  const int64_t* toff;
+  const int64_t* wsoff;
+  const int64_t* uoff;
+  const int64_t* loff;
+  const int64_t* lamoff;
+  int* bad;
+};
+
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) k_factor(FaArgs a, const S* Tpool, const S* cLam, S* ws, S* Upool,
+                                               S* Lpool, S* Lampool) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  S* mult = reinterpret_cast<S*>(smem);
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int n = a.n[b], k = a.k[b], nr = n - k;
+  const int64_t off = a.off[b];
+  const int* lp = a.lperm + off;
+  const S* T = Tpool + (a.toff ? a.toff[b] : 0);
+  S* Aug = ws + a.wsoff[b];
+  S* X = Aug + (size_t)2 * n * n;
+  S* Y = X + (size_t)n * k;
+
+  // D (left half) and I (right half)
+  for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
+    int r = (int)(e % n), c = (int)(e / n);
+    int pr = a.act[off + r], pc = a.act[off + c];
+    S v;
+    if (a.leaf_level) {
+      v = system_entry<S>(a.kp, a.pts, pr, pc);
+    } else {
+      int orow = a.owner[off + r], ocol = a.owner[off + c];
+      if (orow == ocol) {
+        int64_t base = a.cskoff[orow];
+        int kc = a.ck[orow];
+        v = cLam[a.clamoff[orow] + (off + r - base) + (int64_t)(off + c - base) * kc];
+      } else {
+        v = offdiag_entry<S>(a.kp, a.pts, pr, pc);
+      }
+    }
+    Aug[r + (size_t)c * n] = v;
+    Aug[r + (size_t)(n + c) * n] = (r == c) ? S(1.0) : S(0.0);
+  }
+  __syncthreads();
+  gauss_jordan<S, NT>(Aug, n, mult, a.bad);
+  const S* Dinv = Aug + (size_t)n * n;
+  S* U = Upool + a.uoff[b];        // (n + k) x n, ld n + k
+  const int ldu = n + k;
+  if (k == 0) {
+    for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
+      int r = (int)(e % n), c = (int)(e / n);
+      U[r + (size_t)c * ldu] = Dinv[r + (size_t)c * n];
+    }
+    return;
+  }
+  // X = D^-1 P^T : X[:, i] = Dinv[:, sk_i] + sum_e T[i, e] Dinv[:, rd_e]
+  for (int64_t e = tid; e < (int64_t)n * k; e += NT) {
+    int r = (int)(e % n), i = (int)(e / n);
+    S s = Dinv[r + (size_t)lp[i] * n];
+    for (int q = 0; q < nr; ++q) s += T[i + (size_t)q * k] * Dinv[r + (size_t)lp[k + q] * n];
+    X[r + (size_t)i * n] = s;
+  }
+  __syncthreads();
+  // [P X | I] : (P X)[i, c] = X[sk_i, c] + sum_e T[i, e] X[rd_e, c]
+  for (int64_t e = tid; e < (int64_t)k * k; e += NT) {
+    int i = (int)(e % k), c = (int)(e / k);
+    S s = X[lp[i] + (size_t)c * n];
+    for (int q = 0; q < nr; ++q) s += T[i + (size_t)q * k] * X[lp[k + q] + (size_t)c * n];
+    Y[i + (size_t)c * k] = s;
+    Y[i + (size_t)(k + c) * k] = (i == c) ? S(1.0) : S(0.0);
+  }
+  __syncthreads();
+  gauss_jordan<S, NT>(Y, k, mult, a.bad);
+  const S* Lam = Y + (size_t)k * k;
+  S* Lo = Lampool + a.lamoff[b];
+  for (int e = tid; e < k * k; e += NT) Lo[e] = Lam[e];
+  // calL = X Lambda  (n x k)
+  S* Lf = Lpool + a.loff[b];
+  for (int64_t e = tid; e < (int64_t)n * k; e += NT) {
+    int r = (int)(e % n), c = (int)(e / n);
+    S s = S(0.0);
+    for (int q = 0; q < k; ++q) s += X[r + (size_t)q * n] * Lam[q + (size_t)c * k];
+    Lf[r + (size_t)c * n] = s;
+  }
+  // calR = Lambda X^T  (k x n) -> rows n.. of U
+  for (int64_t e = tid; e < (int64_t)k * n; e += NT) {
+    int i = (int)(e % k), c = (int)(e / k);
+    S s = S(0.0);
+    for (int q = 0; q < k; ++q) s += Lam[i + (size_t)q * k] * X[c + (size_t)q * n];
+    U[n + i + (size_t)c * ldu] = s;
+  }
+  __syncthreads();
+  // calD = Dinv - calL X^T  (n x n) -> rows 0..n-1 of U
+  for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
+    int r = (int)(e % n), c = (int)(e / n);
+    S s = Dinv[r + (size_t)c * n];
+    for (int q = 0; q < k; ++q) s -= Lf[r + (size_t)q * n] * X[c + (size_t)q * n];
+    U[r + (size_t)c * ldu] = s;
+  }
+}
+
+// Skeleton ids of every box into the parent depth's active vector.
+__global__ void k_emit(const int* n, const int* k, const int64_t* off, const int64_t* skoff, const int* act,
+                       const int* lperm, int nbox, int* act_up, int* owner_up) {
+  int b = blockIdx.x;
+  if (b >= nbox) return;
+  int kb = k[b];
+  for (int i = threadIdx.x; i < kb; i += blockDim.x) {
+    act_up[skoff[b] + i] = act[off[b] + lperm[off[b] + i]];
+    owner_up[skoff[b] + i] = b;
+  }
+}
+
+template <class S>
+__global__ void k_to_float(const S* in, typename lowp<S>::type* out, int64_t cnt) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) out[i] = typename lowp<S>::type(in[i]);
+}
+
+// ------------------------------------------------------------- host helpers
+template <class T>
+int upload(Handle* h, T** d, const std::vector<T>& v, cudaStream_t st) {
+  RS_TRY(dalloc_t(h, d, std::max<size_t>(1, v.size())));
+  if (!v.empty()) RS_CUDA(cudaMemcpyAsync(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+  return RS_OK;
+}
+
+size_t scal_bytes(const Handle* h) { return h->cplx ? sizeof(c128) : sizeof(double); }
+
+Geo make_geo(const Handle* h, int depth) {
+  Geo g;
+  for (int d = 0; d < 3; ++d) g.lower[d] = h->center[d] - h->half;
+  g.side = (2.0 * h->half) / (double)(1ll << depth);
+  g.dim = h->dim;
+  g.nproxy = h->nproxy;
+  g.ratio = h->ratio;
+  g.constrow = 0;
+  if (h->kp.kind == RS_LAPLACE2D) {
+    double rho = h->ratio * (std::sqrt(2.0) / 2.0) * g.side;
+    g.constrow = std::fabs(std::log(rho)) < 0.1 ? 1 : 0;
+  }
+  return g;
+}
+
+Pts make_pts(const Handle* h) {
+  Pts p;
+  p.x = h->pts;
+  p.y = h->pts + h->N;
+  p.z = h->dim == 3 ? h->pts + 2 * h->N : nullptr;
+  return p;
+}
+
+template <class S>
+int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows, int64_t msum,
+           cudaStream_t st) {
+  IdArgs a = a0;
+  size_t sb = sizeof(S);
+  size_t extra = (size_t)a.mmax * sb + (size_t)a.nmax * sizeof(double) + (size_t)a.nmax * sizeof(int) +
+                 (size_t)a.mmax * sizeof(int) + 64;
+  size_t mbytes = (size_t)a.mmax * a.nmax * sb;
+  const size_t limit = 200 * 1024;
+  S* Mws = nullptr;
+  a.smem_path = (mbytes + extra <= limit) ? 1 : 0;
+  size_t smem = a.smem_path ? mbytes + extra : extra;
+  if (smem > 227 * 1024) return fail(RS_ERR_ARG, "box too large for shared staging (m=%d n=%d)", a.mmax, a.nmax);
+  if (!a.smem_path) {
+    std::vector<int64_t> moff(lv.nbox);
+    int64_t acc = 0;
+    for (int b = 0; b < lv.nbox; ++b) { moff[b] = acc; acc += (int64_t)mrows[b] * lv.h_n[b]; }
+    int64_t* dmoff;
+    RS_TRY(upload(h, &dmoff, moff, st));
+    a.moff = dmoff;
+    RS_CUDA(cudaMallocAsync((void**)&Mws, sb * std::max<int64_t>(1, acc), st));
+  }
+  RS_CUDA(cudaFuncSetAttribute(k_id<S, ID_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_id<S, ID_NT><<<lv.nbox, ID_NT, smem, st>>>(a, Mws, (S*)lv.T);
+  RS_CHECK_LAUNCH();
+  if (Mws) RS_CUDA(cudaFreeAsync(Mws, st));
+  (void)msum;
+  return RS_OK;
+}
+
+template <class S>
+int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t st) {
+  // workspace: [D | I] (2 n^2) + X (n k) + [PX | I] (2 k^2)
+  std::vector<int64_t> wsoff(lv.nbox);
+  int64_t acc = 0;
+  for (int b = 0; b < lv.nbox; ++b) {
+    int64_t n = lv.h_n[b], k = lv.h_k[b];
+    wsoff[b] = acc;
+    acc += 2 * n * n + n * k + 2 * k * k;
+  }
+  int64_t* dws;
+  RS_TRY(upload(h, &dws, wsoff, st));
+  a.wsoff = dws;
+  S* ws = nullptr;
+  RS_CUDA(cudaMallocAsync((void**)&ws, sizeof(S) * std::max<int64_t>(1, acc), st));
+  size_t smem = sizeof(S) * std::max(1, lv.maxn);
+  RS_CUDA(cudaFuncSetAttribute(k_factor<S, FA_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_factor<S, FA_NT><<<lv.nbox, FA_NT, smem, st>>>(a, (const S*)lv.T, child ? (const S*)child->Lam : nullptr, ws,
+                                                   (S*)lv.U, (S*)lv.Lf, (S*)lv.Lam);
+  RS_CHECK_LAUNCH();
+  RS_CUDA(cudaFreeAsync(ws, st));
+  return RS_OK;
+}
+
+int check_bad(Handle* h, cudaStream_t st, const char* where) {
+  int bad = 0;
+  RS_CUDA(cudaMemcpyAsync(&bad, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RS_CUDA(cudaStreamSynchronize(st));
+  if (bad) return fail(RS_ERR_SINGULAR, "rs_build: singular block during %s", where);
+  return RS_OK;
+}
+
+// Sizes and offsets of the factor pools of a level (host), then allocate.
+int alloc_factors(Handle* h, Level& lv, cudaStream_t st) {
+  std::vector<int64_t> uoff(lv.nbox), loff(lv.nbox), lamoff(lv.nbox);
+  int64_t us = 0, ls = 0, lams = 0;
+  for (int b = 0; b < lv.nbox; ++b) {
+    int64_t n = lv.h_n[b], k = lv.h_k[b];
+    uoff[b] = us; us += (n + k) * n;
+    loff[b] = ls; ls += n * k;
+    lamoff[b] = lams; lams += k * k;
+  }
+  lv.usz = us; lv.lsz = ls; lv.lamsz = lams;
+  RS_TRY(upload(h, &lv.uoff, uoff, st));
+  RS_TRY(upload(h, &lv.loff, loff, st));
+  RS_TRY(upload(h, &lv.lamoff, lamoff, st));
+  size_t sb = scal_bytes(h);
+  RS_TRY(dalloc(h, &lv.U, sb * std::max<int64_t>(1, us)));
+  RS_TRY(dalloc(h, &lv.Lf, sb * std::max<int64_t>(1, ls)));
+  RS_TRY(dalloc(h, &lv.Lam, sb * std::max<int64_t>(1, lams)));
+  h->factor_scalars += us + ls;
+  return RS_OK;
+}
+
+}  // namespace
+
+// Skeletonize and factor every box of depth `depth` (1 <= depth <= L); fills
+// the active sets of depth-1.
+int skeletonize_level(Handle* h, int depth, cudaStream_t st) {
+  Level& lv = h->lv[depth];
+  const int nbox = lv.nbox;
+  // active sets of the leaves come from the tree
+  if (depth == h->L) {
+    lv.h_n.resize(nbox);
+    std::vector<int64_t> off(nbox);
+    for (int b = 0; b < nbox; ++b) {
+      int e = b + 1 < nbox ? lv.h_begin[b + 1] : (int)h->N;
+      lv.h_n[b] = e - lv.h_begin[b];
+      off[b] = lv.h_begin[b];
+    }
+    lv.ntot = h->N;
+    RS_TRY(upload(h, &lv.n, lv.h_n, st));
+    RS_TRY(upload(h, &lv.off, off, st));
+  }
+  lv.maxn = 0;
+  for (int b = 0; b < nbox; ++b) lv.maxn = std::max(lv.maxn, lv.h_n[b]);
+
+  Geo geo = make_geo(h, depth);
+  std::vector<int> mrows(nbox);
+  std::vector<int64_t> toff(nbox);
+  int64_t tacc = 0, msum = 0;
+  lv.maxm = 0;
+  for (int b = 0; b < nbox; ++b) {
+    int near = 0;
+    for (int j = 0; j < lv.h_ncoll[b]; ++j) near += lv.h_n[lv.h_coll[(size_t)b * 27 + j]];
+    mrows[b] = near + h->nproxy + geo.constrow;
+    lv.maxm = std::max(lv.maxm, mrows[b]);
+    msum += (int64_t)mrows[b] * lv.h_n[b];
+    toff[b] = tacc;
+    int64_t n = lv.h_n[b];
+    tacc += (n * n) / 4;
+  }
+  lv.tsz = tacc;
+  int* dm;
+  RS_TRY(upload(h, &dm, mrows, st));
+  RS_TRY(upload(h, &lv.toff, toff, st));
+  size_t sb = scal_bytes(h);
+  RS_TRY(dalloc(h, &lv.T, sb * std::max<int64_t>(1, tacc)));
+  RS_TRY(dalloc_t(h, &lv.k, nbox));
+  RS_TRY(dalloc_t(h, &lv.lperm, std::max<int64_t>(1, lv.ntot)));
+
+  IdArgs a{};
+  a.kp = h->kp;
+  a.pts = make_pts(h);
+  a.geo = geo;
+  a.eps = h->eps;
+  a.n = lv.n;
+  a.off = lv.off;
+  a.act = lv.act;
+  a.ncoll = lv.ncoll;
+  a.coll = lv.coll;
+  a.coords = lv.coords;
+  a.mrows = dm;
+  a.toff = lv.toff;
+  a.kout = lv.k;
+  a.lperm = lv.lperm;
+  a.mmax = lv.maxm;
+  a.nmax = lv.maxn;
+  if (h->cplx) RS_TRY(run_id<c128>(h, lv, a, mrows, msum, st));
+  else RS_TRY(run_id<double>(h, lv, a, mrows, msum, st));
+
+  // ranks -> skeleton offsets in the parent depth
+  lv.h_k.resize(nbox);
+  RS_CUDA(cudaMemcpyAsync(lv.h_k.data(), lv.k, sizeof(int) * nbox, cudaMemcpyDeviceToHost, st));
+  RS_CUDA(cudaStreamSynchronize(st));
+  std::vector<int64_t> skoff(nbox);
+  int64_t kacc = 0;
+  lv.maxk = 0;
+  for (int b = 0; b < nbox; ++b) {
+    skoff[b] = kacc;
+    kacc += lv.h_k[b];
+    lv.maxk = std::max(lv.maxk, lv.h_k[b]);
+  }
+  lv.ksum = kacc;
+  RS_TRY(upload(h, &lv.skoff, skoff, st));
+
+  // factor
+  RS_TRY(alloc_factors(h, lv, st));
+  FaArgs f{};
+  f.kp = h->kp;
+  f.pts = make_pts(h);
+  f.leaf_level = depth == h->L;
+  f.n = lv.n;
+  f.k = lv.k;
+  f.off = lv.off;
+  f.act = lv.act;
+  f.owner = lv.owner;
+  const Level* child = depth < h->L ? &h->lv[depth + 1] : nullptr;
+  if (child) {
+    f.cskoff = child->skoff;
+    f.ck = child->k;
+    f.clamoff = child->lamoff;
+  }
+  f.lperm = lv.lperm;
+  f.toff = lv.toff;
+  f.uoff = lv.uoff;
+  f.loff = lv.loff;
+  f.lamoff = lv.lamoff;
+  f.bad = h->status;
+  if (h->cplx) RS_TRY(run_factor<c128>(h, lv, f, child, st));
+  else RS_TRY(run_factor<double>(h, lv, f, child, st));
+  RS_TRY(check_bad(h, st, "factorization"));
+
+  // active sets of depth-1: skeletons of the children, in child order
+  Level& up = h->lv[depth - 1];
+  up.ntot = kacc;
+  RS_TRY(dalloc_t(h, &up.act, std::max<int64_t>(1, kacc)));
+  RS_TRY(dalloc_t(h, &up.owner, std::max<int64_t>(1, kacc)));
+  k_emit<<<nbox, 64, 0, st>>>(lv.n, lv.k, lv.off, lv.skoff, lv.act, lv.lperm, nbox, up.act, up.owner);
+  RS_CHECK_LAUNCH();
+  up.h_n.assign(up.nbox, 0);
+  std::vector<int64_t> upoff(up.nbox, -1);
+  for (int b = 0; b < nbox; ++b) {
+    int p = lv.h_parent[b];
+    if (upoff[p] < 0) upoff[p] = skoff[b];
+    up.h_n[p] += lv.h_k[b];
+  }
+  RS_TRY(upload(h, &up.n, up.h_n, st));
+  RS_TRY(upload(h, &up.off, upoff, st));
+  return RS_OK;
+}
+
+// Root: calS assembled like any upper-level block (or A itself when the tree
+// has a single box), inverted densely.
+int factor_root(Handle* h, cudaStream_t st) {
+  Level& lv = h->lv[0];
+  if (h->L == 0) {
+    lv.h_n.assign(1, (int)h->N);
+    lv.ntot = h->N;
+    std::vector<int64_t> off(1, 0);
+    RS_TRY(upload(h, &lv.n, lv.h_n, st));
+    RS_TRY(upload(h, &lv.off, off, st));
+  }
+  lv.maxn = lv.h_n[0];
+  lv.h_k.assign(1, 0);
+  std::vector<int> k0(1, 0);
+  RS_TRY(upload(h, &lv.k, k0, st));
+  RS_TRY(alloc_factors(h, lv, st));
+  FaArgs f{};
+  f.kp = h->kp;
+  f.pts = make_pts(h);
+  f.leaf_level = h->L == 0;
+  f.n = lv.n;
+  f.k = lv.k;
+  f.off = lv.off;
+  f.act = lv.act;
+  f.owner = lv.owner;
+  const Level* child = h->L > 0 ? &h->lv[1] : nullptr;
+  if (child) {
+    f.cskoff = child->skoff;
+    f.ck = child->k;
+    f.clamoff = child->lamoff;
+  }
+  int* dummy_perm;
+  RS_TRY(dalloc_t(h, &dummy_perm, std::max<int64_t>(1, lv.ntot)));
+  f.lperm = dummy_perm;
+  f.toff = nullptr;
+  f.uoff = lv.uoff;
+  f.loff = lv.loff;
+  f.lamoff = lv.lamoff;
+  f.bad = h->status;
+  if (h->cplx) RS_TRY(run_factor<c128>(h, lv, f, child, st));
+  else RS_TRY(run_factor<double>(h, lv, f, child, st));
+  RS_TRY(check_bad(h, st, "root factorization"));
+  return RS_OK;
+}
+
+int make_fp32_copies(Handle* h, cudaStream_t st) {
+  for (int d = 0; d <= h->L; ++d) {
+    Level& lv = h->lv[d];
+    size_t lb = h->cplx ? sizeof(c64) : sizeof(float);
+    RS_TRY(dalloc(h, &lv.U32, lb * std::max<int64_t>(1, lv.usz)));
+    RS_TRY(dalloc(h, &lv.Lf32, lb * std::max<int64_t>(1, lv.lsz)));
+    if (h->cplx) {
+      if (lv.usz) k_to_float<c128><<<div_up(lv.usz, 256), 256, 0, st>>>((c128*)lv.U, (c64*)lv.U32, lv.usz);
+      if (lv.lsz) k_to_float<c128><<<div_up(lv.lsz, 256), 256, 0, st>>>((c128*)lv.Lf, (c64*)lv.Lf32, lv.lsz);
+    } else {
+      if (lv.usz) k_to_float<double><<<div_up(lv.usz, 256), 256, 0, st>>>((double*)lv.U, (float*)lv.U32, lv.usz);
+      if (lv.lsz) k_to_float<double><<<div_up(lv.lsz, 256), 256, 0, st>>>((double*)lv.Lf, (float*)lv.Lf32, lv.lsz);
+    }
+    RS_CHECK_LAUNCH();
+  }
+  return RS_OK;
+}
+
+}  // namespace rs
