@@ -142,6 +142,22 @@ int rs_tree_level(rs_handle h, int level, int* nbox_out, int64_t* begin,
  * host arrays of nbox entries, either may be NULL. */
 int rs_box_ranks(rs_handle h, int level, int* n, int* k);
 
+/* Launch profiler (off by default).  rs_profile_enable(1) clears the record
+ * and times every following kernel launch of the library with CUDA events
+ * on the stream it runs on, grouped into rs_profile_ncat() categories
+ * ("tree", "id", "factor", "solve_up", "solve_down", "fwd_dblock", ...);
+ * rs_profile_enable(0) stops recording.  rs_profile_read waits for the
+ * recorded events and returns, for one category, the summed device time
+ * (ms), the launch count and the algorithmic bytes and flops of those
+ * launches (counted from the block sizes).  *name is a static string. */
+int rs_profile_enable(int on);
+int rs_profile_ncat(void);
+int rs_profile_read(int cat, double* ms, int64_t* launches, double* bytes, double* flops,
+                    const char** name);
+
+/* Number of kernels the library has launched in this process so far. */
+int64_t rs_launch_count(void);
+
 /* Release every resource of the handle.  NULL is accepted. */
 int rs_free(rs_handle h);
 

@@ -54,6 +54,10 @@ _PROTOS = {
     "rs_tree_level": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P, _P, _P, _P]),
     "rs_box_ranks": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "rs_free": (ctypes.c_int, [_P]),
+    "rs_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "rs_profile_ncat": (ctypes.c_int, []),
+    "rs_launch_count": (ctypes.c_int64, []),
+    "rs_profile_read": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_char_p)]),
     "rs_last_error": (ctypes.c_char_p, []),
     "rs_version": (ctypes.c_char_p, []),
 }
@@ -205,6 +209,31 @@ def rs_box_ranks(h: Handle, level: int, nbox: int):
     k = np.zeros(nbox, dtype=np.int32)
     _check(_lib.rs_box_ranks(h.ptr, level, n.ctypes.data, k.ctypes.data))
     return n, k
+
+
+def rs_profile_enable(on: bool = True):
+    _check(load().rs_profile_enable(1 if on else 0))
+
+
+def rs_profile_read() -> dict:
+    """{category: dict(ms, launches, bytes, flops)} of the recorded launches."""
+    lib = load()
+    out = {}
+    for c in range(lib.rs_profile_ncat()):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        by = ctypes.c_double()
+        fl = ctypes.c_double()
+        name = ctypes.c_char_p()
+        _check(lib.rs_profile_read(c, ctypes.addressof(ms), ctypes.addressof(n), ctypes.addressof(by),
+                                   ctypes.addressof(fl), ctypes.byref(name)))
+        if n.value:
+            out[name.value.decode()] = dict(ms=ms.value, launches=n.value, bytes=by.value, flops=fl.value)
+    return out
+
+
+def rs_launch_count() -> int:
+    return int(load().rs_launch_count())
 
 
 def rs_free(h: Handle):

@@ -1,0 +1,121 @@
+// Launch profiler: CUDA events around each kernel launch, grouped by
+// category, with the launch's algorithmic bytes and flops counted on the
+// host from the known block sizes.  Off unless rs_profile_enable(1).
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "rs_internal.h"
+
+namespace rs {
+
+namespace {
+
+struct Rec {
+  int cat;
+  cudaEvent_t e0, e1;
+  double bytes, flops;
+};
+
+const char* kNames[P_NCAT] = {"tree", "id", "factor", "fp32_copy", "solve_up", "solve_down", "permute",
+                              "fwd_proj", "fwd_dblock", "fwd_down", "residual", "misc"};
+
+std::mutex g_mu;
+bool g_on = false;
+std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_pool;
+size_t g_next = 0;
+std::vector<Rec> g_stack;
+
+cudaEvent_t get_event() {
+  if (g_next < g_pool.size()) return g_pool[g_next++];
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  g_pool.push_back(e);
+  ++g_next;
+  return e;
+}
+
+}  // namespace
+
+bool prof_on() { return g_on; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void prof_begin(int cat, cudaStream_t st) {
+  if (!g_on) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  Rec r{cat, get_event(), nullptr, 0.0, 0.0};
+  cudaEventRecord(r.e0, st);
+  g_stack.push_back(r);
+}
+
+void prof_end(int cat, cudaStream_t st, double bytes, double flops) {
+  if (!g_on) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_stack.empty()) return;
+  Rec r = g_stack.back();
+  g_stack.pop_back();
+  r.cat = cat;
+  r.e1 = get_event();
+  r.bytes = bytes;
+  r.flops = flops;
+  cudaEventRecord(r.e1, st);
+  g_recs.push_back(r);
+}
+
+void prof_amend(int cat, double bytes, double flops) {
+  if (!g_on) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto it = g_recs.rbegin(); it != g_recs.rend(); ++it)
+    if (it->cat == cat) {
+      it->bytes = bytes;
+      it->flops = flops;
+      return;
+    }
+}
+
+}  // namespace rs
+
+extern "C" {
+
+int rs_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(rs::g_mu);
+  rs::g_recs.clear();
+  rs::g_stack.clear();
+  rs::g_next = 0;
+  rs::g_on = on != 0;
+  return RS_OK;
+}
+
+int rs_profile_ncat(void) { return rs::P_NCAT; }
+
+int64_t rs_launch_count(void) { return rs::g_launches.load(); }
+
+int rs_profile_read(int cat, double* ms, int64_t* launches, double* bytes, double* flops, const char** name) {
+  if (cat < 0 || cat >= rs::P_NCAT) return rs::fail(RS_ERR_ARG, "rs_profile_read: bad category");
+  std::lock_guard<std::mutex> lk(rs::g_mu);
+  double t = 0, by = 0, fl = 0;
+  int64_t n = 0;
+  for (auto& r : rs::g_recs) {
+    if (r.cat != cat) continue;
+    float m = 0;
+    if (cudaEventSynchronize(r.e1) != cudaSuccess || cudaEventElapsedTime(&m, r.e0, r.e1) != cudaSuccess) {
+      cudaGetLastError();
+      return rs::fail(RS_ERR_CUDA, "rs_profile_read: event timing failed");
+    }
+    t += m;
+    by += r.bytes;
+    fl += r.flops;
+    ++n;
+  }
+  if (ms) *ms = t;
+  if (launches) *launches = n;
+  if (bytes) *bytes = by;
+  if (flops) *flops = fl;
+  if (name) *name = rs::kNames[cat];
+  return RS_OK;
+}
+
+}  // extern "C"

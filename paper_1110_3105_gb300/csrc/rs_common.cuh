@@ -23,12 +23,21 @@ int fail(int code, const char* fmt, ...);
 #define RS_CUDA(call)                                                          \
   do {                                                                         \
     cudaError_t e_ = (call);                                                   \
-    if (e_ != cudaSuccess)                                                     \
+    if (e_ != cudaSuccess) {                                                   \
+      cudaGetLastError(); /* do not leak a non-sticky error into later calls */ \
       return ::rs::fail(RS_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call, \
                         cudaGetErrorString(e_));                               \
+    }                                                                          \
   } while (0)
 
-#define RS_CHECK_LAUNCH() RS_CUDA(cudaGetLastError())
+// Every kernel launch of the library is followed by RS_CHECK_LAUNCH(), which
+// also counts it (rs_launch_count()).
+void count_launch();
+#define RS_CHECK_LAUNCH()  \
+  do {                     \
+    ::rs::count_launch();  \
+    RS_CUDA(cudaGetLastError()); \
+  } while (0)
 
 #define RS_TRY(expr)            \
   do {                          \

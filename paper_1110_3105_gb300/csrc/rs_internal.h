@@ -30,6 +30,14 @@
 
 namespace rs {
 
+// ------------------------------------------------------------- profiler
+enum ProfCat { P_TREE, P_ID, P_FACTOR, P_COPY32, P_UP, P_DOWN, P_PERM, P_FWD_PROJ, P_FWD_DBLOCK, P_FWD_DOWN,
+               P_RESID, P_MISC, P_NCAT };
+bool prof_on();
+void prof_begin(int cat, cudaStream_t st);
+void prof_end(int cat, cudaStream_t st, double bytes, double flops);
+void prof_amend(int cat, double bytes, double flops);  // fix up the last record of cat
+
 // ------------------------------------------------------------ primitives
 // Exclusive scan of n int64 values; *total (host) receives the sum.
 int scan_i64(const int64_t* d_in, int64_t* d_out, int64_t n, int64_t* total, cudaStream_t st);

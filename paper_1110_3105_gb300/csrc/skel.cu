@@ -466,6 +466,23 @@ __global__ void k_to_float(const S* in, typename lowp<S>::type* out, int64_t cnt
 }
 
 // ------------------------------------------------------------- host helpers
+// Flops of k_factor for one box: Gauss-Jordan on [D | I] (3 n^3), X = D^-1 P^T,
+// P X, Gauss-Jordan on [P X | I] (3 k^3), calL, calR, calD.
+double factor_flops(double n, double k) {
+  double nr = n - k;
+  return 3.0 * n * n * n + 2.0 * n * k * nr + 2.0 * k * k * nr + 3.0 * k * k * k + 4.0 * n * k * k +
+         2.0 * n * n * k;
+}
+// Flops of the column-pivoted QR of an m x n block stopped at rank k:
+// norms (2 per entry) and the reflector update (4 per entry) of every step,
+// the final norm pass, and T = R11^-1 R12 by back substitution.
+double id_flops(double m, double n, double k) {
+  double f = 0.0;
+  for (int j = 0; j < (int)k; ++j) f += 2.0 * (m - j) * (n - j) + 4.0 * (m - j) * (n - j - 1);
+  if (k < std::min(m, n)) f += 2.0 * (m - k) * (n - k);
+  return f + k * k * (n - k);
+}
+
 template <class T>
 int upload(Handle* h, T** d, const std::vector<T>& v, cudaStream_t st) {
   RS_TRY(dalloc_t(h, d, std::max<size_t>(1, v.size())));
@@ -521,8 +538,10 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
     RS_CUDA(cudaMallocAsync((void**)&Mws, sb * std::max<int64_t>(1, acc), st));
   }
   RS_CUDA(cudaFuncSetAttribute(k_id<S, ID_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  prof_begin(P_ID, st);
   k_id<S, ID_NT><<<lv.nbox, ID_NT, smem, st>>>(a, Mws, (S*)lv.T);
   RS_CHECK_LAUNCH();
+  prof_end(P_ID, st, 0.0, 0.0);
   if (Mws) RS_CUDA(cudaFreeAsync(Mws, st));
   (void)msum;
   return RS_OK;
@@ -545,9 +564,18 @@ int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t 
   RS_CUDA(cudaMallocAsync((void**)&ws, sizeof(S) * std::max<int64_t>(1, acc), st));
   size_t smem = sizeof(S) * std::max(1, lv.maxn);
   RS_CUDA(cudaFuncSetAttribute(k_factor<S, FA_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  double fl = 0.0, by = 0.0;
+  for (int b = 0; b < lv.nbox; ++b) {
+    double n = lv.h_n[b], k = lv.h_k[b];
+    fl += factor_flops(n, k);
+    by += (double)sizeof(S) * ((n + k) * n + n * k + k * k);   // factors written
+  }
+  if (is_cplx<S>::value) fl *= 4.0;
+  prof_begin(P_FACTOR, st);
   k_factor<S, FA_NT><<<lv.nbox, FA_NT, smem, st>>>(a, (const S*)lv.T, child ? (const S*)child->Lam : nullptr, ws,
                                                    (S*)lv.U, (S*)lv.Lf, (S*)lv.Lam);
   RS_CHECK_LAUNCH();
+  prof_end(P_FACTOR, st, by, fl);
   RS_CUDA(cudaFreeAsync(ws, st));
   return RS_OK;
 }
@@ -653,6 +681,14 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st) {
   lv.h_k.resize(nbox);
   RS_CUDA(cudaMemcpyAsync(lv.h_k.data(), lv.k, sizeof(int) * nbox, cudaMemcpyDeviceToHost, st));
   RS_CUDA(cudaStreamSynchronize(st));
+  if (prof_on()) {
+    double fl = 0.0, by = 0.0;
+    for (int b = 0; b < nbox; ++b) {
+      fl += id_flops(mrows[b], lv.h_n[b], lv.h_k[b]);
+      by += (double)sb * (double)lv.h_k[b] * (lv.h_n[b] - lv.h_k[b]);   // T written
+    }
+    prof_amend(P_ID, by, h->cplx ? 4.0 * fl : fl);
+  }
   std::vector<int64_t> skoff(nbox);
   int64_t kacc = 0;
   lv.maxk = 0;
@@ -756,6 +792,8 @@ int factor_root(Handle* h, cudaStream_t st) {
 }
 
 int make_fp32_copies(Handle* h, cudaStream_t st) {
+  prof_begin(P_COPY32, st);
+  double by = 0.0;
   for (int d = 0; d <= h->L; ++d) {
     Level& lv = h->lv[d];
     size_t lb = h->cplx ? sizeof(c64) : sizeof(float);
@@ -769,7 +807,9 @@ int make_fp32_copies(Handle* h, cudaStream_t st) {
       if (lv.lsz) k_to_float<double><<<div_up(lv.lsz, 256), 256, 0, st>>>((double*)lv.Lf, (float*)lv.Lf32, lv.lsz);
     }
     RS_CHECK_LAUNCH();
+    by += (double)(lv.usz + lv.lsz) * (scal_bytes(h) + lb);
   }
+  prof_end(P_COPY32, st, by, 0.0);
   return RS_OK;
 }
 

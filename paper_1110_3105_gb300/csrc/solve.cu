@@ -62,8 +62,9 @@ struct BoxView {
 };
 
 // Upward step of one depth: [u ; c] = U b per box.  One CTA per
-// (box, column tile of CT columns).  b is staged in shared memory.
-template <class S, int CT>
+// (box, column tile of CT columns).  b is staged in shared memory when it
+// fits (STAGE), otherwise read through L1.
+template <class S, int CT, bool STAGE>
 __global__ void __launch_bounds__(SV_NT) k_up(BoxView bv, const int64_t* uoff, const S* U, const S* vin, S* uout,
                                              S* cout, int R, int ntile) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -73,23 +74,26 @@ __global__ void __launch_bounds__(SV_NT) k_up(BoxView bv, const int64_t* uoff, c
   const int n = bv.n[b], k = bv.k[b], rows = n + k;
   const int64_t off = bv.off[b];
   const int64_t sk = bv.skoff ? bv.skoff[b] : 0;
-  for (int e = threadIdx.x; e < n * cw; e += SV_NT) {
-    int q = e / cw, c = e % cw;
-    vs[q * CT + c] = vin[(off + q) * R + c0 + c];
+  if (STAGE) {
+    for (int e = threadIdx.x; e < n * cw; e += SV_NT) {
+      int q = e / cw, c = e % cw;
+      vs[q * CT + c] = vin[(off + q) * R + c0 + c];
+    }
+    __syncthreads();
   }
-  __syncthreads();
+  auto V = [&](int q, int c) -> S { return STAGE ? vs[q * CT + c] : vin[(off + q) * R + c0 + c]; };
   const S* Ub = U + uoff[b];
   if (CT == 1) {
     for (int r = threadIdx.x; r < rows; r += SV_NT) {
       S s0 = S(0.0), s1 = S(0.0), s2 = S(0.0), s3 = S(0.0);
       int q = 0;
       for (; q + 4 <= n; q += 4) {
-        s0 += Ub[r + (size_t)q * rows] * vs[q];
-        s1 += Ub[r + (size_t)(q + 1) * rows] * vs[q + 1];
-        s2 += Ub[r + (size_t)(q + 2) * rows] * vs[q + 2];
-        s3 += Ub[r + (size_t)(q + 3) * rows] * vs[q + 3];
+        s0 += Ub[r + (size_t)q * rows] * V(q, 0);
+        s1 += Ub[r + (size_t)(q + 1) * rows] * V(q + 1, 0);
+        s2 += Ub[r + (size_t)(q + 2) * rows] * V(q + 2, 0);
+        s3 += Ub[r + (size_t)(q + 3) * rows] * V(q + 3, 0);
       }
-      for (; q < n; ++q) s0 += Ub[r + (size_t)q * rows] * vs[q];
+      for (; q < n; ++q) s0 += Ub[r + (size_t)q * rows] * V(q, 0);
       S s = (s0 + s1) + (s2 + s3);
       if (r < n) uout[off + r] = s;
       else cout[sk + (r - n)] = s;
@@ -99,7 +103,7 @@ __global__ void __launch_bounds__(SV_NT) k_up(BoxView bv, const int64_t* uoff, c
       int r = e / cw, c = e % cw;
       S s = S(0.0);
 #pragma unroll 4
-      for (int q = 0; q < n; ++q) s += Ub[r + (size_t)q * rows] * vs[q * CT + c];
+      for (int q = 0; q < n; ++q) s += Ub[r + (size_t)q * rows] * V(q, c);
       if (r < n) uout[(off + r) * R + c0 + c] = s;
       else cout[(sk + (r - n)) * R + c0 + c] = s;
     }
@@ -107,7 +111,7 @@ __global__ void __launch_bounds__(SV_NT) k_up(BoxView bv, const int64_t* uoff, c
 }
 
 // Downward step: x = u + calL x_parent, in place on u.
-template <class S, int CT>
+template <class S, int CT, bool STAGE>
 __global__ void __launch_bounds__(SV_NT) k_down(BoxView bv, const int64_t* loff, const S* Lf, const S* xpar, S* u,
                                                int R, int ntile) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -116,22 +120,25 @@ __global__ void __launch_bounds__(SV_NT) k_down(BoxView bv, const int64_t* loff,
   const int c0 = tile * CT, cw = min(CT, R - c0);
   const int n = bv.n[b], k = bv.k[b];
   const int64_t off = bv.off[b], sk = bv.skoff[b];
-  for (int e = threadIdx.x; e < k * cw; e += SV_NT) {
-    int q = e / cw, c = e % cw;
-    xs[q * CT + c] = xpar[(sk + q) * R + c0 + c];
+  if (STAGE) {
+    for (int e = threadIdx.x; e < k * cw; e += SV_NT) {
+      int q = e / cw, c = e % cw;
+      xs[q * CT + c] = xpar[(sk + q) * R + c0 + c];
+    }
+    __syncthreads();
   }
-  __syncthreads();
+  auto XP = [&](int q, int c) -> S { return STAGE ? xs[q * CT + c] : xpar[(sk + q) * R + c0 + c]; };
   const S* Lb = Lf + loff[b];
   if (CT == 1) {
     for (int r = threadIdx.x; r < n; r += SV_NT) {
       S s0 = u[off + r], s1 = S(0.0), s2 = S(0.0), s3 = S(0.0);
       int q = 0;
       for (; q + 3 <= k; q += 3) {
-        s1 += Lb[r + (size_t)q * n] * xs[q];
-        s2 += Lb[r + (size_t)(q + 1) * n] * xs[q + 1];
-        s3 += Lb[r + (size_t)(q + 2) * n] * xs[q + 2];
+        s1 += Lb[r + (size_t)q * n] * XP(q, 0);
+        s2 += Lb[r + (size_t)(q + 1) * n] * XP(q + 1, 0);
+        s3 += Lb[r + (size_t)(q + 2) * n] * XP(q + 2, 0);
       }
-      for (; q < k; ++q) s1 += Lb[r + (size_t)q * n] * xs[q];
+      for (; q < k; ++q) s1 += Lb[r + (size_t)q * n] * XP(q, 0);
       u[off + r] = s0 + (s1 + (s2 + s3));
     }
   } else {
@@ -139,7 +146,7 @@ __global__ void __launch_bounds__(SV_NT) k_down(BoxView bv, const int64_t* loff,
       int r = e / cw, c = e % cw;
       S s = S(0.0);
 #pragma unroll 4
-      for (int q = 0; q < k; ++q) s += Lb[r + (size_t)q * n] * xs[q * CT + c];
+      for (int q = 0; q < k; ++q) s += Lb[r + (size_t)q * n] * XP(q, c);
       int64_t idx = (off + r) * R + c0 + c;
       u[idx] = u[idx] + s;
     }
@@ -324,10 +331,14 @@ int solve_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO* X, in
   const int64_t N = h->N;
   const int L = h->L;
   int nb = div_up(N * R, 256);
+  const double sS = sizeof(S), sIO = sizeof(SIO), cf = is_cplx<S>::value ? 4.0 : 1.0;
+  prof_begin(P_PERM, st);
   k_perm_in<SIO, S><<<nb, 256, 0, st>>>(B, ldb, h->perm, N, R, (S*)w.v[L]);
   RS_CHECK_LAUNCH();
+  prof_end(P_PERM, st, (double)N * R * (sS + sIO) + 4.0 * N, 0.0);
   const int CT = R == 1 ? 1 : 32;
   const int ntile = div_up(R, CT);
+  const size_t stage_limit = 96 * 1024;
   for (int d = L; d >= 0; --d) {
     const Level& lv = h->lv[d];
     const S* U = (const S*)(prec == RS_PREC_FP64 ? lv.U : lv.U32);
@@ -335,32 +346,48 @@ int solve_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO* X, in
     size_t smem = sizeof(S) * (size_t)std::max(1, lv.maxn) * CT;
     BoxView bv = box_view(lv);
     if (d == 0) bv.skoff = nullptr;
-    if (CT == 1) {
-      RS_CUDA(cudaFuncSetAttribute(k_up<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_up<S, 1><<<lv.nbox * ntile, SV_NT, smem, st>>>(bv, lv.uoff, U, (const S*)w.v[d], (S*)w.u[d], cout, R, ntile);
+    const S* vin = (const S*)w.v[d];
+    S* uo = (S*)w.u[d];
+    const int grid = lv.nbox * ntile;
+    const double kup = d > 0 ? (double)lv.ksum : 0.0;
+    prof_begin(P_UP, st);
+    if (smem <= stage_limit) {
+      RS_CUDA(cudaFuncSetAttribute(k_up<S, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_limit));
+      RS_CUDA(cudaFuncSetAttribute(k_up<S, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_limit));
+      if (CT == 1) k_up<S, 1, true><<<grid, SV_NT, smem, st>>>(bv, lv.uoff, U, vin, uo, cout, R, ntile);
+      else k_up<S, 32, true><<<grid, SV_NT, smem, st>>>(bv, lv.uoff, U, vin, uo, cout, R, ntile);
     } else {
-      RS_CUDA(cudaFuncSetAttribute(k_up<S, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_up<S, 32><<<lv.nbox * ntile, SV_NT, smem, st>>>(bv, lv.uoff, U, (const S*)w.v[d], (S*)w.u[d], cout, R, ntile);
+      if (CT == 1) k_up<S, 1, false><<<grid, SV_NT, 0, st>>>(bv, lv.uoff, U, vin, uo, cout, R, ntile);
+      else k_up<S, 32, false><<<grid, SV_NT, 0, st>>>(bv, lv.uoff, U, vin, uo, cout, R, ntile);
     }
     RS_CHECK_LAUNCH();
+    prof_end(P_UP, st, sS * ((double)lv.usz + (double)R * (2.0 * lv.ntot + kup)), 2.0 * cf * lv.usz * R);
   }
   for (int d = 1; d <= L; ++d) {
     const Level& lv = h->lv[d];
     const S* Lf = (const S*)(prec == RS_PREC_FP64 ? lv.Lf : lv.Lf32);
     size_t smem = sizeof(S) * (size_t)std::max(1, lv.maxk) * CT;
-    if (CT == 1) {
-      RS_CUDA(cudaFuncSetAttribute(k_down<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_down<S, 1><<<lv.nbox * ntile, SV_NT, smem, st>>>(box_view(lv), lv.loff, Lf, (const S*)w.u[d - 1],
-                                                         (S*)w.u[d], R, ntile);
+    const S* xp = (const S*)w.u[d - 1];
+    S* uo = (S*)w.u[d];
+    const int grid = lv.nbox * ntile;
+    BoxView bv = box_view(lv);
+    prof_begin(P_DOWN, st);
+    if (smem <= stage_limit) {
+      RS_CUDA(cudaFuncSetAttribute(k_down<S, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_limit));
+      RS_CUDA(cudaFuncSetAttribute(k_down<S, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_limit));
+      if (CT == 1) k_down<S, 1, true><<<grid, SV_NT, smem, st>>>(bv, lv.loff, Lf, xp, uo, R, ntile);
+      else k_down<S, 32, true><<<grid, SV_NT, smem, st>>>(bv, lv.loff, Lf, xp, uo, R, ntile);
     } else {
-      RS_CUDA(cudaFuncSetAttribute(k_down<S, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      k_down<S, 32><<<lv.nbox * ntile, SV_NT, smem, st>>>(box_view(lv), lv.loff, Lf, (const S*)w.u[d - 1],
-                                                          (S*)w.u[d], R, ntile);
+      if (CT == 1) k_down<S, 1, false><<<grid, SV_NT, 0, st>>>(bv, lv.loff, Lf, xp, uo, R, ntile);
+      else k_down<S, 32, false><<<grid, SV_NT, 0, st>>>(bv, lv.loff, Lf, xp, uo, R, ntile);
     }
     RS_CHECK_LAUNCH();
+    prof_end(P_DOWN, st, sS * ((double)lv.lsz + (double)R * (2.0 * lv.ntot + lv.ksum)), 2.0 * cf * lv.lsz * R);
   }
+  prof_begin(P_PERM, st);
   k_perm_out<S, SIO><<<nb, 256, 0, st>>>((const S*)w.u[L], h->perm, N, R, X, ldx);
   RS_CHECK_LAUNCH();
+  prof_end(P_PERM, st, (double)N * R * (sS + sIO) + 4.0 * N, 0.0);
   return RS_OK;
 }
 
@@ -397,20 +424,31 @@ int forward_tree(Handle* h, int R, cudaStream_t st) {
   for (int d = L; d >= 0; --d) {
     const Level& lv = h->lv[d];
     FwdView fv = fwd_view(h, d);
+    const double sS = sizeof(S), cf = is_cplx<S>::value ? 4.0 : 1.0;
     if (d > 0) {
+      prof_begin(P_FWD_PROJ, st);
       k_fwd_proj<S><<<lv.nbox, 128, 0, st>>>(fv, (const S*)lv.T, (const S*)h->fz[d], (S*)h->fz[d - 1], R);
       RS_CHECK_LAUNCH();
+      double tk = 0.0;
+      for (int b = 0; b < lv.nbox; ++b) tk += (double)lv.h_k[b] * (lv.h_n[b] - lv.h_k[b]);
+      prof_end(P_FWD_PROJ, st, sS * (tk + (double)R * (lv.ntot + lv.ksum)), 2.0 * cf * tk * R);
     }
     const int nrt = div_up(std::max(1, lv.maxn), FD_RT);
+    double n2 = 0.0;
+    for (int b = 0; b < lv.nbox; ++b) n2 += (double)lv.h_n[b] * lv.h_n[b];
+    prof_begin(P_FWD_DBLOCK, st);
     k_fwd_dblock<S><<<lv.nbox * nrt * nct, SV_NT, 0, st>>>(fv, h->kp, pts, (const S*)h->fz[d], (S*)h->fy[d], R,
                                                            nrt, nct);
     RS_CHECK_LAUNCH();
+    prof_end(P_FWD_DBLOCK, st, sS * 2.0 * R * lv.ntot, 2.0 * cf * n2 * R);
   }
   for (int d = 1; d <= L; ++d) {
     const Level& lv = h->lv[d];
+    prof_begin(P_FWD_DOWN, st);
     k_fwd_down<S><<<lv.nbox, 128, 0, st>>>(fwd_view(h, d), (const S*)lv.T, (const S*)h->fy[d - 1],
                                            (S*)h->fy[d], R);
     RS_CHECK_LAUNCH();
+    prof_end(P_FWD_DOWN, st, 0.0, 0.0);
   }
   return RS_OK;
 }

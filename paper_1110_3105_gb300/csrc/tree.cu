@@ -265,6 +265,7 @@ int build_tree(Handle* h, const double* d_pts_in, cudaStream_t st) {
   const int NT = 256;
   const int nb = div_up(n, NT);
 
+  prof_begin(P_TREE, st);
   // root box
   int nblk = std::min(nb, 1024);
   double* part = nullptr;
@@ -378,6 +379,7 @@ int build_tree(Handle* h, const double* d_pts_in, cudaStream_t st) {
   RS_TRY(dalloc_t(h, &leaf.act, n));
   k_iota<<<nb, NT, 0, st>>>(leaf.act, n);
   RS_CHECK_LAUNCH();
+  prof_end(P_TREE, st, (double)n * dim * 8.0, 0.0);
   return RS_OK;
 }
 
