@@ -105,6 +105,29 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params,
 int rs_solve(rs_handle h, int precision, const void* B, int64_t ldb, int nrhs,
              void* X, int64_t ldx, void* stream);
 
+/* Allocation-free variant of rs_solve (the paper has no counterpart: it is a
+ * deployment form).  For callers that cannot allocate device memory during a
+ * solve: a latency-critical serving loop (cudaMalloc/cudaFree may synchronize
+ * the device and stall other streams' work) or a process whose device-memory
+ * budget is fixed at start-up.  Same arguments and result as rs_solve, except:
+ *   - B and X must be device memory (RS_ERR_ARG otherwise: host buffers would
+ *     need a staging allocation);
+ *   - the per-level solve vectors live in one static device array of
+ *     RS_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds
+ *     until the process exits; a solve needing more (about 2 * nrhs * scalar
+ *     size * (N + sum of skeleton counts)) is rejected with RS_ERR_ARG and a
+ *     message giving the need and the limit;
+ *   - the call allocates nothing (no cudaMalloc/cudaFree, no allocating
+ *     library routine).  Its first call on a device looks up the array's
+ *     device address (cudaGetSymbolAddress) with that device current; make
+ *     that first call before any stream capture;
+ *   - every call, on every handle, shares the one array and leaves its last
+ *     contents there (nothing in it needs to start at zero): calls whose
+ *     work overlaps on the GPU race -- serialise them on one stream. */
+#define RS_NOALLOC_SCRATCH_BYTES (16u << 20)
+int rs_solve_noalloc(rs_handle h, int precision, const void* B, int64_t ldb, int nrhs,
+                     void* X, int64_t ldx, void* stream);
+
 /* Mixed-precision solve with iterative refinement: x0 = FP32 solve of b;
  * repeat r = b - A_RS x in FP64 (forward operator of eq.
  * multilevel-compression with its kernel blocks evaluated on the fly from the

@@ -46,6 +46,7 @@ _PROTOS = {
     "rs_build": (ctypes.c_int, [_P, _I64, ctypes.c_int, ctypes.POINTER(rs_params), ctypes.c_double,
                                 ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "rs_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, ctypes.c_int, _P, _I64, _P]),
+    "rs_solve_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, ctypes.c_int, _P, _I64, _P]),
     "rs_solve_refined": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, ctypes.c_double, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int), _P, _P]),
     "rs_matvec": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, _P, _I64, _P]),
@@ -164,6 +165,14 @@ def rs_solve(h: Handle, B, X, precision: int = RS_PREC_FP64, stream=None):
     pb, nb, rb, ldb, _ = _ptr(B)
     px, nx, rx, ldx, _ = _ptr(X)
     _check(_lib.rs_solve(h.ptr, precision, pb, ldb, rb, px, ldx, _stream(stream)))
+    return X
+
+
+def rs_solve_noalloc(h: Handle, B, X, precision: int = RS_PREC_FP64, stream=None):
+    """rs_solve without any device allocation (B and X must be device tensors)."""
+    pb, nb, rb, ldb, _ = _ptr(B)
+    px, nx, rx, ldx, _ = _ptr(X)
+    _check(_lib.rs_solve_noalloc(h.ptr, precision, pb, ldb, rb, px, ldx, _stream(stream)))
     return X
 
 

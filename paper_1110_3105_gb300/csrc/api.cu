@@ -232,6 +232,23 @@ int rs_solve(rs_handle h, int precision, const void* B, int64_t ldb, int nrhs, v
   return rc;
 }
 
+int rs_solve_noalloc(rs_handle h, int precision, const void* B, int64_t ldb, int nrhs, void* X, int64_t ldx,
+                     void* stream) {
+  rs::g_err.clear();
+  RS_TRY(check_handle(h));
+  if (!B || !X) return fail(RS_ERR_ARG, "rs_solve_noalloc: null buffer");
+  if (nrhs < 1 || ldb < h->N || ldx < h->N) return fail(RS_ERR_ARG, "rs_solve_noalloc: bad nrhs or leading dimension");
+  if (precision != RS_PREC_FP64 && precision != RS_PREC_FP32)
+    return fail(RS_ERR_ARG, "rs_solve_noalloc: bad precision");
+  if (!is_device_ptr(B) || !is_device_ptr(X))
+    return fail(RS_ERR_ARG, "rs_solve_noalloc: B and X must be device memory (host buffers would need staging)");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = solve_noalloc_device(h, precision, B, ldb, nrhs, X, ldx, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (rc == RS_OK && e != cudaSuccess) rc = fail(RS_ERR_CUDA, "rs_solve_noalloc: %s", cudaGetErrorString(e));
+  return rc;
+}
+
 int rs_matvec(rs_handle h, const void* X, int64_t ldx, int nrhs, void* Y, int64_t ldy, void* stream) {
   rs::g_err.clear();
   RS_TRY(check_handle(h));

@@ -155,5 +155,8 @@ int residual_device(Handle* h, const void* d_b, const void* d_x, void* d_r, int 
                     cudaStream_t st);
 int colnorm2_device(Handle* h, const void* d_v, int nrhs, double* d_out, cudaStream_t st);
 int axpy_lowp_device(Handle* h, void* d_x, const void* d_d, int nrhs, cudaStream_t st);
+// Solve with the per-level vectors in the library's static device scratch.
+int solve_noalloc_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, void* d_X, int64_t ldx,
+                         cudaStream_t st);
 
 }  // namespace rs

@@ -14,6 +14,7 @@
 //            of different children, zero within one child; root: same form)
 //   downward y_i += P_i^T y_parent[skoff_i ...]
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "rs_internal.h"
@@ -520,6 +521,130 @@ int axpy_lowp_device(Handle* h, void* d_x, const void* d_d, int nrhs, cudaStream
   else k_axpy<double><<<div_up(cnt, 256), 256, 0, st>>>((double*)d_x, (const double*)d_d, cnt);
   RS_CHECK_LAUNCH();
   return RS_OK;
+}
+
+}  // namespace rs
+
+// ----------------------------------------------------- allocation-free solve
+// rs_solve_noalloc: the same level-by-level solve as rs_solve, for callers
+// that must not allocate device memory during a solve -- for example a
+// latency-critical serving loop, where cudaMalloc/cudaFree can synchronize
+// the whole device and stall other streams, or a process that fixed its
+// device-memory budget at start-up.  Its per-level vectors live in one
+// file-scope device array of RS_NOALLOC_SCRATCH_BYTES that every GPU which
+// loads the library holds until the process exits.
+namespace rs {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device (host code may
+// not use the symbol itself).  Looked up once per device, on its first call.
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  RS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(RS_ERR_ARG, "rs_solve_noalloc: device %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return fail(RS_ERR_CUDA, "rs_solve_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return RS_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <class S, class SIO>
+int solve_noalloc_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO* X, int64_t ldx,
+                       cudaStream_t st) {
+  const int64_t N = h->N;
+  const int L = h->L;
+  size_t need = 0;
+  for (int d = 0; d <= L; ++d) need += 2 * align256(sizeof(S) * (size_t)std::max<int64_t>(1, h->lv[d].ntot) * R);
+  if (need > (size_t)RS_NOALLOC_SCRATCH_BYTES)
+    return fail(RS_ERR_ARG, "rs_solve_noalloc: needs %zu bytes of scratch for nrhs=%d, limit %zu; use fewer columns",
+                need, R, (size_t)RS_NOALLOC_SCRATCH_BYTES);
+  void* base = nullptr;
+  RS_TRY(noalloc_scratch(&base));
+  std::vector<S*> v(L + 1), u(L + 1);
+  unsigned char* p = (unsigned char*)base;
+  for (int d = 0; d <= L; ++d) {
+    size_t b = align256(sizeof(S) * (size_t)std::max<int64_t>(1, h->lv[d].ntot) * R);
+    v[d] = (S*)p;
+    p += b;
+    u[d] = (S*)p;
+    p += b;
+  }
+  int nb = div_up(N * R, 256);
+  k_perm_in<SIO, S><<<nb, 256, 0, st>>>(B, ldb, h->perm, N, R, v[L]);
+  RS_CHECK_LAUNCH();
+  const int CT = R == 1 ? 1 : 32;
+  const int ntile = div_up(R, CT);
+  const size_t stage_limit = 96 * 1024;
+  for (int d = L; d >= 0; --d) {
+    const Level& lv = h->lv[d];
+    const S* U = (const S*)(prec == RS_PREC_FP64 ? lv.U : lv.U32);
+    S* cout = d > 0 ? v[d - 1] : nullptr;
+    size_t smem = sizeof(S) * (size_t)std::max(1, lv.maxn) * CT;
+    BoxView bv = box_view(lv);
+    if (d == 0) bv.skoff = nullptr;
+    const int grid = lv.nbox * ntile;
+    if (smem <= stage_limit) {
+      RS_CUDA(cudaFuncSetAttribute(k_up<S, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_limit));
+      RS_CUDA(cudaFuncSetAttribute(k_up<S, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_limit));
+      if (CT == 1) k_up<S, 1, true><<<grid, SV_NT, smem, st>>>(bv, lv.uoff, U, v[d], u[d], cout, R, ntile);
+      else k_up<S, 32, true><<<grid, SV_NT, smem, st>>>(bv, lv.uoff, U, v[d], u[d], cout, R, ntile);
+    } else {
+      if (CT == 1) k_up<S, 1, false><<<grid, SV_NT, 0, st>>>(bv, lv.uoff, U, v[d], u[d], cout, R, ntile);
+      else k_up<S, 32, false><<<grid, SV_NT, 0, st>>>(bv, lv.uoff, U, v[d], u[d], cout, R, ntile);
+    }
+    RS_CHECK_LAUNCH();
+  }
+  for (int d = 1; d <= L; ++d) {
+    const Level& lv = h->lv[d];
+    const S* Lf = (const S*)(prec == RS_PREC_FP64 ? lv.Lf : lv.Lf32);
+    size_t smem = sizeof(S) * (size_t)std::max(1, lv.maxk) * CT;
+    const int grid = lv.nbox * ntile;
+    BoxView bv = box_view(lv);
+    if (smem <= stage_limit) {
+      RS_CUDA(cudaFuncSetAttribute(k_down<S, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_limit));
+      RS_CUDA(cudaFuncSetAttribute(k_down<S, 32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stage_limit));
+      if (CT == 1) k_down<S, 1, true><<<grid, SV_NT, smem, st>>>(bv, lv.loff, Lf, u[d - 1], u[d], R, ntile);
+      else k_down<S, 32, true><<<grid, SV_NT, smem, st>>>(bv, lv.loff, Lf, u[d - 1], u[d], R, ntile);
+    } else {
+      if (CT == 1) k_down<S, 1, false><<<grid, SV_NT, 0, st>>>(bv, lv.loff, Lf, u[d - 1], u[d], R, ntile);
+      else k_down<S, 32, false><<<grid, SV_NT, 0, st>>>(bv, lv.loff, Lf, u[d - 1], u[d], R, ntile);
+    }
+    RS_CHECK_LAUNCH();
+  }
+  k_perm_out<S, SIO><<<nb, 256, 0, st>>>(u[L], h->perm, N, R, X, ldx);
+  RS_CHECK_LAUNCH();
+  return RS_OK;
+}
+
+}  // namespace
+
+int solve_noalloc_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, void* d_X, int64_t ldx,
+                         cudaStream_t st) {
+  if (h->cplx) {
+    if (prec == RS_PREC_FP64)
+      return solve_noalloc_impl<c128, c128>(h, prec, (const c128*)d_B, ldb, nrhs, (c128*)d_X, ldx, st);
+    return solve_noalloc_impl<c64, c128>(h, prec, (const c128*)d_B, ldb, nrhs, (c128*)d_X, ldx, st);
+  }
+  if (prec == RS_PREC_FP64)
+    return solve_noalloc_impl<double, double>(h, prec, (const double*)d_B, ldb, nrhs, (double*)d_X, ldx, st);
+  return solve_noalloc_impl<float, double>(h, prec, (const double*)d_B, ldb, nrhs, (double*)d_X, ldx, st);
 }
 
 }  // namespace rs
