@@ -178,6 +178,11 @@ int rs_profile_ncat(void);
 int rs_profile_read(int cat, double* ms, int64_t* launches, double* bytes, double* flops,
                     const char** name);
 
+/* Individual records of the profiler in launch order: rs_profile_nrec()
+ * records; record i gives its category, device time (ms), bytes, flops. */
+int rs_profile_nrec(void);
+int rs_profile_record(int i, int* cat, double* ms, double* bytes, double* flops);
+
 /* Number of kernels the library has launched in this process so far. */
 int64_t rs_launch_count(void);
 

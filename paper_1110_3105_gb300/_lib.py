@@ -58,6 +58,8 @@ _PROTOS = {
     "rs_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "rs_profile_ncat": (ctypes.c_int, []),
     "rs_launch_count": (ctypes.c_int64, []),
+    "rs_profile_nrec": (ctypes.c_int, []),
+    "rs_profile_record": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P]),
     "rs_profile_read": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_char_p)]),
     "rs_last_error": (ctypes.c_char_p, []),
     "rs_version": (ctypes.c_char_p, []),
@@ -238,6 +240,21 @@ def rs_profile_read() -> dict:
                                    ctypes.addressof(fl), ctypes.byref(name)))
         if n.value:
             out[name.value.decode()] = dict(ms=ms.value, launches=n.value, bytes=by.value, flops=fl.value)
+    return out
+
+
+def rs_profile_records() -> list:
+    """[(category index, ms, bytes, flops)] of the recorded launches, in order."""
+    lib = load()
+    out = []
+    for i in range(lib.rs_profile_nrec()):
+        cat = ctypes.c_int()
+        ms = ctypes.c_double()
+        by = ctypes.c_double()
+        fl = ctypes.c_double()
+        _check(lib.rs_profile_record(i, ctypes.addressof(cat), ctypes.addressof(ms), ctypes.addressof(by),
+                                     ctypes.addressof(fl)))
+        out.append((cat.value, ms.value, by.value, fl.value))
     return out
 
 

@@ -60,6 +60,7 @@ static bool is_device_ptr(const void* p) {
 static void destroy(rs_handle_s* h) {
   if (!h) return;
   cudaDeviceSynchronize();
+  free_pers(h);
   for (void* p : h->allocs) cudaFree(p);
   for (auto& w : h->work) {
     for (void* p : w.v) if (p) cudaFree(p);
@@ -193,6 +194,7 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
     if (rc != RS_OK) break;
     if ((rc = factor_root(h, st)) != RS_OK) break;
     if ((rc = make_fp32_copies(h, st)) != RS_OK) break;
+    if ((rc = make_fwd_blocks(h, st)) != RS_OK) break;
   } while (0);
   cudaEventRecord(e1, st);
   cudaError_t se = cudaStreamSynchronize(st);
@@ -223,12 +225,13 @@ int rs_solve(rs_handle h, int precision, const void* B, int64_t ldb, int nrhs, v
   Staged sB, sX;
   int rc = stage_in(B, ldb, h->N, nrhs, sb, st, &sB);
   if (rc == RS_OK) rc = stage_out_alloc(X, ldx, h->N, nrhs, sb, st, &sX);
-  if (rc == RS_OK) rc = solve_device(h, precision, sB.d, sB.ld, nrhs, sX.d, sX.ld, st);
+  if (rc == RS_OK) rc = solve_pers_device(h, precision, sB.d, sB.ld, nrhs, sX.d, sX.ld, st);
   if (rc == RS_OK) rc = stage_out_finish(X, ldx, h->N, nrhs, sb, st, &sX);
   cudaError_t e = cudaStreamSynchronize(st);
   release(&sB, st);
   release(&sX, st);
   if (rc == RS_OK && e != cudaSuccess) rc = fail(RS_ERR_CUDA, "rs_solve: %s", cudaGetErrorString(e));
+  if (rc == RS_OK) rc = pers_check(h);
   return rc;
 }
 
@@ -298,12 +301,24 @@ int rs_solve_refined(rs_handle h, const void* B, int64_t ldb, int nrhs, void* X,
       break;
     }
     if ((rc = colnorm2_device(h, b, nrhs, nrm + nrhs, st)) != RS_OK) break;
-    if ((rc = solve_device(h, RS_PREC_FP32, b, N, nrhs, x, N, st)) != RS_OK) break;
+    if ((rc = solve_pers_device(h, RS_PREC_FP32, b, N, nrhs, x, N, st)) != RS_OK) break;
     cudaMemcpyAsync(hb.data(), nrm + nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
+    // Real kernels: r_0 = b - A x_0 with double-float products; later
+    // residuals by the update r_{j+1} = r_j - A d_j (float products on the
+    // small correction).  Complex kernels: every residual in FP64.
+    const bool dfp = df_supported(h);
+    bool first = true;
     for (;;) {
-      if ((rc = residual_device(h, b, x, r, nrhs, nrm, st)) != RS_OK) break;
+      if (!dfp || first) {
+        if (dfp) rc = residual_df(h, (const double*)b, (const double*)x, (double*)r, nrhs, true, st);
+        else rc = residual_device(h, b, x, r, nrhs, nullptr, st);
+        if (rc != RS_OK) break;
+      }
+      first = false;
+      if ((rc = colnorm2_device(h, r, nrhs, nrm, st)) != RS_OK) break;
       cudaMemcpyAsync(hr.data(), nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
       cudaStreamSynchronize(st);
+      if ((rc = pers_check(h)) != RS_OK) break;
       bool done = true;
       for (int c = 0; c < nrhs; ++c) {
         double rel = hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : std::sqrt(hr[c]);
@@ -312,8 +327,10 @@ int rs_solve_refined(rs_handle h, const void* B, int64_t ldb, int nrhs, void* X,
         if (rel > tol) done = false;
       }
       if (rc != RS_OK || done || its >= max_it) break;
-      if ((rc = solve_device(h, RS_PREC_FP32, r, N, nrhs, d, N, st)) != RS_OK) break;
+      if ((rc = solve_pers_device(h, RS_PREC_FP32, r, N, nrhs, d, N, st)) != RS_OK) break;
       if ((rc = axpy_lowp_device(h, x, d, nrhs, st)) != RS_OK) break;
+      if (dfp && (rc = residual_df(h, (const double*)r, (const double*)d, (double*)r, nrhs, false, st)) != RS_OK)
+        break;
       ++its;
     }
     if (rc != RS_OK) break;

@@ -18,7 +18,8 @@ struct Rec {
 };
 
 const char* kNames[P_NCAT] = {"tree", "id", "factor", "fp32_copy", "solve_up", "solve_down", "permute",
-                              "fwd_proj", "fwd_dblock", "fwd_down", "residual", "misc"};
+                              "fwd_proj", "fwd_dblock", "fwd_down", "residual", "misc", "solve_fp64",
+                              "solve_fp32"};
 
 std::mutex g_mu;
 bool g_on = false;
@@ -92,6 +93,27 @@ int rs_profile_enable(int on) {
 int rs_profile_ncat(void) { return rs::P_NCAT; }
 
 int64_t rs_launch_count(void) { return rs::g_launches.load(); }
+
+int rs_profile_nrec(void) {
+  std::lock_guard<std::mutex> lk(rs::g_mu);
+  return (int)rs::g_recs.size();
+}
+
+int rs_profile_record(int i, int* cat, double* ms, double* bytes, double* flops) {
+  std::lock_guard<std::mutex> lk(rs::g_mu);
+  if (i < 0 || i >= (int)rs::g_recs.size()) return rs::fail(RS_ERR_ARG, "rs_profile_record: index out of range");
+  const auto& r = rs::g_recs[i];
+  float m = 0;
+  if (cudaEventSynchronize(r.e1) != cudaSuccess || cudaEventElapsedTime(&m, r.e0, r.e1) != cudaSuccess) {
+    cudaGetLastError();
+    return rs::fail(RS_ERR_CUDA, "rs_profile_record: event timing failed");
+  }
+  if (cat) *cat = r.cat;
+  if (ms) *ms = m;
+  if (bytes) *bytes = r.bytes;
+  if (flops) *flops = r.flops;
+  return RS_OK;
+}
 
 int rs_profile_read(int cat, double* ms, int64_t* launches, double* bytes, double* flops, const char** name) {
   if (cat < 0 || cat >= rs::P_NCAT) return rs::fail(RS_ERR_ARG, "rs_profile_read: bad category");

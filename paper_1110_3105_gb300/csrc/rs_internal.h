@@ -32,7 +32,7 @@ namespace rs {
 
 // ------------------------------------------------------------- profiler
 enum ProfCat { P_TREE, P_ID, P_FACTOR, P_COPY32, P_UP, P_DOWN, P_PERM, P_FWD_PROJ, P_FWD_DBLOCK, P_FWD_DOWN,
-               P_RESID, P_MISC, P_NCAT };
+               P_RESID, P_MISC, P_SOLVE64, P_SOLVE32, P_NCAT };
 bool prof_on();
 void prof_begin(int cat, cudaStream_t st);
 void prof_end(int cat, cudaStream_t st, double bytes, double flops);
@@ -87,11 +87,17 @@ struct Level {
   void* Lam = nullptr;
   void* U32 = nullptr;
   void* Lf32 = nullptr;
+  // forward-operator blocks as (hi, lo) float pairs (fwd2.cu)
+  int64_t* dfoff = nullptr;
+  void* Dfw = nullptr;
+  void* Tdf = nullptr;
+  int64_t dfsz = 0, tsz_used = 0;
   int64_t ksum = 0;            // sum of k (size of depth-1 active vector)
   int64_t usz = 0, lsz = 0, lamsz = 0, tsz = 0;  // scalars in the pools
   int maxn = 0, maxm = 0, maxk = 0;
   // host copies (for sizes and the inspection API)
   std::vector<int> h_n, h_k, h_begin, h_parent, h_ncoll, h_coll;
+  std::vector<int64_t> h_off, h_skoff, h_uoff, h_loff;
 };
 
 struct Handle {
@@ -121,6 +127,7 @@ struct Handle {
     std::vector<void*> v;       // per depth: input vector of the upward pass
     std::vector<void*> u;       // per depth: calD b, then x in the downward pass
     size_t bytes = 0;
+    int gen = 0;                // bumped whenever the buffers are reallocated
   };
   Work work[2];                 // [0] = FP64 solve, [1] = FP32 solve
   // refinement / matvec workspaces
@@ -129,6 +136,10 @@ struct Handle {
   int fR = 0;
   double* colnorm = nullptr;    // 2 * R
   int ncolnorm = 0;
+  std::vector<void*> dfz, dfy;  // double-float forward vectors per depth
+  int dfR = 0;
+  void* pers = nullptr;         // persistent-solve plans (solve2.cu)
+  void* pers_last = nullptr;
 };
 
 // allocation helper: records in h->allocs
@@ -155,6 +166,18 @@ int residual_device(Handle* h, const void* d_b, const void* d_x, void* d_r, int 
                     cudaStream_t st);
 int colnorm2_device(Handle* h, const void* d_v, int nrhs, double* d_out, cudaStream_t st);
 int axpy_lowp_device(Handle* h, void* d_x, const void* d_d, int nrhs, cudaStream_t st);
+// Double-float forward operator (fwd2.cu).
+int make_fwd_blocks(Handle* h, cudaStream_t st);
+bool df_supported(const Handle* h);
+int residual_df(Handle* h, const double* b, const double* x, double* r, int R, bool full, cudaStream_t st);
+
+// Persistent single-launch solve (solve2.cu).
+int solve_pers_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, void* d_X, int64_t ldx,
+                      cudaStream_t st);
+int pers_check(Handle* h);
+void free_pers(Handle* h);
+int prec_cat(int prec);
+int ensure_work_pub(Handle* h, int prec, int R, cudaStream_t st);
 // Solve with the per-level vectors in the library's static device scratch.
 int solve_noalloc_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, void* d_X, int64_t ldx,
                          cudaStream_t st);

@@ -32,6 +32,7 @@ namespace {
 
 constexpr int ID_NT = 256;
 constexpr int FA_NT = 256;
+constexpr int FA_SM_NT = 128;
 
 template <class S> __device__ inline S scal(S a, double s);
 template <> __device__ inline double scal<double>(double a, double s) { return a * s; }
@@ -93,17 +94,18 @@ __device__ int cpqr(S* M, int m, int n, int ld, double eps, int* piv, double* nr
   constexpr int NW = NT / 32;
   for (int c = tid; c < n; c += NT) piv[c] = c;
   const int kmax = min(m, n);
-  int j = 0;
+  // trailing column norms over rows j..m-1; step 0 computes them here, every
+  // later step recomputes them from the freshly updated columns (no downdating)
+  for (int c = warp; c < n; c += NW) {
+    const S* col = M + (size_t)c * ld;
+    double s = 0.0;
+    for (int r = lane; r < m; r += 32) s += abs2(col[r]);
+    s = warp_sum(s);
+    if (lane == 0) nrm[c] = s;
+  }
   __syncthreads();
+  int j = 0;
   for (; j < kmax; ++j) {
-    for (int c = j + warp; c < n; c += NW) {
-      const S* col = M + (size_t)c * ld;
-      double s = 0.0;
-      for (int r = j + lane; r < m; r += 32) s += abs2(col[r]);
-      s = warp_sum(s);
-      if (lane == 0) nrm[c] = s;
-    }
-    __syncthreads();
     if (warp == 0) {
       double best = -1.0;
       int bi = n;
@@ -160,7 +162,14 @@ __device__ int cpqr(S* M, int m, int n, int ld, double eps, int* piv, double* nr
       s = warp_sum(s);
       s = shfl(s, 0);
       const S fs = scal(s, f);
-      for (int r = j + lane; r < m; r += 32) col[r] -= u[r - j] * fs;
+      double s2 = 0.0;
+      for (int r = j + lane; r < m; r += 32) {
+        const S v = col[r] - u[r - j] * fs;
+        col[r] = v;
+        if (r > j) s2 += abs2(v);
+      }
+      s2 = warp_sum(s2);
+      if (lane == 0) nrm[c] = s2;
     }
     if (tid == 0) M[j + (size_t)j * ld] = beta;
     __syncthreads();
@@ -216,12 +225,13 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
   const int n = a.n[b];
   const int m = a.mrows[b];
   const int64_t off = a.off[b];
-  // shared layout: [M (smem path)] | u[mmax] | nrm[nmax] | piv[nmax] | rowid[mmax]
+  // shared layout: [M (smem path)] | u[mmax] | nrm[nmax] | proxy xyz[3 nproxy] | piv[nmax] | rowid[mmax]
   S* Ms = reinterpret_cast<S*>(smem);
   size_t msz = a.smem_path ? (size_t)a.mmax * a.nmax : 0;
   S* u = Ms + msz;
   double* nrm = reinterpret_cast<double*>(u + a.mmax);
-  int* piv = reinterpret_cast<int*>(nrm + a.nmax);
+  double* pxy = nrm + a.nmax;
+  int* piv = reinterpret_cast<int*>(pxy + 3 * a.geo.nproxy);
   int* rowid = piv + a.nmax;
   S* M = a.smem_path ? Ms : Mws + a.moff[b];
   const int ld = m;
@@ -246,8 +256,11 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
   }
   __syncthreads();
 
-  // fill M column-major: rows = near | proxy | (constant)
+  // proxy surface of this box, once
   const int* bc = a.coords + (size_t)b * a.geo.dim;
+  for (int j = threadIdx.x; j < a.geo.nproxy; j += NT) proxy_point(a.geo, bc, j, pxy + 3 * j);
+  __syncthreads();
+  // fill M column-major: rows = near | proxy | (constant)
   const int64_t total = (int64_t)m * n;
   for (int64_t e = threadIdx.x; e < total; e += NT) {
     int r = (int)(e % m), c = (int)(e / m);
@@ -256,9 +269,7 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
     if (r < nnear) {
       v = offdiag_entry<S>(a.kp, a.pts, rowid[r], pc);
     } else if (r < nnear + a.geo.nproxy) {
-      double q[3];
-      proxy_point(a.geo, bc, r - nnear, q);
-      v = green_at<S>(a.kp, dist_to(a.pts, pc, q));
+      v = green_at<S>(a.kp, dist_to(a.pts, pc, pxy + 3 * (r - nnear)));
     } else {
       v = S(a.kp.w);
     }
@@ -278,6 +289,238 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
   }
   for (int c = threadIdx.x; c < n; c += NT) a.lperm[off + c] = piv[c];
   if (threadIdx.x == 0) a.kout[b] = k;
+}
+
+// ---------------------------------------------------------- big-box ID
+// For boxes whose compressed matrix does not fit one CTA's shared memory:
+// the same pivoted QR, with one launch per pivot step and each CTA owning 32
+// physical columns of one box.  Column exchanges only permute a
+// position -> column map (double-buffered across launches); the trailing
+// norms, the rank and R_00 live in global memory, so every CTA of a box takes
+// the same pivot and stop decision from the previous launch's values.
+struct BigId {
+  const int* m;          // rows per box
+  const int* n;
+  const int64_t* moff;   // M offset per box (scalars)
+  const int64_t* noff;   // offset of per-column arrays per box
+  double* nrm;           // trailing column norms^2 (per physical column), two parities
+  int64_t ntot;          // entries of one parity
+  int* map0;             // position -> physical column, parity 0
+  int* map1;             // parity 1
+  double* r00;           // per box
+  int* kk;               // per box rank (starts at min(m, n))
+  void* rdiag;           // R_jj per position (scalars, same offsets as nrm)
+};
+
+constexpr int BI_NT = 128;
+constexpr int BI_CB = 8;
+
+template <class S>
+__global__ void __launch_bounds__(BI_NT) k_bbid_fill(IdArgs a, BigId g, S* Mws, int maxn) {
+  __shared__ int cstart[28];
+  __shared__ double pxy[3 * 256];
+  const int b = blockIdx.x / maxn, c = blockIdx.x % maxn;
+  const int n = a.n[b];
+  if (c >= n) return;
+  const int m = g.m[b];
+  const int64_t off = a.off[b];
+  const int nc = a.ncoll[b];
+  if (threadIdx.x == 0) {
+    int r = 0;
+    for (int j = 0; j < nc; ++j) {
+      cstart[j] = r;
+      r += a.n[a.coll[b * 27 + j]];
+    }
+    cstart[nc] = r;
+  }
+  const int* bc = a.coords + (size_t)b * a.geo.dim;
+  for (int j = threadIdx.x; j < a.geo.nproxy; j += BI_NT) proxy_point(a.geo, bc, j, pxy + 3 * j);
+  __syncthreads();
+  const int nnear = cstart[nc];
+  const int pc = a.act[off + c];
+  S* col = Mws + g.moff[b] + (size_t)c * m;
+  double s2 = 0.0;
+  for (int r = threadIdx.x; r < m; r += BI_NT) {
+    S v;
+    if (r < nnear) {
+      int j = 0;
+      while (cstart[j + 1] <= r) ++j;
+      int cc = a.coll[b * 27 + j];
+      v = offdiag_entry<S>(a.kp, a.pts, a.act[a.off[cc] + (r - cstart[j])], pc);
+    } else if (r < nnear + a.geo.nproxy) {
+      v = green_at<S>(a.kp, dist_to(a.pts, pc, pxy + 3 * (r - nnear)));
+    } else {
+      v = S(a.kp.w);
+    }
+    col[r] = v;
+    s2 += abs2(v);
+  }
+  __shared__ double red[BI_NT];
+  red[threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = BI_NT / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    g.nrm[g.noff[b] + c] = red[0];
+    g.map0[g.noff[b] + c] = c;
+    if (c == 0) g.kk[b] = min(m, n);
+  }
+}
+
+template <class S>
+__global__ void __launch_bounds__(BI_NT) k_bbid_step(IdArgs a, BigId g, S* Mws, int j, int ncb, int* lperm) {
+  __shared__ S u[1024];
+  __shared__ int mp[512];
+  __shared__ int s_p, s_stop;
+  __shared__ double s_rjj, s_r00;
+  const int b = blockIdx.x / ncb, cb = blockIdx.x % ncb;
+  const int n = a.n[b], m = g.m[b];
+  const int kmax = min(m, n);
+  if (j >= kmax || g.kk[b] < kmax) return;   // past the rank or already stopped
+  if (cb * BI_CB >= n) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t no = g.noff[b];
+  const int* map_in = (j & 1) ? g.map1 + no : g.map0 + no;
+  int* map_out = (j & 1) ? g.map0 + no : g.map1 + no;
+  for (int q = tid; q < n; q += BI_NT) mp[q] = map_in[q];
+  __syncthreads();
+  if (warp == 0) {
+    double best = -1.0;
+    int bi = n;
+    const double* nrm_in = g.nrm + (j & 1) * g.ntot;
+    for (int q = j + lane; q < n; q += 32) {
+      double v = nrm_in[no + mp[q]];
+      if (v > best) { best = v; bi = q; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) {
+      double rjj = sqrt(best);
+      double r00 = j == 0 ? rjj : g.r00[b];
+      int stop = j == 0 ? !(rjj > 0.0) : (rjj <= a.eps * r00);
+      s_p = bi;
+      s_rjj = rjj;
+      s_r00 = r00;
+      s_stop = stop;
+    }
+  }
+  __syncthreads();
+  const int64_t boff = a.off[b];
+  if (s_stop) {
+    if (cb == 0 && tid == 0) {
+      g.kk[b] = j;
+      for (int q = 0; q < n; ++q) lperm[boff + q] = mp[q];
+    }
+    return;
+  }
+  const int p = s_p;
+  const double rjj = s_rjj;
+  if (cb == 0 && tid == 0 && j == 0) g.r00[b] = s_r00;
+  // exchange positions j and p
+  if (tid == 0) {
+    int t = mp[j];
+    mp[j] = mp[p];
+    mp[p] = t;
+  }
+  __syncthreads();
+  if (cb == 0) {
+    for (int q = tid; q < n; q += BI_NT) map_out[q] = mp[q];
+    if (tid == 0 && j + 1 == kmax) {   // ran to the full rank: emit the order now
+      for (int q = 0; q < n; ++q) lperm[boff + q] = mp[q];
+    }
+  }
+  // reflector from the pivot column (rows j..m-1)
+  const int pj = mp[j];
+  const S* pcol = Mws + g.moff[b] + (size_t)pj * m;
+  const S alpha = pcol[j];
+  const double aa = sqrt(abs2(alpha));
+  const S phase = aa > 0.0 ? scal(alpha, 1.0 / aa) : S(1.0);
+  const S beta = scal(phase, -rjj);
+  for (int r = j + tid; r < m; r += BI_NT) u[r - j] = r == j ? alpha - beta : pcol[r];
+  const double f = 1.0 / (rjj * (rjj + aa));
+  __syncthreads();
+  // columns owned by this CTA that are still unpivoted (position > j)
+  __shared__ int posof[BI_CB];
+  for (int cl = tid; cl < BI_CB; cl += BI_NT) posof[cl] = -1;
+  __syncthreads();
+  for (int q = j + tid; q < n; q += BI_NT) {
+    int c = mp[q];
+    if (c >= cb * BI_CB && c < cb * BI_CB + BI_CB) posof[c - cb * BI_CB] = q;
+  }
+  __syncthreads();
+  for (int cl = warp; cl < BI_CB; cl += BI_NT / 32) {
+    const int c = cb * BI_CB + cl;
+    const int q = posof[cl];
+    if (c >= n || q < 0) continue;
+    S* col = Mws + g.moff[b] + (size_t)c * m;
+    if (q == j) {   // the pivot column: R_jj goes to rdiag (its rows are read by every CTA this step)
+      if (lane == 0) reinterpret_cast<S*>(g.rdiag)[no + j] = beta;
+      continue;
+    }
+    S s = S(0.0);
+    for (int r = j + lane; r < m; r += 32) s += conj_(u[r - j]) * col[r];
+    s = warp_sum(s);
+    s = shfl(s, 0);
+    const S fs = scal(s, f);
+    double s2 = 0.0;
+    for (int r = j + lane; r < m; r += 32) {
+      const S v = col[r] - u[r - j] * fs;
+      col[r] = v;
+      if (r > j) s2 += abs2(v);
+    }
+    s2 = warp_sum(s2);
+    if (lane == 0) g.nrm[((j + 1) & 1) * g.ntot + no + c] = s2;   // read by the next step only
+  }
+}
+
+// 1 if some box of the level is still pivoting at step j.
+__global__ void k_bbid_active(BigId g, const int* n, int nb, int j, int* out) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    int kmax = min(g.m[b], n[b]);
+    if (g.kk[b] == kmax && j < kmax) any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *out = any;
+}
+
+// T = R11^-1 R12 for every column of R12 (one warp per column), ranks out.
+template <class S>
+__global__ void k_bbid_T(IdArgs a, BigId g, const S* Mws, S* Tpool, int tiles_per_box) {
+  const int b = blockIdx.x / tiles_per_box;
+  const int e = (blockIdx.x % tiles_per_box) * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int n = a.n[b], m = g.m[b], k = g.kk[b];
+  if (blockIdx.x % tiles_per_box == 0 && threadIdx.x == 0) a.kout[b] = k;
+  if (e >= n - k) return;
+  const int* lp = a.lperm + a.off[b];
+  const S* M = Mws + g.moff[b];
+  S* T = Tpool + a.toff[b];
+  const S* rhs = M + (size_t)lp[k + e] * m;
+  // t = R11^-1 rhs[0:k] with R11[i][i'] = M[i, lp[i']] (column-oriented, lane-parallel updates)
+  S* t = T + (size_t)e * k;
+  for (int i = lane; i < k; i += 32) t[i] = rhs[i];
+  __syncwarp();
+  for (int i = k - 1; i >= 0; --i) {
+    const S* ci = M + (size_t)lp[i] * m;
+    S ti = S(0.0);
+    if (lane == 0) {
+      ti = t[i] / reinterpret_cast<const S*>(g.rdiag)[g.noff[b] + i];
+      t[i] = ti;
+    }
+    ti = shfl(ti, 0);
+    __syncwarp();
+    for (int r = lane; r < i; r += 32) t[r] -= ci[r] * ti;
+    __syncwarp();
+  }
 }
 
 // Gauss-Jordan with partial pivoting on the augmented n x 2n matrix [A | I]
@@ -447,6 +690,416 @@ __global__ void __launch_bounds__(NT) k_factor(FaArgs a, const S* Tpool, const S
   }
 }
 
+// In-place Gauss-Jordan inversion with partial pivoting of the n x n
+// column-major matrix A (shared memory): n^3 multiply-adds.  Rows are
+// swapped as pivots are chosen and the columns unscrambled at the end.
+template <class S, int NT>
+__device__ void gj_inplace(S* A, int n, S* mult, int* piv, int* bad) {
+  __shared__ int s_p;
+  __shared__ double s_best;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = 0; j < n; ++j) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = j;
+      for (int r = j + lane; r < n; r += 32) {
+        double v = abs2(A[r + j * n]);
+        if (v > best) { best = v; bi = r; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { s_p = bi; s_best = best; piv[j] = bi; }
+    }
+    __syncthreads();
+    if (!(s_best > 0.0) || !isfinite(s_best)) {
+      if (tid == 0) atomicOr(bad, 1);
+      __syncthreads();
+      continue;
+    }
+    const int p = s_p;
+    if (p != j)
+      for (int c = tid; c < n; c += NT) {
+        S t = A[j + c * n];
+        A[j + c * n] = A[p + c * n];
+        A[p + c * n] = t;
+      }
+    __syncthreads();
+    const S inv = S(1.0) / A[j + j * n];
+    for (int r = tid; r < n; r += NT) {
+      mult[r] = A[r + j * n];
+      A[r + j * n] = r == j ? S(1.0) : S(0.0);
+    }
+    __syncthreads();
+    for (int c = tid; c < n; c += NT) A[j + c * n] = A[j + c * n] * inv;
+    __syncthreads();
+    for (int e = tid; e < n * n; e += NT) {
+      int r = e % n, c = e / n;
+      if (r != j) A[r + c * n] -= mult[r] * A[j + c * n];
+    }
+    __syncthreads();
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    const int p = piv[j];
+    if (p != j)
+      for (int r = tid; r < n; r += NT) {
+        S t = A[r + j * n];
+        A[r + j * n] = A[r + p * n];
+        A[r + p * n] = t;
+      }
+    __syncthreads();
+  }
+}
+
+// The block elimination of k_factor with every intermediate in shared
+// memory: [D^-1 (n x n) | X (n x k) | (PX)^-1 (k x k) | mult (n) | piv (n)].
+template <class S, int NT>
+__global__ void __launch_bounds__(NT) k_factor_smem(FaArgs a, const S* Tpool, const S* cLam, S* Upool, S* Lpool,
+                                                    S* Lampool) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const int n = a.n[b], k = a.k[b], nr = n - k;
+  const int64_t off = a.off[b];
+  const int* lp = a.lperm + off;
+  const S* T = Tpool + (a.toff ? a.toff[b] : 0);
+  S* Dv = reinterpret_cast<S*>(smem);
+  S* X = Dv + (size_t)n * n;
+  S* Y = X + (size_t)n * k;
+  S* mult = Y + (size_t)k * k;
+  int* piv = reinterpret_cast<int*>(mult + n);
+
+  for (int e = tid; e < n * n; e += NT) {
+    int r = e % n, c = e / n;
+    int pr = a.act[off + r], pc = a.act[off + c];
+    S v;
+    if (a.leaf_level) {
+      v = system_entry<S>(a.kp, a.pts, pr, pc);
+    } else {
+      int orow = a.owner[off + r], ocol = a.owner[off + c];
+      if (orow == ocol) {
+        int64_t base = a.cskoff[orow];
+        int kc = a.ck[orow];
+        v = cLam[a.clamoff[orow] + (off + r - base) + (int64_t)(off + c - base) * kc];
+      } else {
+        v = offdiag_entry<S>(a.kp, a.pts, pr, pc);
+      }
+    }
+    Dv[e] = v;
+  }
+  __syncthreads();
+  gj_inplace<S, NT>(Dv, n, mult, piv, a.bad);    // Dv = D^-1
+  S* U = Upool + a.uoff[b];
+  const int ldu = n + k;
+  if (k == 0) {
+    for (int e = tid; e < n * n; e += NT) U[(e % n) + (size_t)(e / n) * ldu] = Dv[e];
+    return;
+  }
+  // X = D^-1 P^T
+  for (int e = tid; e < n * k; e += NT) {
+    int r = e % n, i = e / n;
+    S s = Dv[r + lp[i] * n];
+    for (int q = 0; q < nr; ++q) s += T[i + (size_t)q * k] * Dv[r + lp[k + q] * n];
+    X[e] = s;
+  }
+  __syncthreads();
+  // Y = P X, then Lambda = Y^-1 in place
+  for (int e = tid; e < k * k; e += NT) {
+    int i = e % k, c = e / k;
+    S s = X[lp[i] + c * n];
+    for (int q = 0; q < nr; ++q) s += T[i + (size_t)q * k] * X[lp[k + q] + c * n];
+    Y[e] = s;
+  }
+  __syncthreads();
+  gj_inplace<S, NT>(Y, k, mult, piv, a.bad);
+  S* Lo = Lampool + a.lamoff[b];
+  for (int e = tid; e < k * k; e += NT) Lo[e] = Y[e];
+  // calL = X Lambda -> global; calR = Lambda X^T -> rows n.. of U
+  S* Lf = Lpool + a.loff[b];
+  for (int e = tid; e < n * k; e += NT) {
+    int r = e % n, c = e / n;
+    S s = S(0.0);
+    for (int q = 0; q < k; ++q) s += X[r + q * n] * Y[q + c * k];
+    Lf[e] = s;
+  }
+  for (int e = tid; e < k * n; e += NT) {
+    int i = e % k, c = e / k;
+    S s = S(0.0);
+    for (int q = 0; q < k; ++q) s += Y[i + q * k] * X[c + q * n];
+    U[n + i + (size_t)c * ldu] = s;
+  }
+  // calD = D^-1 - calL X^T = D^-1 - X Lambda X^T: form W = X Lambda in the Y
+  // slot is not possible (k x k), so reuse the global calL just written.
+  __syncthreads();
+  for (int e = tid; e < n * n; e += NT) {
+    int r = e % n, c = e / n;
+    S s = Dv[e];
+    for (int q = 0; q < k; ++q) s -= Lf[r + (size_t)q * n] * X[c + q * n];
+    U[r + (size_t)c * ldu] = s;
+  }
+}
+
+// ---------------------------------------------------------- big boxes
+// Boxes too large for one CTA's shared memory (the top levels) are
+// factored by many CTAs: the Gauss-Jordan inversion runs one launch per pivot
+// step with each CTA owning 32 columns of one box, and the products of the
+// block elimination run column-parallel.  Workspace per box (offset bo[b]):
+// A (n x n, inverted in place) | Dinv (n x n) | X (n x k) | Y (k x k) |
+// pivot column buffers (2 n) | pivots (n, stored as scalars' worth of ints).
+struct BigArgs {
+  int n_box;
+  const int* n;
+  const int* k;
+  const int64_t* bo;       // workspace offset of each box (scalars)
+};
+
+constexpr int BB_NT = 128;
+constexpr int BB_CB = 8;   // columns per CTA in a pivot step
+
+template <class S>
+__device__ inline S* bb_A(S* ws, const BigArgs& g, int b) { return ws + g.bo[b]; }
+
+// D of every box into A, column 0 into the first pivot buffer.
+template <class S>
+__global__ void k_bb_assemble(FaArgs a, BigArgs g, const S* cLam, S* ws, int maxn) {
+  const int b = blockIdx.x / maxn, c = blockIdx.x % maxn;
+  const int n = g.n[b];
+  if (c >= n) return;
+  const int k = g.k[b];
+  const int64_t off = a.off[b];
+  S* A = bb_A(ws, g, b);
+  S* buf = A + 2 * (size_t)n * n + (size_t)n * k + (size_t)k * k;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    int pr = a.act[off + r], pc = a.act[off + c];
+    S v;
+    if (a.leaf_level) {
+      v = system_entry<S>(a.kp, a.pts, pr, pc);
+    } else {
+      int orow = a.owner[off + r], ocol = a.owner[off + c];
+      if (orow == ocol) {
+        int64_t base = a.cskoff[orow];
+        int kc = a.ck[orow];
+        v = cLam[a.clamoff[orow] + (off + r - base) + (int64_t)(off + c - base) * kc];
+      } else {
+        v = offdiag_entry<S>(a.kp, a.pts, pr, pc);
+      }
+    }
+    A[r + (size_t)c * n] = v;
+    if (c == 0) buf[r] = v;
+  }
+}
+
+// One Gauss-Jordan step j on matrices M (m x m, ld m) of every box:
+// M = base(b) + moff, size m = mdim(b).  The pivot column (before the step)
+// is read from pbuf[j % 2]; the owner of column j+1 writes it, updated, to
+// pbuf[(j+1) % 2].  Every CTA finds the same pivot.
+template <class S, class Dims>
+__global__ void __launch_bounds__(BB_NT) k_bb_gj_step(BigArgs g, S* ws, Dims dims, int j, int ncb, int* bad) {
+  __shared__ S mult[512];
+  __shared__ int s_p;
+  __shared__ double s_best;
+  const int b = blockIdx.x / ncb, cb = blockIdx.x % ncb;
+  int m;
+  S *M, *pb_in, *pb_out;
+  int* piv;
+  dims(ws, g, b, j, m, M, pb_in, pb_out, piv);
+  if (j >= m || cb * BB_CB >= m) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) {
+    double best = -1.0;
+    int bi = j;
+    for (int r = j + lane; r < m; r += 32) {
+      double v = abs2(pb_in[r]);
+      if (v > best) { best = v; bi = r; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { s_p = bi; s_best = best; }
+  }
+  __syncthreads();
+  if (!(s_best > 0.0) || !isfinite(s_best)) {
+    if (tid == 0 && cb == 0) atomicOr(bad, 1);
+    return;
+  }
+  const int p = s_p;
+  if (tid == 0 && cb == 0) piv[j] = p;
+  for (int r = tid; r < m; r += BB_NT) mult[r] = pb_in[r == j ? p : (r == p ? j : r)];
+  __syncthreads();
+  const S inv = S(1.0) / mult[j];
+  const int c_beg = cb * BB_CB, c_end = min(m, c_beg + BB_CB), nc = c_end - c_beg;
+  __shared__ S newj[BB_CB];
+  for (int cl = tid; cl < nc; cl += BB_NT) {
+    const int c = c_beg + cl;
+    newj[cl] = c == j ? inv : M[p + (size_t)c * m] * inv;   // row p moves to row j
+  }
+  __syncthreads();
+  // rows other than j keep their position, row p receives old row j; the
+  // pivot column itself is e_j transformed (identity trick of in-place GJ)
+  for (int e = tid; e < nc * m; e += BB_NT) {
+    const int r = e % m, cl = e / m, c = c_beg + cl;
+    if (r == j) continue;
+    S* col = M + (size_t)c * m;
+    const S old = c == j ? S(0.0) : (r == p ? col[j] : col[r]);
+    const S v = old - mult[r] * newj[cl];
+    col[r] = v;
+    if (c == j + 1) pb_out[r] = v;
+  }
+  __syncthreads();
+  for (int cl = tid; cl < nc; cl += BB_NT) {
+    const int c = c_beg + cl;
+    M[j + (size_t)c * m] = newj[cl];
+    if (c == j + 1) pb_out[j] = newj[cl];
+  }
+}
+
+// Final column order of a Gauss-Jordan inverse: position c holds column idx[c].
+template <class S, class Dims>
+__global__ void k_bb_unscramble(BigArgs g, S* ws, Dims dims, S* dst_base, int dst_kind, int* idx_ws, int maxm) {
+  const int b = blockIdx.x;
+  int m;
+  S *M, *pb_in, *pb_out;
+  int* piv;
+  dims(ws, g, b, 0, m, M, pb_in, pb_out, piv);
+  int* idx = idx_ws + (size_t)b * maxm;
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < m; ++c) idx[c] = c;
+    for (int j = m - 1; j >= 0; --j) {
+      int q = piv[j], t = idx[j];
+      idx[j] = idx[q];
+      idx[q] = t;
+    }
+  }
+  __syncthreads();
+  S* dst = dims.dest(ws, g, b, dst_base, dst_kind);
+  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+    int r = (int)(e % m), c = (int)(e / m);
+    dst[e] = M[r + (size_t)idx[c] * m];
+  }
+}
+
+// Accessors of the two inversions: D (n x n, A slot) and P X (k x k, Y slot).
+struct DimsD {
+  template <class S>
+  __device__ void operator()(S* ws, const BigArgs& g, int b, int j, int& m, S*& M, S*& pin, S*& pout,
+                             int*& piv) const {
+    const int n = g.n[b], k = g.k[b];
+    S* A = ws + g.bo[b];
+    m = n;
+    M = A;
+    S* buf = A + 2 * (size_t)n * n + (size_t)n * k + (size_t)k * k;
+    pin = buf + (size_t)(j & 1) * n;
+    pout = buf + (size_t)((j + 1) & 1) * n;
+    piv = reinterpret_cast<int*>(buf + 2 * (size_t)n);
+  }
+  template <class S>
+  __device__ S* dest(S* ws, const BigArgs& g, int b, S*, int) const {
+    const int n = g.n[b];
+    return ws + g.bo[b] + (size_t)n * n;   // Dinv slot
+  }
+};
+struct DimsY {
+  const int64_t* lamoff;
+  template <class S>
+  __device__ void operator()(S* ws, const BigArgs& g, int b, int j, int& m, S*& M, S*& pin, S*& pout,
+                             int*& piv) const {
+    const int n = g.n[b], k = g.k[b];
+    S* A = ws + g.bo[b];
+    m = k;
+    M = A + 2 * (size_t)n * n + (size_t)n * k;
+    S* buf = A + 2 * (size_t)n * n + (size_t)n * k + (size_t)k * k;
+    pin = buf + (size_t)(j & 1) * n;
+    pout = buf + (size_t)((j + 1) & 1) * n;
+    piv = reinterpret_cast<int*>(buf + 2 * (size_t)n);
+  }
+  template <class S>
+  __device__ S* dest(S* ws, const BigArgs& g, int b, S* lam, int) const {
+    return lam + lamoff[b];
+  }
+};
+
+// X = Dinv P^T (column i per CTA), and its sk rows combined into Y = P X
+// (both from global memory).
+template <class S>
+__global__ void k_bb_X(FaArgs a, BigArgs g, const S* Tpool, S* ws, int maxk) {
+  const int b = blockIdx.x / maxk, i = blockIdx.x % maxk;
+  const int n = g.n[b], k = g.k[b], nr = n - k;
+  if (i >= k) return;
+  const int* lp = a.lperm + a.off[b];
+  const S* T = Tpool + a.toff[b];
+  S* A = ws + g.bo[b];
+  const S* Dinv = A + (size_t)n * n;
+  S* X = A + 2 * (size_t)n * n;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    S s = Dinv[r + (size_t)lp[i] * n];
+    for (int q = 0; q < nr; ++q) s += T[i + (size_t)q * k] * Dinv[r + (size_t)lp[k + q] * n];
+    X[r + (size_t)i * n] = s;
+  }
+}
+
+template <class S>
+__global__ void k_bb_Y(FaArgs a, BigArgs g, const S* Tpool, S* ws, int maxk) {
+  const int b = blockIdx.x / maxk, c = blockIdx.x % maxk;
+  const int n = g.n[b], k = g.k[b], nr = n - k;
+  if (c >= k) return;
+  const int* lp = a.lperm + a.off[b];
+  const S* T = Tpool + a.toff[b];
+  S* A = ws + g.bo[b];
+  const S* X = A + 2 * (size_t)n * n;
+  S* Y = A + 2 * (size_t)n * n + (size_t)n * k;
+  S* buf = Y + (size_t)k * k;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    S s = X[lp[i] + (size_t)c * n];
+    for (int q = 0; q < nr; ++q) s += T[i + (size_t)q * k] * X[lp[k + q] + (size_t)c * n];
+    Y[i + (size_t)c * k] = s;
+    if (c == 0) buf[i] = s;   // first pivot column of the Lambda inversion
+  }
+}
+
+// calL = X Lambda, calR = Lambda X^T, calD = Dinv - calL X^T (column c per CTA).
+template <class S>
+__global__ void k_bb_products(FaArgs a, BigArgs g, S* ws, const S* Lampool, S* Upool, S* Lpool, int maxn) {
+  const int b = blockIdx.x / maxn, c = blockIdx.x % maxn;
+  const int n = g.n[b], k = g.k[b];
+  if (c >= n) return;
+  S* A = ws + g.bo[b];
+  const S* Dinv = A + (size_t)n * n;
+  const S* X = A + 2 * (size_t)n * n;
+  const S* Lam = Lampool + a.lamoff[b];
+  S* U = Upool + a.uoff[b];
+  S* Lf = Lpool + a.loff[b];
+  const int ldu = n + k;
+  if (c < k)
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      S s = S(0.0);
+      for (int q = 0; q < k; ++q) s += X[r + (size_t)q * n] * Lam[q + (size_t)c * k];
+      Lf[r + (size_t)c * n] = s;
+    }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    S s = S(0.0);
+    for (int q = 0; q < k; ++q) s += Lam[i + (size_t)q * k] * X[c + (size_t)q * n];
+    U[n + i + (size_t)c * ldu] = s;
+  }
+  // calD[:, c] = Dinv[:, c] - X Lambda X[c, :]^T: w = Lambda X[c, :]^T first
+  __shared__ S w[512];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    S s = S(0.0);
+    for (int q = 0; q < k; ++q) s += Lam[i + (size_t)q * k] * X[c + (size_t)q * n];
+    w[i] = s;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    S s = Dinv[r + (size_t)c * n];
+    for (int q = 0; q < k; ++q) s -= X[r + (size_t)q * n] * w[q];
+    U[r + (size_t)c * ldu] = s;
+  }
+}
+
 // Skeleton ids of every box into the parent depth's active vector.
 __global__ void k_emit(const int* n, const int* k, const int64_t* off, const int64_t* skoff, const int* act,
                        const int* lperm, int nbox, int* act_up, int* owner_up) {
@@ -516,16 +1169,79 @@ Pts make_pts(const Handle* h) {
 }
 
 template <class S>
+int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cudaStream_t st) {
+  const int nb = lv.nbox;
+  std::vector<int64_t> moff(nb), noff(nb);
+  int64_t macc = 0, nacc = 0;
+  int maxkmax = 0;
+  for (int b = 0; b < nb; ++b) {
+    moff[b] = macc;
+    noff[b] = nacc;
+    macc += (int64_t)mrows[b] * lv.h_n[b];
+    nacc += lv.h_n[b];
+    maxkmax = std::max(maxkmax, std::min(mrows[b], lv.h_n[b]));
+  }
+  BigId g{};
+  int64_t *dmo, *dno;
+  RS_TRY(upload(h, &dmo, moff, st));
+  RS_TRY(upload(h, &dno, noff, st));
+  g.m = a.mrows;
+  g.n = a.n;
+  g.moff = dmo;
+  g.noff = dno;
+  S* Mws = nullptr;
+  RS_CUDA(cudaMallocAsync((void**)&Mws, sizeof(S) * std::max<int64_t>(1, macc), st));
+  g.ntot = std::max<int64_t>(1, nacc);
+  RS_CUDA(cudaMallocAsync((void**)&g.nrm, sizeof(double) * 2 * g.ntot, st));
+  RS_CUDA(cudaMallocAsync((void**)&g.map0, sizeof(int) * std::max<int64_t>(1, nacc), st));
+  RS_CUDA(cudaMallocAsync((void**)&g.map1, sizeof(int) * std::max<int64_t>(1, nacc), st));
+  RS_CUDA(cudaMallocAsync((void**)&g.r00, sizeof(double) * nb, st));
+  RS_CUDA(cudaMallocAsync((void**)&g.kk, sizeof(int) * nb, st));
+  RS_CUDA(cudaMallocAsync(&g.rdiag, sizeof(S) * std::max<int64_t>(1, nacc), st));
+  const int maxn = lv.maxn;
+  prof_begin(P_ID, st);
+  k_bbid_fill<S><<<nb * maxn, BI_NT, 0, st>>>(a, g, Mws, maxn);
+  RS_CHECK_LAUNCH();
+  const int ncb = div_up(maxn, BI_CB);
+  // every 8 steps, stop early once every box of the level has found its rank
+  int* d_active = nullptr;
+  int h_active = 1;
+  RS_CUDA(cudaMallocAsync((void**)&d_active, sizeof(int), st));
+  for (int j = 0; j < maxkmax; ++j) {
+    k_bbid_step<S><<<nb * ncb, BI_NT, 0, st>>>(a, g, Mws, j, ncb, a.lperm);
+    RS_CHECK_LAUNCH();
+    if ((j & 7) == 7 && j + 1 < maxkmax) {
+      k_bbid_active<<<1, 256, 0, st>>>(g, a.n, nb, j + 1, d_active);
+      RS_CHECK_LAUNCH();
+      RS_CUDA(cudaMemcpyAsync(&h_active, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+      RS_CUDA(cudaStreamSynchronize(st));
+      if (!h_active) break;
+    }
+  }
+  RS_CUDA(cudaFreeAsync(d_active, st));
+  const int wpb = BI_NT / 32;
+  const int tb = div_up(maxn, wpb);
+  k_bbid_T<S><<<nb * tb, BI_NT, 0, st>>>(a, g, Mws, (S*)lv.T, tb);
+  RS_CHECK_LAUNCH();
+  prof_end(P_ID, st, 0.0, 0.0);
+  for (void* q : {(void*)Mws, (void*)g.nrm, (void*)g.map0, (void*)g.map1, (void*)g.r00, (void*)g.kk, g.rdiag})
+    RS_CUDA(cudaFreeAsync(q, st));
+  return RS_OK;
+}
+
+template <class S>
 int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows, int64_t msum,
            cudaStream_t st) {
   IdArgs a = a0;
   size_t sb = sizeof(S);
-  size_t extra = (size_t)a.mmax * sb + (size_t)a.nmax * sizeof(double) + (size_t)a.nmax * sizeof(int) +
-                 (size_t)a.mmax * sizeof(int) + 64;
+  size_t extra = (size_t)a.mmax * sb + (size_t)a.nmax * sizeof(double) + 3 * (size_t)a.geo.nproxy * sizeof(double) +
+                 (size_t)a.nmax * sizeof(int) + (size_t)a.mmax * sizeof(int) + 64;
   size_t mbytes = (size_t)a.mmax * a.nmax * sb;
   const size_t limit = 200 * 1024;
   S* Mws = nullptr;
   a.smem_path = (mbytes + extra <= limit) ? 1 : 0;
+  if (!a.smem_path && a.mmax <= 1024 && a.nmax <= 512 && a.geo.nproxy <= 256)
+    return run_id_big<S>(h, lv, a, mrows, st);
   size_t smem = a.smem_path ? mbytes + extra : extra;
   if (smem > 227 * 1024) return fail(RS_ERR_ARG, "box too large for shared staging (m=%d n=%d)", a.mmax, a.nmax);
   if (!a.smem_path) {
@@ -547,6 +1263,70 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
   return RS_OK;
 }
 
+// Big boxes (n <= 512): many CTAs per box, one launch per pivot step.
+template <class S>
+int run_factor_big(Handle* h, Level& lv, FaArgs a, const Level* child, double by, cudaStream_t st) {
+  const int nb = lv.nbox;
+  std::vector<int64_t> bo(nb);
+  int64_t acc = 0;
+  int maxk = 1;
+  for (int b = 0; b < nb; ++b) {
+    int64_t n = lv.h_n[b], k = lv.h_k[b];
+    bo[b] = acc;
+    acc += 2 * n * n + n * k + k * k + 2 * n + n;   // A | Dinv | X | Y | pivot buffers | pivots
+    maxk = std::max<int>(maxk, (int)k);
+  }
+  BigArgs g{};
+  g.n_box = nb;
+  g.n = lv.n;
+  g.k = lv.k;
+  int64_t* dbo;
+  RS_TRY(upload(h, &dbo, bo, st));
+  g.bo = dbo;
+  S* ws = nullptr;
+  int* idx = nullptr;
+  const int maxn = lv.maxn;
+  RS_CUDA(cudaMallocAsync((void**)&ws, sizeof(S) * std::max<int64_t>(1, acc), st));
+  RS_CUDA(cudaMallocAsync((void**)&idx, sizeof(int) * (size_t)nb * maxn, st));
+  const S* cL = child ? (const S*)child->Lam : nullptr;
+  double fl = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    double n = lv.h_n[b], k = lv.h_k[b];
+    fl += factor_flops(n, k) - n * n * n - k * k * k;
+  }
+  if (is_cplx<S>::value) fl *= 4.0;
+  prof_begin(P_FACTOR, st);
+  k_bb_assemble<S><<<nb * maxn, BB_NT, 0, st>>>(a, g, cL, ws, maxn);
+  RS_CHECK_LAUNCH();
+  const int ncb = div_up(maxn, BB_CB);
+  for (int j = 0; j < maxn; ++j) {
+    k_bb_gj_step<S, DimsD><<<nb * ncb, BB_NT, 0, st>>>(g, ws, DimsD{}, j, ncb, a.bad);
+    RS_CHECK_LAUNCH();
+  }
+  k_bb_unscramble<S, DimsD><<<nb, BB_NT, 0, st>>>(g, ws, DimsD{}, (S*)nullptr, 0, idx, maxn);
+  RS_CHECK_LAUNCH();
+  if (lv.maxk > 0) {
+    k_bb_X<S><<<nb * maxk, BB_NT, 0, st>>>(a, g, (const S*)lv.T, ws, maxk);
+    RS_CHECK_LAUNCH();
+    k_bb_Y<S><<<nb * maxk, BB_NT, 0, st>>>(a, g, (const S*)lv.T, ws, maxk);
+    RS_CHECK_LAUNCH();
+    const int nck = div_up(maxk, BB_CB);
+    DimsY dy{lv.lamoff};
+    for (int j = 0; j < maxk; ++j) {
+      k_bb_gj_step<S, DimsY><<<nb * nck, BB_NT, 0, st>>>(g, ws, dy, j, nck, a.bad);
+      RS_CHECK_LAUNCH();
+    }
+    k_bb_unscramble<S, DimsY><<<nb, BB_NT, 0, st>>>(g, ws, dy, (S*)lv.Lam, 1, idx, maxn);
+    RS_CHECK_LAUNCH();
+  }
+  k_bb_products<S><<<nb * maxn, BB_NT, 0, st>>>(a, g, ws, (const S*)lv.Lam, (S*)lv.U, (S*)lv.Lf, maxn);
+  RS_CHECK_LAUNCH();
+  prof_end(P_FACTOR, st, by, fl);
+  RS_CUDA(cudaFreeAsync(ws, st));
+  RS_CUDA(cudaFreeAsync(idx, st));
+  return RS_OK;
+}
+
 template <class S>
 int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t st) {
   // workspace: [D | I] (2 n^2) + X (n k) + [PX | I] (2 k^2)
@@ -557,6 +1337,32 @@ int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t 
     wsoff[b] = acc;
     acc += 2 * n * n + n * k + 2 * k * k;
   }
+  // shared-memory path when every box's D, X and Lambda fit
+  size_t sm_need = 0;
+  for (int b = 0; b < lv.nbox; ++b) {
+    size_t n = lv.h_n[b], k = lv.h_k[b];
+    sm_need = std::max(sm_need, sizeof(S) * (n * n + n * k + k * k + n) + sizeof(int) * n + 16);
+  }
+  const bool smem_path = sm_need <= 200 * 1024;
+  double fl0 = 0.0, by0 = 0.0;
+  for (int b = 0; b < lv.nbox; ++b) {
+    double n = lv.h_n[b], k = lv.h_k[b];
+    fl0 += factor_flops(n, k) - (smem_path ? n * n * n + k * k * k : 0.0);   // in-place GJ: n^3 MACs
+    by0 += (double)sizeof(S) * ((n + k) * n + n * k + k * k);
+  }
+  if (is_cplx<S>::value) fl0 *= 4.0;
+  if (smem_path) {
+    RS_CUDA(cudaFuncSetAttribute(k_factor_smem<S, FA_SM_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm_need));
+    prof_begin(P_FACTOR, st);
+    k_factor_smem<S, FA_SM_NT><<<lv.nbox, FA_SM_NT, sm_need, st>>>(a, (const S*)lv.T,
+                                                                    child ? (const S*)child->Lam : nullptr,
+                                                                    (S*)lv.U, (S*)lv.Lf, (S*)lv.Lam);
+    RS_CHECK_LAUNCH();
+    prof_end(P_FACTOR, st, by0, fl0);
+    return RS_OK;
+  }
+  if (lv.maxn <= 512) return run_factor_big<S>(h, lv, a, child, by0, st);
   int64_t* dws;
   RS_TRY(upload(h, &dws, wsoff, st));
   a.wsoff = dws;
@@ -599,6 +1405,8 @@ int alloc_factors(Handle* h, Level& lv, cudaStream_t st) {
     lamoff[b] = lams; lams += k * k;
   }
   lv.usz = us; lv.lsz = ls; lv.lamsz = lams;
+  lv.h_uoff = uoff;
+  lv.h_loff = loff;
   RS_TRY(upload(h, &lv.uoff, uoff, st));
   RS_TRY(upload(h, &lv.loff, loff, st));
   RS_TRY(upload(h, &lv.lamoff, lamoff, st));
@@ -627,6 +1435,7 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st) {
       off[b] = lv.h_begin[b];
     }
     lv.ntot = h->N;
+    lv.h_off = off;
     RS_TRY(upload(h, &lv.n, lv.h_n, st));
     RS_TRY(upload(h, &lv.off, off, st));
   }
@@ -698,6 +1507,7 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st) {
     lv.maxk = std::max(lv.maxk, lv.h_k[b]);
   }
   lv.ksum = kacc;
+  lv.h_skoff = skoff;
   RS_TRY(upload(h, &lv.skoff, skoff, st));
 
   // factor
@@ -741,6 +1551,7 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st) {
     if (upoff[p] < 0) upoff[p] = skoff[b];
     up.h_n[p] += lv.h_k[b];
   }
+  up.h_off = upoff;
   RS_TRY(upload(h, &up.n, up.h_n, st));
   RS_TRY(upload(h, &up.off, upoff, st));
   return RS_OK;
@@ -754,6 +1565,7 @@ int factor_root(Handle* h, cudaStream_t st) {
     lv.h_n.assign(1, (int)h->N);
     lv.ntot = h->N;
     std::vector<int64_t> off(1, 0);
+    lv.h_off = off;
     RS_TRY(upload(h, &lv.n, lv.h_n, st));
     RS_TRY(upload(h, &lv.off, off, st));
   }

@@ -320,6 +320,7 @@ int ensure_work(Handle* h, int prec, int R, cudaStream_t st) {
   }
   w.R = R;
   w.prec = prec;
+  ++w.gen;
   return RS_OK;
 }
 
@@ -483,6 +484,8 @@ int residual_impl(Handle* h, const S* b, const S* x, S* r, int R, double* rn2, c
 }
 
 }  // namespace
+
+int ensure_work_pub(Handle* h, int prec, int R, cudaStream_t st) { return ensure_work(h, prec, R, st); }
 
 int solve_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, void* d_X, int64_t ldx,
                  cudaStream_t st) {

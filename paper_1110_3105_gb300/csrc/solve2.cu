@@ -1,0 +1,517 @@
+// Persistent, dependency-driven solve: the whole upward pass, the root and
+// the downward pass (eq. multilevel-inverse applied right to left, Sec. 4.3)
+// in one kernel launch.
+//
+// Work is cut into tiles of at most 32 rows x CT columns of one box's block
+// product:
+//   up tile    rows of [calD ; calR] b   (box b of depth d >= 1; its rows
+//              beyond n land in the parent's input vector)
+//   root tile  rows of calS^-1 c          (depth 0)
+//   down tile  rows of u + calL x_parent  (depth d >= 1)
+// Tiles are listed in topological order (leaves first, then up to the root,
+// then down to the leaves) and handed out to warps by an atomic counter, so a
+// warp only ever waits on tiles that were handed out before its own and are
+// being worked on by resident warps.  A box's up tiles wait until every up
+// tile of its children has finished (one counter per box); a down tile waits
+// until every down (or root) tile of its parent has finished.  Counters grow
+// monotonically across solves (target = epoch * count), waits are bounded
+// spins: past the limit a warp sets the error flag and leaves, and so in turn
+// does every warp waiting on it.
+//
+// Lanes own rows (column-major factors -> coalesced loads); every lane keeps
+// CT accumulators for the tile's columns; the right-hand-side rows of the box
+// are staged 32 at a time in per-warp shared memory.  Leaf tiles read B and
+// write X in the caller's order through the tree permutation.
+#include <algorithm>
+#include <cuda/atomic>
+#include <vector>
+
+#include "rs_internal.h"
+
+namespace rs {
+
+namespace {
+
+constexpr int P_NT = 256;
+constexpr int P_WARPS = P_NT / 32;
+constexpr int MAX_SPIN = 1 << 22;
+
+enum TileKind { T_UP = 0, T_ROOT = 1, T_DOWN = 2 };
+
+struct Tile {
+  int g;      // global box index
+  int r0;     // first row
+  int c0;     // columns [c0, c1)
+  int c1;
+  int kind;
+};
+
+// Per global box (all depths concatenated, leaves first).
+struct BoxTab {
+  int* depth;
+  int* n;
+  int* k;
+  int64_t* off;
+  int64_t* skoff;
+  int64_t* uoff;
+  int64_t* loff;
+  int* parent;      // global index of the parent (-1 for the root)
+  int* up_need;     // up tiles of all children
+  int* dn_need;     // own down tiles (root: root tiles)
+};
+
+template <class S>
+struct Plan {
+  const Tile* tiles;
+  int ntiles;
+  BoxTab bt;
+  int L;
+  const int* perm;
+  S* const* v;          // per depth: input of the up pass (v[L] unused: B is read directly)
+  S* const* u;          // per depth: calD b, then x
+  const S* const* U;    // per depth factors
+  const S* const* Lf;
+  int* dispatch;
+  int* up_cnt;
+  int* dn_cnt;
+};
+
+__device__ inline int ld_acquire(const int* p) {
+  cuda::atomic_ref<const int, cuda::thread_scope_device> a(*p);
+  return a.load(cuda::memory_order_acquire);
+}
+
+// Lane 0 waits until *cnt >= target; returns false (and raises the flag) on timeout.
+__device__ inline bool wait_at_least(const int* cnt, int target, int* flag) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) {
+    int spins = 0;
+    while (ld_acquire(cnt) < target) {
+      if (++spins > MAX_SPIN) {
+        atomicExch(flag, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(100);
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  return ok != 0;
+}
+
+__device__ inline void signal(int* cnt) {
+  __threadfence();
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) atomicAdd(cnt, 1);
+}
+
+template <class S> __device__ inline S ldcg(const S* p) { return __ldcg(p); }
+template <> __device__ inline c128 ldcg<c128>(const c128* p) {
+  double2 t = __ldcg(reinterpret_cast<const double2*>(p));
+  return c128(t.x, t.y);
+}
+template <> __device__ inline c64 ldcg<c64>(const c64* p) {
+  float2 t = __ldcg(reinterpret_cast<const float2*>(p));
+  return c64(t.x, t.y);
+}
+
+// Read-only (non-coherent) loads for the factors, which no kernel writes
+// during a solve.
+template <class S> __device__ inline S ldro(const S* p) { return __ldg(p); }
+template <> __device__ inline c128 ldro<c128>(const c128* p) {
+  double2 t = __ldg(reinterpret_cast<const double2*>(p));
+  return c128(t.x, t.y);
+}
+template <> __device__ inline c64 ldro<c64>(const c64* p) {
+  float2 t = __ldg(reinterpret_cast<const float2*>(p));
+  return c64(t.x, t.y);
+}
+
+template <class D, class S> __device__ inline D cv(S v) { return D(v); }
+template <> __device__ inline float cv<float, double>(double v) { return (float)v; }
+template <> __device__ inline double cv<double, float>(float v) { return (double)v; }
+template <> __device__ inline c64 cv<c64, c128>(c128 v) { return c64((float)v.re, (float)v.im); }
+template <> __device__ inline c128 cv<c128, c64>(c64 v) { return c128((double)v.re, (double)v.im); }
+
+// acc[c] += sum_{q < qn} col[q * ld] * stage[q][c] for one 32-column chunk.
+// All factor loads of the chunk are issued before the FMAs (QB at a time)
+// so a lane keeps up to QB loads in flight instead of one per iteration.
+template <class S, int CT>
+__device__ __forceinline__ void chunk_fma(const S* col, size_t ld, int qn, const S* stage, S* acc) {
+  constexpr int QB = CT == 1 ? 32 : (CT <= 8 ? 16 : 8);
+  for (int q0 = 0; q0 < qn; q0 += QB) {
+    S a[QB];
+#pragma unroll
+    for (int j = 0; j < QB; ++j) a[j] = (q0 + j < qn) ? ldro(col + (size_t)(q0 + j) * ld) : S(0.0);
+#pragma unroll
+    for (int j = 0; j < QB; ++j) {
+#pragma unroll
+      for (int c = 0; c < CT; ++c) acc[c] += a[j] * stage[(q0 + j) * CT + c];
+    }
+  }
+}
+
+template <class S, class SIO, int CT>
+__global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, int64_t ldb, SIO* X, int64_t ldx,
+                                                     int R, int epoch, int* flag) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  S* stage = reinterpret_cast<S*>(smem) + (size_t)warp * 32 * CT;   // [32][CT]
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(p.dispatch, 1);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= p.ntiles) break;
+    const Tile tl = p.tiles[t];
+    const int g = tl.g;
+    const int d = p.bt.depth[g];
+    const int n = p.bt.n[g], k = p.bt.k[g];
+    const int64_t off = p.bt.off[g];
+
+    if (tl.kind != T_DOWN) {
+      // ---- up / root tile: rows of U b, U = [calD ; calR] ((n+k) x n)
+      if (p.bt.up_need[g] > 0 && !wait_at_least(&p.up_cnt[g], epoch * p.bt.up_need[g], flag)) return;
+      const int rows = n + k;
+      const int r = tl.r0 + lane;
+      const S* Ub = p.U[d] + p.bt.uoff[g];
+      const bool leaf = d == p.L;
+      const S* vin = leaf ? nullptr : p.v[d];
+      for (int c0 = tl.c0; c0 < tl.c1; c0 += CT) {
+        const int cw = min(CT, tl.c1 - c0);
+        S acc[CT];
+#pragma unroll
+        for (int c = 0; c < CT; ++c) acc[c] = S(0.0);
+        for (int q0 = 0; q0 < n; q0 += 32) {
+          const int qn = min(32, n - q0);
+          if (lane >= qn) {   // rows past the chunk end stay zero (chunk_fma reads them times 0)
+#pragma unroll
+            for (int c = 0; c < CT; ++c) stage[lane * CT + c] = S(0.0);
+          } else {
+            const int64_t pos = off + q0 + lane;
+            if (leaf) {
+              const int64_t src = p.perm[pos];
+#pragma unroll
+              for (int c = 0; c < CT; ++c)
+                stage[lane * CT + c] = c < cw ? cv<S, SIO>(B[src + (int64_t)(c0 + c) * ldb]) : S(0.0);
+            } else {
+#pragma unroll
+              for (int c = 0; c < CT; ++c)
+                stage[lane * CT + c] = c < cw ? ldcg(vin + pos * R + c0 + c) : S(0.0);
+            }
+          }
+          __syncwarp();
+          if (r < rows) chunk_fma<S, CT>(Ub + r + (size_t)q0 * rows, (size_t)rows, qn, stage, acc);
+          __syncwarp();
+        }
+        if (r < rows) {
+          if (r < n && tl.kind == T_ROOT && d == p.L) {   // single-box tree: the root is the answer
+            const int64_t dst = p.perm[off + r];
+#pragma unroll
+            for (int c = 0; c < CT; ++c)
+              if (c < cw) X[dst + (int64_t)(c0 + c) * ldx] = cv<SIO, S>(acc[c]);
+          } else if (r < n) {
+            S* uo = p.u[d] + (off + r) * R + c0;
+#pragma unroll
+            for (int c = 0; c < CT; ++c)
+              if (c < cw) uo[c] = acc[c];
+          } else {
+            S* vo = p.v[d - 1] + (p.bt.skoff[g] + (r - n)) * R + c0;
+#pragma unroll
+            for (int c = 0; c < CT; ++c)
+              if (c < cw) vo[c] = acc[c];
+          }
+        }
+      }
+      if (tl.kind == T_ROOT) signal(&p.dn_cnt[g]);
+      else signal(&p.up_cnt[p.bt.parent[g]]);
+    } else {
+      // ---- down tile: rows of u + calL x_parent (n x k)
+      const int par = p.bt.parent[g];
+      if (!wait_at_least(&p.dn_cnt[par], epoch * p.bt.dn_need[par], flag)) return;
+      const int r = tl.r0 + lane;
+      const S* Lb = p.Lf[d] + p.bt.loff[g];
+      const S* xpar = p.u[d - 1] + p.bt.skoff[g] * R;
+      for (int c0 = tl.c0; c0 < tl.c1; c0 += CT) {
+        const int cw = min(CT, tl.c1 - c0);
+        S acc[CT];
+#pragma unroll
+        for (int c = 0; c < CT; ++c) acc[c] = S(0.0);
+        for (int q0 = 0; q0 < k; q0 += 32) {
+          const int qn = min(32, k - q0);
+#pragma unroll
+          for (int c = 0; c < CT; ++c)
+            stage[lane * CT + c] = (lane < qn && c < cw) ? ldcg(xpar + (int64_t)(q0 + lane) * R + c0 + c) : S(0.0);
+          __syncwarp();
+          if (r < n) chunk_fma<S, CT>(Lb + r + (size_t)q0 * n, (size_t)n, qn, stage, acc);
+          __syncwarp();
+        }
+        if (r < n) {
+          if (d == p.L) {
+            const int64_t dst = p.perm[off + r];
+            const S* uo = p.u[d] + (off + r) * R + c0;
+#pragma unroll
+            for (int c = 0; c < CT; ++c)
+              if (c < cw) X[dst + (int64_t)(c0 + c) * ldx] = cv<SIO, S>(ldcg(uo + c) + acc[c]);
+          } else {
+            S* uo = p.u[d] + (off + r) * R + c0;
+#pragma unroll
+            for (int c = 0; c < CT; ++c)
+              if (c < cw) uo[c] = ldcg(uo + c) + acc[c];
+          }
+        }
+      }
+      signal(&p.dn_cnt[g]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------- host
+struct PersPlan {
+  int prec = -1, R = 0, CT = 0;
+  int ntiles = 0, nbox = 0;
+  Tile* tiles = nullptr;
+  BoxTab bt{};
+  int* counters = nullptr;   // dispatch | up_cnt[G] | dn_cnt[G]
+  int epoch = 0;
+  void** ptrs = nullptr;     // v[L+1] | u[L+1] | U[L+1] | Lf[L+1]
+  int* flag_host = nullptr;  // mapped pinned
+  int* flag_dev = nullptr;
+  int grid = 0;
+  int work_gen = -1;         // generation of the work buffers captured in ptrs
+  std::vector<void*> mem;
+};
+
+struct PersCache {
+  std::vector<PersPlan*> plans;
+};
+
+int ct_for(bool cplx, int prec, int R) {
+  if (R == 1) return 1;
+  if (R <= 8) return 8;
+  if (prec == RS_PREC_FP64) return cplx ? 8 : 16;
+  return cplx ? 16 : 32;
+}
+
+template <class T>
+int dev_upload(PersPlan* P, T** d, const std::vector<T>& v, cudaStream_t st) {
+  RS_CUDA(cudaMalloc((void**)d, sizeof(T) * std::max<size_t>(1, v.size())));
+  P->mem.push_back(*d);
+  if (!v.empty()) RS_CUDA(cudaMemcpyAsync(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+  return RS_OK;
+}
+
+template <class S, class SIO, int CT>
+int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X, int64_t ldx, cudaStream_t st) {
+  size_t smem = sizeof(S) * 32 * CT * P_WARPS;
+  if (smem > 48 * 1024)
+    RS_CUDA(cudaFuncSetAttribute(k_solve_pers<S, SIO, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (P->grid == 0) {
+    int dev = 0, nsm = 0, occ = 0;
+    RS_CUDA(cudaGetDevice(&dev));
+    RS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_pers<S, SIO, CT>, P_NT, smem));
+    P->grid = std::max(1, std::min(nsm * std::max(occ, 1), div_up(P->ntiles, P_WARPS)));
+  }
+  if (++P->epoch > (1 << 20)) {
+    RS_CUDA(cudaMemsetAsync(P->counters, 0, sizeof(int) * (1 + 2 * (size_t)P->nbox), st));
+    P->epoch = 1;
+  }
+  RS_CUDA(cudaMemsetAsync(P->counters, 0, sizeof(int), st));
+  Plan<S> pl;
+  pl.tiles = P->tiles;
+  pl.ntiles = P->ntiles;
+  pl.bt = P->bt;
+  pl.L = h->L;
+  pl.perm = h->perm;
+  const int L1 = h->L + 1;
+  pl.v = (S* const*)P->ptrs;
+  pl.u = (S* const*)(P->ptrs + L1);
+  pl.U = (const S* const*)(P->ptrs + 2 * L1);
+  pl.Lf = (const S* const*)(P->ptrs + 3 * L1);
+  pl.dispatch = P->counters;
+  pl.up_cnt = P->counters + 1;
+  pl.dn_cnt = P->counters + 1 + P->nbox;
+  *P->flag_host = 0;
+  prof_begin(prec_cat(P->prec), st);
+  k_solve_pers<S, SIO, CT><<<P->grid, P_NT, smem, st>>>(pl, B, ldb, X, ldx, R, P->epoch, P->flag_dev);
+  RS_CHECK_LAUNCH();
+  double sS = sizeof(S), fac = 0.0;
+  for (auto& lv : h->lv) fac += (double)lv.usz + (double)lv.lsz;
+  prof_end(prec_cat(P->prec), st, sS * fac + (double)R * h->N * 2.0 * sizeof(SIO),
+           2.0 * (is_cplx<S>::value ? 4.0 : 1.0) * fac * R);
+  return RS_OK;
+}
+
+}  // namespace
+
+int prec_cat(int prec) { return prec == RS_PREC_FP64 ? P_SOLVE64 : P_SOLVE32; }
+
+void free_pers(Handle* h) {
+  PersCache* c = (PersCache*)h->pers;
+  if (!c) return;
+  for (PersPlan* P : c->plans) {
+    for (void* m : P->mem) cudaFree(m);
+    if (P->flag_host) cudaFreeHost(P->flag_host);
+    delete P;
+  }
+  delete c;
+  h->pers = nullptr;
+}
+
+// Device pointer table of a plan: the work vectors (which may have been
+// regrown for a larger R since the plan was made) and the factors.
+static int refresh_ptrs(Handle* h, PersPlan* P, cudaStream_t st) {
+  const int L = h->L;
+  const Handle::Work& w = h->work[P->prec];
+  std::vector<void*> ptrs(4 * (L + 1));
+  for (int d = 0; d <= L; ++d) {
+    ptrs[d] = w.v[d];
+    ptrs[(L + 1) + d] = w.u[d];
+    ptrs[2 * (L + 1) + d] = P->prec == RS_PREC_FP64 ? h->lv[d].U : h->lv[d].U32;
+    ptrs[3 * (L + 1) + d] = P->prec == RS_PREC_FP64 ? h->lv[d].Lf : h->lv[d].Lf32;
+  }
+  if (!P->ptrs) {
+    RS_CUDA(cudaMalloc((void**)&P->ptrs, sizeof(void*) * ptrs.size()));
+    P->mem.push_back(P->ptrs);
+  }
+  RS_CUDA(cudaMemcpyAsync(P->ptrs, ptrs.data(), sizeof(void*) * ptrs.size(), cudaMemcpyHostToDevice, st));
+  RS_CUDA(cudaStreamSynchronize(st));
+  P->work_gen = w.gen;
+  return RS_OK;
+}
+
+// Tile list and counters for (precision, R); built once per handle.
+static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out) {
+  if (!h->pers) h->pers = new PersCache();
+  PersCache* c = (PersCache*)h->pers;
+  RS_TRY(ensure_work_pub(h, prec, R, st));
+  for (PersPlan* P : c->plans)
+    if (P->prec == prec && P->R == R) {
+      if (P->work_gen != h->work[prec].gen) RS_TRY(refresh_ptrs(h, P, st));
+      *out = P;
+      return RS_OK;
+    }
+  PersPlan* P = new PersPlan();
+  c->plans.push_back(P);
+  P->prec = prec;
+  P->R = R;
+  P->CT = ct_for(h->cplx, prec, R);
+  const int L = h->L;
+  // global box numbering: depth L first, ..., depth 0 last
+  std::vector<int> gbase(L + 1);
+  int G = 0;
+  for (int d = L; d >= 0; --d) { gbase[d] = G; G += h->lv[d].nbox; }
+  P->nbox = G;
+  std::vector<int> depth(G), n(G), k(G), parent(G), up_need(G, 0), dn_need(G, 0);
+  std::vector<int64_t> off(G), skoff(G), uoff(G), loff(G);
+  for (int d = 0; d <= L; ++d) {
+    const Level& lv = h->lv[d];
+    for (int b = 0; b < lv.nbox; ++b) {
+      int g = gbase[d] + b;
+      depth[g] = d;
+      n[g] = lv.h_n[b];
+      k[g] = lv.h_k[b];
+      off[g] = lv.h_off[b];
+      skoff[g] = d > 0 ? lv.h_skoff[b] : 0;
+      uoff[g] = lv.h_uoff[b];
+      loff[g] = d > 0 ? lv.h_loff[b] : 0;
+      parent[g] = d > 0 ? gbase[d - 1] + lv.h_parent[b] : -1;
+    }
+  }
+  // Column ranges per depth: a depth with few row tiles splits its columns
+  // (in CT-aligned ranges) so that its tiles still fill the GPU.
+  const int nchunk = div_up(R, P->CT);
+  auto col_ranges = [&](int d, bool down) {
+    const Level& lv = h->lv[d];
+    int64_t rt = 0;
+    for (int b = 0; b < lv.nbox; ++b) rt += div_up(down ? lv.h_n[b] : lv.h_n[b] + lv.h_k[b], 32);
+    int split = (int)std::max<int64_t>(1, std::min<int64_t>(nchunk, 8192 / std::max<int64_t>(1, rt)));
+    int per = div_up(nchunk, split) * P->CT;
+    std::vector<std::pair<int, int>> cr;
+    for (int c = 0; c < R; c += per) cr.push_back({c, std::min(R, c + per)});
+    return cr;
+  };
+  std::vector<Tile> tiles;
+  for (int d = L; d >= 1; --d) {
+    auto cr = col_ranges(d, false);
+    for (int b = 0; b < h->lv[d].nbox; ++b) {
+      int g = gbase[d] + b;
+      for (int r0 = 0; r0 < n[g] + k[g]; r0 += 32)
+        for (auto& c : cr) tiles.push_back(Tile{g, r0, c.first, c.second, T_UP});
+      up_need[parent[g]] += div_up(n[g] + k[g], 32) * (int)cr.size();
+    }
+  }
+  {
+    auto cr = col_ranges(0, false);
+    int g = gbase[0];
+    for (int r0 = 0; r0 < n[g]; r0 += 32)
+      for (auto& c : cr) tiles.push_back(Tile{g, r0, c.first, c.second, T_ROOT});
+    dn_need[g] = div_up(n[g], 32) * (int)cr.size();
+  }
+  for (int d = 1; d <= L; ++d) {
+    auto cr = col_ranges(d, true);
+    for (int b = 0; b < h->lv[d].nbox; ++b) {
+      int g = gbase[d] + b;
+      for (int r0 = 0; r0 < n[g]; r0 += 32)
+        for (auto& c : cr) tiles.push_back(Tile{g, r0, c.first, c.second, T_DOWN});
+      dn_need[g] = div_up(n[g], 32) * (int)cr.size();
+    }
+  }
+  P->ntiles = (int)tiles.size();
+  RS_TRY(dev_upload(P, &P->tiles, tiles, st));
+  RS_TRY(dev_upload(P, &P->bt.depth, depth, st));
+  RS_TRY(dev_upload(P, &P->bt.n, n, st));
+  RS_TRY(dev_upload(P, &P->bt.k, k, st));
+  RS_TRY(dev_upload(P, &P->bt.off, off, st));
+  RS_TRY(dev_upload(P, &P->bt.skoff, skoff, st));
+  RS_TRY(dev_upload(P, &P->bt.uoff, uoff, st));
+  RS_TRY(dev_upload(P, &P->bt.loff, loff, st));
+  RS_TRY(dev_upload(P, &P->bt.parent, parent, st));
+  RS_TRY(dev_upload(P, &P->bt.up_need, up_need, st));
+  RS_TRY(dev_upload(P, &P->bt.dn_need, dn_need, st));
+  std::vector<int> zeros(1 + 2 * (size_t)G, 0);
+  RS_TRY(dev_upload(P, &P->counters, zeros, st));
+  RS_TRY(refresh_ptrs(h, P, st));
+  RS_CUDA(cudaHostAlloc((void**)&P->flag_host, sizeof(int), cudaHostAllocMapped));
+  *P->flag_host = 0;
+  RS_CUDA(cudaHostGetDevicePointer((void**)&P->flag_dev, P->flag_host, 0));
+  RS_CUDA(cudaStreamSynchronize(st));
+  *out = P;
+  return RS_OK;
+}
+
+template <class S, class SIO>
+static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO* X, int64_t ldx, cudaStream_t st) {
+  PersPlan* P = nullptr;
+  RS_TRY(get_plan(h, prec, R, st, &P));
+  switch (P->CT) {
+    case 1: RS_TRY((launch_pers<S, SIO, 1>(h, P, B, ldb, R, X, ldx, st))); break;
+    case 8: RS_TRY((launch_pers<S, SIO, 8>(h, P, B, ldb, R, X, ldx, st))); break;
+    case 16: RS_TRY((launch_pers<S, SIO, 16>(h, P, B, ldb, R, X, ldx, st))); break;
+    case 32: RS_TRY((launch_pers<S, SIO, 32>(h, P, B, ldb, R, X, ldx, st))); break;
+    default: return fail(RS_ERR_ARG, "bad column tile");
+  }
+  h->pers_last = P;
+  return RS_OK;
+}
+
+int solve_pers_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, void* d_X, int64_t ldx,
+                      cudaStream_t st) {
+  if (h->cplx) {
+    if (prec == RS_PREC_FP64) return pers_impl<c128, c128>(h, prec, (const c128*)d_B, ldb, nrhs, (c128*)d_X, ldx, st);
+    return pers_impl<c64, c128>(h, prec, (const c128*)d_B, ldb, nrhs, (c128*)d_X, ldx, st);
+  }
+  if (prec == RS_PREC_FP64) return pers_impl<double, double>(h, prec, (const double*)d_B, ldb, nrhs, (double*)d_X, ldx, st);
+  return pers_impl<float, double>(h, prec, (const double*)d_B, ldb, nrhs, (double*)d_X, ldx, st);
+}
+
+// After the stream has been synchronized: timeout flag of the last solve.
+int pers_check(Handle* h) {
+  PersPlan* P = (PersPlan*)h->pers_last;
+  if (P && P->flag_host && *(volatile int*)P->flag_host)
+    return fail(RS_ERR_TIMEOUT, "solve: a dependency wait ran out (flag set by the device)");
+  return RS_OK;
+}
+
+}  // namespace rs

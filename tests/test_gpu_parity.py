@@ -148,6 +148,12 @@ def test_fp32_solve_and_refinement(built):
     assert np.all(rel <= 1e-10), rel
     assert its >= 1
     assert np.linalg.norm(Xr - X64) / np.linalg.norm(X64) < 1e-9
+    # the reported residual is what an independent FP64 apply of A_RS measures
+    Y = np.zeros_like(Xr)
+    rs.rs_matvec(built["H"], Xr, Y)
+    true_rel = np.linalg.norm(Y - B, axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(true_rel <= 1e-10), true_rel
+    assert np.all(np.abs(true_rel - rel) <= 1e-12 + 1e-3 * true_rel), (true_rel, rel)
 
 
 def test_device_pointers_same_as_host(built):
