@@ -160,6 +160,59 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def serving_session(rs, torch, P, h, w, window_s=1.0, rate=2000.0, seed=7):
+    """Poisson arrivals (mean `rate` req/s, 1..64 columns each) for `window_s`
+    seconds against the resident factorization, plus one memory-admitted
+    build of a random starfish (serving mix form); returns RHS/s and
+    latency percentiles of the completed requests."""
+    n = w["n"]
+    H = rs.rs_build(P, "laplace2d", h, w["eps"], w["leaf"], w["nproxy"])
+    S = rs.Server(max_cols=NRHS)
+    hid = S.add(H)
+    # warm the server's buffers with one full batch
+    Bw = torch.from_numpy(ri.rhs(n, NRHS, seed=900)).t().contiguous().pin_memory().t()
+    Xw = torch.empty((NRHS, n), dtype=torch.float64).pin_memory().t()
+    S.wait(S.submit(hid, Bw, Xw))
+    nb, arms, amp, rot = ri.serving_curve(seed, 0)
+    pts2, h2 = ri.starfish(16384, arms=arms, amp=amp, rotation=rot)
+    bt = S.submit_build(pts2, "laplace2d", h2, w["eps"], w["leaf"], w["nproxy"])
+    S.reset_stats()
+    u = ri.uniform01(seed, 200000, stream=7)
+    gaps = -np.log(u) / rate
+    cols = 1 + (ri.uniform01(seed, 200000, stream=8) * 64).astype(int).clip(0, 63)
+    B = torch.from_numpy(ri.rhs(n, 64, seed=901)).t().contiguous().pin_memory().t()
+    ring = [torch.empty((64, n), dtype=torch.float64).pin_memory().t() for _ in range(8)]
+    tickets, i = [], 0
+    t0 = time.perf_counter()
+    t_next = t0
+    while True:
+        now = time.perf_counter()
+        if now - t0 >= window_s:
+            break
+        if now < t_next:
+            time.sleep(min(t_next - now, 0.0005))
+            continue
+        c = int(cols[i])
+        tickets.append(S.submit(hid, B[:, :c], ring[i % len(ring)][:, :c]))
+        t_next += gaps[i]
+        i += 1
+    offered = sum(int(cols[j]) for j in range(i)) / window_s
+    worst, bad = 0.0, 0
+    for t in tickets:
+        r = S.wait(t)
+        bad += r["status"] != 0
+        worst = max(worst, r["relres"])
+    st = S.stats()
+    rb = S.wait(bt)
+    S.destroy()
+    H.free()
+    return {"rhs_per_s": st["rhs"] / st["elapsed_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "requests": st["requests"], "failed": bad, "mean_batch_cols": st["mean_batch_cols"],
+            "offered_rhs_per_s": offered, "arrival_rate_per_s": rate, "window_s": window_s,
+            "relres_max": worst, "admitted_build_status": rb["status"],
+            "note": "offered load above capacity: latency includes queueing"}
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_1110_3105_gb300 as rs
@@ -271,6 +324,8 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t) / e2e_steps
 
+    serving = serving_session(rs, torch, P, h, w) if not args.no_serve else None
+
     # roofline of the dominant kernel category in the timed region
     pk = peaks()
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
@@ -311,7 +366,9 @@ def run_ours(args, ws, rank, local):
         "resident_refined_ms_per_batch": refined_ms,
         "resident_refined_rhs_per_s": NRHS / (refined_ms / 1e3),
         "plain_fp64_rhs_per_s": 1e6 / plain_us,
-        "served_vs_plain": (NRHS / (refined_ms / 1e3)) / (1e6 / plain_us),
+        "batched_vs_plain": (NRHS / (refined_ms / 1e3)) / (1e6 / plain_us),
+        "serving": serving,
+        "served_vs_plain": (serving["rhs_per_s"] / (1e6 / plain_us)) if serving else None,
         "refine_iterations": itss,
         "relres_max": max(rels),
         "plain_fp64_relres": plain_rel,
@@ -324,6 +381,21 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+def profile_step():
+    """One build + one refined 256-column solve of the workload, nothing else."""
+    import torch
+    import paper_1110_3105_gb300 as rs
+    w, pts, h = workload_inputs()
+    P = torch.from_numpy(np.ascontiguousarray(pts.T)).cuda().t()
+    B = torch.from_numpy(ri.rhs(w["n"], NRHS, seed=100)).cuda().t().contiguous().t()
+    X = torch.zeros_like(B)
+    H = rs.rs_build(P, "laplace2d", h, w["eps"], w["leaf"], w["nproxy"])
+    its, rel = rs.rs_solve_refined(H, B, X, tol=TOL, max_it=8)
+    torch.cuda.synchronize()
+    H.free()
+    print(json.dumps({"profile_step": WORKLOAD, "refine_iterations": its, "relres_max": float(np.max(rel))}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -331,8 +403,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving session")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run exactly one step (build + refined solve) and exit: the command profiled by ncu")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
+    if args.profile_step:
+        profile_step()
+        return
     if args.impl == "reference":
         run_reference(args, ws, rank)
     else:

@@ -186,6 +186,66 @@ int rs_profile_record(int i, int* cat, double* ms, double* bytes, double* flops)
 /* Number of kernels the library has launched in this process so far. */
 int64_t rs_launch_count(void);
 
+/* ------------------------------------------------------------------ serving
+ * A server keeps factorizations resident and answers solve requests by
+ * continuous batching (the paper has no serving layer; it motivates one:
+ * Sec. 1 point (ii), many right-hand sides per factorization).  Every
+ * registered handle gets a worker thread and a stream; the worker repeatedly
+ * takes all requests queued for its handle (up to max_cols columns), packs
+ * them into one batch, runs rs_solve_refined on it and completes each
+ * request.  Requests arriving while a batch is on the GPU join the next
+ * batch; different handles' batches overlap on the device.  Builds submitted
+ * to the server run on a builder thread and are admitted only while the
+ * estimated device memory of the resident factorizations plus the new one
+ * stays under hbm_budget_bytes (<= 0: 90% of the free memory at creation);
+ * an inadmissible build completes with RS_ERR_OOM.
+ * B and X of a request are host buffers the caller keeps alive until the
+ * request is waited for.  A handle registered with a server must not be
+ * used directly while the server runs.  Latency = host time from submit to
+ * completion. */
+typedef struct rs_server_s* rs_server;
+typedef struct {
+  int64_t requests;        /* completed solve requests */
+  int64_t rhs;             /* columns solved */
+  int64_t batches;
+  double mean_batch_cols;
+  double p50_ms, p99_ms;   /* request latency percentiles */
+  double elapsed_s;        /* since creation or the last reset */
+  int handles;
+  int64_t resident_bytes;  /* estimated device memory of the resident handles */
+} rs_server_stats_t;
+
+int rs_server_create(int max_cols, int64_t hbm_budget_bytes, rs_server* out);
+/* Register a built handle (still owned by the caller); *handle_id names it. */
+int rs_server_add_handle(rs_server s, rs_handle h, int* handle_id);
+/* Queue a solve of ncols columns (tol: relative residual target). */
+int rs_server_submit_solve(rs_server s, int handle_id, const void* B, int64_t ldb, int ncols,
+                           void* X, int64_t ldx, double tol, int64_t* ticket);
+/* Queue a build; on success the request's result is the new handle id. */
+int rs_server_submit_build(rs_server s, const double* pts, int64_t n, int dim,
+                           const rs_params* params, double eps, int leaf, int64_t* ticket);
+/* Wait (up to timeout_s; <= 0 waits indefinitely) for a request; status is
+ * its rs_status, result the refinement count (solve) or the handle id
+ * (build).  Each ticket can be waited for once. */
+int rs_server_wait(rs_server s, int64_t ticket, double timeout_s, int* status,
+                   double* latency_ms, double* relres, int* result);
+int rs_server_stats(rs_server s, rs_server_stats_t* out);
+int rs_server_reset_stats(rs_server s);
+/* Handle behind an id (for builds made by the server). */
+int rs_server_handle(rs_server s, int handle_id, rs_handle* out);
+/* Drain the queues, stop the threads, free handles the server built. */
+int rs_server_destroy(rs_server s);
+
+/* Host-side fault injection for failure-path tests (no GPU fault is ever
+ * caused):
+ *   "alloc:n"  the n-th device allocation from now fails (RS_ERR_OOM);
+ *   "wait"     the next solve's dependency waits target a round of tiles
+ *              that never finishes, so the bounded spins run out, the kernel
+ *              raises its flag and leaves, and the call returns
+ *              RS_ERR_TIMEOUT; the next solve restarts its counters;
+ *   "off" / NULL  disarm. */
+int rs_set_fault(const char* spec);
+
 /* Release every resource of the handle.  NULL is accepted. */
 int rs_free(rs_handle h);
 

@@ -40,6 +40,12 @@ class rs_stats_t(ctypes.Structure):
                 ("max_box_n", ctypes.c_int), ("max_box_m", ctypes.c_int), ("max_rank", ctypes.c_int)]
 
 
+class rs_server_stats_t(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_int64), ("rhs", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("mean_batch_cols", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("elapsed_s", ctypes.c_double), ("handles", ctypes.c_int), ("resident_bytes", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _PROTOS = {
@@ -55,6 +61,20 @@ _PROTOS = {
     "rs_tree_level": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _P, _P, _P, _P]),
     "rs_box_ranks": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "rs_free": (ctypes.c_int, [_P]),
+    "rs_set_fault": (ctypes.c_int, [ctypes.c_char_p]),
+    "rs_server_create": (ctypes.c_int, [ctypes.c_int, _I64, ctypes.POINTER(_P)]),
+    "rs_server_add_handle": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "rs_server_submit_solve": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, ctypes.c_int, _P, _I64, ctypes.c_double,
+                                              ctypes.POINTER(_I64)]),
+    "rs_server_submit_build": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int, ctypes.POINTER(rs_params), ctypes.c_double,
+                                              ctypes.c_int, ctypes.POINTER(_I64)]),
+    "rs_server_wait": (ctypes.c_int, [_P, _I64, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "rs_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(rs_server_stats_t)]),
+    "rs_server_reset_stats": (ctypes.c_int, [_P]),
+    "rs_server_handle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "rs_server_destroy": (ctypes.c_int, [_P]),
     "rs_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "rs_profile_ncat": (ctypes.c_int, []),
     "rs_launch_count": (ctypes.c_int64, []),
@@ -260,6 +280,76 @@ def rs_profile_records() -> list:
 
 def rs_launch_count() -> int:
     return int(load().rs_launch_count())
+
+
+class Server:
+    """Continuous-batching solve server over resident factorizations (rs_server_*)."""
+
+    def __init__(self, max_cols: int = 256, hbm_budget_bytes: int = 0):
+        load()
+        out = ctypes.c_void_p()
+        _check(_lib.rs_server_create(int(max_cols), int(hbm_budget_bytes), ctypes.byref(out)))
+        self._s = out.value
+        self._keep = {}          # ticket -> buffers kept alive until waited
+        self._built = {}         # handle id -> Handle wrapper (not owned)
+
+    def add(self, h: Handle) -> int:
+        hid = ctypes.c_int()
+        _check(_lib.rs_server_add_handle(self._s, h.ptr, ctypes.byref(hid)))
+        return hid.value
+
+    def submit(self, hid: int, B, X, tol: float = 1e-10) -> int:
+        pb, nb, rb, ldb, _ = _ptr(B)
+        px, nx, rx, ldx, _ = _ptr(X)
+        t = ctypes.c_int64()
+        _check(_lib.rs_server_submit_solve(self._s, int(hid), pb, ldb, rb, px, ldx, float(tol), ctypes.byref(t)))
+        self._keep[t.value] = (B, X)
+        return t.value
+
+    def submit_build(self, points, kernel: str, weight: float, eps: float, leaf: int, proxy_n: int,
+                     proxy_ratio: float = 1.5, k_wave: float = 0.0) -> int:
+        pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).T)   # point-major
+        n, dim = pts.shape
+        p = rs_params(KERNELS[kernel], float(k_wave), float(weight), int(proxy_n), float(proxy_ratio))
+        t = ctypes.c_int64()
+        _check(_lib.rs_server_submit_build(self._s, pts.ctypes.data, n, dim, ctypes.byref(p), float(eps), int(leaf),
+                                           ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 0.0) -> dict:
+        st = ctypes.c_int()
+        lat = ctypes.c_double()
+        rel = ctypes.c_double()
+        res = ctypes.c_int()
+        _check(_lib.rs_server_wait(self._s, int(ticket), float(timeout_s), ctypes.byref(st), ctypes.byref(lat),
+                                   ctypes.byref(rel), ctypes.byref(res)))
+        self._keep.pop(ticket, None)
+        return dict(status=st.value, latency_ms=lat.value, relres=rel.value, result=res.value)
+
+    def stats(self) -> dict:
+        s = rs_server_stats_t()
+        _check(_lib.rs_server_stats(self._s, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in rs_server_stats_t._fields_}
+
+    def reset_stats(self):
+        _check(_lib.rs_server_reset_stats(self._s))
+
+    def destroy(self):
+        if self._s:
+            _lib.rs_server_destroy(self._s)
+            self._s = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def rs_set_fault(spec):
+    """Arm host-side fault injection: "alloc:n", "wait" or "off"."""
+    _check(load().rs_set_fault(None if spec is None else spec.encode()))
 
 
 def rs_free(h: Handle):

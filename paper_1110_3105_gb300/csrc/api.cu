@@ -3,6 +3,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <string>
@@ -36,8 +37,18 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+// Host-side fault injection (rs_set_fault): the n-th device allocation
+// fails, or the next persistent solve waits on a target no tile reaches.
+static std::atomic<long> g_fault_alloc{0};   // 0 = off, else allocations left before the failing one
+static std::atomic<int> g_fault_wait{0};
+
+bool take_wait_fault() { return g_fault_wait.exchange(0) != 0; }
+
 int dalloc(Handle* h, void** p, size_t bytes) {
   *p = nullptr;
+  long left = g_fault_alloc.load();
+  if (left > 0 && g_fault_alloc.fetch_sub(1) == 1)
+    return fail(RS_ERR_OOM, "cudaMalloc(%zu): injected allocation failure", bytes);
   cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -405,6 +416,27 @@ int rs_box_ranks(rs_handle h, int level, int* n, int* k) {
     if (k) k[b] = lv.h_k[b];
   }
   return RS_OK;
+}
+
+int rs_set_fault(const char* spec) {
+  rs::g_err.clear();
+  if (!spec || !*spec || std::string(spec) == "off") {
+    g_fault_alloc = 0;
+    g_fault_wait = 0;
+    return RS_OK;
+  }
+  std::string s(spec);
+  if (s == "wait") {
+    g_fault_wait = 1;
+    return RS_OK;
+  }
+  if (s.rfind("alloc:", 0) == 0) {
+    long n = std::atol(s.c_str() + 6);
+    if (n < 1) return fail(RS_ERR_ARG, "rs_set_fault: alloc:n needs n >= 1");
+    g_fault_alloc = n;
+    return RS_OK;
+  }
+  return fail(RS_ERR_ARG, "rs_set_fault: unknown fault '%s'", spec);
 }
 
 int rs_free(rs_handle h) {

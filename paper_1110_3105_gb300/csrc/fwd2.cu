@@ -73,7 +73,6 @@ __device__ __forceinline__ void add(df& s, df b) {
 }
 
 constexpr int F_NT = 256;
-constexpr int F_CT = 32;   // columns per CTA (one per lane)
 
 struct FwdTab {
   const int* n;
@@ -143,7 +142,8 @@ __device__ void tile_gemm(const df* A, int64_t sa_o, int64_t sa_q, int nout, int
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wr = warp / WC, wc = warp % WC;
   const int cbase = wc * CT;
-  for (int o0 = 0; o0 < nout; o0 += 32 * WR) {
+  // row chunks of 32 WR rows are spread over the grid (blockIdx.y)
+  for (int o0 = blockIdx.y * 32 * WR; o0 < nout; o0 += gridDim.y * 32 * WR) {
     const int o = o0 + wr * 32 + lane;
     df acc[CT];
 #pragma unroll
@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(F_NT) k_df_down(FwdTab t, const df* T, const d
                       add<DF>(v, s);
                       y[idx] = df_norm(v);
                     });
+  if (blockIdx.y == 0)   // skeleton rows once per box (the grid's row chunks cover the redundant rows)
   for (int e = threadIdx.x; e < k * cw; e += F_NT) {
     int a = e / cw, c = e % cw;
     int64_t idx = (off + lp[a]) * R + c0 + c;
@@ -242,7 +243,7 @@ FwdTab fwd_tab(const Level& lv) { return FwdTab{lv.n, lv.k, lv.off, lv.skoff, lv
 template <bool DF, int CT, int WC>
 int set_df_smem_ct() {
   const int lim = (int)(sizeof(df) * CT * WC * F_QC);
-  if (lim <= 48 * 1024) return RS_OK;
+  if (lim <= 48 * 1024) return RS_OK;   // default limit suffices for this shape
   RS_CUDA(cudaFuncSetAttribute(k_df_dblock<DF, CT, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   RS_CUDA(cudaFuncSetAttribute(k_df_proj<DF, CT, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
   RS_CUDA(cudaFuncSetAttribute(k_df_down<DF, CT, WC>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
@@ -278,6 +279,12 @@ int ensure_df(Handle* h, int R, cudaStream_t st) {
   return RS_OK;
 }
 
+// Row chunks of a level's largest box (32 rows per warp row of the CTA).
+int rchunks(int maxrows, int WC) {
+  const int WR = (F_NT / 32) / WC;
+  return std::max(1, div_up(std::max(1, maxrows), 32 * WR));
+}
+
 template <bool DF, int CT, int WC>
 int forward_df_ct(Handle* h, const double* x, int64_t ldx, int R, cudaStream_t st) {
   RS_TRY(ensure_df(h, R, st));
@@ -294,11 +301,11 @@ int forward_df_ct(Handle* h, const double* x, int64_t ldx, int R, cudaStream_t s
     const Level& lv = h->lv[d];
     if (lv.maxn > F_MAXK) return fail(RS_ERR_ARG, "refinement: box of %d points exceeds the tile limit", lv.maxn);
     if (d > 0) {
-      k_df_proj<DF, CT, WC><<<lv.nbox * ntile, F_NT, smem, st>>>(fwd_tab(lv), (const df*)lv.Tdf, (const df*)h->dfz[d],
+      k_df_proj<DF, CT, WC><<<dim3(lv.nbox * ntile, rchunks(lv.maxk, WC)), F_NT, smem, st>>>(fwd_tab(lv), (const df*)lv.Tdf, (const df*)h->dfz[d],
                                                              (df*)h->dfz[d - 1], R, ntile);
       RS_CHECK_LAUNCH();
     }
-    k_df_dblock<DF, CT, WC><<<lv.nbox * ntile, F_NT, smem, st>>>(fwd_tab(lv), (const df*)lv.Dfw, (const df*)h->dfz[d],
+    k_df_dblock<DF, CT, WC><<<dim3(lv.nbox * ntile, rchunks(lv.maxn, WC)), F_NT, smem, st>>>(fwd_tab(lv), (const df*)lv.Dfw, (const df*)h->dfz[d],
                                                              (df*)h->dfy[d], R, ntile);
     RS_CHECK_LAUNCH();
     macs += (double)R * ((double)lv.dfsz + 2.0 * (double)lv.tsz_used);
@@ -306,7 +313,7 @@ int forward_df_ct(Handle* h, const double* x, int64_t ldx, int R, cudaStream_t s
   }
   for (int d = 1; d <= L; ++d) {
     const Level& lv = h->lv[d];
-    k_df_down<DF, CT, WC><<<lv.nbox * ntile, F_NT, smem, st>>>(fwd_tab(lv), (const df*)lv.Tdf, (const df*)h->dfy[d - 1],
+    k_df_down<DF, CT, WC><<<dim3(lv.nbox * ntile, rchunks(lv.maxn, WC)), F_NT, smem, st>>>(fwd_tab(lv), (const df*)lv.Tdf, (const df*)h->dfy[d - 1],
                                                            (df*)h->dfy[d], R, ntile);
     RS_CHECK_LAUNCH();
   }

@@ -142,6 +142,9 @@ struct Handle {
   void* pers_last = nullptr;
 };
 
+// fault injection (api.cu): true once after rs_set_fault("wait")
+bool take_wait_fault();
+
 // allocation helper: records in h->allocs
 int dalloc(Handle* h, void** p, size_t bytes);
 template <class T> int dalloc_t(Handle* h, T** p, size_t count) {

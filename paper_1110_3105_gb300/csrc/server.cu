@@ -1,0 +1,417 @@
+// Serving loop: resident factorizations, memory-admitted builds, and
+// continuous batching of right-hand sides.
+//
+// Each registered handle owns a worker thread and a CUDA stream.  The worker
+// repeatedly takes every solve request queued for its handle (up to
+// max_cols columns in total), copies their columns from the callers' host
+// buffers into one device batch, runs one mixed-precision refined solve
+// (rs_solve_refined) on it and copies each request's columns back.
+// Requests that arrive while a batch is on the GPU wait for the next one,
+// so batches form continuously; workers of different handles run
+// concurrently and their device work overlaps on separate streams.  Builds
+// run on a builder thread and are admitted only while the estimated device
+// memory of the resident factorizations plus the new one stays under the
+// server's budget.
+//
+// A request's latency is the host time from submit to completion.
+#include <time.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "rs_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  int64_t ticket = 0;
+  int kind = 0;              // 0 solve, 1 build
+  int hid = -1;              // handle id (solve)
+  const void* B = nullptr;   // host, column-major
+  int64_t ldb = 0;
+  void* X = nullptr;
+  int64_t ldx = 0;
+  int ncols = 0;
+  double tol = 1e-10;
+  // build
+  std::vector<double> pts;
+  int64_t n = 0;
+  int dim = 2;
+  rs_params params{};
+  double eps = 0;
+  int leaf = 0;
+  // completion
+  Clock::time_point t_submit, t_done;
+  bool done = false;
+  int status = RS_OK;
+  double relres = 0;
+  int its = 0;
+  int result_hid = -1;       // build: id of the new handle
+};
+
+struct Worker;
+
+struct Server {
+  int max_cols = 256;
+  size_t budget = 0;
+  std::mutex mu;
+  std::condition_variable cv_done;
+  std::map<int64_t, std::shared_ptr<Request>> reqs;
+  int64_t next_ticket = 1;
+  std::vector<std::unique_ptr<Worker>> workers;   // index = handle id
+  // builder
+  std::deque<std::shared_ptr<Request>> build_q;
+  std::condition_variable cv_build;
+  std::thread builder;
+  bool stop = false;
+  size_t resident_bytes = 0;
+  // statistics
+  std::vector<double> lat_ms;
+  int64_t rhs_done = 0, batches = 0, batch_cols = 0;
+  Clock::time_point t0 = Clock::now();
+};
+
+struct Worker {
+  Server* s = nullptr;
+  rs_handle h = nullptr;
+  bool owned = false;
+  int id = -1;
+  int64_t n = 0;
+  bool cplx = false;
+  cudaStream_t stream = nullptr;
+  std::deque<std::shared_ptr<Request>> q;
+  std::condition_variable cv;
+  std::thread th;
+  void* db = nullptr;     // device batch buffers (n x max_cols scalars)
+  void* dx = nullptr;
+  size_t cap = 0;
+
+  void run();
+};
+
+size_t handle_bytes(rs_handle h) {
+  rs_stats_t st;
+  if (rs_stats(h, &st) != RS_OK) return 0;
+  // FP64 + FP32 factors, forward blocks and solve workspaces: about 3x the FP64 factors
+  return (size_t)st.factor_bytes * 3;
+}
+
+void complete(Server* s, const std::shared_ptr<Request>& r, int status) {
+  r->t_done = Clock::now();
+  r->status = status;
+  r->done = true;
+  double ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  if (status == RS_OK && r->kind == 0) {
+    s->lat_ms.push_back(ms);
+    s->rhs_done += r->ncols;
+  }
+}
+
+void Worker::run() {
+  const size_t sb = cplx ? 16 : 8;
+  for (;;) {
+    std::vector<std::shared_ptr<Request>> batch;
+    int cols = 0;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      cv.wait(lk, [&] { return s->stop || !q.empty(); });
+      if (s->stop && q.empty()) return;
+      while (!q.empty() && (batch.empty() || cols + q.front()->ncols <= s->max_cols)) {
+        cols += q.front()->ncols;
+        batch.push_back(q.front());
+        q.pop_front();
+      }
+    }
+    size_t need = (size_t)n * cols * sb;
+    int rc = RS_OK;
+    if (need > cap) {
+      if (db) cudaFree(db);
+      if (dx) cudaFree(dx);
+      db = dx = nullptr;
+      size_t want = (size_t)n * s->max_cols * sb;
+      if (cudaMalloc(&db, want) != cudaSuccess || cudaMalloc(&dx, want) != cudaSuccess) {
+        cudaGetLastError();
+        rc = RS_ERR_OOM;
+        cap = 0;
+      } else {
+        cap = want;
+      }
+    }
+    double tol = 1e-10;
+    if (rc == RS_OK) {
+      // each request's columns straight into the device batch (no host packing)
+      size_t col = 0;
+      for (auto& r : batch) {
+        tol = std::min(tol, r->tol);
+        if (cudaMemcpy2DAsync((char*)db + col * n * sb, n * sb, r->B, r->ldb * sb, n * sb, r->ncols,
+                              cudaMemcpyHostToDevice, stream) != cudaSuccess) {
+          cudaGetLastError();
+          rc = RS_ERR_CUDA;
+        }
+        col += r->ncols;
+      }
+      std::vector<double> rel(cols, 0.0);
+      int its = 0;
+      if (rc == RS_OK) rc = rs_solve_refined(h, db, n, cols, dx, n, tol, 8, &its, rel.data(), stream);
+      col = 0;
+      for (auto& r : batch) {
+        double worst = 0;
+        if (rc == RS_OK &&
+            cudaMemcpy2DAsync(r->X, r->ldx * sb, (const char*)dx + col * n * sb, n * sb, n * sb, r->ncols,
+                              cudaMemcpyDeviceToHost, stream) != cudaSuccess) {
+          cudaGetLastError();
+          rc = RS_ERR_CUDA;
+        }
+        for (int c = 0; c < r->ncols; ++c, ++col) worst = std::max(worst, rel[col]);
+        r->relres = worst;
+        r->its = its;
+      }
+      if (cudaStreamSynchronize(stream) != cudaSuccess && rc == RS_OK) {
+        cudaGetLastError();
+        rc = RS_ERR_CUDA;
+      }
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (auto& r : batch) complete(s, r, rc);
+      s->batches += 1;
+      s->batch_cols += cols;
+    }
+    s->cv_done.notify_all();
+  }
+}
+
+int add_worker(Server* s, rs_handle h, bool owned, int* id_out) {
+  auto w = std::make_unique<Worker>();
+  w->s = s;
+  w->h = h;
+  w->owned = owned;
+  rs_stats_t st;
+  RS_TRY(rs_stats(h, &st));
+  w->n = st.n;
+  w->cplx = static_cast<rs::Handle*>(reinterpret_cast<rs::Handle*>(h))->cplx;
+  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return rs::fail(RS_ERR_CUDA, "rs_server: stream creation failed");
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  Worker* wp = w.get();
+  w->th = std::thread([wp, dev] {
+    cudaSetDevice(dev);
+    wp->run();
+  });
+  w->id = (int)s->workers.size();
+  *id_out = w->id;
+  s->resident_bytes += handle_bytes(h);
+  s->workers.push_back(std::move(w));
+  return RS_OK;
+}
+
+void builder_loop(Server* s, int dev) {
+  cudaSetDevice(dev);
+  cudaStream_t st;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  for (;;) {
+    std::shared_ptr<Request> r;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv_build.wait(lk, [&] { return s->stop || !s->build_q.empty(); });
+      if (s->stop && s->build_q.empty()) break;
+      r = s->build_q.front();
+      s->build_q.pop_front();
+    }
+    // admission: estimated footprint (same 2D proportion as resident ones) under the budget
+    size_t est = (size_t)r->n * 1800 * 3;
+    int rc = RS_OK;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      size_t free_b = 0, total_b = 0;
+      cudaMemGetInfo(&free_b, &total_b);
+      if (s->resident_bytes + est > s->budget || est > free_b) rc = RS_ERR_OOM;
+    }
+    rs_handle h = nullptr;
+    if (rc == RS_OK) rc = rs_build(r->pts.data(), r->n, r->dim, &r->params, r->eps, r->leaf, st, &h);
+    int id = -1;
+    if (rc == RS_OK) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      rc = add_worker(s, h, true, &id);
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      r->result_hid = id;
+      complete(s, r, rc);
+    }
+    s->cv_done.notify_all();
+  }
+  cudaStreamDestroy(st);
+}
+
+}  // namespace
+
+struct rs_server_s : public Server {};
+
+extern "C" {
+
+int rs_server_create(int max_cols, int64_t hbm_budget_bytes, rs_server* out) {
+  if (!out || max_cols < 1) return rs::fail(RS_ERR_ARG, "rs_server_create: bad arguments");
+  rs_server_s* s = new rs_server_s();
+  s->max_cols = max_cols;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return rs::fail(RS_ERR_CUDA, "rs_server_create: no device");
+  }
+  s->budget = hbm_budget_bytes > 0 ? (size_t)hbm_budget_bytes : (size_t)(free_b * 0.9);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  s->builder = std::thread(builder_loop, s, dev);
+  *out = s;
+  return RS_OK;
+}
+
+int rs_server_add_handle(rs_server s, rs_handle h, int* handle_id) {
+  if (!s || !h || !handle_id) return rs::fail(RS_ERR_ARG, "rs_server_add_handle: null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  return add_worker(s, h, false, handle_id);
+}
+
+int rs_server_submit_solve(rs_server s, int handle_id, const void* B, int64_t ldb, int ncols, void* X, int64_t ldx,
+                           double tol, int64_t* ticket) {
+  if (!s || !B || !X || !ticket || ncols < 1) return rs::fail(RS_ERR_ARG, "rs_server_submit_solve: bad arguments");
+  auto r = std::make_shared<Request>();
+  r->kind = 0;
+  r->hid = handle_id;
+  r->B = B;
+  r->ldb = ldb;
+  r->X = X;
+  r->ldx = ldx;
+  r->ncols = ncols;
+  r->tol = tol;
+  r->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (handle_id < 0 || handle_id >= (int)s->workers.size())
+    return rs::fail(RS_ERR_ARG, "rs_server_submit_solve: unknown handle id %d", handle_id);
+  Worker* w = s->workers[handle_id].get();
+  if (ldb < w->n || ldx < w->n) return rs::fail(RS_ERR_ARG, "rs_server_submit_solve: leading dimension < N");
+  if (ncols > s->max_cols) return rs::fail(RS_ERR_ARG, "rs_server_submit_solve: more columns than a batch holds");
+  r->ticket = s->next_ticket++;
+  s->reqs[r->ticket] = r;
+  w->q.push_back(r);
+  w->cv.notify_one();
+  *ticket = r->ticket;
+  return RS_OK;
+}
+
+int rs_server_submit_build(rs_server s, const double* pts, int64_t n, int dim, const rs_params* params, double eps,
+                           int leaf, int64_t* ticket) {
+  if (!s || !pts || !params || !ticket || n < 1) return rs::fail(RS_ERR_ARG, "rs_server_submit_build: bad arguments");
+  auto r = std::make_shared<Request>();
+  r->kind = 1;
+  r->pts.assign(pts, pts + (size_t)n * dim);
+  r->n = n;
+  r->dim = dim;
+  r->params = *params;
+  r->eps = eps;
+  r->leaf = leaf;
+  r->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lk(s->mu);
+  r->ticket = s->next_ticket++;
+  s->reqs[r->ticket] = r;
+  s->build_q.push_back(r);
+  s->cv_build.notify_one();
+  *ticket = r->ticket;
+  return RS_OK;
+}
+
+int rs_server_wait(rs_server s, int64_t ticket, double timeout_s, int* status, double* latency_ms, double* relres,
+                   int* result) {
+  if (!s) return rs::fail(RS_ERR_ARG, "rs_server_wait: null server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return rs::fail(RS_ERR_ARG, "rs_server_wait: unknown ticket");
+  auto r = it->second;
+  bool ok = s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 1e9),
+                                [&] { return r->done; });
+  if (!ok) return rs::fail(RS_ERR_TIMEOUT, "rs_server_wait: request %lld not done", (long long)ticket);
+  if (status) *status = r->status;
+  if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  if (relres) *relres = r->relres;
+  if (result) *result = r->kind == 1 ? r->result_hid : r->its;
+  s->reqs.erase(it);
+  return RS_OK;
+}
+
+int rs_server_stats(rs_server s, rs_server_stats_t* out) {
+  if (!s || !out) return rs::fail(RS_ERR_ARG, "rs_server_stats: null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::vector<double> v = s->lat_ms;
+  std::sort(v.begin(), v.end());
+  auto pct = [&](double p) {
+    if (v.empty()) return 0.0;
+    size_t i = (size_t)std::min<double>(v.size() - 1, std::ceil(p * v.size()) - 1);
+    return v[i];
+  };
+  out->requests = (int64_t)v.size();
+  out->rhs = s->rhs_done;
+  out->batches = s->batches;
+  out->mean_batch_cols = s->batches ? (double)s->batch_cols / s->batches : 0.0;
+  out->p50_ms = pct(0.50);
+  out->p99_ms = pct(0.99);
+  out->elapsed_s = std::chrono::duration<double>(Clock::now() - s->t0).count();
+  out->handles = (int)s->workers.size();
+  out->resident_bytes = (int64_t)s->resident_bytes;
+  return RS_OK;
+}
+
+int rs_server_reset_stats(rs_server s) {
+  if (!s) return rs::fail(RS_ERR_ARG, "rs_server_reset_stats: null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->lat_ms.clear();
+  s->rhs_done = s->batches = s->batch_cols = 0;
+  s->t0 = Clock::now();
+  return RS_OK;
+}
+
+int rs_server_destroy(rs_server s) {
+  if (!s) return RS_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    for (auto& w : s->workers) w->cv.notify_all();
+    s->cv_build.notify_all();
+  }
+  for (auto& w : s->workers)
+    if (w->th.joinable()) w->th.join();
+  if (s->builder.joinable()) s->builder.join();
+  for (auto& w : s->workers) {
+    if (w->stream) cudaStreamDestroy(w->stream);
+    if (w->db) cudaFree(w->db);
+    if (w->dx) cudaFree(w->dx);
+    if (w->owned) rs_free(w->h);
+  }
+  delete s;
+  return RS_OK;
+}
+
+int rs_server_handle(rs_server s, int handle_id, rs_handle* out) {
+  if (!s || !out) return rs::fail(RS_ERR_ARG, "rs_server_handle: null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (handle_id < 0 || handle_id >= (int)s->workers.size()) return rs::fail(RS_ERR_ARG, "rs_server_handle: bad id");
+  *out = s->workers[handle_id]->h;
+  return RS_OK;
+}
+
+}  // extern "C"

@@ -371,8 +371,9 @@ __global__ void __launch_bounds__(BI_NT) k_bbid_fill(IdArgs a, BigId g, S* Mws, 
 
 template <class S>
 __global__ void __launch_bounds__(BI_NT) k_bbid_step(IdArgs a, BigId g, S* Mws, int j, int ncb, int* lperm) {
-  __shared__ S u[1024];
-  __shared__ int mp[512];
+  extern __shared__ __align__(16) unsigned char bi_smem[];
+  S* u = reinterpret_cast<S*>(bi_smem);                  // mmax entries
+  int* mp = reinterpret_cast<int*>(u + a.mmax);          // nmax entries
   __shared__ int s_p, s_stop;
   __shared__ double s_rjj, s_r00;
   const int b = blockIdx.x / ncb, cb = blockIdx.x % ncb;
@@ -897,7 +898,8 @@ __global__ void k_bb_assemble(FaArgs a, BigArgs g, const S* cLam, S* ws, int max
 // pbuf[(j+1) % 2].  Every CTA finds the same pivot.
 template <class S, class Dims>
 __global__ void __launch_bounds__(BB_NT) k_bb_gj_step(BigArgs g, S* ws, Dims dims, int j, int ncb, int* bad) {
-  __shared__ S mult[512];
+  extern __shared__ __align__(16) unsigned char bb_smem[];
+  S* mult = reinterpret_cast<S*>(bb_smem);   // m entries
   __shared__ int s_p;
   __shared__ double s_best;
   const int b = blockIdx.x / ncb, cb = blockIdx.x % ncb;
@@ -1086,7 +1088,8 @@ __global__ void k_bb_products(FaArgs a, BigArgs g, S* ws, const S* Lampool, S* U
     U[n + i + (size_t)c * ldu] = s;
   }
   // calD[:, c] = Dinv[:, c] - X Lambda X[c, :]^T: w = Lambda X[c, :]^T first
-  __shared__ S w[512];
+  extern __shared__ __align__(16) unsigned char bp_smem[];
+  S* w = reinterpret_cast<S*>(bp_smem);   // k entries
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     S s = S(0.0);
     for (int q = 0; q < k; ++q) s += Lam[i + (size_t)q * k] * X[c + (size_t)q * n];
@@ -1203,12 +1206,14 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
   k_bbid_fill<S><<<nb * maxn, BI_NT, 0, st>>>(a, g, Mws, maxn);
   RS_CHECK_LAUNCH();
   const int ncb = div_up(maxn, BI_CB);
+  const size_t id_smem = sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax;
+  RS_CUDA(cudaFuncSetAttribute(k_bbid_step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)id_smem));
   // every 8 steps, stop early once every box of the level has found its rank
   int* d_active = nullptr;
   int h_active = 1;
   RS_CUDA(cudaMallocAsync((void**)&d_active, sizeof(int), st));
   for (int j = 0; j < maxkmax; ++j) {
-    k_bbid_step<S><<<nb * ncb, BI_NT, 0, st>>>(a, g, Mws, j, ncb, a.lperm);
+    k_bbid_step<S><<<nb * ncb, BI_NT, id_smem, st>>>(a, g, Mws, j, ncb, a.lperm);
     RS_CHECK_LAUNCH();
     if ((j & 7) == 7 && j + 1 < maxkmax) {
       k_bbid_active<<<1, 256, 0, st>>>(g, a.n, nb, j + 1, d_active);
@@ -1240,7 +1245,7 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
   const size_t limit = 200 * 1024;
   S* Mws = nullptr;
   a.smem_path = (mbytes + extra <= limit) ? 1 : 0;
-  if (!a.smem_path && a.mmax <= 1024 && a.nmax <= 512 && a.geo.nproxy <= 256)
+  if (!a.smem_path && a.geo.nproxy <= 256 && sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax <= 200 * 1024)
     return run_id_big<S>(h, lv, a, mrows, st);
   size_t smem = a.smem_path ? mbytes + extra : extra;
   if (smem > 227 * 1024) return fail(RS_ERR_ARG, "box too large for shared staging (m=%d n=%d)", a.mmax, a.nmax);
@@ -1299,8 +1304,10 @@ int run_factor_big(Handle* h, Level& lv, FaArgs a, const Level* child, double by
   k_bb_assemble<S><<<nb * maxn, BB_NT, 0, st>>>(a, g, cL, ws, maxn);
   RS_CHECK_LAUNCH();
   const int ncb = div_up(maxn, BB_CB);
+  const size_t gj_smem = sizeof(S) * (size_t)maxn;
+  RS_CUDA(cudaFuncSetAttribute(k_bb_gj_step<S, DimsD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem));
   for (int j = 0; j < maxn; ++j) {
-    k_bb_gj_step<S, DimsD><<<nb * ncb, BB_NT, 0, st>>>(g, ws, DimsD{}, j, ncb, a.bad);
+    k_bb_gj_step<S, DimsD><<<nb * ncb, BB_NT, gj_smem, st>>>(g, ws, DimsD{}, j, ncb, a.bad);
     RS_CHECK_LAUNCH();
   }
   k_bb_unscramble<S, DimsD><<<nb, BB_NT, 0, st>>>(g, ws, DimsD{}, (S*)nullptr, 0, idx, maxn);
@@ -1312,14 +1319,18 @@ int run_factor_big(Handle* h, Level& lv, FaArgs a, const Level* child, double by
     RS_CHECK_LAUNCH();
     const int nck = div_up(maxk, BB_CB);
     DimsY dy{lv.lamoff};
+    const size_t gy_smem = sizeof(S) * (size_t)maxk;
+    RS_CUDA(cudaFuncSetAttribute(k_bb_gj_step<S, DimsY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gy_smem));
     for (int j = 0; j < maxk; ++j) {
-      k_bb_gj_step<S, DimsY><<<nb * nck, BB_NT, 0, st>>>(g, ws, dy, j, nck, a.bad);
+      k_bb_gj_step<S, DimsY><<<nb * nck, BB_NT, gy_smem, st>>>(g, ws, dy, j, nck, a.bad);
       RS_CHECK_LAUNCH();
     }
     k_bb_unscramble<S, DimsY><<<nb, BB_NT, 0, st>>>(g, ws, dy, (S*)lv.Lam, 1, idx, maxn);
     RS_CHECK_LAUNCH();
   }
-  k_bb_products<S><<<nb * maxn, BB_NT, 0, st>>>(a, g, ws, (const S*)lv.Lam, (S*)lv.U, (S*)lv.Lf, maxn);
+  const size_t pr_smem = sizeof(S) * (size_t)std::max(1, maxk);
+  RS_CUDA(cudaFuncSetAttribute(k_bb_products<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pr_smem));
+  k_bb_products<S><<<nb * maxn, BB_NT, pr_smem, st>>>(a, g, ws, (const S*)lv.Lam, (S*)lv.U, (S*)lv.Lf, maxn);
   RS_CHECK_LAUNCH();
   prof_end(P_FACTOR, st, by, fl);
   RS_CUDA(cudaFreeAsync(ws, st));
@@ -1362,7 +1373,7 @@ int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t 
     prof_end(P_FACTOR, st, by0, fl0);
     return RS_OK;
   }
-  if (lv.maxn <= 512) return run_factor_big<S>(h, lv, a, child, by0, st);
+  if (sizeof(S) * (size_t)lv.maxn <= 200 * 1024) return run_factor_big<S>(h, lv, a, child, by0, st);
   int64_t* dws;
   RS_TRY(upload(h, &dws, wsoff, st));
   a.wsoff = dws;

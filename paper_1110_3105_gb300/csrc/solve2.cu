@@ -72,6 +72,7 @@ struct Plan {
   const S* const* U;    // per depth factors
   const S* const* Lf;
   int* dispatch;
+  int* dflag;           // device copy of the timeout flag (checked per tile)
   int* up_cnt;
   int* dn_cnt;
 };
@@ -81,13 +82,16 @@ __device__ inline int ld_acquire(const int* p) {
   return a.load(cuda::memory_order_acquire);
 }
 
-// Lane 0 waits until *cnt >= target; returns false (and raises the flag) on timeout.
-__device__ inline bool wait_at_least(const int* cnt, int target, int* flag) {
+// Lane 0 waits until *cnt >= target; returns false (and raises both flags:
+// the device one every warp polls, the host-mapped one the caller reads) on
+// timeout.
+__device__ inline bool wait_at_least(const int* cnt, int target, int* flag, int* dflag) {
   int ok = 1;
   if ((threadIdx.x & 31) == 0) {
     int spins = 0;
     while (ld_acquire(cnt) < target) {
       if (++spins > MAX_SPIN) {
+        atomicExch(dflag, 1);
         atomicExch(flag, 1);
         ok = 0;
         break;
@@ -136,7 +140,53 @@ template <> __device__ inline c128 cv<c128, c64>(c64 v) { return c128((double)v.
 
 // acc[c] += sum_{q < qn} col[q * ld] * stage[q][c] for one 32-column chunk.
 // All factor loads of the chunk are issued before the FMAs (QB at a time)
-// so a lane keeps up to QB loads in flight instead of one per iteration.
+// so a lane keeps up to QB loads in flight instead of one per iteration; the
+// staged row stage[q][0..CT) is read with 128-bit loads (every lane reads the
+// same address, so each load is one broadcast wavefront).
+template <class S, int CT>
+struct StageRow {
+  __device__ static void fma(S* acc, S a, const S* row) {
+#pragma unroll
+    for (int c = 0; c < CT; ++c) acc[c] += a * row[c];
+  }
+};
+template <int CT>
+struct StageRow<float, CT> {
+  __device__ static void fma(float* acc, float a, const float* row) {
+    if (CT % 4 == 0) {
+      const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+      for (int c = 0; c < CT / 4; ++c) {
+        const float4 v = r4[c];
+        acc[4 * c] += a * v.x;
+        acc[4 * c + 1] += a * v.y;
+        acc[4 * c + 2] += a * v.z;
+        acc[4 * c + 3] += a * v.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CT; ++c) acc[c] += a * row[c];
+    }
+  }
+};
+template <int CT>
+struct StageRow<double, CT> {
+  __device__ static void fma(double* acc, double a, const double* row) {
+    if (CT % 2 == 0) {
+      const double2* r2 = reinterpret_cast<const double2*>(row);
+#pragma unroll
+      for (int c = 0; c < CT / 2; ++c) {
+        const double2 v = r2[c];
+        acc[2 * c] += a * v.x;
+        acc[2 * c + 1] += a * v.y;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CT; ++c) acc[c] += a * row[c];
+    }
+  }
+};
+
 template <class S, int CT>
 __device__ __forceinline__ void chunk_fma(const S* col, size_t ld, int qn, const S* stage, S* acc) {
   constexpr int QB = CT == 1 ? 32 : (CT <= 8 ? 16 : 8);
@@ -145,10 +195,7 @@ __device__ __forceinline__ void chunk_fma(const S* col, size_t ld, int qn, const
 #pragma unroll
     for (int j = 0; j < QB; ++j) a[j] = (q0 + j < qn) ? ldro(col + (size_t)(q0 + j) * ld) : S(0.0);
 #pragma unroll
-    for (int j = 0; j < QB; ++j) {
-#pragma unroll
-      for (int c = 0; c < CT; ++c) acc[c] += a[j] * stage[(q0 + j) * CT + c];
-    }
+    for (int j = 0; j < QB; ++j) StageRow<S, CT>::fma(acc, a[j], stage + (size_t)(q0 + j) * CT);
   }
 }
 
@@ -163,6 +210,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
     if (lane == 0) t = atomicAdd(p.dispatch, 1);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= p.ntiles) break;
+    if (*(volatile int*)p.dflag) return;   // another warp gave up waiting: leave too
     const Tile tl = p.tiles[t];
     const int g = tl.g;
     const int d = p.bt.depth[g];
@@ -171,7 +219,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
 
     if (tl.kind != T_DOWN) {
       // ---- up / root tile: rows of U b, U = [calD ; calR] ((n+k) x n)
-      if (p.bt.up_need[g] > 0 && !wait_at_least(&p.up_cnt[g], epoch * p.bt.up_need[g], flag)) return;
+      if (p.bt.up_need[g] > 0 && !wait_at_least(&p.up_cnt[g], epoch * p.bt.up_need[g], flag, p.dflag)) return;
       const int rows = n + k;
       const int r = tl.r0 + lane;
       const S* Ub = p.U[d] + p.bt.uoff[g];
@@ -228,7 +276,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
     } else {
       // ---- down tile: rows of u + calL x_parent (n x k)
       const int par = p.bt.parent[g];
-      if (!wait_at_least(&p.dn_cnt[par], epoch * p.bt.dn_need[par], flag)) return;
+      if (!wait_at_least(&p.dn_cnt[par], epoch * p.bt.dn_need[par], flag, p.dflag)) return;
       const int r = tl.r0 + lane;
       const S* Lb = p.Lf[d] + p.bt.loff[g];
       const S* xpar = p.u[d - 1] + p.bt.skoff[g] * R;
@@ -272,13 +320,14 @@ struct PersPlan {
   int ntiles = 0, nbox = 0;
   Tile* tiles = nullptr;
   BoxTab bt{};
-  int* counters = nullptr;   // dispatch | up_cnt[G] | dn_cnt[G]
+  int* counters = nullptr;   // dispatch | device flag | up_cnt[G] | dn_cnt[G]
   int epoch = 0;
   void** ptrs = nullptr;     // v[L+1] | u[L+1] | U[L+1] | Lf[L+1]
   int* flag_host = nullptr;  // mapped pinned
   int* flag_dev = nullptr;
   int grid = 0;
   int work_gen = -1;         // generation of the work buffers captured in ptrs
+  bool dirty = false;        // a wait timed out: counters must restart
   std::vector<void*> mem;
 };
 
@@ -313,11 +362,14 @@ int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X
     RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_pers<S, SIO, CT>, P_NT, smem));
     P->grid = std::max(1, std::min(nsm * std::max(occ, 1), div_up(P->ntiles, P_WARPS)));
   }
-  if (++P->epoch > (1 << 20)) {
-    RS_CUDA(cudaMemsetAsync(P->counters, 0, sizeof(int) * (1 + 2 * (size_t)P->nbox), st));
+  if (++P->epoch > (1 << 20) || P->dirty) {   // counters restart (overflow guard, or after a timeout)
+    RS_CUDA(cudaMemsetAsync(P->counters, 0, sizeof(int) * (2 + 2 * (size_t)P->nbox), st));
     P->epoch = 1;
+    P->dirty = false;
   }
-  RS_CUDA(cudaMemsetAsync(P->counters, 0, sizeof(int), st));
+  // injected fault: wait for one more round of tiles than will ever finish
+  const int wait_epoch = take_wait_fault() ? P->epoch + 1 : P->epoch;
+  RS_CUDA(cudaMemsetAsync(P->counters, 0, 2 * sizeof(int), st));   // dispatch and device flag
   Plan<S> pl;
   pl.tiles = P->tiles;
   pl.ntiles = P->ntiles;
@@ -330,11 +382,12 @@ int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X
   pl.U = (const S* const*)(P->ptrs + 2 * L1);
   pl.Lf = (const S* const*)(P->ptrs + 3 * L1);
   pl.dispatch = P->counters;
-  pl.up_cnt = P->counters + 1;
-  pl.dn_cnt = P->counters + 1 + P->nbox;
+  pl.dflag = P->counters + 1;
+  pl.up_cnt = P->counters + 2;
+  pl.dn_cnt = P->counters + 2 + P->nbox;
   *P->flag_host = 0;
   prof_begin(prec_cat(P->prec), st);
-  k_solve_pers<S, SIO, CT><<<P->grid, P_NT, smem, st>>>(pl, B, ldb, X, ldx, R, P->epoch, P->flag_dev);
+  k_solve_pers<S, SIO, CT><<<P->grid, P_NT, smem, st>>>(pl, B, ldb, X, ldx, R, wait_epoch, P->flag_dev);
   RS_CHECK_LAUNCH();
   double sS = sizeof(S), fac = 0.0;
   for (auto& lv : h->lv) fac += (double)lv.usz + (double)lv.lsz;
@@ -470,7 +523,7 @@ static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out)
   RS_TRY(dev_upload(P, &P->bt.parent, parent, st));
   RS_TRY(dev_upload(P, &P->bt.up_need, up_need, st));
   RS_TRY(dev_upload(P, &P->bt.dn_need, dn_need, st));
-  std::vector<int> zeros(1 + 2 * (size_t)G, 0);
+  std::vector<int> zeros(2 + 2 * (size_t)G, 0);
   RS_TRY(dev_upload(P, &P->counters, zeros, st));
   RS_TRY(refresh_ptrs(h, P, st));
   RS_CUDA(cudaHostAlloc((void**)&P->flag_host, sizeof(int), cudaHostAllocMapped));
@@ -509,8 +562,11 @@ int solve_pers_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrh
 // After the stream has been synchronized: timeout flag of the last solve.
 int pers_check(Handle* h) {
   PersPlan* P = (PersPlan*)h->pers_last;
-  if (P && P->flag_host && *(volatile int*)P->flag_host)
+  if (P && P->flag_host && *(volatile int*)P->flag_host) {
+    P->dirty = true;
+    *P->flag_host = 0;
     return fail(RS_ERR_TIMEOUT, "solve: a dependency wait ran out (flag set by the device)");
+  }
   return RS_OK;
 }
 

@@ -42,3 +42,12 @@ def test_no_compute_without_gpu_errors_cleanly(lib):
     assert rc == -1 and out.value is None
     assert b"null" in _lib._lib.rs_last_error()
     assert _lib._lib.rs_free(None) == 0
+
+
+def test_fault_spec_validation(lib):
+    from paper_1110_3105_gb300 import _lib
+    _lib.load()
+    assert _lib._lib.rs_set_fault(b"bogus") == -1
+    assert _lib._lib.rs_set_fault(b"alloc:0") == -1
+    assert _lib._lib.rs_set_fault(b"off") == 0
+    assert _lib._lib.rs_set_fault(None) == 0
