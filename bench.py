@@ -49,6 +49,11 @@ def peaks():
     return dict(hbm=6800.0, bf16=1900.0, src="fallback")
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per
+# kernel category, from the ncu captures summarised in profiles/ (the leaf-level
+# launch of the bench workload); None where no capture of the current kernel exists.
+NCU_TRAFFIC = {"id": (3365376, "k_id leaf-level launch (profiles/k_id_leaf_laplace2d_starfish_131072.md)")}
+
 # FP64 FMA throughput of GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 # = 1.26 TFLOP/s nominal; a dependent-chain-free probe measured 1.195 TFLOP/s.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
@@ -335,8 +340,10 @@ def run_ours(args, ws, rank, local):
     else:
         bound, achieved, peak, unit = "alu", dom["flops"] / dom["ms"] / 1e6, FP64_PEAK_GFLOPS, "GFLOP/s"
         peak_src = "FP64 FMA peak 152 SM x 2 FMA/clk x 2.07 GHz (derived)"
+    traffic = NCU_TRAFFIC.get(dom_name)
     roof = {"bound": bound, "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+            "frac": achieved / peak, "traffic": traffic[0] if traffic else None,
+            "traffic_source": traffic[1] if traffic else None, "peak_source": peak_src,
             "launches": dom["launches"], "avg_launch_ms": dom["ms"] / dom["launches"]}
     kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                    "GB_s": v["bytes"] / v["ms"] / 1e6 if v["ms"] else 0.0,

@@ -170,6 +170,17 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
     return fail(RS_ERR_ARG, "rs_build: Helmholtz needs k_wave > 0");
 
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    // keep stream-ordered allocations cached between calls (the default
+    // release threshold returns them to the driver at every synchronize)
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+  }
   rs_handle_s* h = new rs_handle_s();
   h->dim = dim;
   h->N = n;
