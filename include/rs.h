@@ -182,6 +182,9 @@ int rs_profile_read(int cat, double* ms, int64_t* launches, double* bytes, doubl
  * records; record i gives its category, device time (ms), bytes, flops. */
 int rs_profile_nrec(void);
 int rs_profile_record(int i, int* cat, double* ms, double* bytes, double* flops);
+/* Start of record i in ms after the start of record 0 (gaps between records
+ * are host time or launch latency). */
+int rs_profile_record_start(int i, double* start_ms);
 
 /* Number of kernels the library has launched in this process so far. */
 int64_t rs_launch_count(void);

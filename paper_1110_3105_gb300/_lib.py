@@ -80,6 +80,7 @@ _PROTOS = {
     "rs_launch_count": (ctypes.c_int64, []),
     "rs_profile_nrec": (ctypes.c_int, []),
     "rs_profile_record": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P]),
+    "rs_profile_record_start": (ctypes.c_int, [ctypes.c_int, _P]),
     "rs_profile_read": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_char_p)]),
     "rs_last_error": (ctypes.c_char_p, []),
     "rs_version": (ctypes.c_char_p, []),
@@ -263,8 +264,9 @@ def rs_profile_read() -> dict:
     return out
 
 
-def rs_profile_records() -> list:
-    """[(category index, ms, bytes, flops)] of the recorded launches, in order."""
+def rs_profile_records(with_start: bool = False) -> list:
+    """[(category index, ms, bytes, flops[, start ms])] of the recorded launches, in order;
+    start is measured from the start of the first record."""
     lib = load()
     out = []
     for i in range(lib.rs_profile_nrec()):
@@ -274,7 +276,12 @@ def rs_profile_records() -> list:
         fl = ctypes.c_double()
         _check(lib.rs_profile_record(i, ctypes.addressof(cat), ctypes.addressof(ms), ctypes.addressof(by),
                                      ctypes.addressof(fl)))
-        out.append((cat.value, ms.value, by.value, fl.value))
+        rec = (cat.value, ms.value, by.value, fl.value)
+        if with_start:
+            t0 = ctypes.c_double()
+            _check(lib.rs_profile_record_start(i, ctypes.addressof(t0)))
+            rec = rec + (t0.value,)
+        out.append(rec)
     return out
 
 

@@ -44,18 +44,38 @@ static std::atomic<int> g_fault_wait{0};
 
 bool take_wait_fault() { return g_fault_wait.exchange(0) != 0; }
 
+// Handle memory is carved out of chunks taken from the stream-ordered pool
+// (whose memory the library keeps cached), so a build makes a handful of
+// allocation calls instead of one per table, and a rebuild reuses the memory
+// of a freed handle without going back to the driver.
 int dalloc(Handle* h, void** p, size_t bytes) {
+  constexpr size_t kChunk = 64u << 20, kAlign = 256;
   *p = nullptr;
   long left = g_fault_alloc.load();
   if (left > 0 && g_fault_alloc.fetch_sub(1) == 1)
-    return fail(RS_ERR_OOM, "cudaMalloc(%zu): injected allocation failure", bytes);
-  cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(e == cudaErrorMemoryAllocation ? RS_ERR_OOM : RS_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
-                cudaGetErrorString(e));
+    return fail(RS_ERR_OOM, "device allocation of %zu bytes: injected failure", bytes);
+  bytes = (std::max<size_t>(bytes, 16) + kAlign - 1) & ~(kAlign - 1);
+  auto take = [&](void** q, size_t sz) -> int {
+    cudaError_t e = cudaMallocAsync(q, sz, h->bst);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      *q = nullptr;
+      return fail(e == cudaErrorMemoryAllocation ? RS_ERR_OOM : RS_ERR_CUDA, "device allocation of %zu bytes: %s", sz,
+                  cudaGetErrorString(e));
+    }
+    h->allocs.push_back(*q);
+    return RS_OK;
+  };
+  if (bytes > kChunk / 4) return take(p, bytes);   // large tables get their own block
+  if (bytes > h->arena_left) {
+    void* c = nullptr;
+    RS_TRY(take(&c, kChunk));
+    h->arena_cur = (char*)c;
+    h->arena_left = kChunk;
   }
-  h->allocs.push_back(*p);
+  *p = h->arena_cur;
+  h->arena_cur += bytes;
+  h->arena_left -= bytes;
   return RS_OK;
 }
 
@@ -72,7 +92,7 @@ static void destroy(rs_handle_s* h) {
   if (!h) return;
   cudaDeviceSynchronize();
   free_pers(h);
-  for (void* p : h->allocs) cudaFree(p);
+  for (void* p : h->allocs) cudaFreeAsync(p, 0);
   for (auto& w : h->work) {
     for (void* p : w.v) if (p) cudaFree(p);
     for (void* p : w.u) if (p) cudaFree(p);
@@ -197,6 +217,7 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
+  h->bst = st;
   int rc = RS_OK;
   do {
     if ((rc = dalloc_t(h, &h->status, 4)) != RS_OK) break;

@@ -115,6 +115,19 @@ int rs_profile_record(int i, int* cat, double* ms, double* bytes, double* flops)
   return RS_OK;
 }
 
+int rs_profile_record_start(int i, double* start_ms) {
+  std::lock_guard<std::mutex> lk(rs::g_mu);
+  if (i < 0 || i >= (int)rs::g_recs.size()) return rs::fail(RS_ERR_ARG, "rs_profile_record_start: index out of range");
+  float m = 0;
+  const auto& r = rs::g_recs[i];
+  if (cudaEventSynchronize(r.e1) != cudaSuccess || cudaEventElapsedTime(&m, rs::g_recs[0].e0, r.e0) != cudaSuccess) {
+    cudaGetLastError();
+    return rs::fail(RS_ERR_CUDA, "rs_profile_record_start: event timing failed");
+  }
+  if (start_ms) *start_ms = m;
+  return RS_OK;
+}
+
 int rs_profile_read(int cat, double* ms, int64_t* launches, double* bytes, double* flops, const char** name) {
   if (cat < 0 || cat >= rs::P_NCAT) return rs::fail(RS_ERR_ARG, "rs_profile_read: bad category");
   std::lock_guard<std::mutex> lk(rs::g_mu);

@@ -112,12 +112,13 @@ struct Pts {
   const double* z;  // null in 2D
 };
 
-__device__ inline double dist(const Pts& p, int i, int j) {
+__device__ inline double dist2(const Pts& p, int i, int j) {
   double dx = p.x[i] - p.x[j], dy = p.y[i] - p.y[j];
   double s = dx * dx + dy * dy;
   if (p.z) { double dz = p.z[i] - p.z[j]; s += dz * dz; }
-  return sqrt(s);
+  return s;
 }
+__device__ inline double dist(const Pts& p, int i, int j) { return sqrt(dist2(p, i, j)); }
 
 // Kernel parameters shared by every device routine.
 struct KParams {
@@ -132,6 +133,12 @@ __device__ inline double green_real(int kind, double r) {
   if (kind == RS_LAPLACE3D) return 1.0 / (4.0 * M_PI * r);
   return -log(r) * (1.0 / (2.0 * M_PI));
 }
+// The same from the squared distance s = r^2 (no square root on the FP64
+// pipe: log r = log(s) / 2, 1 / r = rsqrt(s)).
+__device__ inline double green_real_s2(int kind, double s) {
+  if (kind == RS_LAPLACE3D) return rsqrt(s) * (1.0 / (4.0 * M_PI));
+  return -log(s) * (1.0 / (4.0 * M_PI));
+}
 __device__ inline c128 green_cplx(double kwave, double r) {
   double kr = kwave * r;
   return c128(-0.25 * y0(kr), 0.25 * j0(kr));   // (i/4)(J0 + i Y0)
@@ -139,7 +146,7 @@ __device__ inline c128 green_cplx(double kwave, double r) {
 // w G(x_i, x_j) for distinct points.
 template <class S> __device__ inline S offdiag_entry(const KParams& kp, const Pts& p, int i, int j);
 template <> __device__ inline double offdiag_entry<double>(const KParams& kp, const Pts& p, int i, int j) {
-  return kp.w * green_real(kp.kind, dist(p, i, j));
+  return kp.w * green_real_s2(kp.kind, dist2(p, i, j));
 }
 template <> __device__ inline c128 offdiag_entry<c128>(const KParams& kp, const Pts& p, int i, int j) {
   c128 g = green_cplx(kp.kwave, dist(p, i, j));
@@ -158,7 +165,50 @@ template <> __device__ inline c128 green_at<c128>(const KParams& kp, double r) {
   c128 g = green_cplx(kp.kwave, r);
   return c128(kp.w * g.re, kp.w * g.im);
 }
+// The same from the squared distance.
+template <class S> __device__ inline S green_at_s2(const KParams& kp, double s);
+template <> __device__ inline double green_at_s2<double>(const KParams& kp, double s) {
+  return kp.w * green_real_s2(kp.kind, s);
+}
+template <> __device__ inline c128 green_at_s2<c128>(const KParams& kp, double s) { return green_at<c128>(kp, sqrt(s)); }
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------------------ double-float
+// An unevaluated sum hi + lo of two floats (about 48 significant bits).
+// Products use the exact FMA two-product, sums the exact two-sum (Dekker
+// 1971; Knuth, TAOCP vol. 2, Sec. 4.2.2); every operation is explicitly
+// rounded so the compiler cannot fuse a product into a following sum.
+struct dfloat {
+  float hi, lo;
+  dfloat() = default;
+  __host__ __device__ dfloat(float h, float l) : hi(h), lo(l) {}
+  __device__ explicit dfloat(double x) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(__dsub_rn(x, (double)hi));
+  }
+};
+__device__ __forceinline__ dfloat df_renorm(dfloat s) {
+  float t = __fadd_rn(s.hi, s.lo);
+  return dfloat(t, __fsub_rn(s.lo, __fsub_rn(t, s.hi)));
+}
+// s += a * b
+__device__ __forceinline__ void df_fma(dfloat& s, dfloat a, dfloat b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  float t = __fadd_rn(s.hi, p);
+  float bb = __fsub_rn(t, s.hi);
+  float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  s.lo = __fadd_rn(s.lo, __fadd_rn(err, e));
+  s.hi = t;
+}
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+  float t = __fadd_rn(a.hi, b.hi);
+  float bb = __fsub_rn(t, a.hi);
+  float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(t, bb)), __fsub_rn(b.hi, bb));
+  return df_renorm(dfloat(t, __fadd_rn(a.lo, __fadd_rn(err, b.lo))));
+}
 
 }  // namespace rs

@@ -18,6 +18,8 @@
 //       Lf  at loff[b]: n x k     = calL
 //       Lam at lamoff[b]: k x k   = Lambda (read by the parent's assembly)
 //     float copies U32 / Lf32 for the mixed-precision solve
+//     forward factors FU32/FUdf ((n+k) x n = [D ; P] at uoff) and FL32/FLdf
+//       (n x k = P^T at loff), float and double-float (real kernels)
 //   the root is depth 0 with k = 0, so its U holds calS^{-1}.
 #pragma once
 
@@ -87,11 +89,12 @@ struct Level {
   void* Lam = nullptr;
   void* U32 = nullptr;
   void* Lf32 = nullptr;
-  // forward-operator blocks as (hi, lo) float pairs (fwd2.cu)
-  int64_t* dfoff = nullptr;
-  void* Dfw = nullptr;
-  void* Tdf = nullptr;
-  int64_t dfsz = 0, tsz_used = 0;
+  // forward operator in the solve's two-pass form (fwd2.cu): FU = [D ; P]
+  // ((n+k) x n at uoff) and FL = P^T (n x k at loff), in float and double-float
+  void* FU32 = nullptr;
+  void* FL32 = nullptr;
+  void* FUdf = nullptr;
+  void* FLdf = nullptr;
   int64_t ksum = 0;            // sum of k (size of depth-1 active vector)
   int64_t usz = 0, lsz = 0, lamsz = 0, tsz = 0;  // scalars in the pools
   int maxn = 0, maxm = 0, maxk = 0;
@@ -115,7 +118,10 @@ struct Handle {
   double* pts = nullptr;       // 3 * N (x, y, z blocks)
   int* perm = nullptr;
   std::vector<Level> lv;       // index = depth
-  std::vector<void*> allocs;   // everything to cudaFree
+  std::vector<void*> allocs;   // pool blocks owned by the handle (freed by rs_free)
+  cudaStream_t bst = nullptr;  // stream of the build (allocations are ordered on it)
+  char* arena_cur = nullptr;   // bump pointer into the current block
+  size_t arena_left = 0;
   double build_ms = 0;
   int64_t factor_scalars = 0;
   int* status = nullptr;       // device status word (singularity etc.)
@@ -129,15 +135,13 @@ struct Handle {
     size_t bytes = 0;
     int gen = 0;                // bumped whenever the buffers are reallocated
   };
-  Work work[2];                 // [0] = FP64 solve, [1] = FP32 solve
+  Work work[4];                 // [0] FP64 solve, [1] FP32 solve, [2] float forward, [3] double-float forward
   // refinement / matvec workspaces
   void* r64 = nullptr; void* x64 = nullptr; void* b64 = nullptr;
   std::vector<void*> fz, fy;    // forward operator vectors per depth
   int fR = 0;
   double* colnorm = nullptr;    // 2 * R
   int ncolnorm = 0;
-  std::vector<void*> dfz, dfy;  // double-float forward vectors per depth
-  int dfR = 0;
   void* pers = nullptr;         // persistent-solve plans (solve2.cu)
   void* pers_last = nullptr;
 };
@@ -174,7 +178,13 @@ int make_fwd_blocks(Handle* h, cudaStream_t st);
 bool df_supported(const Handle* h);
 int residual_df(Handle* h, const double* b, const double* x, double* r, int R, bool full, cudaStream_t st);
 
-// Persistent single-launch solve (solve2.cu).
+// Persistent single-launch solve (solve2.cu).  Besides RS_PREC_FP64 and
+// RS_PREC_FP32 it runs the forward operator (real kernels) from the forward
+// factors, in float or double-float arithmetic, and then writes
+// X = sub - A_RS B.
+enum { MODE_FWD_F32 = 2, MODE_FWD_DF = 3 };
+int solve_pers_device_sub(Handle* h, int mode, const double* d_B, int64_t ldb, int nrhs, double* d_X, int64_t ldx,
+                          const double* d_sub, cudaStream_t st);
 int solve_pers_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, void* d_X, int64_t ldx,
                       cudaStream_t st);
 int pers_check(Handle* h);

@@ -76,32 +76,40 @@ __device__ inline void proxy_point(const Geo& g, const int* coords, int j, doubl
   for (int d = 0; d < 3; ++d) out[d] = c[d] + p[d];
 }
 
-__device__ inline double dist_to(const Pts& p, int i, const double* q) {
+__device__ inline double dist2_to(const Pts& p, int i, const double* q) {
   double dx = p.x[i] - q[0], dy = p.y[i] - q[1];
   double s = dx * dx + dy * dy;
   if (p.z) { double dz = p.z[i] - q[2]; s += dz * dz; }
-  return sqrt(s);
+  return s;
 }
 
 // Column-pivoted Householder QR of M (m x n, column-major, leading dim ld),
 // stopped at relative precision eps.  On return piv holds the column order,
 // M[0:k, 0:n] the triangular factor; returns k.
+//
+// The trailing column norms that choose the pivots are downdated after each
+// step (|R_jc|^2 subtracted) and recomputed from the column once the
+// downdate has cancelled more than a factor 1.5e-8 of the last exact value
+// (the safeguard of LAPACK's xGEQP3, Drmac & Bujanovic 2008), so a step costs
+// two FP64 passes over the trailing matrix instead of three.  The pivot's own
+// norm, which sets R_jj, the reflector and the stopping test, is always
+// recomputed exactly.  nrm holds 2 n doubles (current | last exact).
 template <class S, int NT>
 __device__ int cpqr(S* M, int m, int n, int ld, double eps, int* piv, double* nrm, S* u) {
   __shared__ int s_p, s_stop;
   __shared__ double s_rjj, s_r00;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = NT / 32;
+  constexpr double kTol = 1.49e-8;   // sqrt of the double unit roundoff
+  double* nref = nrm + n;
   for (int c = tid; c < n; c += NT) piv[c] = c;
   const int kmax = min(m, n);
-  // trailing column norms over rows j..m-1; step 0 computes them here, every
-  // later step recomputes them from the freshly updated columns (no downdating)
   for (int c = warp; c < n; c += NW) {
     const S* col = M + (size_t)c * ld;
     double s = 0.0;
     for (int r = lane; r < m; r += 32) s += abs2(col[r]);
     s = warp_sum(s);
-    if (lane == 0) nrm[c] = s;
+    if (lane == 0) nrm[c] = nref[c] = s;
   }
   __syncthreads();
   int j = 0;
@@ -119,8 +127,30 @@ __device__ int cpqr(S* M, int m, int n, int ld, double eps, int* piv, double* nr
         int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
+      if (lane == 0) s_p = bi;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j) {
+      for (int r = tid; r < m; r += NT) {
+        S t = M[r + (size_t)j * ld];
+        M[r + (size_t)j * ld] = M[r + (size_t)p * ld];
+        M[r + (size_t)p * ld] = t;
+      }
+      if (tid == 0) {
+        int t = piv[j]; piv[j] = piv[p]; piv[p] = t;
+        double a = nrm[j]; nrm[j] = nrm[p]; nrm[p] = a;
+        a = nref[j]; nref[j] = nref[p]; nref[p] = a;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {   // exact norm of the pivot column over rows j..m-1
+      const S* col = M + (size_t)j * ld;
+      double s = 0.0;
+      for (int r = j + lane; r < m; r += 32) s += abs2(col[r]);
+      s = warp_sum(s);
       if (lane == 0) {
-        double rjj = sqrt(best);
+        const double rjj = sqrt(s);
         int stop = 0;
         if (j == 0) {
           s_r00 = rjj;
@@ -128,24 +158,13 @@ __device__ int cpqr(S* M, int m, int n, int ld, double eps, int* piv, double* nr
         } else if (rjj <= eps * s_r00) {
           stop = 1;
         }
-        s_p = bi;
         s_rjj = rjj;
         s_stop = stop;
       }
     }
     __syncthreads();
     if (s_stop) break;
-    const int p = s_p;
     const double rjj = s_rjj;
-    if (p != j) {
-      for (int r = tid; r < m; r += NT) {
-        S t = M[r + (size_t)j * ld];
-        M[r + (size_t)j * ld] = M[r + (size_t)p * ld];
-        M[r + (size_t)p * ld] = t;
-      }
-      if (tid == 0) { int t = piv[j]; piv[j] = piv[p]; piv[p] = t; }
-    }
-    __syncthreads();
     // Householder reflector H = I - f u u^H mapping column j onto beta e_1,
     // beta = -phase(alpha) ||x||, u = x - beta e_1, f = 2 / (u^H u).
     const S alpha = M[j + (size_t)j * ld];
@@ -162,14 +181,20 @@ __device__ int cpqr(S* M, int m, int n, int ld, double eps, int* piv, double* nr
       s = warp_sum(s);
       s = shfl(s, 0);
       const S fs = scal(s, f);
-      double s2 = 0.0;
-      for (int r = j + lane; r < m; r += 32) {
-        const S v = col[r] - u[r - j] * fs;
-        col[r] = v;
-        if (r > j) s2 += abs2(v);
+      for (int r = j + lane; r < m; r += 32) col[r] = col[r] - u[r - j] * fs;
+      __syncwarp();
+      int again = 0;
+      if (lane == 0) {
+        const double left = nrm[c] - abs2(col[j]);
+        if (left <= kTol * nref[c]) again = 1;
+        else nrm[c] = left;
       }
-      s2 = warp_sum(s2);
-      if (lane == 0) nrm[c] = s2;
+      if (__shfl_sync(0xffffffffu, again, 0)) {   // too much cancelled: recompute
+        double s2 = 0.0;
+        for (int r = j + 1 + lane; r < m; r += 32) s2 += abs2(col[r]);
+        s2 = warp_sum(s2);
+        if (lane == 0) nrm[c] = nref[c] = s2;
+      }
     }
     if (tid == 0) M[j + (size_t)j * ld] = beta;
     __syncthreads();
@@ -225,12 +250,12 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
   const int n = a.n[b];
   const int m = a.mrows[b];
   const int64_t off = a.off[b];
-  // shared layout: [M (smem path)] | u[mmax] | nrm[nmax] | proxy xyz[3 nproxy] | piv[nmax] | rowid[mmax]
+  // shared layout: [M (smem path)] | u[mmax] | nrm[2 nmax] | proxy xyz[3 nproxy] | piv[nmax] | rowid[mmax]
   S* Ms = reinterpret_cast<S*>(smem);
   size_t msz = a.smem_path ? (size_t)a.mmax * a.nmax : 0;
   S* u = Ms + msz;
   double* nrm = reinterpret_cast<double*>(u + a.mmax);
-  double* pxy = nrm + a.nmax;
+  double* pxy = nrm + 2 * a.nmax;
   int* piv = reinterpret_cast<int*>(pxy + 3 * a.geo.nproxy);
   int* rowid = piv + a.nmax;
   S* M = a.smem_path ? Ms : Mws + a.moff[b];
@@ -269,7 +294,7 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
     if (r < nnear) {
       v = offdiag_entry<S>(a.kp, a.pts, rowid[r], pc);
     } else if (r < nnear + a.geo.nproxy) {
-      v = green_at<S>(a.kp, dist_to(a.pts, pc, pxy + 3 * (r - nnear)));
+      v = green_at_s2<S>(a.kp, dist2_to(a.pts, pc, pxy + 3 * (r - nnear)));
     } else {
       v = S(a.kp.w);
     }
@@ -348,7 +373,7 @@ __global__ void __launch_bounds__(BI_NT) k_bbid_fill(IdArgs a, BigId g, S* Mws, 
       int cc = a.coll[b * 27 + j];
       v = offdiag_entry<S>(a.kp, a.pts, a.act[a.off[cc] + (r - cstart[j])], pc);
     } else if (r < nnear + a.geo.nproxy) {
-      v = green_at<S>(a.kp, dist_to(a.pts, pc, pxy + 3 * (r - nnear)));
+      v = green_at_s2<S>(a.kp, dist2_to(a.pts, pc, pxy + 3 * (r - nnear)));
     } else {
       v = S(a.kp.w);
     }
@@ -1239,7 +1264,7 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
            cudaStream_t st) {
   IdArgs a = a0;
   size_t sb = sizeof(S);
-  size_t extra = (size_t)a.mmax * sb + (size_t)a.nmax * sizeof(double) + 3 * (size_t)a.geo.nproxy * sizeof(double) +
+  size_t extra = (size_t)a.mmax * sb + 2 * (size_t)a.nmax * sizeof(double) + 3 * (size_t)a.geo.nproxy * sizeof(double) +
                  (size_t)a.nmax * sizeof(int) + (size_t)a.mmax * sizeof(int) + 64;
   size_t mbytes = (size_t)a.mmax * a.nmax * sb;
   const size_t limit = 200 * 1024;

@@ -20,9 +20,12 @@
 //
 // Lanes own rows (column-major factors -> coalesced loads); every lane keeps
 // CT accumulators for the tile's columns; the right-hand-side rows of the box
-// are staged 32 at a time in per-warp shared memory.  Leaf tiles read B and
-// write X in the caller's order through the tree permutation.
+// are staged 32 at a time in per-warp shared memory.  The per-depth vectors
+// are column-major (one column per right-hand side), so staging loads and
+// result stores are coalesced along the rows.  Leaf tiles read B and write X
+// in the caller's order through the tree permutation.
 #include <algorithm>
+#include <cstdlib>
 #include <cuda/atomic>
 #include <vector>
 
@@ -69,6 +72,7 @@ struct Plan {
   const int* perm;
   S* const* v;          // per depth: input of the up pass (v[L] unused: B is read directly)
   S* const* u;          // per depth: calD b, then x
+  const int64_t* ldv;   // per depth: leading dimension of v and u (column-major, ntot of the depth)
   const S* const* U;    // per depth factors
   const S* const* Lf;
   int* dispatch;
@@ -82,23 +86,26 @@ __device__ inline int ld_acquire(const int* p) {
   return a.load(cuda::memory_order_acquire);
 }
 
-// Lane 0 waits until *cnt >= target; returns false (and raises both flags:
-// the device one every warp polls, the host-mapped one the caller reads) on
-// timeout.
+// One thread waits until *cnt >= target; returns false (and raises both
+// flags: the device one every warp polls, the host-mapped one the caller
+// reads) on timeout.
+__device__ inline bool spin_until(const int* cnt, int target, int* flag, int* dflag) {
+  int spins = 0;
+  while (ld_acquire(cnt) < target) {
+    if (++spins > MAX_SPIN) {
+      atomicExch(dflag, 1);
+      atomicExch(flag, 1);
+      return false;
+    }
+    __nanosleep(100);
+  }
+  return true;
+}
+
+// Lane 0 of the warp waits (spin_until); the verdict is broadcast.
 __device__ inline bool wait_at_least(const int* cnt, int target, int* flag, int* dflag) {
   int ok = 1;
-  if ((threadIdx.x & 31) == 0) {
-    int spins = 0;
-    while (ld_acquire(cnt) < target) {
-      if (++spins > MAX_SPIN) {
-        atomicExch(dflag, 1);
-        atomicExch(flag, 1);
-        ok = 0;
-        break;
-      }
-      __nanosleep(100);
-    }
-  }
+  if ((threadIdx.x & 31) == 0) ok = spin_until(cnt, target, flag, dflag) ? 1 : 0;
   ok = __shfl_sync(0xffffffffu, ok, 0);
   __syncwarp();
   return ok != 0;
@@ -119,6 +126,10 @@ template <> __device__ inline c64 ldcg<c64>(const c64* p) {
   float2 t = __ldcg(reinterpret_cast<const float2*>(p));
   return c64(t.x, t.y);
 }
+template <> __device__ inline dfloat ldcg<dfloat>(const dfloat* p) {
+  float2 t = __ldcg(reinterpret_cast<const float2*>(p));
+  return dfloat(t.x, t.y);
+}
 
 // Read-only (non-coherent) loads for the factors, which no kernel writes
 // during a solve.
@@ -131,12 +142,17 @@ template <> __device__ inline c64 ldro<c64>(const c64* p) {
   float2 t = __ldg(reinterpret_cast<const float2*>(p));
   return c64(t.x, t.y);
 }
+template <> __device__ inline dfloat ldro<dfloat>(const dfloat* p) {
+  float2 t = __ldg(reinterpret_cast<const float2*>(p));
+  return dfloat(t.x, t.y);
+}
 
 template <class D, class S> __device__ inline D cv(S v) { return D(v); }
 template <> __device__ inline float cv<float, double>(double v) { return (float)v; }
 template <> __device__ inline double cv<double, float>(float v) { return (double)v; }
 template <> __device__ inline c64 cv<c64, c128>(c128 v) { return c64((float)v.re, (float)v.im); }
 template <> __device__ inline c128 cv<c128, c64>(c64 v) { return c128((double)v.re, (double)v.im); }
+template <> __device__ inline double cv<double, dfloat>(dfloat v) { return __dadd_rn((double)v.hi, (double)v.lo); }
 
 // acc[c] += sum_{q < qn} col[q * ld] * stage[q][c] for one 32-column chunk.
 // All factor loads of the chunk are issued before the FMAs (QB at a time)
@@ -187,6 +203,31 @@ struct StageRow<double, CT> {
   }
 };
 
+template <int CT>
+struct StageRow<dfloat, CT> {
+  __device__ static void fma(dfloat* acc, dfloat a, const dfloat* row) {
+    if (CT % 2 == 0) {
+      const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+      for (int c = 0; c < CT / 2; ++c) {
+        const float4 v = r4[c];
+        df_fma(acc[2 * c], a, dfloat(v.x, v.y));
+        df_fma(acc[2 * c + 1], a, dfloat(v.z, v.w));
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CT; ++c) df_fma(acc[c], a, row[c]);
+    }
+  }
+};
+
+// Leaf output: the value itself, or sub - value (forward operator used for a
+// residual b - A x).
+template <class SIO>
+__device__ __forceinline__ SIO leaf_out(const SIO* sub, int64_t i, SIO y) {
+  return sub ? sub[i] - y : y;
+}
+
 template <class S, int CT>
 __device__ __forceinline__ void chunk_fma(const S* col, size_t ld, int qn, const S* stage, S* acc) {
   constexpr int QB = CT == 1 ? 32 : (CT <= 8 ? 16 : 8);
@@ -201,7 +242,7 @@ __device__ __forceinline__ void chunk_fma(const S* col, size_t ld, int qn, const
 
 template <class S, class SIO, int CT>
 __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, int64_t ldb, SIO* X, int64_t ldx,
-                                                     int R, int epoch, int* flag) {
+                                                     const SIO* sub, int R, int epoch, int* flag) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   S* stage = reinterpret_cast<S*>(smem) + (size_t)warp * 32 * CT;   // [32][CT]
@@ -225,6 +266,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
       const S* Ub = p.U[d] + p.bt.uoff[g];
       const bool leaf = d == p.L;
       const S* vin = leaf ? nullptr : p.v[d];
+      const int64_t ldd = p.ldv[d];
       for (int c0 = tl.c0; c0 < tl.c1; c0 += CT) {
         const int cw = min(CT, tl.c1 - c0);
         S acc[CT];
@@ -245,7 +287,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
             } else {
 #pragma unroll
               for (int c = 0; c < CT; ++c)
-                stage[lane * CT + c] = c < cw ? ldcg(vin + pos * R + c0 + c) : S(0.0);
+                stage[lane * CT + c] = c < cw ? ldcg(vin + (int64_t)(c0 + c) * ldd + pos) : S(0.0);
             }
           }
           __syncwarp();
@@ -257,17 +299,21 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
             const int64_t dst = p.perm[off + r];
 #pragma unroll
             for (int c = 0; c < CT; ++c)
-              if (c < cw) X[dst + (int64_t)(c0 + c) * ldx] = cv<SIO, S>(acc[c]);
+              if (c < cw) {
+                const int64_t i = dst + (int64_t)(c0 + c) * ldx;
+                X[i] = leaf_out(sub, i, cv<SIO, S>(acc[c]));
+              }
           } else if (r < n) {
-            S* uo = p.u[d] + (off + r) * R + c0;
+            S* uo = p.u[d] + (int64_t)c0 * ldd + off + r;
 #pragma unroll
             for (int c = 0; c < CT; ++c)
-              if (c < cw) uo[c] = acc[c];
+              if (c < cw) uo[(int64_t)c * ldd] = acc[c];
           } else {
-            S* vo = p.v[d - 1] + (p.bt.skoff[g] + (r - n)) * R + c0;
+            const int64_t ldp = p.ldv[d - 1];
+            S* vo = p.v[d - 1] + (int64_t)c0 * ldp + p.bt.skoff[g] + (r - n);
 #pragma unroll
             for (int c = 0; c < CT; ++c)
-              if (c < cw) vo[c] = acc[c];
+              if (c < cw) vo[(int64_t)c * ldp] = acc[c];
           }
         }
       }
@@ -279,7 +325,8 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
       if (!wait_at_least(&p.dn_cnt[par], epoch * p.bt.dn_need[par], flag, p.dflag)) return;
       const int r = tl.r0 + lane;
       const S* Lb = p.Lf[d] + p.bt.loff[g];
-      const S* xpar = p.u[d - 1] + p.bt.skoff[g] * R;
+      const int64_t ldd = p.ldv[d], ldp = p.ldv[d - 1];
+      const S* xpar = p.u[d - 1] + p.bt.skoff[g];
       for (int c0 = tl.c0; c0 < tl.c1; c0 += CT) {
         const int cw = min(CT, tl.c1 - c0);
         S acc[CT];
@@ -289,23 +336,25 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
           const int qn = min(32, k - q0);
 #pragma unroll
           for (int c = 0; c < CT; ++c)
-            stage[lane * CT + c] = (lane < qn && c < cw) ? ldcg(xpar + (int64_t)(q0 + lane) * R + c0 + c) : S(0.0);
+            stage[lane * CT + c] = (lane < qn && c < cw) ? ldcg(xpar + (int64_t)(c0 + c) * ldp + q0 + lane) : S(0.0);
           __syncwarp();
           if (r < n) chunk_fma<S, CT>(Lb + r + (size_t)q0 * n, (size_t)n, qn, stage, acc);
           __syncwarp();
         }
         if (r < n) {
+          S* uo = p.u[d] + (int64_t)c0 * ldd + off + r;
           if (d == p.L) {
             const int64_t dst = p.perm[off + r];
-            const S* uo = p.u[d] + (off + r) * R + c0;
 #pragma unroll
             for (int c = 0; c < CT; ++c)
-              if (c < cw) X[dst + (int64_t)(c0 + c) * ldx] = cv<SIO, S>(ldcg(uo + c) + acc[c]);
+              if (c < cw) {
+                const int64_t i = dst + (int64_t)(c0 + c) * ldx;
+                X[i] = leaf_out(sub, i, cv<SIO, S>(ldcg(uo + (int64_t)c * ldd) + acc[c]));
+              }
           } else {
-            S* uo = p.u[d] + (off + r) * R + c0;
 #pragma unroll
             for (int c = 0; c < CT; ++c)
-              if (c < cw) uo[c] = ldcg(uo + c) + acc[c];
+              if (c < cw) uo[(int64_t)c * ldd] = ldcg(uo + (int64_t)c * ldd) + acc[c];
           }
         }
       }
@@ -314,15 +363,236 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
   }
 }
 
+
+// ------------------------------------------------------------- CTA tiles
+// Many right-hand sides: the same tile list and dependency counters, but a
+// tile is a 32-row x TN-column block of one box's product computed by a
+// whole CTA as a small register-blocked GEMM.  Factor and input chunks
+// (32 deep) are staged in shared memory with coalesced loads (the factor
+// along its rows, the inputs along their column-major rows); every thread
+// accumulates an RPT x CPT block; the result block is transposed through
+// shared memory so that its stores are coalesced along the rows as well.
+constexpr int C_NT = 128, C_TM = 32, C_TK = 32;
+
+template <int TN> struct CtaShape;
+template <> struct CtaShape<128> { static constexpr int CG = 16, CPT = 8, RPT = 4; };
+template <> struct CtaShape<64> { static constexpr int CG = 16, CPT = 4, RPT = 4; };
+template <> struct CtaShape<32> { static constexpr int CG = 8, CPT = 4, RPT = 2; };
+
+template <class S> __device__ __forceinline__ void mac(S& acc, S a, S b) { acc += a * b; }
+template <> __device__ __forceinline__ void mac<dfloat>(dfloat& acc, dfloat a, dfloat b) { df_fma(acc, a, b); }
+
+// N consecutive elements from 16-byte aligned shared memory.
+template <class S, int N> struct Lds {
+  __device__ static void run(const S* p, S* o) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[i] = p[i];
+  }
+};
+template <int N> struct Lds<float, N> {
+  __device__ static void run(const float* p, float* o) {
+    static_assert(N % 2 == 0, "even vector");
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+      for (int i = 0; i < N / 4; ++i) {
+        const float4 v = reinterpret_cast<const float4*>(p)[i];
+        o[4 * i] = v.x; o[4 * i + 1] = v.y; o[4 * i + 2] = v.z; o[4 * i + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < N / 2; ++i) {
+        const float2 v = reinterpret_cast<const float2*>(p)[i];
+        o[2 * i] = v.x; o[2 * i + 1] = v.y;
+      }
+    }
+  }
+};
+template <int N> struct Lds<dfloat, N> {
+  __device__ static void run(const dfloat* p, dfloat* o) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const float4 v = reinterpret_cast<const float4*>(p)[i];
+      o[2 * i] = dfloat(v.x, v.y);
+      o[2 * i + 1] = dfloat(v.z, v.w);
+    }
+  }
+};
+template <int N> struct Lds<double, N> {
+  __device__ static void run(const double* p, double* o) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const double2 v = reinterpret_cast<const double2*>(p)[i];
+      o[2 * i] = v.x; o[2 * i + 1] = v.y;
+    }
+  }
+};
+
+template <class S, class SIO, int TN>
+__global__ void __launch_bounds__(C_NT) k_solve_cta(Plan<S> p, const SIO* B, int64_t ldb, SIO* X, int64_t ldx,
+                                                    const SIO* sub, int epoch, int* flag) {
+  using Sh = CtaShape<TN>;
+  constexpr int RPT = Sh::RPT, CPT = Sh::CPT, CG = Sh::CG;
+  constexpr int BP = TN + 16 / (int)sizeof(S);   // padded input row (keeps 16-byte alignment)
+  constexpr int OP = C_TM + 1;                   // padded output column
+  constexpr int BSZ = C_TK * BP > TN * OP ? C_TK * BP : TN * OP;
+  extern __shared__ __align__(16) unsigned char smem[];
+  S* As = reinterpret_cast<S*>(smem);   // [TK][TM]
+  S* Bs = As + C_TK * C_TM;             // [TK][BP]; the output block [TN][OP] reuses it
+  (void)BSZ;
+  __shared__ int s_tile, s_ok;
+  const int tid = threadIdx.x;
+  const int tx = tid % CG, ty = tid / CG;
+  for (;;) {
+    if (tid == 0) {
+      const int t = atomicAdd(p.dispatch, 1);
+      int ok = 1;
+      if (t < p.ntiles) {
+        if (*(volatile int*)p.dflag) {
+          ok = 0;   // another CTA gave up waiting: leave too
+        } else {
+          const Tile tl = p.tiles[t];
+          if (tl.kind != T_DOWN) {
+            if (p.bt.up_need[tl.g] > 0)
+              ok = spin_until(&p.up_cnt[tl.g], epoch * p.bt.up_need[tl.g], flag, p.dflag);
+          } else {
+            const int par = p.bt.parent[tl.g];
+            ok = spin_until(&p.dn_cnt[par], epoch * p.bt.dn_need[par], flag, p.dflag);
+          }
+        }
+      }
+      s_tile = t;
+      s_ok = ok;
+    }
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= p.ntiles || !s_ok) return;
+    const Tile tl = p.tiles[t];
+    const int g = tl.g;
+    const int d = p.bt.depth[g];
+    const int n = p.bt.n[g], k = p.bt.k[g];
+    const int64_t off = p.bt.off[g];
+    const bool down = tl.kind == T_DOWN;
+    const int rows = down ? n : n + k;     // the root has k = 0
+    const int K = down ? k : n;
+    const S* A = down ? p.Lf[d] + p.bt.loff[g] : p.U[d] + p.bt.uoff[g];
+    const bool leaf_in = !down && d == p.L;
+    const S* vin = down ? p.u[d - 1] : (leaf_in ? nullptr : p.v[d]);
+    const int64_t ldin = down ? p.ldv[d - 1] : p.ldv[d];
+    const int64_t in0 = down ? p.bt.skoff[g] : off;
+    const int r0 = tl.r0, c0 = tl.c0;
+    const int cw = min(TN, tl.c1 - c0);
+
+    S acc[RPT][CPT];
+#pragma unroll
+    for (int a = 0; a < RPT; ++a)
+#pragma unroll
+      for (int b = 0; b < CPT; ++b) acc[a][b] = S(0.0);
+
+    for (int k0 = 0; k0 < K; k0 += C_TK) {
+      const int kn = min(C_TK, K - k0);
+      __syncthreads();   // the previous chunk (or tile) is done with As / Bs
+      {
+        const int i = tid & 31;
+        const bool oki = r0 + i < rows;
+#pragma unroll
+        for (int kk = tid >> 5; kk < C_TK; kk += C_NT / 32)
+          As[kk * C_TM + i] = (oki && kk < kn) ? ldro(A + (r0 + i) + (size_t)(k0 + kk) * rows) : S(0.0);
+      }
+      {
+        const int kk = tid & 31;
+        const bool okk = kk < kn;
+        int64_t src = 0;
+        if (okk) src = leaf_in ? (int64_t)p.perm[off + k0 + kk] : in0 + k0 + kk;
+#pragma unroll 8
+        for (int j = tid >> 5; j < TN; j += C_NT / 32) {
+          S v = S(0.0);
+          if (okk && j < cw)
+            v = leaf_in ? cv<S, SIO>(B[src + (int64_t)(c0 + j) * ldb]) : ldcg(vin + (int64_t)(c0 + j) * ldin + src);
+          Bs[kk * BP + j] = v;
+        }
+      }
+      __syncthreads();
+      for (int kk = 0; kk < kn; ++kk) {
+        S a[RPT], b[CPT];
+        Lds<S, RPT>::run(As + kk * C_TM + ty * RPT, a);
+        Lds<S, CPT>::run(Bs + kk * BP + tx * CPT, b);
+#pragma unroll
+        for (int x = 0; x < RPT; ++x)
+#pragma unroll
+          for (int y = 0; y < CPT; ++y) mac(acc[x][y], a[x], b[y]);
+      }
+    }
+    __syncthreads();   // every thread is done reading As / Bs
+    S* Os = Bs;
+#pragma unroll
+    for (int x = 0; x < RPT; ++x)
+#pragma unroll
+      for (int y = 0; y < CPT; ++y) Os[(tx * CPT + y) * OP + ty * RPT + x] = acc[x][y];
+    __syncthreads();
+    {
+      const int i = tid & 31;
+      const int r = r0 + i;
+      if (r < rows) {
+        if (!down) {
+          if (r < n && tl.kind == T_ROOT && d == p.L) {   // single-box tree: the root is the answer
+            const int64_t dst = p.perm[off + r];
+            for (int j = tid >> 5; j < cw; j += C_NT / 32) {
+              const int64_t idx = dst + (int64_t)(c0 + j) * ldx;
+              X[idx] = leaf_out(sub, idx, cv<SIO, S>(Os[j * OP + i]));
+            }
+          } else if (r < n) {
+            const int64_t ld = p.ldv[d];
+            S* uo = p.u[d] + (int64_t)c0 * ld + off + r;
+            for (int j = tid >> 5; j < cw; j += C_NT / 32) uo[(int64_t)j * ld] = Os[j * OP + i];
+          } else {
+            const int64_t ld = p.ldv[d - 1];
+            S* vo = p.v[d - 1] + (int64_t)c0 * ld + p.bt.skoff[g] + (r - n);
+            for (int j = tid >> 5; j < cw; j += C_NT / 32) vo[(int64_t)j * ld] = Os[j * OP + i];
+          }
+        } else {
+          const int64_t ld = p.ldv[d];
+          S* uo = p.u[d] + (int64_t)c0 * ld + off + r;
+          if (d == p.L) {
+            const int64_t dst = p.perm[off + r];
+            for (int j = tid >> 5; j < cw; j += C_NT / 32) {
+              const int64_t idx = dst + (int64_t)(c0 + j) * ldx;
+              X[idx] = leaf_out(sub, idx, cv<SIO, S>(ldcg(uo + (int64_t)j * ld) + Os[j * OP + i]));
+            }
+          } else {
+            for (int j = tid >> 5; j < cw; j += C_NT / 32)
+              uo[(int64_t)j * ld] = ldcg(uo + (int64_t)j * ld) + Os[j * OP + i];
+          }
+        }
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      if (tl.kind == T_UP) atomicAdd(&p.up_cnt[p.bt.parent[g]], 1);
+      else atomicAdd(&p.dn_cnt[g], 1);
+    }
+  }
+}
+
+template <class S, int TN>
+constexpr size_t cta_smem() {
+  constexpr int BP = TN + 16 / (int)sizeof(S);
+  constexpr int OP = C_TM + 1;
+  constexpr int BSZ = C_TK * BP > TN * OP ? C_TK * BP : TN * OP;
+  return sizeof(S) * (size_t)(C_TK * C_TM + BSZ);
+}
+
 // ------------------------------------------------------------------- host
 struct PersPlan {
   int prec = -1, R = 0, CT = 0;
+  int TN = 0;                // > 0: CTA-tile kernel with TN columns per tile
   int ntiles = 0, nbox = 0;
   Tile* tiles = nullptr;
   BoxTab bt{};
   int* counters = nullptr;   // dispatch | device flag | up_cnt[G] | dn_cnt[G]
   int epoch = 0;
   void** ptrs = nullptr;     // v[L+1] | u[L+1] | U[L+1] | Lf[L+1]
+  int64_t* ldv = nullptr;    // per depth ntot (leading dimension of v and u)
   int* flag_host = nullptr;  // mapped pinned
   int* flag_dev = nullptr;
   int grid = 0;
@@ -335,10 +605,25 @@ struct PersCache {
   std::vector<PersPlan*> plans;
 };
 
+// Column block of the CTA-tile kernel for R right-hand sides (0: the warp
+// kernel, which suits few columns).  RS_SOLVE_TN overrides it (32, 64, 128;
+// 0 forces the warp kernel).
+int cta_tn(bool cplx, int prec, int R) {
+  static const int forced = [] {
+    const char* e = getenv("RS_SOLVE_TN");
+    return e ? atoi(e) : -1;
+  }();
+  const int cap = cplx && prec == RS_PREC_FP64 ? 64 : 128;
+  if (forced == 0) return 0;
+  if (forced == 32 || forced == 64 || forced == 128) return R < 16 ? 0 : std::min(forced, cap);
+  if (R < 32) return 0;
+  return std::min(cap, R >= 128 ? 128 : R >= 64 ? 64 : 32);
+}
+
 int ct_for(bool cplx, int prec, int R) {
   if (R == 1) return 1;
   if (R <= 8) return 8;
-  if (prec == RS_PREC_FP64) return cplx ? 8 : 16;
+  if (prec == RS_PREC_FP64 || prec == MODE_FWD_DF) return cplx ? 8 : 16;
   return cplx ? 16 : 32;
 }
 
@@ -350,17 +635,20 @@ int dev_upload(PersPlan* P, T** d, const std::vector<T>& v, cudaStream_t st) {
   return RS_OK;
 }
 
-template <class S, class SIO, int CT>
-int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X, int64_t ldx, cudaStream_t st) {
-  size_t smem = sizeof(S) * 32 * CT * P_WARPS;
-  if (smem > 48 * 1024)
-    RS_CUDA(cudaFuncSetAttribute(k_solve_pers<S, SIO, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+template <class S, class SIO, int CT, int TN>
+int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X, int64_t ldx, const SIO* sub,
+                cudaStream_t st) {
+  const size_t smem = TN ? cta_smem<S, (TN ? TN : 32)>() : sizeof(S) * 32 * CT * P_WARPS;
+  const int nt = TN ? C_NT : P_NT;
+  const void* fn = TN ? (const void*)k_solve_cta<S, SIO, (TN ? TN : 32)> : (const void*)k_solve_pers<S, SIO, CT>;
+  if (smem > 48 * 1024) RS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (P->grid == 0) {
     int dev = 0, nsm = 0, occ = 0;
     RS_CUDA(cudaGetDevice(&dev));
     RS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_pers<S, SIO, CT>, P_NT, smem));
-    P->grid = std::max(1, std::min(nsm * std::max(occ, 1), div_up(P->ntiles, P_WARPS)));
+    RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, smem));
+    const int per_block = TN ? 1 : P_WARPS;   // tiles a block works on at once
+    P->grid = std::max(1, std::min(nsm * std::max(occ, 1), div_up(P->ntiles, per_block)));
   }
   if (++P->epoch > (1 << 20) || P->dirty) {   // counters restart (overflow guard, or after a timeout)
     RS_CUDA(cudaMemsetAsync(P->counters, 0, sizeof(int) * (2 + 2 * (size_t)P->nbox), st));
@@ -381,13 +669,17 @@ int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X
   pl.u = (S* const*)(P->ptrs + L1);
   pl.U = (const S* const*)(P->ptrs + 2 * L1);
   pl.Lf = (const S* const*)(P->ptrs + 3 * L1);
+  pl.ldv = P->ldv;
   pl.dispatch = P->counters;
   pl.dflag = P->counters + 1;
   pl.up_cnt = P->counters + 2;
   pl.dn_cnt = P->counters + 2 + P->nbox;
   *P->flag_host = 0;
   prof_begin(prec_cat(P->prec), st);
-  k_solve_pers<S, SIO, CT><<<P->grid, P_NT, smem, st>>>(pl, B, ldb, X, ldx, R, wait_epoch, P->flag_dev);
+  if constexpr (TN > 0)
+    k_solve_cta<S, SIO, TN><<<P->grid, C_NT, smem, st>>>(pl, B, ldb, X, ldx, sub, wait_epoch, P->flag_dev);
+  else
+    k_solve_pers<S, SIO, CT><<<P->grid, P_NT, smem, st>>>(pl, B, ldb, X, ldx, sub, R, wait_epoch, P->flag_dev);
   RS_CHECK_LAUNCH();
   double sS = sizeof(S), fac = 0.0;
   for (auto& lv : h->lv) fac += (double)lv.usz + (double)lv.lsz;
@@ -398,7 +690,9 @@ int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X
 
 }  // namespace
 
-int prec_cat(int prec) { return prec == RS_PREC_FP64 ? P_SOLVE64 : P_SOLVE32; }
+int prec_cat(int prec) {
+  return prec == RS_PREC_FP64 ? P_SOLVE64 : prec == RS_PREC_FP32 ? P_SOLVE32 : P_RESID;
+}
 
 void free_pers(Handle* h) {
   PersCache* c = (PersCache*)h->pers;
@@ -421,8 +715,11 @@ static int refresh_ptrs(Handle* h, PersPlan* P, cudaStream_t st) {
   for (int d = 0; d <= L; ++d) {
     ptrs[d] = w.v[d];
     ptrs[(L + 1) + d] = w.u[d];
-    ptrs[2 * (L + 1) + d] = P->prec == RS_PREC_FP64 ? h->lv[d].U : h->lv[d].U32;
-    ptrs[3 * (L + 1) + d] = P->prec == RS_PREC_FP64 ? h->lv[d].Lf : h->lv[d].Lf32;
+    const Level& lv = h->lv[d];
+    void* const Us[4] = {lv.U, lv.U32, lv.FU32, lv.FUdf};
+    void* const Ls[4] = {lv.Lf, lv.Lf32, lv.FL32, lv.FLdf};
+    ptrs[2 * (L + 1) + d] = Us[P->prec];
+    ptrs[3 * (L + 1) + d] = Ls[P->prec];
   }
   if (!P->ptrs) {
     RS_CUDA(cudaMalloc((void**)&P->ptrs, sizeof(void*) * ptrs.size()));
@@ -450,6 +747,7 @@ static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out)
   P->prec = prec;
   P->R = R;
   P->CT = ct_for(h->cplx, prec, R);
+  P->TN = cta_tn(h->cplx, prec, R);
   const int L = h->L;
   // global box numbering: depth L first, ..., depth 0 last
   std::vector<int> gbase(L + 1);
@@ -480,7 +778,7 @@ static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out)
     int64_t rt = 0;
     for (int b = 0; b < lv.nbox; ++b) rt += div_up(down ? lv.h_n[b] : lv.h_n[b] + lv.h_k[b], 32);
     int split = (int)std::max<int64_t>(1, std::min<int64_t>(nchunk, 8192 / std::max<int64_t>(1, rt)));
-    int per = div_up(nchunk, split) * P->CT;
+    int per = P->TN ? P->TN : div_up(nchunk, split) * P->CT;
     std::vector<std::pair<int, int>> cr;
     for (int c = 0; c < R; c += per) cr.push_back({c, std::min(R, c + per)});
     return cr;
@@ -523,6 +821,9 @@ static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out)
   RS_TRY(dev_upload(P, &P->bt.parent, parent, st));
   RS_TRY(dev_upload(P, &P->bt.up_need, up_need, st));
   RS_TRY(dev_upload(P, &P->bt.dn_need, dn_need, st));
+  std::vector<int64_t> ldv(L + 1);
+  for (int d = 0; d <= L; ++d) ldv[d] = std::max<int64_t>(1, h->lv[d].ntot);
+  RS_TRY(dev_upload(P, &P->ldv, ldv, st));
   std::vector<int> zeros(2 + 2 * (size_t)G, 0);
   RS_TRY(dev_upload(P, &P->counters, zeros, st));
   RS_TRY(refresh_ptrs(h, P, st));
@@ -535,14 +836,28 @@ static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out)
 }
 
 template <class S, class SIO>
-static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO* X, int64_t ldx, cudaStream_t st) {
+static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO* X, int64_t ldx, cudaStream_t st,
+                     const SIO* sub = nullptr) {
   PersPlan* P = nullptr;
   RS_TRY(get_plan(h, prec, R, st, &P));
-  switch (P->CT) {
-    case 1: RS_TRY((launch_pers<S, SIO, 1>(h, P, B, ldb, R, X, ldx, st))); break;
-    case 8: RS_TRY((launch_pers<S, SIO, 8>(h, P, B, ldb, R, X, ldx, st))); break;
-    case 16: RS_TRY((launch_pers<S, SIO, 16>(h, P, B, ldb, R, X, ldx, st))); break;
-    case 32: RS_TRY((launch_pers<S, SIO, 32>(h, P, B, ldb, R, X, ldx, st))); break;
+  switch (P->TN) {
+    case 128:
+      if constexpr (sizeof(S) <= 8) {
+        RS_TRY((launch_pers<S, SIO, 1, 128>(h, P, B, ldb, R, X, ldx, sub, st)));
+        break;
+      }
+      return fail(RS_ERR_ARG, "bad column tile");
+    case 64: RS_TRY((launch_pers<S, SIO, 1, 64>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+    case 32: RS_TRY((launch_pers<S, SIO, 1, 32>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+    case 0:
+      switch (P->CT) {
+        case 1: RS_TRY((launch_pers<S, SIO, 1, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+        case 8: RS_TRY((launch_pers<S, SIO, 8, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+        case 16: RS_TRY((launch_pers<S, SIO, 16, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+        case 32: RS_TRY((launch_pers<S, SIO, 32, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+        default: return fail(RS_ERR_ARG, "bad column tile");
+      }
+      break;
     default: return fail(RS_ERR_ARG, "bad column tile");
   }
   h->pers_last = P;
@@ -559,14 +874,27 @@ int solve_pers_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrh
   return pers_impl<float, double>(h, prec, (const double*)d_B, ldb, nrhs, (double*)d_X, ldx, st);
 }
 
-// After the stream has been synchronized: timeout flag of the last solve.
+int solve_pers_device_sub(Handle* h, int mode, const double* d_B, int64_t ldb, int nrhs, double* d_X, int64_t ldx,
+                          const double* d_sub, cudaStream_t st) {
+  if (h->cplx || (mode != MODE_FWD_F32 && mode != MODE_FWD_DF))
+    return fail(RS_ERR_ARG, "forward operator: real kernels only");
+  if (mode == MODE_FWD_DF) return pers_impl<dfloat, double>(h, mode, d_B, ldb, nrhs, d_X, ldx, st, d_sub);
+  return pers_impl<float, double>(h, mode, d_B, ldb, nrhs, d_X, ldx, st, d_sub);
+}
+
+// After the stream has been synchronized: timeout flags of every plan that
+// ran since the last check.
 int pers_check(Handle* h) {
-  PersPlan* P = (PersPlan*)h->pers_last;
-  if (P && P->flag_host && *(volatile int*)P->flag_host) {
-    P->dirty = true;
-    *P->flag_host = 0;
-    return fail(RS_ERR_TIMEOUT, "solve: a dependency wait ran out (flag set by the device)");
-  }
+  PersCache* c = (PersCache*)h->pers;
+  if (!c) return RS_OK;
+  int rc = RS_OK;
+  for (PersPlan* P : c->plans)
+    if (P->flag_host && *(volatile int*)P->flag_host) {
+      P->dirty = true;
+      *P->flag_host = 0;
+      rc = RS_ERR_TIMEOUT;
+    }
+  if (rc != RS_OK) return fail(RS_ERR_TIMEOUT, "solve: a dependency wait ran out (flag set by the device)");
   return RS_OK;
 }
 
