@@ -211,4 +211,54 @@ __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
   return df_renorm(dfloat(t, __fadd_rn(a.lo, __fadd_rn(err, b.lo))));
 }
 
+
+// ------------------------------------------------- conversions off the FP64 pipe
+// Double <-> float conversions issue on the FP64 pipe, which on this GPU runs
+// at 1/64 of the FP32 rate; in the bandwidth kernels they would cost more
+// than the arithmetic.  These do the same conversions with integer
+// instructions, by the IEEE-754 binary64/binary32 layouts (sign | biased
+// exponent | fraction; biases 1023 and 127): round to nearest even by adding
+// half an ulp (minus one, plus the kept lowest bit) before the shift.  Values
+// outside the float normal range take the hardware conversion.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hi = (unsigned int)(u >> 32);
+  const unsigned int e = (hi >> 20) & 0x7FFu;
+  if (e - 897u < 253u) {   // float exponent e - 896 in [1, 253]: no overflow after a rounding carry
+    const unsigned long long m = u & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long r = m + 0x0FFFFFFFull + ((m >> 29) & 1ull);
+    return __uint_as_float(((unsigned int)(r >> 29) - (896u << 23)) | (hi & 0x80000000u));
+  }
+  return __double2float_rn(x);
+}
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int mag = b & 0x7FFFFFFFu;
+  if (mag - 0x00800000u < 0x7F000000u)   // normal
+    return __hiloint2double((int)((b & 0x80000000u) | ((mag >> 3) + (896u << 20))), (int)(b << 29));
+  if (mag == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  return (double)f;
+}
+// x = hi + lo: hi is x truncated to 24 significant bits (exact), lo the
+// remaining 29 bits rounded to a float (|lo| < ulp(hi), error <= 2^-24 |lo|).
+__device__ __forceinline__ dfloat f64_to_df(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hiw = (unsigned int)(u >> 32);
+  const unsigned int e = (hiw >> 20) & 0x7FFu;
+  if (e - 949u < 202u) {   // both parts normal floats: e in [949, 1150]
+    const unsigned int sign = hiw & 0x80000000u;
+    const unsigned long long m = u & 0x7FFFFFFFFFFFFFFFull;
+    const float h = __uint_as_float(((unsigned int)(m >> 29) - (896u << 23)) | sign);
+    const unsigned int L = (unsigned int)m & 0x1FFFFFFFu;   // low 29 fraction bits
+    // float(L) from two exact pieces (2^23 + v has v in its fraction field)
+    const float lh = __uint_as_float(0x4B000000u | (L >> 6)) - 8388608.0f;
+    const float ll = __uint_as_float(0x4B000000u | (L & 63u)) - 8388608.0f;
+    const float lf = __fmaf_rn(lh, 64.0f, ll);
+    const float scale = __uint_as_float((e - 948u) << 23);   // 2^(e - 1023 - 52)
+    return dfloat(h, __uint_as_float(__float_as_uint(__fmul_rn(lf, scale)) | sign));
+  }
+  return dfloat(x);
+}
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+
 }  // namespace rs

@@ -24,6 +24,8 @@
 #include <cmath>
 #include <vector>
 
+#include <cuda/atomic>
+
 #include "rs_internal.h"
 
 namespace rs {
@@ -33,6 +35,13 @@ namespace {
 constexpr int ID_NT = 256;
 constexpr int FA_NT = 256;
 constexpr int FA_SM_NT = 128;
+
+// Load through L2 (data another CTA of the same launch may have written).
+template <class S> __device__ inline S ldcg_s(const S* p) { return __ldcg(p); }
+template <> __device__ inline c128 ldcg_s<c128>(const c128* p) {
+  const double2 t = __ldcg(reinterpret_cast<const double2*>(p));
+  return c128(t.x, t.y);
+}
 
 template <class S> __device__ inline S scal(S a, double s);
 template <> __device__ inline double scal<double>(double a, double s) { return a * s; }
@@ -340,6 +349,38 @@ struct BigId {
 constexpr int BI_NT = 128;
 constexpr int BI_CB = 8;
 
+// Grid-wide barrier of a cooperative launch (every CTA resident): CTAs add
+// to a monotonic arrival counter and wait for gridDim.x arrivals per step.
+// Waits are bounded: past BAR_SPIN polls a CTA raises *flag and leaves, and
+// every waiter also polls the flag, so a stuck grid drains instead of hanging.
+constexpr int BAR_SPIN = 1 << 22;
+struct GridBar {
+  unsigned int* count;
+  int* flag;
+};
+__device__ inline bool grid_sync(GridBar gb, unsigned int target) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(gb.count, 1u);
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(*gb.count);
+    int ok = 1, spins = 0;
+    while (cnt.load(cuda::memory_order_acquire) < target) {
+      if (*(volatile int*)gb.flag || ++spins > BAR_SPIN) {
+        atomicExch(gb.flag, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 template <class S>
 __global__ void __launch_bounds__(BI_NT) k_bbid_fill(IdArgs a, BigId g, S* Mws, int maxn) {
   __shared__ int cstart[28];
@@ -394,30 +435,38 @@ __global__ void __launch_bounds__(BI_NT) k_bbid_fill(IdArgs a, BigId g, S* Mws, 
   }
 }
 
+// One pivot step.  With Ms (cooperative launch) the CTA's own columns are
+// also kept in shared memory, [BI_CB][m]: read from there, written to both.
 template <class S>
-__global__ void __launch_bounds__(BI_NT) k_bbid_step(IdArgs a, BigId g, S* Mws, int j, int ncb, int* lperm) {
+__device__ void bbid_body(const IdArgs& a, const BigId& g, S* Mws, int j, int ncb, int* lperm, S* Ms) {
   extern __shared__ __align__(16) unsigned char bi_smem[];
   S* u = reinterpret_cast<S*>(bi_smem);                  // mmax entries
   int* mp = reinterpret_cast<int*>(u + a.mmax);          // nmax entries
   __shared__ int s_p, s_stop;
   __shared__ double s_rjj, s_r00;
+  __shared__ int s_kk;
   const int b = blockIdx.x / ncb, cb = blockIdx.x % ncb;
   const int n = a.n[b], m = g.m[b];
   const int kmax = min(m, n);
-  if (j >= kmax || g.kk[b] < kmax) return;   // past the rank or already stopped
+  // Data written by other CTAs during the step loop (maps, norms, the pivot
+  // column, rank and R_00) is read through L2 (__ldcg).  The rank is read
+  // once per CTA so the early exit below is uniform.
+  if (threadIdx.x == 0) s_kk = __ldcg(g.kk + b);
+  __syncthreads();
+  if (j >= kmax || s_kk < kmax) return;   // past the rank or already stopped
   if (cb * BI_CB >= n) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t no = g.noff[b];
   const int* map_in = (j & 1) ? g.map1 + no : g.map0 + no;
   int* map_out = (j & 1) ? g.map0 + no : g.map1 + no;
-  for (int q = tid; q < n; q += BI_NT) mp[q] = map_in[q];
+  for (int q = tid; q < n; q += BI_NT) mp[q] = __ldcg(map_in + q);
   __syncthreads();
   if (warp == 0) {
     double best = -1.0;
     int bi = n;
     const double* nrm_in = g.nrm + (j & 1) * g.ntot;
     for (int q = j + lane; q < n; q += 32) {
-      double v = nrm_in[no + mp[q]];
+      double v = __ldcg(nrm_in + no + mp[q]);
       if (v > best) { best = v; bi = q; }
     }
 #pragma unroll
@@ -428,7 +477,7 @@ __global__ void __launch_bounds__(BI_NT) k_bbid_step(IdArgs a, BigId g, S* Mws, 
     }
     if (lane == 0) {
       double rjj = sqrt(best);
-      double r00 = j == 0 ? rjj : g.r00[b];
+      double r00 = j == 0 ? rjj : __ldcg(g.r00 + b);
       int stop = j == 0 ? !(rjj > 0.0) : (rjj <= a.eps * r00);
       s_p = bi;
       s_rjj = rjj;
@@ -464,11 +513,11 @@ __global__ void __launch_bounds__(BI_NT) k_bbid_step(IdArgs a, BigId g, S* Mws, 
   // reflector from the pivot column (rows j..m-1)
   const int pj = mp[j];
   const S* pcol = Mws + g.moff[b] + (size_t)pj * m;
-  const S alpha = pcol[j];
+  const S alpha = ldcg_s(pcol + j);
   const double aa = sqrt(abs2(alpha));
   const S phase = aa > 0.0 ? scal(alpha, 1.0 / aa) : S(1.0);
   const S beta = scal(phase, -rjj);
-  for (int r = j + tid; r < m; r += BI_NT) u[r - j] = r == j ? alpha - beta : pcol[r];
+  for (int r = j + tid; r < m; r += BI_NT) u[r - j] = r == j ? alpha - beta : ldcg_s(pcol + r);
   const double f = 1.0 / (rjj * (rjj + aa));
   __syncthreads();
   // columns owned by this CTA that are still unpivoted (position > j)
@@ -485,23 +534,64 @@ __global__ void __launch_bounds__(BI_NT) k_bbid_step(IdArgs a, BigId g, S* Mws, 
     const int q = posof[cl];
     if (c >= n || q < 0) continue;
     S* col = Mws + g.moff[b] + (size_t)c * m;
+    S* cs = Ms ? Ms + (size_t)cl * m : col;
     if (q == j) {   // the pivot column: R_jj goes to rdiag (its rows are read by every CTA this step)
       if (lane == 0) reinterpret_cast<S*>(g.rdiag)[no + j] = beta;
       continue;
     }
     S s = S(0.0);
-    for (int r = j + lane; r < m; r += 32) s += conj_(u[r - j]) * col[r];
+    for (int r = j + lane; r < m; r += 32) s += conj_(u[r - j]) * cs[r];
     s = warp_sum(s);
     s = shfl(s, 0);
     const S fs = scal(s, f);
     double s2 = 0.0;
     for (int r = j + lane; r < m; r += 32) {
-      const S v = col[r] - u[r - j] * fs;
-      col[r] = v;
+      const S v = cs[r] - u[r - j] * fs;
+      cs[r] = v;
+      if (Ms) col[r] = v;
       if (r > j) s2 += abs2(v);
     }
     s2 = warp_sum(s2);
     if (lane == 0) g.nrm[((j + 1) & 1) * g.ntot + no + c] = s2;   // read by the next step only
+  }
+}
+
+template <class S>
+__global__ void __launch_bounds__(BI_NT) k_bbid_step(IdArgs a, BigId g, S* Mws, int j, int ncb, int* lperm) {
+  bbid_body<S>(a, g, Mws, j, ncb, lperm, nullptr);
+}
+
+// All pivot steps of a level in one cooperative launch: a grid barrier
+// between steps, and an exit once every box has found its rank.
+template <class S>
+__global__ void __launch_bounds__(BI_NT) k_bbid_coop(IdArgs a, BigId g, S* Mws, int nsteps, int ncb, int nb,
+                                                     int* lperm, GridBar gb) {
+  __shared__ int s_any;
+  extern __shared__ __align__(16) unsigned char bi_smem[];
+  // after u[mmax] | mp[nmax]: the CTA's own columns [BI_CB][m]
+  const size_t head = ((sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax) + 15) & ~(size_t)15;
+  S* Ms = reinterpret_cast<S*>(bi_smem + head);
+  {
+    const int b = blockIdx.x / ncb, cb = blockIdx.x % ncb;
+    const int n = a.n[b], m = g.m[b];
+    const int nc = max(0, min(n, cb * BI_CB + BI_CB) - cb * BI_CB);
+    const S* src = Mws + g.moff[b] + (size_t)cb * BI_CB * m;
+    for (int e = threadIdx.x; e < nc * m; e += BI_NT) Ms[e] = src[e];
+    __syncthreads();
+  }
+  for (int j = 0; j < nsteps; ++j) {
+    bbid_body<S>(a, g, Mws, j, ncb, lperm, Ms);
+    if (!grid_sync(gb, (unsigned int)(j + 1) * gridDim.x)) return;
+    if (threadIdx.x == 0) {
+      int any = 0;
+      for (int b = 0; b < nb && !any; ++b) {
+        const int kmax = min(g.m[b], a.n[b]);
+        if (__ldcg(g.kk + b) == kmax && j + 1 < kmax) any = 1;
+      }
+      s_any = any;
+    }
+    __syncthreads();
+    if (!s_any) return;
   }
 }
 
@@ -922,7 +1012,7 @@ __global__ void k_bb_assemble(FaArgs a, BigArgs g, const S* cLam, S* ws, int max
 // is read from pbuf[j % 2]; the owner of column j+1 writes it, updated, to
 // pbuf[(j+1) % 2].  Every CTA finds the same pivot.
 template <class S, class Dims>
-__global__ void __launch_bounds__(BB_NT) k_bb_gj_step(BigArgs g, S* ws, Dims dims, int j, int ncb, int* bad) {
+__device__ void bb_gj_body(const BigArgs& g, S* ws, const Dims& dims, int j, int ncb, int* bad) {
   extern __shared__ __align__(16) unsigned char bb_smem[];
   S* mult = reinterpret_cast<S*>(bb_smem);   // m entries
   __shared__ int s_p;
@@ -938,7 +1028,7 @@ __global__ void __launch_bounds__(BB_NT) k_bb_gj_step(BigArgs g, S* ws, Dims dim
     double best = -1.0;
     int bi = j;
     for (int r = j + lane; r < m; r += 32) {
-      double v = abs2(pb_in[r]);
+      double v = abs2(ldcg_s(pb_in + r));
       if (v > best) { best = v; bi = r; }
     }
 #pragma unroll
@@ -956,7 +1046,7 @@ __global__ void __launch_bounds__(BB_NT) k_bb_gj_step(BigArgs g, S* ws, Dims dim
   }
   const int p = s_p;
   if (tid == 0 && cb == 0) piv[j] = p;
-  for (int r = tid; r < m; r += BB_NT) mult[r] = pb_in[r == j ? p : (r == p ? j : r)];
+  for (int r = tid; r < m; r += BB_NT) mult[r] = ldcg_s(pb_in + (r == j ? p : (r == p ? j : r)));
   __syncthreads();
   const S inv = S(1.0) / mult[j];
   const int c_beg = cb * BB_CB, c_end = min(m, c_beg + BB_CB), nc = c_end - c_beg;
@@ -983,6 +1073,85 @@ __global__ void __launch_bounds__(BB_NT) k_bb_gj_step(BigArgs g, S* ws, Dims dim
     M[j + (size_t)c * m] = newj[cl];
     if (c == j + 1) pb_out[j] = newj[cl];
   }
+}
+
+template <class S, class Dims>
+__global__ void __launch_bounds__(BB_NT) k_bb_gj_step(BigArgs g, S* ws, Dims dims, int j, int ncb, int* bad) {
+  bb_gj_body<S, Dims>(g, ws, dims, j, ncb, bad);
+}
+
+// All pivot steps in one cooperative launch, a grid barrier between steps.
+// The same arithmetic as bb_gj_body, but each CTA keeps its BB_CB columns in
+// shared memory for the whole inversion: per step it reads only the pivot
+// column (written by that column's owner in the previous step) from global
+// memory, and writes back its columns once at the end.
+template <class S, class Dims>
+__global__ void __launch_bounds__(BB_NT) k_bb_gj_coop(BigArgs g, S* ws, Dims dims, int nsteps, int ncb, int* bad,
+                                                      GridBar gb) {
+  extern __shared__ __align__(16) unsigned char bb_smem[];
+  __shared__ int s_p;
+  __shared__ double s_best;
+  __shared__ S newj[BB_CB];
+  const int b = blockIdx.x / ncb, cb = blockIdx.x % ncb;
+  int m;
+  S *M, *pb_in, *pb_out;
+  int* piv;
+  dims(ws, g, b, 0, m, M, pb_in, pb_out, piv);
+  const int c_beg = cb * BB_CB, nc = max(0, min(m, c_beg + BB_CB) - c_beg);
+  S* Ms = reinterpret_cast<S*>(bb_smem);   // own columns, [nc][m]
+  S* pc = Ms + (size_t)BB_CB * m;          // pivot column of the step, [m]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < nc * m; e += BB_NT) Ms[e] = M[(size_t)c_beg * m + e];
+  for (int j = 0; j < nsteps; ++j) {
+    if (j < m && nc > 0) {
+      dims(ws, g, b, j, m, M, pb_in, pb_out, piv);
+      for (int r = tid; r < m; r += BB_NT) pc[r] = ldcg_s(pb_in + r);
+      __syncthreads();
+      if (warp == 0) {
+        double best = -1.0;
+        int bi = j;
+        for (int r = j + lane; r < m; r += 32) {
+          double v = abs2(pc[r]);
+          if (v > best) { best = v; bi = r; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { s_p = bi; s_best = best; }
+      }
+      __syncthreads();
+      if (!(s_best > 0.0) || !isfinite(s_best)) {
+        if (tid == 0 && cb == 0) atomicOr(bad, 1);
+      } else {
+        const int p = s_p;
+        if (tid == 0 && cb == 0) piv[j] = p;
+        const S inv = S(1.0) / pc[p];
+        for (int cl = tid; cl < nc; cl += BB_NT) {
+          const int c = c_beg + cl;
+          newj[cl] = c == j ? inv : Ms[(size_t)cl * m + p] * inv;   // row p moves to row j
+        }
+        __syncthreads();
+        for (int e = tid; e < nc * m; e += BB_NT) {
+          const int r = e % m, cl = e / m, c = c_beg + cl;
+          if (r == j) continue;
+          S* col = Ms + (size_t)cl * m;
+          const S old = c == j ? S(0.0) : (r == p ? col[j] : col[r]);
+          const S mr = pc[r == j ? p : (r == p ? j : r)];
+          col[r] = old - mr * newj[cl];
+        }
+        __syncthreads();
+        for (int cl = tid; cl < nc; cl += BB_NT) Ms[(size_t)cl * m + j] = newj[cl];
+        __syncthreads();
+        if (j + 1 >= c_beg && j + 1 < c_beg + nc)   // owner of the next pivot column publishes it
+          for (int r = tid; r < m; r += BB_NT) pb_out[r] = Ms[(size_t)(j + 1 - c_beg) * m + r];
+      }
+    }
+    if (!grid_sync(gb, (unsigned int)(j + 1) * gridDim.x)) return;
+  }
+  for (int e = tid; e < nc * m; e += BB_NT) M[(size_t)c_beg * m + e] = Ms[e];
 }
 
 // Final column order of a Gauss-Jordan inverse: position c holds column idx[c].
@@ -1196,6 +1365,28 @@ Pts make_pts(const Handle* h) {
   return p;
 }
 
+// Whether `grid` CTAs of `kern` can all be resident at once (the condition
+// of a cooperative launch).
+bool coop_fits(const void* kern, int grid, int nt, size_t smem) {
+  int dev = 0, nsm = 0, occ = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, smem)) {
+    cudaGetLastError();
+    return false;
+  }
+  return coop && grid <= occ * nsm;
+}
+
+// Arrival counter of a grid barrier (zeroed, stream ordered); the give-up
+// flag is the handle's status word 1.
+int make_bar(Handle* h, GridBar* gb, cudaStream_t st) {
+  RS_CUDA(cudaMallocAsync((void**)&gb->count, sizeof(unsigned int), st));
+  RS_CUDA(cudaMemsetAsync(gb->count, 0, sizeof(unsigned int), st));
+  gb->flag = h->status + 1;
+  return RS_OK;
+}
+
 template <class S>
 int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cudaStream_t st) {
   const int nb = lv.nbox;
@@ -1233,22 +1424,39 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
   const int ncb = div_up(maxn, BI_CB);
   const size_t id_smem = sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax;
   RS_CUDA(cudaFuncSetAttribute(k_bbid_step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)id_smem));
-  // every 8 steps, stop early once every box of the level has found its rank
-  int* d_active = nullptr;
-  int h_active = 1;
-  RS_CUDA(cudaMallocAsync((void**)&d_active, sizeof(int), st));
-  for (int j = 0; j < maxkmax; ++j) {
-    k_bbid_step<S><<<nb * ncb, BI_NT, id_smem, st>>>(a, g, Mws, j, ncb, a.lperm);
+  const size_t co_smem = ((id_smem + 15) & ~(size_t)15) + sizeof(S) * (size_t)BI_CB * a.mmax;
+  const bool co_ok = co_smem <= 200 * 1024;
+  if (co_ok)
+    RS_CUDA(cudaFuncSetAttribute(k_bbid_coop<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)co_smem));
+  if (co_ok && coop_fits((const void*)k_bbid_coop<S>, nb * ncb, BI_NT, co_smem)) {
+    // every pivot step in one cooperative launch
+    GridBar gb{};
+    RS_TRY(make_bar(h, &gb, st));
+    int nsteps = maxkmax, ncbv = ncb, nbv = nb;
+    int* lp = a.lperm;
+    void* args[] = {&a, &g, &Mws, &nsteps, &ncbv, &nbv, &lp, &gb};
+    RS_CUDA(cudaLaunchCooperativeKernel((const void*)k_bbid_coop<S>, dim3(nb * ncb), dim3(BI_NT), args, co_smem, st));
     RS_CHECK_LAUNCH();
-    if ((j & 7) == 7 && j + 1 < maxkmax) {
-      k_bbid_active<<<1, 256, 0, st>>>(g, a.n, nb, j + 1, d_active);
+    RS_CUDA(cudaFreeAsync(gb.count, st));
+  } else {
+    // one launch per step; every 8 steps, stop early once every box of the
+    // level has found its rank
+    int* d_active = nullptr;
+    int h_active = 1;
+    RS_CUDA(cudaMallocAsync((void**)&d_active, sizeof(int), st));
+    for (int j = 0; j < maxkmax; ++j) {
+      k_bbid_step<S><<<nb * ncb, BI_NT, id_smem, st>>>(a, g, Mws, j, ncb, a.lperm);
       RS_CHECK_LAUNCH();
-      RS_CUDA(cudaMemcpyAsync(&h_active, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-      RS_CUDA(cudaStreamSynchronize(st));
-      if (!h_active) break;
+      if ((j & 7) == 7 && j + 1 < maxkmax) {
+        k_bbid_active<<<1, 256, 0, st>>>(g, a.n, nb, j + 1, d_active);
+        RS_CHECK_LAUNCH();
+        RS_CUDA(cudaMemcpyAsync(&h_active, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        RS_CUDA(cudaStreamSynchronize(st));
+        if (!h_active) break;
+      }
     }
+    RS_CUDA(cudaFreeAsync(d_active, st));
   }
-  RS_CUDA(cudaFreeAsync(d_active, st));
   const int wpb = BI_NT / 32;
   const int tb = div_up(maxn, wpb);
   k_bbid_T<S><<<nb * tb, BI_NT, 0, st>>>(a, g, Mws, (S*)lv.T, tb);
@@ -1293,7 +1501,35 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
   return RS_OK;
 }
 
-// Big boxes (n <= 512): many CTAs per box, one launch per pivot step.
+// The nsteps Gauss-Jordan steps of every box: one cooperative launch when the
+// grid fits on the GPU at once, else one launch per step.
+template <class S, class Dims>
+int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int ncb, size_t smem, int* bad,
+                 cudaStream_t st) {
+  const size_t csmem = sizeof(S) * (size_t)(BB_CB + 1) * nsteps;   // own columns + pivot column (m <= nsteps)
+  const bool co_ok = csmem <= 200 * 1024;
+  if (co_ok)
+    RS_CUDA(cudaFuncSetAttribute(k_bb_gj_coop<S, Dims>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
+  if (co_ok && coop_fits((const void*)k_bb_gj_coop<S, Dims>, nb * ncb, BB_NT, csmem)) {
+    GridBar gb{};
+    RS_TRY(make_bar(h, &gb, st));
+    void* args[] = {&g, &ws, &dims, &nsteps, &ncb, &bad, &gb};
+    RS_CUDA(cudaLaunchCooperativeKernel((const void*)k_bb_gj_coop<S, Dims>, dim3(nb * ncb), dim3(BB_NT), args, csmem,
+                                        st));
+    RS_CHECK_LAUNCH();
+    RS_CUDA(cudaFreeAsync(gb.count, st));
+    return RS_OK;
+  }
+  RS_CUDA(cudaFuncSetAttribute(k_bb_gj_step<S, Dims>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int j = 0; j < nsteps; ++j) {
+    k_bb_gj_step<S, Dims><<<nb * ncb, BB_NT, smem, st>>>(g, ws, dims, j, ncb, bad);
+    RS_CHECK_LAUNCH();
+  }
+  return RS_OK;
+}
+
+// Big boxes (n <= 512): many CTAs per box; the pivot steps in one
+// cooperative launch (or one launch per step).
 template <class S>
 int run_factor_big(Handle* h, Level& lv, FaArgs a, const Level* child, double by, cudaStream_t st) {
   const int nb = lv.nbox;
@@ -1330,11 +1566,7 @@ int run_factor_big(Handle* h, Level& lv, FaArgs a, const Level* child, double by
   RS_CHECK_LAUNCH();
   const int ncb = div_up(maxn, BB_CB);
   const size_t gj_smem = sizeof(S) * (size_t)maxn;
-  RS_CUDA(cudaFuncSetAttribute(k_bb_gj_step<S, DimsD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem));
-  for (int j = 0; j < maxn; ++j) {
-    k_bb_gj_step<S, DimsD><<<nb * ncb, BB_NT, gj_smem, st>>>(g, ws, DimsD{}, j, ncb, a.bad);
-    RS_CHECK_LAUNCH();
-  }
+  RS_TRY((run_gj_steps<S, DimsD>(h, g, ws, DimsD{}, maxn, nb, ncb, gj_smem, a.bad, st)));
   k_bb_unscramble<S, DimsD><<<nb, BB_NT, 0, st>>>(g, ws, DimsD{}, (S*)nullptr, 0, idx, maxn);
   RS_CHECK_LAUNCH();
   if (lv.maxk > 0) {
@@ -1345,11 +1577,7 @@ int run_factor_big(Handle* h, Level& lv, FaArgs a, const Level* child, double by
     const int nck = div_up(maxk, BB_CB);
     DimsY dy{lv.lamoff};
     const size_t gy_smem = sizeof(S) * (size_t)maxk;
-    RS_CUDA(cudaFuncSetAttribute(k_bb_gj_step<S, DimsY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gy_smem));
-    for (int j = 0; j < maxk; ++j) {
-      k_bb_gj_step<S, DimsY><<<nb * nck, BB_NT, gy_smem, st>>>(g, ws, dy, j, nck, a.bad);
-      RS_CHECK_LAUNCH();
-    }
+    RS_TRY((run_gj_steps<S, DimsY>(h, g, ws, dy, maxk, nb, nck, gy_smem, a.bad, st)));
     k_bb_unscramble<S, DimsY><<<nb, BB_NT, 0, st>>>(g, ws, dy, (S*)lv.Lam, 1, idx, maxn);
     RS_CHECK_LAUNCH();
   }
@@ -1422,11 +1650,13 @@ int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t 
   return RS_OK;
 }
 
+// Status words: [0] a singular or non-finite pivot, [1] a grid barrier gave up.
 int check_bad(Handle* h, cudaStream_t st, const char* where) {
-  int bad = 0;
-  RS_CUDA(cudaMemcpyAsync(&bad, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int bad[2] = {0, 0};
+  RS_CUDA(cudaMemcpyAsync(bad, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   RS_CUDA(cudaStreamSynchronize(st));
-  if (bad) return fail(RS_ERR_SINGULAR, "rs_build: singular block during %s", where);
+  if (bad[1]) return fail(RS_ERR_TIMEOUT, "rs_build: a grid barrier wait ran out during %s", where);
+  if (bad[0]) return fail(RS_ERR_SINGULAR, "rs_build: singular block during %s", where);
   return RS_OK;
 }
 
@@ -1521,6 +1751,7 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st) {
   a.nmax = lv.maxn;
   if (h->cplx) RS_TRY(run_id<c128>(h, lv, a, mrows, msum, st));
   else RS_TRY(run_id<double>(h, lv, a, mrows, msum, st));
+  RS_TRY(check_bad(h, st, "skeletonization"));
 
   // ranks -> skeleton offsets in the parent depth
   lv.h_k.resize(nbox);

@@ -25,6 +25,7 @@
 // result stores are coalesced along the rows.  Leaf tiles read B and write X
 // in the caller's order through the tree permutation.
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <cuda/atomic>
 #include <vector>
@@ -97,6 +98,7 @@ __device__ inline bool spin_until(const int* cnt, int target, int* flag, int* df
       atomicExch(flag, 1);
       return false;
     }
+    if ((spins & 63) == 0 && *(volatile int*)dflag) return false;   // another waiter gave up
     __nanosleep(100);
   }
   return true;
@@ -148,11 +150,10 @@ template <> __device__ inline dfloat ldro<dfloat>(const dfloat* p) {
 }
 
 template <class D, class S> __device__ inline D cv(S v) { return D(v); }
-template <> __device__ inline float cv<float, double>(double v) { return (float)v; }
-template <> __device__ inline double cv<double, float>(float v) { return (double)v; }
+template <> __device__ inline float cv<float, double>(double v) { return f64_to_f32_rn(v); }
+template <> __device__ inline double cv<double, float>(float v) { return f32_to_f64(v); }
 template <> __device__ inline c64 cv<c64, c128>(c128 v) { return c64((float)v.re, (float)v.im); }
 template <> __device__ inline c128 cv<c128, c64>(c64 v) { return c128((double)v.re, (double)v.im); }
-template <> __device__ inline double cv<double, dfloat>(dfloat v) { return __dadd_rn((double)v.hi, (double)v.lo); }
 
 // acc[c] += sum_{q < qn} col[q * ld] * stage[q][c] for one 32-column chunk.
 // All factor loads of the chunk are issued before the FMAs (QB at a time)
@@ -221,11 +222,26 @@ struct StageRow<dfloat, CT> {
   }
 };
 
+// Right-hand-side entries into the working type (integer-instruction
+// conversions for float and double-float, see rs_common.cuh).
+template <class S, class SIO> __device__ __forceinline__ S in_cv(SIO v) { return cv<S, SIO>(v); }
+template <> __device__ __forceinline__ float in_cv<float, double>(double v) { return f64_to_f32_rn(v); }
+template <> __device__ __forceinline__ dfloat in_cv<dfloat, double>(double v) { return f64_to_df(v); }
+
 // Leaf output: the value itself, or sub - value (forward operator used for a
-// residual b - A x).
-template <class SIO>
-__device__ __forceinline__ SIO leaf_out(const SIO* sub, int64_t i, SIO y) {
-  return sub ? sub[i] - y : y;
+// residual b - A x).  In float and double-float the subtraction is done in
+// the working type and the result, whose leading bits cancelled, is
+// returned rounded to float precision relative to itself.
+template <class S, class SIO> __device__ __forceinline__ SIO out_cv(const SIO* sub, int64_t i, S y) {
+  const SIO v = cv<SIO, S>(y);
+  return sub ? sub[i] - v : v;
+}
+template <> __device__ __forceinline__ double out_cv<float, double>(const double* sub, int64_t i, float y) {
+  return f32_to_f64(sub ? __fsub_rn(f64_to_f32_rn(sub[i]), y) : y);
+}
+template <> __device__ __forceinline__ double out_cv<dfloat, double>(const double* sub, int64_t i, dfloat y) {
+  if (sub) return f32_to_f64((f64_to_df(sub[i]) + (-y)).hi);
+  return __dadd_rn(f32_to_f64(y.hi), f32_to_f64(y.lo));
 }
 
 template <class S, int CT>
@@ -283,7 +299,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
               const int64_t src = p.perm[pos];
 #pragma unroll
               for (int c = 0; c < CT; ++c)
-                stage[lane * CT + c] = c < cw ? cv<S, SIO>(B[src + (int64_t)(c0 + c) * ldb]) : S(0.0);
+                stage[lane * CT + c] = c < cw ? in_cv<S, SIO>(B[src + (int64_t)(c0 + c) * ldb]) : S(0.0);
             } else {
 #pragma unroll
               for (int c = 0; c < CT; ++c)
@@ -301,7 +317,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
             for (int c = 0; c < CT; ++c)
               if (c < cw) {
                 const int64_t i = dst + (int64_t)(c0 + c) * ldx;
-                X[i] = leaf_out(sub, i, cv<SIO, S>(acc[c]));
+                X[i] = out_cv<S, SIO>(sub, i, acc[c]);
               }
           } else if (r < n) {
             S* uo = p.u[d] + (int64_t)c0 * ldd + off + r;
@@ -349,7 +365,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
             for (int c = 0; c < CT; ++c)
               if (c < cw) {
                 const int64_t i = dst + (int64_t)(c0 + c) * ldx;
-                X[i] = leaf_out(sub, i, cv<SIO, S>(ldcg(uo + (int64_t)c * ldd) + acc[c]));
+                X[i] = out_cv<S, SIO>(sub, i, ldcg(uo + (int64_t)c * ldd) + acc[c]);
               }
           } else {
 #pragma unroll
@@ -366,18 +382,24 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
 
 // ------------------------------------------------------------- CTA tiles
 // Many right-hand sides: the same tile list and dependency counters, but a
-// tile is a 32-row x TN-column block of one box's product computed by a
-// whole CTA as a small register-blocked GEMM.  Factor and input chunks
-// (32 deep) are staged in shared memory with coalesced loads (the factor
-// along its rows, the inputs along their column-major rows); every thread
-// accumulates an RPT x CPT block; the result block is transposed through
-// shared memory so that its stores are coalesced along the rows as well.
-constexpr int C_NT = 128, C_TM = 32, C_TK = 32;
+// tile is a TM-row x TN-column block of one box's product computed by a
+// whole CTA as a small register-blocked GEMM.  Factor and input chunks (32
+// deep) are staged in shared memory with coalesced loads (the factor along
+// its rows, the inputs along their column-major rows); every thread
+// accumulates an RPT x CPT block and a warp owns TM / 4 consecutive rows, so
+// warps past the box's last row skip the arithmetic; the result block is
+// transposed through shared memory so that its stores are coalesced along the
+// rows as well.
+constexpr int C_NT = 128, C_TK = 32;
+static_assert(C_TK == 32, "input staging maps a warp onto the 32 rows of a chunk");
 
-template <int TN> struct CtaShape;
-template <> struct CtaShape<128> { static constexpr int CG = 16, CPT = 8, RPT = 4; };
-template <> struct CtaShape<64> { static constexpr int CG = 16, CPT = 4, RPT = 4; };
-template <> struct CtaShape<32> { static constexpr int CG = 8, CPT = 4, RPT = 2; };
+// Thread layout of a TM x TN tile: CG column groups of CPT columns, the rest
+// row groups of RPT rows; a warp owns TM / 4 consecutive rows.
+template <int TM, int TN> struct CtaShape {
+  static constexpr int CG = TN >= 64 ? 16 : 8;
+  static constexpr int CPT = TN / CG;
+  static constexpr int RPT = TM * CG / C_NT;
+};
 
 template <class S> __device__ __forceinline__ void mac(S& acc, S a, S b) { acc += a * b; }
 template <> __device__ __forceinline__ void mac<dfloat>(dfloat& acc, dfloat a, dfloat b) { df_fma(acc, a, b); }
@@ -427,38 +449,48 @@ template <int N> struct Lds<double, N> {
   }
 };
 
-template <class S, class SIO, int TN>
+template <class S, int TM, int TN>
+struct CtaSmem {
+  static constexpr int BP = TN + 16 / (int)sizeof(S);   // padded input row (keeps 16-byte alignment)
+  static constexpr int OP = TM + 1;                     // padded output column
+  static constexpr int BSZ = C_TK * BP > TN * OP ? C_TK * BP : TN * OP;
+  static constexpr size_t bytes = sizeof(S) * (size_t)(C_TK * TM + BSZ);
+};
+
+template <class S, class SIO, int TM, int TN>
 __global__ void __launch_bounds__(C_NT) k_solve_cta(Plan<S> p, const SIO* B, int64_t ldb, SIO* X, int64_t ldx,
                                                     const SIO* sub, int epoch, int* flag) {
-  using Sh = CtaShape<TN>;
+  using Sh = CtaShape<TM, TN>;
   constexpr int RPT = Sh::RPT, CPT = Sh::CPT, CG = Sh::CG;
-  constexpr int BP = TN + 16 / (int)sizeof(S);   // padded input row (keeps 16-byte alignment)
-  constexpr int OP = C_TM + 1;                   // padded output column
-  constexpr int BSZ = C_TK * BP > TN * OP ? C_TK * BP : TN * OP;
+  constexpr int BP = CtaSmem<S, TM, TN>::BP, OP = CtaSmem<S, TM, TN>::OP;
+  constexpr int C_TM = TM;
+  static_assert((C_NT / CG) * RPT == TM && CG * CPT == TN, "tile shape");
+  static_assert((32 / CG) * RPT == TM / 4, "a warp owns TM / 4 rows");
   extern __shared__ __align__(16) unsigned char smem[];
   S* As = reinterpret_cast<S*>(smem);   // [TK][TM]
   S* Bs = As + C_TK * C_TM;             // [TK][BP]; the output block [TN][OP] reuses it
-  (void)BSZ;
   __shared__ int s_tile, s_ok;
   const int tid = threadIdx.x;
   const int tx = tid % CG, ty = tid / CG;
+  const int wrow = (tid >> 5) * (TM / 4);   // first row of this warp's rows
+  // Thread 0 claims the next tile while the CTA works on the current one (the
+  // list is topological, so a claimed tile never precedes one it waits on).
+  int next = 0;
+  if (tid == 0) next = atomicAdd(p.dispatch, 1);
   for (;;) {
     if (tid == 0) {
-      const int t = atomicAdd(p.dispatch, 1);
+      const int t = next;
       int ok = 1;
       if (t < p.ntiles) {
-        if (*(volatile int*)p.dflag) {
-          ok = 0;   // another CTA gave up waiting: leave too
+        const Tile tl = p.tiles[t];
+        if (tl.kind != T_DOWN) {
+          if (p.bt.up_need[tl.g] > 0)
+            ok = spin_until(&p.up_cnt[tl.g], epoch * p.bt.up_need[tl.g], flag, p.dflag);
         } else {
-          const Tile tl = p.tiles[t];
-          if (tl.kind != T_DOWN) {
-            if (p.bt.up_need[tl.g] > 0)
-              ok = spin_until(&p.up_cnt[tl.g], epoch * p.bt.up_need[tl.g], flag, p.dflag);
-          } else {
-            const int par = p.bt.parent[tl.g];
-            ok = spin_until(&p.dn_cnt[par], epoch * p.bt.dn_need[par], flag, p.dflag);
-          }
+          const int par = p.bt.parent[tl.g];
+          ok = spin_until(&p.dn_cnt[par], epoch * p.bt.dn_need[par], flag, p.dflag);
         }
+        if (ok) next = atomicAdd(p.dispatch, 1);
       }
       s_tile = t;
       s_ok = ok;
@@ -481,6 +513,7 @@ __global__ void __launch_bounds__(C_NT) k_solve_cta(Plan<S> p, const SIO* B, int
     const int64_t in0 = down ? p.bt.skoff[g] : off;
     const int r0 = tl.r0, c0 = tl.c0;
     const int cw = min(TN, tl.c1 - c0);
+    const bool busy = wrow < rows - r0;    // warp-uniform
 
     S acc[RPT][CPT];
 #pragma unroll
@@ -492,100 +525,100 @@ __global__ void __launch_bounds__(C_NT) k_solve_cta(Plan<S> p, const SIO* B, int
       const int kn = min(C_TK, K - k0);
       __syncthreads();   // the previous chunk (or tile) is done with As / Bs
       {
-        const int i = tid & 31;
+        const int i = tid % C_TM;
         const bool oki = r0 + i < rows;
-#pragma unroll
-        for (int kk = tid >> 5; kk < C_TK; kk += C_NT / 32)
-          As[kk * C_TM + i] = (oki && kk < kn) ? ldro(A + (r0 + i) + (size_t)(k0 + kk) * rows) : S(0.0);
+        const S* Ai = A + (r0 + i) + (size_t)k0 * rows;
+#pragma unroll 8
+        for (int kk = tid / C_TM; kk < C_TK; kk += C_NT / C_TM)
+          As[kk * C_TM + i] = (oki && kk < kn) ? ldro(Ai + (size_t)kk * rows) : S(0.0);
       }
       {
-        const int kk = tid & 31;
+        const int kk = tid % C_TK;
         const bool okk = kk < kn;
         int64_t src = 0;
         if (okk) src = leaf_in ? (int64_t)p.perm[off + k0 + kk] : in0 + k0 + kk;
 #pragma unroll 8
-        for (int j = tid >> 5; j < TN; j += C_NT / 32) {
+        for (int j = tid / C_TK; j < TN; j += C_NT / C_TK) {
           S v = S(0.0);
           if (okk && j < cw)
-            v = leaf_in ? cv<S, SIO>(B[src + (int64_t)(c0 + j) * ldb]) : ldcg(vin + (int64_t)(c0 + j) * ldin + src);
+            v = leaf_in ? in_cv<S, SIO>(B[src + (int64_t)(c0 + j) * ldb]) : ldcg(vin + (int64_t)(c0 + j) * ldin + src);
           Bs[kk * BP + j] = v;
         }
       }
       __syncthreads();
-      for (int kk = 0; kk < kn; ++kk) {
-        S a[RPT], b[CPT];
-        Lds<S, RPT>::run(As + kk * C_TM + ty * RPT, a);
-        Lds<S, CPT>::run(Bs + kk * BP + tx * CPT, b);
+      if (busy) {
+        for (int kk = 0; kk < kn; ++kk) {
+          S a[RPT], b[CPT];
+          Lds<S, RPT>::run(As + kk * C_TM + ty * RPT, a);
+          Lds<S, CPT>::run(Bs + kk * BP + tx * CPT, b);
 #pragma unroll
-        for (int x = 0; x < RPT; ++x)
+          for (int x = 0; x < RPT; ++x)
 #pragma unroll
-          for (int y = 0; y < CPT; ++y) mac(acc[x][y], a[x], b[y]);
+            for (int y = 0; y < CPT; ++y) mac(acc[x][y], a[x], b[y]);
+        }
       }
     }
     __syncthreads();   // every thread is done reading As / Bs
     S* Os = Bs;
+    if (busy) {
 #pragma unroll
-    for (int x = 0; x < RPT; ++x)
+      for (int x = 0; x < RPT; ++x)
 #pragma unroll
-      for (int y = 0; y < CPT; ++y) Os[(tx * CPT + y) * OP + ty * RPT + x] = acc[x][y];
+        for (int y = 0; y < CPT; ++y) Os[(tx * CPT + y) * OP + ty * RPT + x] = acc[x][y];
+    }
     __syncthreads();
     {
-      const int i = tid & 31;
+      const int i = tid % C_TM;
       const int r = r0 + i;
+      const int j0 = tid / C_TM;
+      constexpr int JS = C_NT / C_TM;
       if (r < rows) {
         if (!down) {
           if (r < n && tl.kind == T_ROOT && d == p.L) {   // single-box tree: the root is the answer
             const int64_t dst = p.perm[off + r];
-            for (int j = tid >> 5; j < cw; j += C_NT / 32) {
+            for (int j = j0; j < cw; j += JS) {
               const int64_t idx = dst + (int64_t)(c0 + j) * ldx;
-              X[idx] = leaf_out(sub, idx, cv<SIO, S>(Os[j * OP + i]));
+              X[idx] = out_cv<S, SIO>(sub, idx, Os[j * OP + i]);
             }
           } else if (r < n) {
             const int64_t ld = p.ldv[d];
             S* uo = p.u[d] + (int64_t)c0 * ld + off + r;
-            for (int j = tid >> 5; j < cw; j += C_NT / 32) uo[(int64_t)j * ld] = Os[j * OP + i];
+            for (int j = j0; j < cw; j += JS) uo[(int64_t)j * ld] = Os[j * OP + i];
           } else {
             const int64_t ld = p.ldv[d - 1];
             S* vo = p.v[d - 1] + (int64_t)c0 * ld + p.bt.skoff[g] + (r - n);
-            for (int j = tid >> 5; j < cw; j += C_NT / 32) vo[(int64_t)j * ld] = Os[j * OP + i];
+            for (int j = j0; j < cw; j += JS) vo[(int64_t)j * ld] = Os[j * OP + i];
           }
         } else {
           const int64_t ld = p.ldv[d];
           S* uo = p.u[d] + (int64_t)c0 * ld + off + r;
           if (d == p.L) {
             const int64_t dst = p.perm[off + r];
-            for (int j = tid >> 5; j < cw; j += C_NT / 32) {
+            for (int j = j0; j < cw; j += JS) {
               const int64_t idx = dst + (int64_t)(c0 + j) * ldx;
-              X[idx] = leaf_out(sub, idx, cv<SIO, S>(ldcg(uo + (int64_t)j * ld) + Os[j * OP + i]));
+              X[idx] = out_cv<S, SIO>(sub, idx, ldcg(uo + (int64_t)j * ld) + Os[j * OP + i]);
             }
           } else {
-            for (int j = tid >> 5; j < cw; j += C_NT / 32)
-              uo[(int64_t)j * ld] = ldcg(uo + (int64_t)j * ld) + Os[j * OP + i];
+            for (int j = j0; j < cw; j += JS) uo[(int64_t)j * ld] = ldcg(uo + (int64_t)j * ld) + Os[j * OP + i];
           }
         }
       }
     }
-    __threadfence();
+    // every thread's stores of this tile precede the barrier; thread 0's
+    // release add publishes them to the waiter that acquires the counter
     __syncthreads();
     if (tid == 0) {
-      if (tl.kind == T_UP) atomicAdd(&p.up_cnt[p.bt.parent[g]], 1);
-      else atomicAdd(&p.dn_cnt[g], 1);
+      cuda::atomic_ref<int, cuda::thread_scope_device> c(tl.kind == T_UP ? p.up_cnt[p.bt.parent[g]] : p.dn_cnt[g]);
+      c.fetch_add(1, cuda::memory_order_release);
     }
   }
-}
-
-template <class S, int TN>
-constexpr size_t cta_smem() {
-  constexpr int BP = TN + 16 / (int)sizeof(S);
-  constexpr int OP = C_TM + 1;
-  constexpr int BSZ = C_TK * BP > TN * OP ? C_TK * BP : TN * OP;
-  return sizeof(S) * (size_t)(C_TK * C_TM + BSZ);
 }
 
 // ------------------------------------------------------------------- host
 struct PersPlan {
   int prec = -1, R = 0, CT = 0;
-  int TN = 0;                // > 0: CTA-tile kernel with TN columns per tile
+  int TN = 0;                // > 0: CTA-tile kernel with TM x TN tiles
+  int TM = 32;
   int ntiles = 0, nbox = 0;
   Tile* tiles = nullptr;
   BoxTab bt{};
@@ -605,19 +638,21 @@ struct PersCache {
   std::vector<PersPlan*> plans;
 };
 
-// Column block of the CTA-tile kernel for R right-hand sides (0: the warp
-// kernel, which suits few columns).  RS_SOLVE_TN overrides it (32, 64, 128;
-// 0 forces the warp kernel).
-int cta_tn(bool cplx, int prec, int R) {
+// Tile of the CTA kernel for R right-hand sides: rows * 1000 + columns (0:
+// the warp kernel, which suits few columns).  RS_SOLVE_TILE overrides it
+// ("TMxTN" with TM, TN in {32, 64}; "0" forces the warp kernel).
+int cta_tile(int R) {
   static const int forced = [] {
-    const char* e = getenv("RS_SOLVE_TN");
-    return e ? atoi(e) : -1;
+    const char* e = getenv("RS_SOLVE_TILE");
+    if (!e) return -1;
+    int tm = 0, tn = 0;
+    if (sscanf(e, "%dx%d", &tm, &tn) == 2 && (tm == 32 || tm == 64) && (tn == 32 || tn == 64)) return tm * 1000 + tn;
+    return 0;
   }();
-  const int cap = cplx && prec == RS_PREC_FP64 ? 64 : 128;
   if (forced == 0) return 0;
-  if (forced == 32 || forced == 64 || forced == 128) return R < 16 ? 0 : std::min(forced, cap);
+  if (forced > 0) return R < 16 ? 0 : forced;
   if (R < 32) return 0;
-  return std::min(cap, R >= 128 ? 128 : R >= 64 ? 64 : 32);
+  return R >= 64 ? 32064 : 32032;
 }
 
 int ct_for(bool cplx, int prec, int R) {
@@ -635,12 +670,13 @@ int dev_upload(PersPlan* P, T** d, const std::vector<T>& v, cudaStream_t st) {
   return RS_OK;
 }
 
-template <class S, class SIO, int CT, int TN>
+template <class S, class SIO, int CT, int TM, int TN>
 int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X, int64_t ldx, const SIO* sub,
                 cudaStream_t st) {
-  const size_t smem = TN ? cta_smem<S, (TN ? TN : 32)>() : sizeof(S) * 32 * CT * P_WARPS;
+  constexpr int TMv = TN ? TM : 32, TNv = TN ? TN : 32;
+  const size_t smem = TN ? CtaSmem<S, TMv, TNv>::bytes : sizeof(S) * 32 * CT * P_WARPS;
   const int nt = TN ? C_NT : P_NT;
-  const void* fn = TN ? (const void*)k_solve_cta<S, SIO, (TN ? TN : 32)> : (const void*)k_solve_pers<S, SIO, CT>;
+  const void* fn = TN ? (const void*)k_solve_cta<S, SIO, TMv, TNv> : (const void*)k_solve_pers<S, SIO, CT>;
   if (smem > 48 * 1024) RS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (P->grid == 0) {
     int dev = 0, nsm = 0, occ = 0;
@@ -677,7 +713,7 @@ int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X
   *P->flag_host = 0;
   prof_begin(prec_cat(P->prec), st);
   if constexpr (TN > 0)
-    k_solve_cta<S, SIO, TN><<<P->grid, C_NT, smem, st>>>(pl, B, ldb, X, ldx, sub, wait_epoch, P->flag_dev);
+    k_solve_cta<S, SIO, TMv, TNv><<<P->grid, C_NT, smem, st>>>(pl, B, ldb, X, ldx, sub, wait_epoch, P->flag_dev);
   else
     k_solve_pers<S, SIO, CT><<<P->grid, P_NT, smem, st>>>(pl, B, ldb, X, ldx, sub, R, wait_epoch, P->flag_dev);
   RS_CHECK_LAUNCH();
@@ -747,7 +783,9 @@ static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out)
   P->prec = prec;
   P->R = R;
   P->CT = ct_for(h->cplx, prec, R);
-  P->TN = cta_tn(h->cplx, prec, R);
+  const int tile = cta_tile(R);
+  P->TN = tile % 1000;
+  P->TM = tile ? tile / 1000 : 32;
   const int L = h->L;
   // global box numbering: depth L first, ..., depth 0 last
   std::vector<int> gbase(L + 1);
@@ -773,10 +811,11 @@ static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out)
   // Column ranges per depth: a depth with few row tiles splits its columns
   // (in CT-aligned ranges) so that its tiles still fill the GPU.
   const int nchunk = div_up(R, P->CT);
+  const int rb = P->TN ? P->TM : 32;   // rows per tile
   auto col_ranges = [&](int d, bool down) {
     const Level& lv = h->lv[d];
     int64_t rt = 0;
-    for (int b = 0; b < lv.nbox; ++b) rt += div_up(down ? lv.h_n[b] : lv.h_n[b] + lv.h_k[b], 32);
+    for (int b = 0; b < lv.nbox; ++b) rt += div_up(down ? lv.h_n[b] : lv.h_n[b] + lv.h_k[b], rb);
     int split = (int)std::max<int64_t>(1, std::min<int64_t>(nchunk, 8192 / std::max<int64_t>(1, rt)));
     int per = P->TN ? P->TN : div_up(nchunk, split) * P->CT;
     std::vector<std::pair<int, int>> cr;
@@ -788,25 +827,25 @@ static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out)
     auto cr = col_ranges(d, false);
     for (int b = 0; b < h->lv[d].nbox; ++b) {
       int g = gbase[d] + b;
-      for (int r0 = 0; r0 < n[g] + k[g]; r0 += 32)
+      for (int r0 = 0; r0 < n[g] + k[g]; r0 += rb)
         for (auto& c : cr) tiles.push_back(Tile{g, r0, c.first, c.second, T_UP});
-      up_need[parent[g]] += div_up(n[g] + k[g], 32) * (int)cr.size();
+      up_need[parent[g]] += div_up(n[g] + k[g], rb) * (int)cr.size();
     }
   }
   {
     auto cr = col_ranges(0, false);
     int g = gbase[0];
-    for (int r0 = 0; r0 < n[g]; r0 += 32)
+    for (int r0 = 0; r0 < n[g]; r0 += rb)
       for (auto& c : cr) tiles.push_back(Tile{g, r0, c.first, c.second, T_ROOT});
-    dn_need[g] = div_up(n[g], 32) * (int)cr.size();
+    dn_need[g] = div_up(n[g], rb) * (int)cr.size();
   }
   for (int d = 1; d <= L; ++d) {
     auto cr = col_ranges(d, true);
     for (int b = 0; b < h->lv[d].nbox; ++b) {
       int g = gbase[d] + b;
-      for (int r0 = 0; r0 < n[g]; r0 += 32)
+      for (int r0 = 0; r0 < n[g]; r0 += rb)
         for (auto& c : cr) tiles.push_back(Tile{g, r0, c.first, c.second, T_DOWN});
-      dn_need[g] = div_up(n[g], 32) * (int)cr.size();
+      dn_need[g] = div_up(n[g], rb) * (int)cr.size();
     }
   }
   P->ntiles = (int)tiles.size();
@@ -840,21 +879,18 @@ static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO*
                      const SIO* sub = nullptr) {
   PersPlan* P = nullptr;
   RS_TRY(get_plan(h, prec, R, st, &P));
-  switch (P->TN) {
-    case 128:
-      if constexpr (sizeof(S) <= 8) {
-        RS_TRY((launch_pers<S, SIO, 1, 128>(h, P, B, ldb, R, X, ldx, sub, st)));
-        break;
-      }
-      return fail(RS_ERR_ARG, "bad column tile");
-    case 64: RS_TRY((launch_pers<S, SIO, 1, 64>(h, P, B, ldb, R, X, ldx, sub, st))); break;
-    case 32: RS_TRY((launch_pers<S, SIO, 1, 32>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+  const int tile = P->TN ? P->TM * 1000 + P->TN : 0;
+  switch (tile) {
+    case 32032: RS_TRY((launch_pers<S, SIO, 1, 32, 32>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+    case 32064: RS_TRY((launch_pers<S, SIO, 1, 32, 64>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+    case 64032: RS_TRY((launch_pers<S, SIO, 1, 64, 32>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+    case 64064: RS_TRY((launch_pers<S, SIO, 1, 64, 64>(h, P, B, ldb, R, X, ldx, sub, st))); break;
     case 0:
       switch (P->CT) {
-        case 1: RS_TRY((launch_pers<S, SIO, 1, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
-        case 8: RS_TRY((launch_pers<S, SIO, 8, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
-        case 16: RS_TRY((launch_pers<S, SIO, 16, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
-        case 32: RS_TRY((launch_pers<S, SIO, 32, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+        case 1: RS_TRY((launch_pers<S, SIO, 1, 32, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+        case 8: RS_TRY((launch_pers<S, SIO, 8, 32, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+        case 16: RS_TRY((launch_pers<S, SIO, 16, 32, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
+        case 32: RS_TRY((launch_pers<S, SIO, 32, 32, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
         default: return fail(RS_ERR_ARG, "bad column tile");
       }
       break;
