@@ -52,7 +52,7 @@ def peaks():
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per
 # kernel category, from the ncu captures summarised in profiles/ (the leaf-level
 # launch of the bench workload); None where no capture of the current kernel exists.
-NCU_TRAFFIC = {"id": (3365376, "k_id leaf-level launch (profiles/k_id_leaf_laplace2d_starfish_131072.md)")}
+NCU_TRAFFIC = {}
 
 # FP64 FMA throughput of GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 # = 1.26 TFLOP/s nominal; a dependent-chain-free probe measured 1.195 TFLOP/s.
@@ -279,10 +279,13 @@ def run_ours(args, ws, rank, local):
     H = rs.rs_build(P, "laplace2d", h, w["eps"], w["leaf"], w["nproxy"], stream=stream)
     st = H.stats()
     torch.cuda.synchronize()
-    tb = []
+    tb, tbd = [], []
     for _ in range(3):
         Ht = rs.rs_build(P, "laplace2d", h, w["eps"], w["leaf"], w["nproxy"], stream=stream)
         tb.append(Ht.stats()["build_ms"])
+        Ht.free()
+        Ht = rs.rs_build(P, "laplace2d", h, w["eps"], w["leaf"], w["nproxy"], stream=stream, id_arith="dfloat")
+        tbd.append(Ht.stats()["build_ms"])
         Ht.free()
     rs.rs_solve_refined(H, B, X, tol=TOL, max_it=8, stream=stream)
     torch.cuda.synchronize()
@@ -370,6 +373,7 @@ def run_ours(args, ws, rank, local):
         "roofline": roof,
         "cpu_baseline": cpu,
         "build_ms": statistics.median(tb),
+        "build_ms_dfloat_id": statistics.median(tbd),
         "resident_refined_ms_per_batch": refined_ms,
         "resident_refined_rhs_per_s": NRHS / (refined_ms / 1e3),
         "plain_fp64_rhs_per_s": 1e6 / plain_us,

@@ -67,12 +67,24 @@ typedef struct rs_handle_s* rs_handle;
 /* Build parameters.  proxy_n: points on the proxy surface (2D: a circle of
  * radius proxy_ratio * box circumradius; 3D: 6 g^2 cell centres on a cube of
  * half-width proxy_ratio * box half-width, Sec. 3.2).  weight: w in A. */
+/* Arithmetic of the ID's pivoted QR (Sec. 2.2) for real kernels.  RS_ID_FP64
+ * (0, the default) runs it in FP64.  RS_ID_DFLOAT runs the O(m n) passes in
+ * double-float arithmetic on the FP32 pipes (hi + lo floats, ~48 significant
+ * bits; backward error ~1e-12, far below any eps >= 1e-10), with the norms,
+ * R_jj and the stopping test still in FP64 scalars; ranks then agree with the
+ * FP64 build up to pivot near-ties.  Complex kernels always use FP64. */
+enum rs_id_arith {
+  RS_ID_FP64 = 0,
+  RS_ID_DFLOAT = 1
+};
+
 typedef struct {
   int kernel_id;      /* enum rs_kernel */
   double k_wave;      /* Helmholtz wavenumber k (ignored otherwise) */
   double weight;      /* w > 0 */
   int proxy_n;        /* > 0; 3D needs 6 g^2 */
   double proxy_ratio; /* > 1 */
+  int id_arith;       /* enum rs_id_arith */
 } rs_params;
 
 /* Summary of a built handle (Table solve-lap-2d fields plus timings). */

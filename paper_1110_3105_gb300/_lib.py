@@ -30,7 +30,7 @@ class RSError(RuntimeError):
 
 class rs_params(ctypes.Structure):
     _fields_ = [("kernel_id", ctypes.c_int), ("k_wave", ctypes.c_double), ("weight", ctypes.c_double),
-                ("proxy_n", ctypes.c_int), ("proxy_ratio", ctypes.c_double)]
+                ("proxy_n", ctypes.c_int), ("proxy_ratio", ctypes.c_double), ("id_arith", ctypes.c_int)]
 
 
 class rs_stats_t(ctypes.Structure):
@@ -162,9 +162,13 @@ class Handle:
         return {f: getattr(s, f) for f, _ in rs_stats_t._fields_}
 
 
+ID_ARITH = {"fp64": 0, "dfloat": 1}
+
+
 def rs_build(points, kernel: str, weight: float, eps: float, leaf: int, proxy_n: int,
-             proxy_ratio: float = 1.5, k_wave: float = 0.0, stream=None) -> Handle:
-    """points: (dim, N) array (any order numpy, or a column-major torch tensor)."""
+             proxy_ratio: float = 1.5, k_wave: float = 0.0, stream=None, id_arith: str = "fp64") -> Handle:
+    """points: (dim, N) array (any order numpy, or a column-major torch tensor).
+    id_arith: "fp64" or "dfloat" (arithmetic of the ID's pivoted QR, rs_id_arith)."""
     load()
     if hasattr(points, "data_ptr"):
         dim, n = points.shape
@@ -176,7 +180,8 @@ def rs_build(points, kernel: str, weight: float, eps: float, leaf: int, proxy_n:
         dim, n = pts.shape
         ptr = pts.ctypes.data
         keep = pts
-    p = rs_params(KERNELS[kernel], float(k_wave), float(weight), int(proxy_n), float(proxy_ratio))
+    p = rs_params(KERNELS[kernel], float(k_wave), float(weight), int(proxy_n), float(proxy_ratio),
+                  ID_ARITH[id_arith])
     out = ctypes.c_void_p()
     rc = _lib.rs_build(ptr, n, dim, ctypes.byref(p), float(eps), int(leaf), _stream(stream), ctypes.byref(out))
     del keep
@@ -314,10 +319,11 @@ class Server:
         return t.value
 
     def submit_build(self, points, kernel: str, weight: float, eps: float, leaf: int, proxy_n: int,
-                     proxy_ratio: float = 1.5, k_wave: float = 0.0) -> int:
+                     proxy_ratio: float = 1.5, k_wave: float = 0.0, id_arith: str = "fp64") -> int:
         pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).T)   # point-major
         n, dim = pts.shape
-        p = rs_params(KERNELS[kernel], float(k_wave), float(weight), int(proxy_n), float(proxy_ratio))
+        p = rs_params(KERNELS[kernel], float(k_wave), float(weight), int(proxy_n), float(proxy_ratio),
+                      ID_ARITH[id_arith])
         t = ctypes.c_int64()
         _check(_lib.rs_server_submit_build(self._s, pts.ctypes.data, n, dim, ctypes.byref(p), float(eps), int(leaf),
                                            ctypes.byref(t)))

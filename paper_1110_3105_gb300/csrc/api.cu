@@ -182,6 +182,8 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
   if (!(params->weight > 0.0) || !std::isfinite(params->weight)) return fail(RS_ERR_ARG, "rs_build: weight must be > 0");
   if (params->proxy_n < 1) return fail(RS_ERR_ARG, "rs_build: proxy_n must be >= 1");
   if (!(params->proxy_ratio > 1.0)) return fail(RS_ERR_ARG, "rs_build: proxy_ratio must be > 1");
+  if (params->id_arith != RS_ID_FP64 && params->id_arith != RS_ID_DFLOAT)
+    return fail(RS_ERR_ARG, "rs_build: unknown id_arith %d", params->id_arith);
   if (dim == 3) {
     int g = (int)std::lround(std::sqrt(params->proxy_n / 6.0));
     if (6 * g * g != params->proxy_n) return fail(RS_ERR_ARG, "rs_build: 3D proxy_n must be 6 g^2");
@@ -210,6 +212,7 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
   h->cplx = params->kernel_id == RS_HELMHOLTZ2D;
   h->nproxy = params->proxy_n;
   h->ratio = params->proxy_ratio;
+  h->id_df = params->id_arith == RS_ID_DFLOAT;
   h->eps = eps;
   h->leaf = leaf;
 

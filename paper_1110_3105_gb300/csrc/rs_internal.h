@@ -112,6 +112,7 @@ struct Handle {
   double eps = 1e-9;
   int leaf = 64;
   bool cplx = false;
+  bool id_df = false;          // double-float pivoted QR in the ID (real kernels)
   int L = 0;
   double center[3] = {0, 0, 0};
   double half = 1.0;           // root half-width a

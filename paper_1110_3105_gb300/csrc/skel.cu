@@ -25,6 +25,7 @@
 #include <vector>
 
 #include <cuda/atomic>
+#include <type_traits>
 
 #include "rs_internal.h"
 
@@ -231,6 +232,158 @@ __device__ void back_substitute(S* M, int k, int n, int ld) {
   }
 }
 
+
+// ------------------------------------------------ double-float pivoted QR
+// The real-kernel ID runs its QR on the FP32 pipes in double-float
+// arithmetic (hi + lo floats, about 48 significant bits; see rs_common.cuh):
+// on GB300 an FP64 FMA costs as much issue as 64 FP32 FMAs, and the ~12 FP32
+// instructions of a double-float multiply-add still come out five times
+// cheaper.  A backward error near m * 2^-48 ~ 1e-12 is far below the
+// skeletonization tolerance (eps >= 1e-10 in every configuration), so ranks,
+// pivots (up to near-ties) and T agree with the FP64 factorization.  The
+// O(n) scalars of a step (norms, R_jj, the reflector's alpha, beta and f)
+// stay in FP64; only the O(m n) passes run in double-float.
+__device__ __forceinline__ double df_to_d(dfloat v) { return __dadd_rn(f32_to_f64(v.hi), f32_to_f64(v.lo)); }
+__device__ __forceinline__ dfloat df_warp_sum(dfloat v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = v + dfloat(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+  return v;
+}
+// s += a * b, renormalized (|lo| <= ulp(hi) / 2) for values that are updated
+// again and again.
+__device__ __forceinline__ void df_fma_n(dfloat& s, dfloat a, dfloat b) {
+  df_fma(s, a, b);
+  s = df_renorm(s);
+}
+
+template <int NT>
+__device__ int cpqr_df(dfloat* M, int m, int n, int ld, double eps, int* piv, double* nrm, dfloat* u) {
+  __shared__ int s_p, s_stop;
+  __shared__ double s_rjj, s_r00;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NT / 32;
+  constexpr double kTol = 1.49e-8;
+  double* nref = nrm + n;
+  for (int c = tid; c < n; c += NT) piv[c] = c;
+  const int kmax = min(m, n);
+  for (int c = warp; c < n; c += NW) {
+    const dfloat* col = M + (size_t)c * ld;
+    dfloat s(0.0f, 0.0f);
+    for (int r = lane; r < m; r += 32) df_fma(s, col[r], col[r]);
+    s = df_warp_sum(s);
+    if (lane == 0) nrm[c] = nref[c] = df_to_d(s);
+  }
+  __syncthreads();
+  int j = 0;
+  for (; j < kmax; ++j) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = n;
+      for (int c = j + lane; c < n; c += 32) {
+        double v = nrm[c];
+        if (v > best) { best = v; bi = c; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) s_p = bi;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != j) {
+      for (int r = tid; r < m; r += NT) {
+        dfloat t = M[r + (size_t)j * ld];
+        M[r + (size_t)j * ld] = M[r + (size_t)p * ld];
+        M[r + (size_t)p * ld] = t;
+      }
+      if (tid == 0) {
+        int t = piv[j]; piv[j] = piv[p]; piv[p] = t;
+        double a = nrm[j]; nrm[j] = nrm[p]; nrm[p] = a;
+        a = nref[j]; nref[j] = nref[p]; nref[p] = a;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {   // norm of the pivot column over rows j..m-1
+      const dfloat* col = M + (size_t)j * ld;
+      dfloat s(0.0f, 0.0f);
+      for (int r = j + lane; r < m; r += 32) df_fma(s, col[r], col[r]);
+      s = df_warp_sum(s);
+      if (lane == 0) {
+        const double rjj = sqrt(df_to_d(s));
+        int stop = 0;
+        if (j == 0) {
+          s_r00 = rjj;
+          if (!(rjj > 0.0)) stop = 1;
+        } else if (rjj <= eps * s_r00) {
+          stop = 1;
+        }
+        s_rjj = rjj;
+        s_stop = stop;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const double rjj = s_rjj;
+    // Householder reflector H = I - f u u^T mapping column j onto beta e_1
+    const double alpha = df_to_d(M[j + (size_t)j * ld]);
+    const double aa = fabs(alpha);
+    const double beta = alpha < 0.0 ? rjj : -rjj;
+    for (int r = j + tid; r < m; r += NT) u[r - j] = (r == j) ? f64_to_df(alpha - beta) : M[r + (size_t)j * ld];
+    const double f = 1.0 / (rjj * (rjj + aa));
+    __syncthreads();
+    for (int c = j + 1 + warp; c < n; c += NW) {
+      dfloat* col = M + (size_t)c * ld;
+      dfloat s(0.0f, 0.0f);
+      for (int r = j + lane; r < m; r += 32) df_fma(s, u[r - j], col[r]);
+      s = df_warp_sum(s);
+      const dfloat nfs = f64_to_df(-f * df_to_d(s));
+      for (int r = j + lane; r < m; r += 32) df_fma_n(col[r], u[r - j], nfs);
+      __syncwarp();
+      int again = 0;
+      if (lane == 0) {
+        const double rj = df_to_d(col[j]);
+        const double left = nrm[c] - rj * rj;
+        if (left <= kTol * nref[c]) again = 1;
+        else nrm[c] = left;
+      }
+      if (__shfl_sync(0xffffffffu, again, 0)) {   // too much cancelled: recompute
+        dfloat s2(0.0f, 0.0f);
+        for (int r = j + 1 + lane; r < m; r += 32) df_fma(s2, col[r], col[r]);
+        s2 = df_warp_sum(s2);
+        if (lane == 0) nrm[c] = nref[c] = df_to_d(s2);
+      }
+    }
+    if (tid == 0) M[j + (size_t)j * ld] = f64_to_df(beta);
+    __syncthreads();
+  }
+  return j;
+}
+
+// T = R11^-1 R12 in place in M[0:k, k:n] (double-float); one warp per column.
+template <int NT>
+__device__ void back_substitute_df(dfloat* M, int k, int n, int ld) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  for (int c = k + warp; c < n; c += NW) {
+    dfloat* col = M + (size_t)c * ld;
+    for (int i = k - 1; i >= 0; --i) {
+      double ti = 0.0;
+      if (lane == 0) {
+        ti = df_to_d(col[i]) / df_to_d(M[i + (size_t)i * ld]);
+        col[i] = f64_to_df(ti);
+      }
+      ti = __shfl_sync(0xffffffffu, ti, 0);
+      const dfloat nti = f64_to_df(-ti);
+      for (int r = lane; r < i; r += 32) df_fma_n(col[r], M[r + (size_t)i * ld], nti);
+      __syncwarp();
+    }
+  }
+}
+
 struct IdArgs {
   KParams kp;
   Pts pts;
@@ -248,6 +401,7 @@ struct IdArgs {
   int* kout;
   int* lperm;
   int smem_path;         // 1: M in shared memory
+  int qr_df;             // 1: double-float QR (real kernels, rs_id_arith)
   int mmax, nmax;
 };
 
@@ -307,19 +461,42 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
     } else {
       v = S(a.kp.w);
     }
+    if constexpr (std::is_same<S, double>::value)
+      if (a.qr_df) {
+        reinterpret_cast<dfloat*>(M)[r + (size_t)c * ld] = f64_to_df(v);
+        continue;
+      }
     M[r + (size_t)c * ld] = v;
   }
   __syncthreads();
 
-  const int k = cpqr<S, NT>(M, m, n, ld, a.eps, piv, nrm, u);
-  __syncthreads();
-  back_substitute<S, NT>(M, k, n, ld);
-  __syncthreads();
   S* T = Tpool + a.toff[b];
-  const int nr = n - k;
-  for (int e = threadIdx.x; e < k * nr; e += NT) {
-    int r = e % k, c = e / k;
-    T[r + (size_t)c * k] = M[r + (size_t)(k + c) * ld];
+  int k;
+  bool done = false;
+  if constexpr (std::is_same<S, double>::value)
+    if (a.qr_df) {   // the fill stored the matrix as double-float
+      dfloat* Md = reinterpret_cast<dfloat*>(M);
+      k = cpqr_df<NT>(Md, m, n, ld, a.eps, piv, nrm, reinterpret_cast<dfloat*>(u));
+      __syncthreads();
+      back_substitute_df<NT>(Md, k, n, ld);
+      __syncthreads();
+      const int nr = n - k;
+      for (int e = threadIdx.x; e < k * nr; e += NT) {
+        int r = e % k, c = e / k;
+        T[r + (size_t)c * k] = df_to_d(Md[r + (size_t)(k + c) * ld]);
+      }
+      done = true;
+    }
+  if (!done) {
+    k = cpqr<S, NT>(M, m, n, ld, a.eps, piv, nrm, u);
+    __syncthreads();
+    back_substitute<S, NT>(M, k, n, ld);
+    __syncthreads();
+    const int nr = n - k;
+    for (int e = threadIdx.x; e < k * nr; e += NT) {
+      int r = e % k, c = e / k;
+      T[r + (size_t)c * k] = M[r + (size_t)(k + c) * ld];
+    }
   }
   for (int c = threadIdx.x; c < n; c += NT) a.lperm[off + c] = piv[c];
   if (threadIdx.x == 0) a.kout[b] = k;
@@ -1749,6 +1926,7 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st) {
   a.lperm = lv.lperm;
   a.mmax = lv.maxm;
   a.nmax = lv.maxn;
+  a.qr_df = h->id_df && !h->cplx;
   if (h->cplx) RS_TRY(run_id<c128>(h, lv, a, mrows, msum, st));
   else RS_TRY(run_id<double>(h, lv, a, mrows, msum, st));
   RS_TRY(check_bad(h, st, "skeletonization"));

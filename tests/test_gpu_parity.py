@@ -193,6 +193,29 @@ def test_device_pointers_same_as_host(built):
     assert np.array_equal(Xd.cpu().numpy(), Xh)
 
 
+def test_dfloat_id_matches_oracle(built):
+    """The double-float QR of the ID (rs_id_arith) against the same oracle:
+    ranks within +-2 per leaf, solutions within 10 eps (real kernels)."""
+    if built["cplx"]:
+        pytest.skip("complex kernels always run the FP64 QR")
+    rs = rs_mod()
+    F, n, eps = built["F"], built["n"], built["eps"]
+    leaf, nproxy = (128, 216) if built["kind"] == "laplace3d" else (64, 64)
+    H = rs.rs_build(built["pts"], built["kind"], built["w"], eps, leaf, nproxy, id_arith="dfloat")
+    try:
+        _compare_tree(H, F.tree)
+        L = F.tree.L
+        nb, kb = rs.rs_box_ranks(H, L, F.tree.levels[L].nbox)
+        assert np.max(np.abs(kb - np.array([f.k for f in F.boxes[L]]))) <= 2
+        B = ri.rhs(n, 3, seed=23)
+        X = np.zeros_like(B)
+        rs.rs_solve(H, B, X)
+        Xo = F.solve(B)
+        assert np.linalg.norm(X - Xo) / np.linalg.norm(Xo) <= 10 * eps
+    finally:
+        H.free()
+
+
 def _circle_eig(n, m):
     s = math.fsum(math.log(2 * math.sin(math.pi * j / n)) * math.cos(2 * math.pi * m * j / n)
                   for j in range(1, n))

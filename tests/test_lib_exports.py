@@ -51,3 +51,20 @@ def test_fault_spec_validation(lib):
     assert _lib._lib.rs_set_fault(b"alloc:0") == -1
     assert _lib._lib.rs_set_fault(b"off") == 0
     assert _lib._lib.rs_set_fault(None) == 0
+
+
+def test_build_parameter_validation(lib):
+    """Bad build parameters are rejected before any device work (no GPU needed)."""
+    import numpy as np
+    from paper_1110_3105_gb300 import _lib
+    _lib.load()
+    pts = np.asfortranarray(np.random.default_rng(0).random((2, 100)))
+    out = ctypes.c_void_p()
+    good = dict(kernel_id=0, k_wave=0.0, weight=0.01, proxy_n=64, proxy_ratio=1.5, id_arith=0)
+    for field, bad in (("id_arith", 7), ("proxy_ratio", 1.0), ("proxy_n", 0), ("weight", -1.0), ("kernel_id", 9)):
+        kw = dict(good)
+        kw[field] = bad
+        p = _lib.rs_params(**kw)
+        rc = _lib._lib.rs_build(pts.ctypes.data, 100, 2, ctypes.byref(p), 1e-9, 64, None, ctypes.byref(out))
+        assert rc == -1, field
+        assert out.value is None
