@@ -197,6 +197,17 @@ int rs_profile_record(int i, int* cat, double* ms, double* bytes, double* flops)
 /* Start of record i in ms after the start of record 0 (gaps between records
  * are host time or launch latency). */
 int rs_profile_record_start(int i, double* start_ms);
+/* Tile timeline of the last persistent solve launch made while profiling was
+ * on, for the plan of `mode` (RS_PREC_FP64 or RS_PREC_FP32 solve; 2: float
+ * and 3: double-float forward operator of the refinement residual, real
+ * kernels) and nrhs columns.  Each tile is a block of one box's product at
+ * one tree depth (kind 0 upward, 1 root, 2 downward); per tile: kind, depth,
+ * first row, column count, and the times in microseconds from the earliest
+ * claim at which it was claimed by a CTA or warp, its dependencies were met
+ * and it was finished.  Arrays hold cap entries (any may be NULL); *count
+ * receives the tile count.  RS_ERR_STATE if no such launch was profiled. */
+int rs_profile_tiles(rs_handle h, int mode, int nrhs, int64_t cap, int* kind, int* depth, int* row0, int* ncol,
+                     double* t_claim_us, double* t_start_us, double* t_end_us, int64_t* count);
 
 /* Number of kernels the library has launched in this process so far. */
 int64_t rs_launch_count(void);

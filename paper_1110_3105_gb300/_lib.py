@@ -81,6 +81,8 @@ _PROTOS = {
     "rs_profile_nrec": (ctypes.c_int, []),
     "rs_profile_record": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P]),
     "rs_profile_record_start": (ctypes.c_int, [ctypes.c_int, _P]),
+    "rs_profile_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P,
+                                         _P, _P, _P, _P]),
     "rs_profile_read": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_char_p)]),
     "rs_last_error": (ctypes.c_char_p, []),
     "rs_version": (ctypes.c_char_p, []),
@@ -287,6 +289,22 @@ def rs_profile_records(with_start: bool = False) -> list:
             _check(lib.rs_profile_record_start(i, ctypes.addressof(t0)))
             rec = rec + (t0.value,)
         out.append(rec)
+    return out
+
+
+def rs_profile_tiles(h: "Handle", mode: int, nrhs: int) -> dict:
+    """Tile timeline of the last profiled persistent launch of (mode, nrhs): numpy
+    arrays kind, depth, row0, ncol, t_claim, t_start, t_end (microseconds)."""
+    lib = load()
+    cnt = ctypes.c_int64()
+    _check(lib.rs_profile_tiles(h.ptr, int(mode), int(nrhs), 0, None, None, None, None, None, None, None,
+                                ctypes.byref(cnt)))
+    n = cnt.value
+    out = {k: np.zeros(n, dtype=np.int32) for k in ("kind", "depth", "row0", "ncol")}
+    out.update({k: np.zeros(n, dtype=np.float64) for k in ("t_claim", "t_start", "t_end")})
+    _check(lib.rs_profile_tiles(h.ptr, int(mode), int(nrhs), n, out["kind"].ctypes.data, out["depth"].ctypes.data,
+                                out["row0"].ctypes.data, out["ncol"].ctypes.data, out["t_claim"].ctypes.data,
+                                out["t_start"].ctypes.data, out["t_end"].ctypes.data, ctypes.byref(cnt)))
     return out
 
 

@@ -397,6 +397,13 @@ int rs_solve_refined(rs_handle h, const void* B, int64_t ldb, int nrhs, void* X,
   return rc;
 }
 
+int rs_profile_tiles(rs_handle h, int mode, int nrhs, int64_t cap, int* kind, int* depth, int* row0, int* ncol,
+                     double* t_claim_us, double* t_start_us, double* t_end_us, int64_t* count) {
+  RS_TRY(check_handle(h));
+  if (mode < 0 || mode > 3 || nrhs < 1 || cap < 0) return fail(RS_ERR_ARG, "rs_profile_tiles: bad arguments");
+  return rs::tile_trace(h, mode, nrhs, cap, kind, depth, row0, ncol, t_claim_us, t_start_us, t_end_us, count);
+}
+
 int rs_stats(rs_handle h, rs_stats_t* out) {
   RS_TRY(check_handle(h));
   if (!out) return fail(RS_ERR_ARG, "rs_stats: null output");

@@ -189,6 +189,8 @@ int solve_pers_device_sub(Handle* h, int mode, const double* d_B, int64_t ldb, i
 int solve_pers_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, void* d_X, int64_t ldx,
                       cudaStream_t st);
 int pers_check(Handle* h);
+int tile_trace(Handle* h, int prec, int R, int64_t cap, int* kind, int* depth, int* r0, int* ncol, double* t_claim,
+               double* t_start, double* t_end, int64_t* count);
 void free_pers(Handle* h);
 int prec_cat(int prec);
 int ensure_work_pub(Handle* h, int prec, int R, cudaStream_t st);

@@ -80,7 +80,14 @@ struct Plan {
   int* dflag;           // device copy of the timeout flag (checked per tile)
   int* up_cnt;
   int* dn_cnt;
+  unsigned long long* trace;   // per tile: claimed, dependencies met, done (ns); null unless profiling
 };
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ inline int ld_acquire(const int* p) {
   cuda::atomic_ref<const int, cuda::thread_scope_device> a(*p);
@@ -268,6 +275,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= p.ntiles) break;
     if (*(volatile int*)p.dflag) return;   // another warp gave up waiting: leave too
+    if (p.trace && lane == 0) p.trace[3 * (size_t)t] = gtime();
     const Tile tl = p.tiles[t];
     const int g = tl.g;
     const int d = p.bt.depth[g];
@@ -277,6 +285,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
     if (tl.kind != T_DOWN) {
       // ---- up / root tile: rows of U b, U = [calD ; calR] ((n+k) x n)
       if (p.bt.up_need[g] > 0 && !wait_at_least(&p.up_cnt[g], epoch * p.bt.up_need[g], flag, p.dflag)) return;
+      if (p.trace && lane == 0) p.trace[3 * (size_t)t + 1] = gtime();
       const int rows = n + k;
       const int r = tl.r0 + lane;
       const S* Ub = p.U[d] + p.bt.uoff[g];
@@ -335,10 +344,12 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
       }
       if (tl.kind == T_ROOT) signal(&p.dn_cnt[g]);
       else signal(&p.up_cnt[p.bt.parent[g]]);
+      if (p.trace && lane == 0) p.trace[3 * (size_t)t + 2] = gtime();
     } else {
       // ---- down tile: rows of u + calL x_parent (n x k)
       const int par = p.bt.parent[g];
       if (!wait_at_least(&p.dn_cnt[par], epoch * p.bt.dn_need[par], flag, p.dflag)) return;
+      if (p.trace && lane == 0) p.trace[3 * (size_t)t + 1] = gtime();
       const int r = tl.r0 + lane;
       const S* Lb = p.Lf[d] + p.bt.loff[g];
       const int64_t ldd = p.ldv[d], ldp = p.ldv[d - 1];
@@ -375,6 +386,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
         }
       }
       signal(&p.dn_cnt[g]);
+      if (p.trace && lane == 0) p.trace[3 * (size_t)t + 2] = gtime();
     }
   }
 }
@@ -482,6 +494,7 @@ __global__ void __launch_bounds__(C_NT) k_solve_cta(Plan<S> p, const SIO* B, int
       const int t = next;
       int ok = 1;
       if (t < p.ntiles) {
+        if (p.trace) p.trace[3 * (size_t)t] = gtime();
         const Tile tl = p.tiles[t];
         if (tl.kind != T_DOWN) {
           if (p.bt.up_need[tl.g] > 0)
@@ -491,6 +504,7 @@ __global__ void __launch_bounds__(C_NT) k_solve_cta(Plan<S> p, const SIO* B, int
           ok = spin_until(&p.dn_cnt[par], epoch * p.bt.dn_need[par], flag, p.dflag);
         }
         if (ok) next = atomicAdd(p.dispatch, 1);
+        if (p.trace) p.trace[3 * (size_t)t + 1] = gtime();
       }
       s_tile = t;
       s_ok = ok;
@@ -511,10 +525,12 @@ __global__ void __launch_bounds__(C_NT) k_solve_cta(Plan<S> p, const SIO* B, int
     const S* vin = down ? p.u[d - 1] : (leaf_in ? nullptr : p.v[d]);
     const int64_t ldin = down ? p.ldv[d - 1] : p.ldv[d];
     const int64_t in0 = down ? p.bt.skoff[g] : off;
-    const int r0 = tl.r0, c0 = tl.c0;
-    const int cw = min(TN, tl.c1 - c0);
+    const int r0 = tl.r0;
     const bool busy = wrow < rows - r0;    // warp-uniform
-
+    // the tile's columns in blocks of TN; a single-chunk factor block is
+    // staged once for all of them
+    for (int c0 = tl.c0; c0 < tl.c1; c0 += TN) {
+    const int cw = min(TN, tl.c1 - c0);
     S acc[RPT][CPT];
 #pragma unroll
     for (int a = 0; a < RPT; ++a)
@@ -524,7 +540,7 @@ __global__ void __launch_bounds__(C_NT) k_solve_cta(Plan<S> p, const SIO* B, int
     for (int k0 = 0; k0 < K; k0 += C_TK) {
       const int kn = min(C_TK, K - k0);
       __syncthreads();   // the previous chunk (or tile) is done with As / Bs
-      {
+      if (K > C_TK || c0 == tl.c0) {
         const int i = tid % C_TM;
         const bool oki = r0 + i < rows;
         const S* Ai = A + (r0 + i) + (size_t)k0 * rows;
@@ -604,12 +620,14 @@ __global__ void __launch_bounds__(C_NT) k_solve_cta(Plan<S> p, const SIO* B, int
         }
       }
     }
+    }   // column blocks
     // every thread's stores of this tile precede the barrier; thread 0's
     // release add publishes them to the waiter that acquires the counter
     __syncthreads();
     if (tid == 0) {
       cuda::atomic_ref<int, cuda::thread_scope_device> c(tl.kind == T_UP ? p.up_cnt[p.bt.parent[g]] : p.dn_cnt[g]);
       c.fetch_add(1, cuda::memory_order_release);
+      if (p.trace) p.trace[3 * (size_t)t + 2] = gtime();
     }
   }
 }
@@ -630,6 +648,10 @@ struct PersPlan {
   int* flag_dev = nullptr;
   int grid = 0;
   int work_gen = -1;         // generation of the work buffers captured in ptrs
+  unsigned long long* trace = nullptr;   // tile timeline of the last profiled launch (3 per tile)
+  bool traced = false;
+  std::vector<Tile> h_tiles;             // host copy of the tile list
+  std::vector<int> h_depth;              // depth per global box
   bool dirty = false;        // a wait timed out: counters must restart
   std::vector<void*> mem;
 };
@@ -710,6 +732,16 @@ int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X
   pl.dflag = P->counters + 1;
   pl.up_cnt = P->counters + 2;
   pl.dn_cnt = P->counters + 2 + P->nbox;
+  pl.trace = nullptr;
+  P->traced = false;
+  if (prof_on()) {   // tile timeline for rs_profile_tiles
+    if (!P->trace) {
+      RS_CUDA(cudaMalloc((void**)&P->trace, sizeof(unsigned long long) * 3 * (size_t)P->ntiles));
+      P->mem.push_back(P->trace);
+    }
+    pl.trace = P->trace;
+    P->traced = true;
+  }
   *P->flag_host = 0;
   prof_begin(prec_cat(P->prec), st);
   if constexpr (TN > 0)
@@ -817,7 +849,12 @@ static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out)
     int64_t rt = 0;
     for (int b = 0; b < lv.nbox; ++b) rt += div_up(down ? lv.h_n[b] : lv.h_n[b] + lv.h_k[b], rb);
     int split = (int)std::max<int64_t>(1, std::min<int64_t>(nchunk, 8192 / std::max<int64_t>(1, rt)));
-    int per = P->TN ? P->TN : div_up(nchunk, split) * P->CT;
+    int per = div_up(nchunk, split) * P->CT;
+    if (P->TN) {   // CTA tiles: whole column blocks, split only while a level has few row tiles
+      const int nb = div_up(R, P->TN);
+      const int sp = (int)std::max<int64_t>(1, std::min<int64_t>(nb, 2048 / std::max<int64_t>(1, rt)));
+      per = div_up(nb, sp) * P->TN;
+    }
     std::vector<std::pair<int, int>> cr;
     for (int c = 0; c < R; c += per) cr.push_back({c, std::min(R, c + per)});
     return cr;
@@ -849,6 +886,8 @@ static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out)
     }
   }
   P->ntiles = (int)tiles.size();
+  P->h_tiles = tiles;
+  P->h_depth = depth;
   RS_TRY(dev_upload(P, &P->tiles, tiles, st));
   RS_TRY(dev_upload(P, &P->bt.depth, depth, st));
   RS_TRY(dev_upload(P, &P->bt.n, n, st));
@@ -920,6 +959,37 @@ int solve_pers_device_sub(Handle* h, int mode, const double* d_B, int64_t ldb, i
 
 // After the stream has been synchronized: timeout flags of every plan that
 // ran since the last check.
+// Tile timeline of the last profiled persistent launch of plan (prec, R):
+// per tile its kind, depth, rows from, columns, and the times (us, from the
+// earliest claim) it was claimed, its dependencies were met and it finished.
+int tile_trace(Handle* h, int prec, int R, int64_t cap, int* kind, int* depth, int* r0, int* ncol, double* t_claim,
+               double* t_start, double* t_end, int64_t* count) {
+  PersCache* c = (PersCache*)h->pers;
+  PersPlan* P = nullptr;
+  if (c)
+    for (PersPlan* q : c->plans)
+      if (q->prec == prec && q->R == R) P = q;
+  if (!P || !P->traced) return fail(RS_ERR_STATE, "rs_profile_tiles: no profiled launch of this plan");
+  std::vector<unsigned long long> tr(3 * (size_t)P->ntiles);
+  RS_CUDA(cudaDeviceSynchronize());
+  RS_CUDA(cudaMemcpy(tr.data(), P->trace, sizeof(unsigned long long) * tr.size(), cudaMemcpyDeviceToHost));
+  unsigned long long t0 = ~0ull;
+  for (int t = 0; t < P->ntiles; ++t) t0 = std::min(t0, tr[3 * (size_t)t]);
+  const int64_t n = std::min<int64_t>(cap, P->ntiles);
+  for (int64_t t = 0; t < n; ++t) {
+    const Tile& tl = P->h_tiles[t];
+    if (kind) kind[t] = tl.kind;
+    if (depth) depth[t] = P->h_depth[tl.g];
+    if (r0) r0[t] = tl.r0;
+    if (ncol) ncol[t] = tl.c1 - tl.c0;
+    if (t_claim) t_claim[t] = 1e-3 * (double)(tr[3 * t] - t0);
+    if (t_start) t_start[t] = 1e-3 * (double)(tr[3 * t + 1] - t0);
+    if (t_end) t_end[t] = 1e-3 * (double)(tr[3 * t + 2] - t0);
+  }
+  if (count) *count = P->ntiles;
+  return RS_OK;
+}
+
 int pers_check(Handle* h) {
   PersCache* c = (PersCache*)h->pers;
   if (!c) return RS_OK;
