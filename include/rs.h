@@ -180,8 +180,11 @@ int rs_box_ranks(rs_handle h, int level, int* n, int* k);
 /* Launch profiler (off by default).  rs_profile_enable(1) clears the record
  * and times every following kernel launch of the library with CUDA events
  * on the stream it runs on, grouped into rs_profile_ncat() categories
- * ("tree", "id", "factor", "solve_up", "solve_down", "fwd_dblock", ...);
- * rs_profile_enable(0) stops recording.  rs_profile_read waits for the
+ * ("tree", "id", "factor", "solve_fp64", "solve_fp32", "residual", ...);
+ * rs_profile_enable(2) also records the tile timeline of every persistent
+ * solve launch (rs_profile_tiles; a few stores per tile, and the first
+ * launch of each plan allocates its buffer); rs_profile_enable(0) stops
+ * recording.  rs_profile_read waits for the
  * recorded events and returns, for one category, the summed device time
  * (ms), the launch count and the algorithmic bytes and flops of those
  * launches (counted from the block sizes).  *name is a static string. */
@@ -197,8 +200,8 @@ int rs_profile_record(int i, int* cat, double* ms, double* bytes, double* flops)
 /* Start of record i in ms after the start of record 0 (gaps between records
  * are host time or launch latency). */
 int rs_profile_record_start(int i, double* start_ms);
-/* Tile timeline of the last persistent solve launch made while profiling was
- * on, for the plan of `mode` (RS_PREC_FP64 or RS_PREC_FP32 solve; 2: float
+/* Tile timeline of the last persistent solve launch made while
+ * rs_profile_enable(2) was on, for the plan of `mode` (RS_PREC_FP64 or RS_PREC_FP32 solve; 2: float
  * and 3: double-float forward operator of the refinement residual, real
  * kernels) and nrhs columns.  Each tile is a block of one box's product at
  * one tree depth (kind 0 upward, 1 root, 2 downward); per tile: kind, depth,
@@ -280,6 +283,13 @@ const char* rs_last_error(void);
 
 /* Library version string. */
 const char* rs_version(void);
+
+/* The Green's function exactly as the library evaluates it (eqs. 2d-laplace,
+ * 3d-laplace, 2d-helmholtz; no quadrature weight), at n squared distances
+ * s2 > 0 (host array): out[n] for the real kernels, interleaved (re, im)
+ * out[2 n] for Helmholtz (host).  For verification of the device evaluation
+ * (2D Laplace uses a table-driven logarithm, Tang 1990); synchronous. */
+int rs_green(int kernel_id, double k_wave, const double* s2, int64_t n, double* out);
 
 #ifdef __cplusplus
 }

@@ -81,6 +81,7 @@ _PROTOS = {
     "rs_profile_nrec": (ctypes.c_int, []),
     "rs_profile_record": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P]),
     "rs_profile_record_start": (ctypes.c_int, [ctypes.c_int, _P]),
+    "rs_green": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _P, ctypes.c_int64, _P]),
     "rs_profile_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _P, _P, _P, _P,
                                          _P, _P, _P, _P]),
     "rs_profile_read": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_char_p)]),
@@ -250,8 +251,9 @@ def rs_box_ranks(h: Handle, level: int, nbox: int):
     return n, k
 
 
-def rs_profile_enable(on: bool = True):
-    _check(load().rs_profile_enable(1 if on else 0))
+def rs_profile_enable(on=True):
+    """True/1: time every launch; 2: also record tile timelines (rs_profile_tiles); False/0: off."""
+    _check(load().rs_profile_enable(2 if on == 2 else (1 if on else 0)))
 
 
 def rs_profile_read() -> dict:
@@ -306,6 +308,16 @@ def rs_profile_tiles(h: "Handle", mode: int, nrhs: int) -> dict:
                                 out["row0"].ctypes.data, out["ncol"].ctypes.data, out["t_claim"].ctypes.data,
                                 out["t_start"].ctypes.data, out["t_end"].ctypes.data, ctypes.byref(cnt)))
     return out
+
+
+def rs_green(kernel: str, s2, k_wave: float = 0.0) -> np.ndarray:
+    """The device evaluation of G at squared distances s2 (no weight)."""
+    lib = load()
+    s2 = np.ascontiguousarray(np.asarray(s2, dtype=np.float64))
+    cplx = kernel == "helmholtz2d"
+    out = np.zeros(2 * s2.size if cplx else s2.size, dtype=np.float64)
+    _check(lib.rs_green(KERNELS[kernel], float(k_wave), s2.ctypes.data, s2.size, out.ctypes.data))
+    return out.view(np.complex128) if cplx else out
 
 
 def rs_launch_count() -> int:

@@ -9,6 +9,9 @@
 #include <string>
 #include <vector>
 
+#include <map>
+#include <mutex>
+#include <cstring>
 #include "rs_internal.h"
 
 // The opaque handle type of the C ABI is the runtime's Handle.
@@ -77,6 +80,55 @@ int dalloc(Handle* h, void** p, size_t bytes) {
   h->arena_cur += bytes;
   h->arena_left -= bytes;
   return RS_OK;
+}
+
+// Per-device table of log_tab (rs_common.cuh): (log c_i, 1 / c_i) for
+// c_i = 1 + i/256, then log 2 as a 32-bit head and the rest, computed in long
+// double on the host.  One 4 KiB allocation per device, kept for the process.
+static std::mutex g_logtab_mu;
+static std::map<int, double*> g_logtab;
+
+static int log_table(const double** out) {
+  int dev = 0;
+  RS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_logtab_mu);
+  auto it = g_logtab.find(dev);
+  if (it != g_logtab.end()) {
+    *out = it->second;
+    return RS_OK;
+  }
+  std::vector<double> t(2 * (rs::LOGTAB_N + 1));
+  for (int i = 0; i < rs::LOGTAB_N; ++i) {
+    const long double c = 1.0L + (long double)i / rs::LOGTAB_N;
+    t[2 * i] = (double)logl(c);
+    t[2 * i + 1] = (double)(1.0L / c);
+  }
+  const long double ln2 = logl(2.0L);
+  uint64_t bits;
+  double head = (double)ln2;
+  std::memcpy(&bits, &head, sizeof(bits));
+  bits &= ~((uint64_t(1) << 21) - 1);   // 32 significant bits: e * head is exact for |e| < 2^21
+  std::memcpy(&head, &bits, sizeof(bits));
+  t[2 * rs::LOGTAB_N] = head;
+  t[2 * rs::LOGTAB_N + 1] = (double)(ln2 - (long double)head);
+  double* d = nullptr;
+  RS_CUDA(cudaMalloc((void**)&d, sizeof(double) * t.size()));
+  RS_CUDA(cudaMemcpy(d, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice));
+  g_logtab[dev] = d;
+  *out = d;
+  return RS_OK;
+}
+
+__global__ void k_green(rs::KParams kp, const double* s2, int64_t n, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (kp.kind == RS_HELMHOLTZ2D) {
+    const rs::c128 g = rs::green_cplx(kp.kwave, sqrt(s2[i]));
+    out[2 * i] = g.re;
+    out[2 * i + 1] = g.im;
+  } else {
+    out[i] = rs::green_real_s2(kp, s2[i]);
+  }
 }
 
 static bool is_device_ptr(const void* p) {
@@ -163,6 +215,35 @@ extern "C" {
 
 const char* rs_last_error(void) { return rs::g_err.c_str(); }
 
+int rs_green(int kernel_id, double k_wave, const double* s2, int64_t n, double* out) {
+  rs::g_err.clear();
+  if (kernel_id < RS_LAPLACE2D || kernel_id > RS_LAPLACE3D || n < 0 || (n > 0 && (!s2 || !out)))
+    return fail(RS_ERR_ARG, "rs_green: bad arguments");
+  if (n == 0) return RS_OK;
+  rs::KParams kp{};
+  kp.kind = kernel_id;
+  kp.w = 1.0;
+  kp.kwave = k_wave;
+  RS_TRY(log_table(&kp.logtab));
+  const int64_t nout = kernel_id == RS_HELMHOLTZ2D ? 2 * n : n;
+  double *ds = nullptr, *dout = nullptr;
+  int rc = RS_OK;
+  if (cudaMalloc((void**)&ds, sizeof(double) * n) || cudaMalloc((void**)&dout, sizeof(double) * nout)) {
+    rc = fail(RS_ERR_OOM, "rs_green: allocation failed");
+  } else if (cudaMemcpy(ds, s2, sizeof(double) * n, cudaMemcpyHostToDevice)) {
+    rc = fail(RS_ERR_CUDA, "rs_green: copy failed");
+  } else {
+    k_green<<<(unsigned)((n + 255) / 256), 256>>>(kp, ds, n, dout);
+    rs::count_launch();
+    if (cudaGetLastError() || cudaMemcpy(out, dout, sizeof(double) * nout, cudaMemcpyDeviceToHost))
+      rc = fail(RS_ERR_CUDA, "rs_green: evaluation failed");
+  }
+  cudaGetLastError();
+  if (ds) cudaFree(ds);
+  if (dout) cudaFree(dout);
+  return rc;
+}
+
 const char* rs_version(void) { return "rs-gb300 0.1 (sm_103a)"; }
 
 int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, double eps, int leaf, void* stream,
@@ -209,6 +290,13 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
   h->kp.kind = params->kernel_id;
   h->kp.w = params->weight;
   h->kp.kwave = params->k_wave;
+  {
+    const int rc0 = log_table(&h->kp.logtab);
+    if (rc0 != RS_OK) {
+      delete h;
+      return rc0;
+    }
+  }
   h->cplx = params->kernel_id == RS_HELMHOLTZ2D;
   h->nproxy = params->proxy_n;
   h->ratio = params->proxy_ratio;

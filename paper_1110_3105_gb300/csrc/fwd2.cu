@@ -37,22 +37,21 @@ struct FwdTab {
 };
 
 // Forward operator factors of one depth, in the solve's two-pass form:
-//   FU = [D ; P] ((n+k) x n): D the kernel block of the box (leaf: A(I, I);
-//        above: w G between skeletons of different children, zero within one
-//        child; root: the same form), P = [I T] Pi the projection;
+//   FU = [D ; P] ((n+k) x n): rows 0..n-1, the kernel block D of the box, are
+//        written by the factorization while it assembles its block (skel.cu:
+//        emit_fwd); rows n.. hold the projection P = [I T] Pi;
 //   FL = P^T (n x k).
-// Entries are evaluated in FP64 and stored as float and as double-float.
-__global__ void k_fwd_factors(FwdTab t, KParams kp, Pts pts, const int* act, const int* owner, int leaf_level,
-                              const double* T, const int64_t* uoff, const int64_t* loff, float* FU32, dfloat* FUdf,
-                              float* FL32, dfloat* FLdf) {
+// Stored as float and as double-float.
+__global__ void k_fwd_factors(FwdTab t, const double* T, const int64_t* uoff, const int64_t* loff, float* FU32,
+                              dfloat* FUdf, float* FL32, dfloat* FLdf) {
   extern __shared__ int inv[];   // position within I -> index in the ID order
   const int b = blockIdx.x;
   const int n = t.n[b], k = t.k ? t.k[b] : 0, rows = n + k;
+  if (k == 0) return;
   const int64_t off = t.off[b];
-  const int* lp = k > 0 ? t.lperm + off : nullptr;
-  const double* Tb = k > 0 ? T + t.toff[b] : nullptr;
-  if (k > 0)
-    for (int q = threadIdx.x; q < n; q += blockDim.x) inv[lp[q]] = q;
+  const int* lp = t.lperm + off;
+  const double* Tb = T + t.toff[b];
+  for (int q = threadIdx.x; q < n; q += blockDim.x) inv[lp[q]] = q;
   __syncthreads();
   auto pval = [&](int a, int c) -> double {   // P[a, c]
     int q = inv[c];
@@ -60,51 +59,36 @@ __global__ void k_fwd_factors(FwdTab t, KParams kp, Pts pts, const int* act, con
   };
   float* U32 = FU32 + uoff[b];
   dfloat* Udf = FUdf + uoff[b];
-  for (int64_t e = threadIdx.x; e < (int64_t)rows * n; e += blockDim.x) {
-    int r = (int)(e % rows), c = (int)(e / rows);
-    double v;
-    if (r < n) {
-      if (leaf_level) v = system_entry<double>(kp, pts, act[off + r], act[off + c]);
-      else v = owner[off + r] == owner[off + c] ? 0.0 : offdiag_entry<double>(kp, pts, act[off + r], act[off + c]);
-    } else {
-      v = pval(r - n, c);
-    }
-    U32[e] = (float)v;
-    Udf[e] = dfloat(v);
+  for (int64_t e = threadIdx.x; e < (int64_t)k * n; e += blockDim.x) {
+    const int a = (int)(e % k), c = (int)(e / k);
+    const double v = pval(a, c);
+    const int64_t i = n + a + (int64_t)c * rows;
+    U32[i] = f64_to_f32_rn(v);
+    Udf[i] = f64_to_df(v);
   }
-  if (k > 0) {
-    float* L32 = FL32 + loff[b];
-    dfloat* Ldf = FLdf + loff[b];
-    for (int64_t e = threadIdx.x; e < (int64_t)n * k; e += blockDim.x) {
-      int r = (int)(e % n), a = (int)(e / n);
-      double v = pval(a, r);
-      L32[e] = (float)v;
-      Ldf[e] = dfloat(v);
-    }
+  float* L32 = FL32 + loff[b];
+  dfloat* Ldf = FLdf + loff[b];
+  for (int64_t e = threadIdx.x; e < (int64_t)n * k; e += blockDim.x) {
+    const int r = (int)(e % n), a = (int)(e / n);
+    const double v = pval(a, r);
+    L32[e] = f64_to_f32_rn(v);
+    Ldf[e] = f64_to_df(v);
   }
 }
 
 }  // namespace
 
-// Build-time: forward-operator factors of every depth (real kernels).
+// Build-time: the projection rows of the forward factors of every depth
+// (real kernels; the factors were allocated with the level's pools).
 int make_fwd_blocks(Handle* h, cudaStream_t st) {
   if (h->cplx) return RS_OK;
-  Pts pts;
-  pts.x = h->pts;
-  pts.y = h->pts + h->N;
-  pts.z = h->dim == 3 ? h->pts + 2 * h->N : nullptr;
-  for (int d = 0; d <= h->L; ++d) {
+  for (int d = 1; d <= h->L; ++d) {
     Level& lv = h->lv[d];
-    RS_TRY(dalloc(h, &lv.FU32, sizeof(float) * std::max<int64_t>(1, lv.usz)));
-    RS_TRY(dalloc(h, &lv.FUdf, sizeof(dfloat) * std::max<int64_t>(1, lv.usz)));
-    RS_TRY(dalloc(h, &lv.FL32, sizeof(float) * std::max<int64_t>(1, lv.lsz)));
-    RS_TRY(dalloc(h, &lv.FLdf, sizeof(dfloat) * std::max<int64_t>(1, lv.lsz)));
-    FwdTab t{lv.n, d > 0 ? lv.k : nullptr, lv.off, lv.skoff, lv.lperm, lv.toff};
+    FwdTab t{lv.n, lv.k, lv.off, lv.skoff, lv.lperm, lv.toff};
     const size_t smem = sizeof(int) * (size_t)std::max(1, lv.maxn);
     RS_CUDA(cudaFuncSetAttribute(k_fwd_factors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_fwd_factors<<<lv.nbox, 256, smem, st>>>(t, h->kp, pts, lv.act, lv.owner, d == h->L, (const double*)lv.T,
-                                              lv.uoff, lv.loff, (float*)lv.FU32, (dfloat*)lv.FUdf,
-                                              (float*)lv.FL32, (dfloat*)lv.FLdf);
+    k_fwd_factors<<<lv.nbox, 256, smem, st>>>(t, (const double*)lv.T, lv.uoff, lv.loff, (float*)lv.FU32,
+                                              (dfloat*)lv.FUdf, (float*)lv.FL32, (dfloat*)lv.FLdf);
     RS_CHECK_LAUNCH();
   }
   return RS_OK;

@@ -23,6 +23,7 @@ const char* kNames[P_NCAT] = {"tree", "id", "factor", "fp32_copy", "solve_up", "
 
 std::mutex g_mu;
 bool g_on = false;
+bool g_tiles = false;   // also record the persistent launches' tile timelines
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_pool;
 size_t g_next = 0;
@@ -40,6 +41,7 @@ cudaEvent_t get_event() {
 }  // namespace
 
 bool prof_on() { return g_on; }
+bool prof_tiles_on() { return g_on && g_tiles; }
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -87,6 +89,7 @@ int rs_profile_enable(int on) {
   rs::g_stack.clear();
   rs::g_next = 0;
   rs::g_on = on != 0;
+  rs::g_tiles = on == 2;
   return RS_OK;
 }
 

@@ -36,6 +36,7 @@ namespace rs {
 enum ProfCat { P_TREE, P_ID, P_FACTOR, P_COPY32, P_UP, P_DOWN, P_PERM, P_FWD_PROJ, P_FWD_DBLOCK, P_FWD_DOWN,
                P_RESID, P_MISC, P_SOLVE64, P_SOLVE32, P_NCAT };
 bool prof_on();
+bool prof_tiles_on();   // rs_profile_enable(2): tile timelines as well
 void prof_begin(int cat, cudaStream_t st);
 void prof_end(int cat, cudaStream_t st, double bytes, double flops);
 void prof_amend(int cat, double bytes, double flops);  // fix up the last record of cat

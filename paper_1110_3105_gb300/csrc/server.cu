@@ -1,14 +1,18 @@
 // Serving loop: resident factorizations, memory-admitted builds, and
 // continuous batching of right-hand sides.
 //
-// Each registered handle owns a worker thread and a CUDA stream.  The worker
-// repeatedly takes every solve request queued for its handle (up to
-// max_cols columns in total), copies their columns from the callers' host
-// buffers into one device batch, runs one mixed-precision refined solve
-// (rs_solve_refined) on it and copies each request's columns back.
-// Requests that arrive while a batch is on the GPU wait for the next one,
-// so batches form continuously; workers of different handles run
-// concurrently and their device work overlaps on separate streams.  Builds
+// Each registered handle owns a worker thread, a compute stream and a copy
+// stream.  The worker repeatedly takes every solve request queued for its
+// handle (up to max_cols columns in total), copies their columns from the
+// callers' host buffers into one device batch, runs one mixed-precision
+// refined solve (rs_solve_refined) on it and copies each request's columns
+// back.  Two batch buffers form a pipeline: before a batch's solve starts,
+// the next batch (the requests queued by then) is taken and its columns
+// copied in on the copy stream, and a finished batch's columns are copied
+// back on the copy stream while the next solve runs; its requests complete
+// from a host callback once that copy lands.  Requests that arrive while a
+// batch is on the GPU wait for a later one, so batches form continuously;
+// workers of different handles run concurrently.  Builds
 // run on a builder thread and are admitted only while the estimated device
 // memory of the resident factorizations plus the new one stays under the
 // server's budget.
@@ -89,15 +93,29 @@ struct Worker {
   int id = -1;
   int64_t n = 0;
   bool cplx = false;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;   // solves
+  cudaStream_t cstream = nullptr;  // copies in and out
   std::deque<std::shared_ptr<Request>> q;
   std::condition_variable cv;
   std::thread th;
-  void* db = nullptr;     // device batch buffers (n x max_cols scalars)
-  void* dx = nullptr;
+  // two pipeline slots: device batch buffers (n x max_cols scalars) and events
+  void* db[2] = {nullptr, nullptr};
+  void* dx[2] = {nullptr, nullptr};
+  cudaEvent_t in_done[2] = {nullptr, nullptr};    // columns copied in
+  cudaEvent_t out_done[2] = {nullptr, nullptr};   // columns copied back (slot free again)
   size_t cap = 0;
 
   void run();
+  int take(std::vector<std::shared_ptr<Request>>& batch, int& cols, bool wait);
+  int stage_in(int slot, const std::vector<std::shared_ptr<Request>>& batch);
+};
+
+// A finished batch whose columns are on their way back to the callers.
+struct Finished {
+  Server* s;
+  std::vector<std::shared_ptr<Request>> batch;
+  int rc;
+  int cols;
 };
 
 size_t handle_bytes(rs_handle h) {
@@ -118,77 +136,130 @@ void complete(Server* s, const std::shared_ptr<Request>& r, int status) {
   }
 }
 
+// Requests for one batch (up to max_cols columns); waits for the first one
+// only if `wait`.  Returns 0 when the server stops with nothing queued.
+int Worker::take(std::vector<std::shared_ptr<Request>>& batch, int& cols, bool wait) {
+  batch.clear();
+  cols = 0;
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (wait) cv.wait(lk, [&] { return s->stop || !q.empty(); });
+  if (q.empty()) return s->stop ? 0 : 1;
+  while (!q.empty() && (batch.empty() || cols + q.front()->ncols <= s->max_cols)) {
+    cols += q.front()->ncols;
+    batch.push_back(q.front());
+    q.pop_front();
+  }
+  return 1;
+}
+
+// Copy a batch's columns into slot `slot` on the copy stream (after the
+// slot's previous columns have gone back to their callers).
+int Worker::stage_in(int slot, const std::vector<std::shared_ptr<Request>>& batch) {
+  const size_t sb = cplx ? 16 : 8;
+  if (cudaEventSynchronize(out_done[slot]) != cudaSuccess) {
+    cudaGetLastError();
+    return RS_ERR_CUDA;
+  }
+  size_t col = 0;
+  for (auto& r : batch) {
+    if (cudaMemcpy2DAsync((char*)db[slot] + col * n * sb, n * sb, r->B, r->ldb * sb, n * sb, r->ncols,
+                          cudaMemcpyHostToDevice, cstream) != cudaSuccess) {
+      cudaGetLastError();
+      return RS_ERR_CUDA;
+    }
+    col += r->ncols;
+  }
+  if (cudaEventRecord(in_done[slot], cstream) != cudaSuccess) {
+    cudaGetLastError();
+    return RS_ERR_CUDA;
+  }
+  return RS_OK;
+}
+
+void finish_batch(void* p) {   // host callback: no CUDA calls
+  Finished* f = static_cast<Finished*>(p);
+  {
+    std::lock_guard<std::mutex> lk(f->s->mu);
+    for (auto& r : f->batch) complete(f->s, r, f->rc);
+    f->s->batches += 1;
+    f->s->batch_cols += f->cols;
+  }
+  f->s->cv_done.notify_all();
+  delete f;
+}
+
 void Worker::run() {
   const size_t sb = cplx ? 16 : 8;
+  int rc0 = RS_OK;
+  const size_t want = (size_t)n * s->max_cols * sb;
+  for (int i = 0; i < 2 && rc0 == RS_OK; ++i) {
+    if (cudaMalloc(&db[i], want) != cudaSuccess || cudaMalloc(&dx[i], want) != cudaSuccess ||
+        cudaEventCreateWithFlags(&in_done[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&out_done[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(out_done[i], cstream) != cudaSuccess) {
+      cudaGetLastError();
+      rc0 = RS_ERR_OOM;
+    }
+  }
+  cap = rc0 == RS_OK ? want : 0;
+  std::vector<std::shared_ptr<Request>> cur, next;
+  int cur_cols = 0, next_cols = 0, slot = 0;
+  bool staged = false;   // cur is already in slot `slot`
   for (;;) {
-    std::vector<std::shared_ptr<Request>> batch;
-    int cols = 0;
-    {
-      std::unique_lock<std::mutex> lk(s->mu);
-      cv.wait(lk, [&] { return s->stop || !q.empty(); });
-      if (s->stop && q.empty()) return;
-      while (!q.empty() && (batch.empty() || cols + q.front()->ncols <= s->max_cols)) {
-        cols += q.front()->ncols;
-        batch.push_back(q.front());
-        q.pop_front();
-      }
+    if (cur.empty()) {
+      if (!take(cur, cur_cols, true)) return;
+      staged = false;
     }
-    size_t need = (size_t)n * cols * sb;
-    int rc = RS_OK;
-    if (need > cap) {
-      if (db) cudaFree(db);
-      if (dx) cudaFree(dx);
-      db = dx = nullptr;
-      size_t want = (size_t)n * s->max_cols * sb;
-      if (cudaMalloc(&db, want) != cudaSuccess || cudaMalloc(&dx, want) != cudaSuccess) {
-        cudaGetLastError();
-        rc = RS_ERR_OOM;
-        cap = 0;
-      } else {
-        cap = want;
-      }
-    }
+    int rc = rc0;
+    if (rc == RS_OK && !staged) rc = stage_in(slot, cur);
+    // the next batch goes in on the copy stream while this one is solved
+    next.clear();
+    next_cols = 0;
+    bool next_staged = false;
+    if (rc == RS_OK && take(next, next_cols, false) && !next.empty())
+      next_staged = stage_in(slot ^ 1, next) == RS_OK;
     double tol = 1e-10;
-    if (rc == RS_OK) {
-      // each request's columns straight into the device batch (no host packing)
-      size_t col = 0;
-      for (auto& r : batch) {
-        tol = std::min(tol, r->tol);
-        if (cudaMemcpy2DAsync((char*)db + col * n * sb, n * sb, r->B, r->ldb * sb, n * sb, r->ncols,
-                              cudaMemcpyHostToDevice, stream) != cudaSuccess) {
-          cudaGetLastError();
-          rc = RS_ERR_CUDA;
-        }
-        col += r->ncols;
-      }
-      std::vector<double> rel(cols, 0.0);
-      int its = 0;
-      if (rc == RS_OK) rc = rs_solve_refined(h, db, n, cols, dx, n, tol, 8, &its, rel.data(), stream);
-      col = 0;
-      for (auto& r : batch) {
-        double worst = 0;
-        if (rc == RS_OK &&
-            cudaMemcpy2DAsync(r->X, r->ldx * sb, (const char*)dx + col * n * sb, n * sb, n * sb, r->ncols,
-                              cudaMemcpyDeviceToHost, stream) != cudaSuccess) {
-          cudaGetLastError();
-          rc = RS_ERR_CUDA;
-        }
-        for (int c = 0; c < r->ncols; ++c, ++col) worst = std::max(worst, rel[col]);
-        r->relres = worst;
-        r->its = its;
-      }
-      if (cudaStreamSynchronize(stream) != cudaSuccess && rc == RS_OK) {
+    for (auto& r : cur) tol = std::min(tol, r->tol);
+    std::vector<double> rel(cur_cols, 0.0);
+    int its = 0;
+    if (rc == RS_OK && cudaStreamWaitEvent(stream, in_done[slot], 0) != cudaSuccess) {
+      cudaGetLastError();
+      rc = RS_ERR_CUDA;
+    }
+    if (rc == RS_OK) rc = rs_solve_refined(h, db[slot], n, cur_cols, dx[slot], n, tol, 8, &its, rel.data(), stream);
+    // columns back on the copy stream once the solve is done; completion from a callback
+    cudaEvent_t solved;
+    bool ok = cudaEventCreateWithFlags(&solved, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventRecord(solved, stream) == cudaSuccess && cudaStreamWaitEvent(cstream, solved, 0) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      if (rc == RS_OK) rc = RS_ERR_CUDA;
+    }
+    size_t col = 0;
+    for (auto& r : cur) {
+      double worst = 0;
+      if (rc == RS_OK &&
+          cudaMemcpy2DAsync(r->X, r->ldx * sb, (const char*)dx[slot] + col * n * sb, n * sb, n * sb, r->ncols,
+                            cudaMemcpyDeviceToHost, cstream) != cudaSuccess) {
         cudaGetLastError();
         rc = RS_ERR_CUDA;
       }
+      for (int c = 0; c < r->ncols; ++c, ++col) worst = std::max(worst, rel[col]);
+      r->relres = worst;
+      r->its = its;
     }
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      for (auto& r : batch) complete(s, r, rc);
-      s->batches += 1;
-      s->batch_cols += cols;
+    cudaEventRecord(out_done[slot], cstream);
+    Finished* f = new Finished{s, cur, rc, cur_cols};
+    if (cudaLaunchHostFunc(cstream, finish_batch, f) != cudaSuccess) {   // complete here instead
+      cudaGetLastError();
+      cudaStreamSynchronize(cstream);
+      finish_batch(f);
     }
-    s->cv_done.notify_all();
+    if (ok) cudaEventDestroy(solved);   // released once the recorded work completes
+    cur.swap(next);
+    cur_cols = next_cols;
+    staged = next_staged;
+    slot ^= 1;
   }
 }
 
@@ -201,7 +272,8 @@ int add_worker(Server* s, rs_handle h, bool owned, int* id_out) {
   RS_TRY(rs_stats(h, &st));
   w->n = st.n;
   w->cplx = static_cast<rs::Handle*>(reinterpret_cast<rs::Handle*>(h))->cplx;
-  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&w->cstream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     return rs::fail(RS_ERR_CUDA, "rs_server: stream creation failed");
   }
@@ -397,9 +469,15 @@ int rs_server_destroy(rs_server s) {
     if (w->th.joinable()) w->th.join();
   if (s->builder.joinable()) s->builder.join();
   for (auto& w : s->workers) {
+    if (w->cstream) cudaStreamSynchronize(w->cstream);   // last columns back and callbacks run
     if (w->stream) cudaStreamDestroy(w->stream);
-    if (w->db) cudaFree(w->db);
-    if (w->dx) cudaFree(w->dx);
+    if (w->cstream) cudaStreamDestroy(w->cstream);
+    for (int i = 0; i < 2; ++i) {
+      if (w->db[i]) cudaFree(w->db[i]);
+      if (w->dx[i]) cudaFree(w->dx[i]);
+      if (w->in_done[i]) cudaEventDestroy(w->in_done[i]);
+      if (w->out_done[i]) cudaEventDestroy(w->out_done[i]);
+    }
     if (w->owned) rs_free(w->h);
   }
   delete s;

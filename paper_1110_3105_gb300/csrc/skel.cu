@@ -612,9 +612,10 @@ __global__ void __launch_bounds__(BI_NT) k_bbid_fill(IdArgs a, BigId g, S* Mws, 
   }
 }
 
-// One pivot step.  With Ms (cooperative launch) the CTA's own columns are
-// also kept in shared memory, [BI_CB][m]: read from there, written to both.
-template <class S>
+// One pivot step; each CTA owns CB physical columns of one box.  With Ms
+// (cooperative launch) the CTA's own columns are also kept in shared memory,
+// [CB][m]: read from there, written to both.
+template <class S, int CB>
 __device__ void bbid_body(const IdArgs& a, const BigId& g, S* Mws, int j, int ncb, int* lperm, S* Ms) {
   extern __shared__ __align__(16) unsigned char bi_smem[];
   S* u = reinterpret_cast<S*>(bi_smem);                  // mmax entries
@@ -631,7 +632,7 @@ __device__ void bbid_body(const IdArgs& a, const BigId& g, S* Mws, int j, int nc
   if (threadIdx.x == 0) s_kk = __ldcg(g.kk + b);
   __syncthreads();
   if (j >= kmax || s_kk < kmax) return;   // past the rank or already stopped
-  if (cb * BI_CB >= n) return;
+  if (cb * CB >= n) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t no = g.noff[b];
   const int* map_in = (j & 1) ? g.map1 + no : g.map0 + no;
@@ -698,16 +699,16 @@ __device__ void bbid_body(const IdArgs& a, const BigId& g, S* Mws, int j, int nc
   const double f = 1.0 / (rjj * (rjj + aa));
   __syncthreads();
   // columns owned by this CTA that are still unpivoted (position > j)
-  __shared__ int posof[BI_CB];
-  for (int cl = tid; cl < BI_CB; cl += BI_NT) posof[cl] = -1;
+  __shared__ int posof[CB];
+  for (int cl = tid; cl < CB; cl += BI_NT) posof[cl] = -1;
   __syncthreads();
   for (int q = j + tid; q < n; q += BI_NT) {
     int c = mp[q];
-    if (c >= cb * BI_CB && c < cb * BI_CB + BI_CB) posof[c - cb * BI_CB] = q;
+    if (c >= cb * CB && c < cb * CB + CB) posof[c - cb * CB] = q;
   }
   __syncthreads();
-  for (int cl = warp; cl < BI_CB; cl += BI_NT / 32) {
-    const int c = cb * BI_CB + cl;
+  for (int cl = warp; cl < CB; cl += BI_NT / 32) {
+    const int c = cb * CB + cl;
     const int q = posof[cl];
     if (c >= n || q < 0) continue;
     S* col = Mws + g.moff[b] + (size_t)c * m;
@@ -735,29 +736,29 @@ __device__ void bbid_body(const IdArgs& a, const BigId& g, S* Mws, int j, int nc
 
 template <class S>
 __global__ void __launch_bounds__(BI_NT) k_bbid_step(IdArgs a, BigId g, S* Mws, int j, int ncb, int* lperm) {
-  bbid_body<S>(a, g, Mws, j, ncb, lperm, nullptr);
+  bbid_body<S, BI_CB>(a, g, Mws, j, ncb, lperm, nullptr);
 }
 
 // All pivot steps of a level in one cooperative launch: a grid barrier
 // between steps, and an exit once every box has found its rank.
-template <class S>
+template <class S, int CB>
 __global__ void __launch_bounds__(BI_NT) k_bbid_coop(IdArgs a, BigId g, S* Mws, int nsteps, int ncb, int nb,
                                                      int* lperm, GridBar gb) {
   __shared__ int s_any;
   extern __shared__ __align__(16) unsigned char bi_smem[];
-  // after u[mmax] | mp[nmax]: the CTA's own columns [BI_CB][m]
+  // after u[mmax] | mp[nmax]: the CTA's own columns [CB][m]
   const size_t head = ((sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax) + 15) & ~(size_t)15;
   S* Ms = reinterpret_cast<S*>(bi_smem + head);
   {
     const int b = blockIdx.x / ncb, cb = blockIdx.x % ncb;
     const int n = a.n[b], m = g.m[b];
-    const int nc = max(0, min(n, cb * BI_CB + BI_CB) - cb * BI_CB);
-    const S* src = Mws + g.moff[b] + (size_t)cb * BI_CB * m;
+    const int nc = max(0, min(n, cb * CB + CB) - cb * CB);
+    const S* src = Mws + g.moff[b] + (size_t)cb * CB * m;
     for (int e = threadIdx.x; e < nc * m; e += BI_NT) Ms[e] = src[e];
     __syncthreads();
   }
   for (int j = 0; j < nsteps; ++j) {
-    bbid_body<S>(a, g, Mws, j, ncb, lperm, Ms);
+    bbid_body<S, CB>(a, g, Mws, j, ncb, lperm, Ms);
     if (!grid_sync(gb, (unsigned int)(j + 1) * gridDim.x)) return;
     if (threadIdx.x == 0) {
       int any = 0;
@@ -889,7 +890,24 @@ struct FaArgs {
   const int64_t* loff;
   const int64_t* lamoff;
   int* bad;
+  float* fu32;            // forward-operator rows [D ; P] (real kernels; null otherwise)
+  dfloat* fudf;
 };
+
+// The forward operator's D block shares the assembled block's entries: the
+// same at the leaves; above, zero inside one child's block (where the
+// assembled block holds the child's Lambda).  Written while assembling, as
+// float and double-float, into rows 0..n-1 of FU ((n+k) x n at uoff).
+template <class S>
+__device__ __forceinline__ void emit_fwd(const FaArgs& a, int b, int n, int k, int r, int c, S v, bool same_child) {
+  if constexpr (std::is_same<S, double>::value) {
+    if (!a.fu32) return;
+    const double f = (a.leaf_level || !same_child) ? v : 0.0;
+    const int64_t i = a.uoff[b] + r + (int64_t)c * (n + k);
+    a.fu32[i] = f64_to_f32_rn(f);
+    a.fudf[i] = f64_to_df(f);
+  }
+}
 
 template <class S, int NT>
 __global__ void __launch_bounds__(NT) k_factor(FaArgs a, const S* Tpool, const S* cLam, S* ws, S* Upool,
@@ -924,6 +942,7 @@ __global__ void __launch_bounds__(NT) k_factor(FaArgs a, const S* Tpool, const S
     }
     Aug[r + (size_t)c * n] = v;
     Aug[r + (size_t)(n + c) * n] = (r == c) ? S(1.0) : S(0.0);
+    emit_fwd<S>(a, b, n, k, r, c, v, !a.leaf_level && a.owner[off + r] == a.owner[off + c]);
   }
   __syncthreads();
   gauss_jordan<S, NT>(Aug, n, mult, a.bad);
@@ -1081,6 +1100,7 @@ __global__ void __launch_bounds__(NT) k_factor_smem(FaArgs a, const S* Tpool, co
       }
     }
     Dv[e] = v;
+    emit_fwd<S>(a, b, n, k, r, c, v, !a.leaf_level && a.owner[off + r] == a.owner[off + c]);
   }
   __syncthreads();
   gj_inplace<S, NT>(Dv, n, mult, piv, a.bad);    // Dv = D^-1
@@ -1181,6 +1201,7 @@ __global__ void k_bb_assemble(FaArgs a, BigArgs g, const S* cLam, S* ws, int max
     }
     A[r + (size_t)c * n] = v;
     if (c == 0) buf[r] = v;
+    emit_fwd<S>(a, b, n, k, r, c, v, !a.leaf_level && a.owner[off + r] == a.owner[off + c]);
   }
 }
 
@@ -1500,14 +1521,12 @@ double factor_flops(double n, double k) {
   return 3.0 * n * n * n + 2.0 * n * k * nr + 2.0 * k * k * nr + 3.0 * k * k * k + 4.0 * n * k * k +
          2.0 * n * n * k;
 }
-// Flops of the column-pivoted QR of an m x n block stopped at rank k:
-// norms (2 per entry) and the reflector update (4 per entry) of every step,
-// the final norm pass, and T = R11^-1 R12 by back substitution.
+// Algorithmic flops of the column-pivoted QR of an m x n block stopped at
+// rank k (Householder QR with downdated norms: 4mnk - 2k^2(m + n) + 4k^3/3)
+// and of T = R11^-1 R12 by back substitution (k^2 (n - k)).  The m n kernel
+// evaluations of the fill are not counted as flops.
 double id_flops(double m, double n, double k) {
-  double f = 0.0;
-  for (int j = 0; j < (int)k; ++j) f += 2.0 * (m - j) * (n - j) + 4.0 * (m - j) * (n - j - 1);
-  if (k < std::min(m, n)) f += 2.0 * (m - k) * (n - k);
-  return f + k * k * (n - k);
+  return 4.0 * m * n * k - 2.0 * k * k * (m + n) + 4.0 * k * k * k / 3.0 + k * k * (n - k);
 }
 
 template <class T>
@@ -1540,6 +1559,21 @@ Pts make_pts(const Handle* h) {
   p.y = h->pts + h->N;
   p.z = h->dim == 3 ? h->pts + 2 * h->N : nullptr;
   return p;
+}
+
+// Largest dynamic shared memory a CTA may opt into (minus room for the
+// kernels' static shared variables).
+int max_dyn_smem() {
+  static const int v = [] {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 200 * 1024;
+    }
+    return optin - 4096;
+  }();
+  return v;
 }
 
 // Whether `grid` CTAs of `kern` can all be resident at once (the condition
@@ -1601,21 +1635,33 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
   const int ncb = div_up(maxn, BI_CB);
   const size_t id_smem = sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax;
   RS_CUDA(cudaFuncSetAttribute(k_bbid_step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)id_smem));
-  const size_t co_smem = ((id_smem + 15) & ~(size_t)15) + sizeof(S) * (size_t)BI_CB * a.mmax;
-  const bool co_ok = co_smem <= 200 * 1024;
-  if (co_ok)
-    RS_CUDA(cudaFuncSetAttribute(k_bbid_coop<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)co_smem));
-  if (co_ok && coop_fits((const void*)k_bbid_coop<S>, nb * ncb, BI_NT, co_smem)) {
-    // every pivot step in one cooperative launch
+  // cooperative launch: CB = 8, 4 or 2 columns per CTA, the widest whose
+  // column cache fits in shared memory and whose grid fits on the GPU at once
+  bool coop_done = false;
+  auto try_coop = [&](auto cbc) -> int {
+    constexpr int CB = decltype(cbc)::value;
+    if (coop_done) return RS_OK;
+    const int ncbc = div_up(maxn, CB);
+    const size_t co_smem = ((id_smem + 15) & ~(size_t)15) + sizeof(S) * (size_t)CB * a.mmax;
+    if (co_smem > (size_t)max_dyn_smem()) return RS_OK;
+    RS_CUDA(cudaFuncSetAttribute(k_bbid_coop<S, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)co_smem));
+    if (!coop_fits((const void*)k_bbid_coop<S, CB>, nb * ncbc, BI_NT, co_smem)) return RS_OK;
     GridBar gb{};
     RS_TRY(make_bar(h, &gb, st));
-    int nsteps = maxkmax, ncbv = ncb, nbv = nb;
+    int nsteps = maxkmax, ncbv = ncbc, nbv = nb;
     int* lp = a.lperm;
     void* args[] = {&a, &g, &Mws, &nsteps, &ncbv, &nbv, &lp, &gb};
-    RS_CUDA(cudaLaunchCooperativeKernel((const void*)k_bbid_coop<S>, dim3(nb * ncb), dim3(BI_NT), args, co_smem, st));
+    RS_CUDA(cudaLaunchCooperativeKernel((const void*)k_bbid_coop<S, CB>, dim3(nb * ncbc), dim3(BI_NT), args, co_smem,
+                                        st));
     RS_CHECK_LAUNCH();
     RS_CUDA(cudaFreeAsync(gb.count, st));
-  } else {
+    coop_done = true;
+    return RS_OK;
+  };
+  RS_TRY(try_coop(std::integral_constant<int, 8>{}));
+  RS_TRY(try_coop(std::integral_constant<int, 4>{}));
+  RS_TRY(try_coop(std::integral_constant<int, 2>{}));
+  if (!coop_done) {
     // one launch per step; every 8 steps, stop early once every box of the
     // level has found its rank
     int* d_active = nullptr;
@@ -1684,7 +1730,7 @@ template <class S, class Dims>
 int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int ncb, size_t smem, int* bad,
                  cudaStream_t st) {
   const size_t csmem = sizeof(S) * (size_t)(BB_CB + 1) * nsteps;   // own columns + pivot column (m <= nsteps)
-  const bool co_ok = csmem <= 200 * 1024;
+  const bool co_ok = csmem <= (size_t)max_dyn_smem();
   if (co_ok)
     RS_CUDA(cudaFuncSetAttribute(k_bb_gj_coop<S, Dims>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
   if (co_ok && coop_fits((const void*)k_bb_gj_coop<S, Dims>, nb * ncb, BB_NT, csmem)) {
@@ -1793,12 +1839,12 @@ int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t 
   }
   if (is_cplx<S>::value) fl0 *= 4.0;
   if (smem_path) {
+    const S* cL = child ? (const S*)child->Lam : nullptr;
+    prof_begin(P_FACTOR, st);
     RS_CUDA(cudaFuncSetAttribute(k_factor_smem<S, FA_SM_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm_need));
-    prof_begin(P_FACTOR, st);
-    k_factor_smem<S, FA_SM_NT><<<lv.nbox, FA_SM_NT, sm_need, st>>>(a, (const S*)lv.T,
-                                                                    child ? (const S*)child->Lam : nullptr,
-                                                                    (S*)lv.U, (S*)lv.Lf, (S*)lv.Lam);
+    k_factor_smem<S, FA_SM_NT><<<lv.nbox, FA_SM_NT, sm_need, st>>>(a, (const S*)lv.T, cL, (S*)lv.U, (S*)lv.Lf,
+                                                                    (S*)lv.Lam);
     RS_CHECK_LAUNCH();
     prof_end(P_FACTOR, st, by0, fl0);
     return RS_OK;
@@ -1857,6 +1903,12 @@ int alloc_factors(Handle* h, Level& lv, cudaStream_t st) {
   RS_TRY(dalloc(h, &lv.U, sb * std::max<int64_t>(1, us)));
   RS_TRY(dalloc(h, &lv.Lf, sb * std::max<int64_t>(1, ls)));
   RS_TRY(dalloc(h, &lv.Lam, sb * std::max<int64_t>(1, lams)));
+  if (!h->cplx) {   // forward-operator factors of the refinement residual (fwd2.cu)
+    RS_TRY(dalloc(h, &lv.FU32, sizeof(float) * std::max<int64_t>(1, us)));
+    RS_TRY(dalloc(h, &lv.FUdf, sizeof(dfloat) * std::max<int64_t>(1, us)));
+    RS_TRY(dalloc(h, &lv.FL32, sizeof(float) * std::max<int64_t>(1, ls)));
+    RS_TRY(dalloc(h, &lv.FLdf, sizeof(dfloat) * std::max<int64_t>(1, ls)));
+  }
   h->factor_scalars += us + ls;
   return RS_OK;
 }
@@ -1978,6 +2030,8 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st) {
   f.loff = lv.loff;
   f.lamoff = lv.lamoff;
   f.bad = h->status;
+  f.fu32 = (float*)lv.FU32;
+  f.fudf = (dfloat*)lv.FUdf;
   if (h->cplx) RS_TRY(run_factor<c128>(h, lv, f, child, st));
   else RS_TRY(run_factor<double>(h, lv, f, child, st));
   RS_TRY(check_bad(h, st, "factorization"));
@@ -2042,6 +2096,8 @@ int factor_root(Handle* h, cudaStream_t st) {
   f.loff = lv.loff;
   f.lamoff = lv.lamoff;
   f.bad = h->status;
+  f.fu32 = (float*)lv.FU32;
+  f.fudf = (dfloat*)lv.FUdf;
   if (h->cplx) RS_TRY(run_factor<c128>(h, lv, f, child, st));
   else RS_TRY(run_factor<double>(h, lv, f, child, st));
   RS_TRY(check_bad(h, st, "root factorization"));

@@ -25,6 +25,9 @@
 // result stores are coalesced along the rows.  Leaf tiles read B and write X
 // in the caller's order through the tree permutation.
 #include <algorithm>
+#include <map>
+#include <tuple>
+#include <mutex>
 #include <cstdio>
 #include <cstdlib>
 #include <cuda/atomic>
@@ -263,7 +266,9 @@ __device__ __forceinline__ void chunk_fma(const S* col, size_t ld, int qn, const
   }
 }
 
-template <class S, class SIO, int CT>
+// TR: record the tile timeline (a separate instantiation: the timer reads
+// constrain instruction scheduling even when not taken).
+template <class S, class SIO, int CT, bool TR>
 __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, int64_t ldb, SIO* X, int64_t ldx,
                                                      const SIO* sub, int R, int epoch, int* flag) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -275,7 +280,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= p.ntiles) break;
     if (*(volatile int*)p.dflag) return;   // another warp gave up waiting: leave too
-    if (p.trace && lane == 0) p.trace[3 * (size_t)t] = gtime();
+    if (TR && lane == 0) p.trace[3 * (size_t)t] = gtime();
     const Tile tl = p.tiles[t];
     const int g = tl.g;
     const int d = p.bt.depth[g];
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
     if (tl.kind != T_DOWN) {
       // ---- up / root tile: rows of U b, U = [calD ; calR] ((n+k) x n)
       if (p.bt.up_need[g] > 0 && !wait_at_least(&p.up_cnt[g], epoch * p.bt.up_need[g], flag, p.dflag)) return;
-      if (p.trace && lane == 0) p.trace[3 * (size_t)t + 1] = gtime();
+      if (TR && lane == 0) p.trace[3 * (size_t)t + 1] = gtime();
       const int rows = n + k;
       const int r = tl.r0 + lane;
       const S* Ub = p.U[d] + p.bt.uoff[g];
@@ -344,12 +349,12 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
       }
       if (tl.kind == T_ROOT) signal(&p.dn_cnt[g]);
       else signal(&p.up_cnt[p.bt.parent[g]]);
-      if (p.trace && lane == 0) p.trace[3 * (size_t)t + 2] = gtime();
+      if (TR && lane == 0) p.trace[3 * (size_t)t + 2] = gtime();
     } else {
       // ---- down tile: rows of u + calL x_parent (n x k)
       const int par = p.bt.parent[g];
       if (!wait_at_least(&p.dn_cnt[par], epoch * p.bt.dn_need[par], flag, p.dflag)) return;
-      if (p.trace && lane == 0) p.trace[3 * (size_t)t + 1] = gtime();
+      if (TR && lane == 0) p.trace[3 * (size_t)t + 1] = gtime();
       const int r = tl.r0 + lane;
       const S* Lb = p.Lf[d] + p.bt.loff[g];
       const int64_t ldd = p.ldv[d], ldp = p.ldv[d - 1];
@@ -386,7 +391,7 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
         }
       }
       signal(&p.dn_cnt[g]);
-      if (p.trace && lane == 0) p.trace[3 * (size_t)t + 2] = gtime();
+      if (TR && lane == 0) p.trace[3 * (size_t)t + 2] = gtime();
     }
   }
 }
@@ -646,7 +651,9 @@ struct PersPlan {
   int64_t* ldv = nullptr;    // per depth ntot (leading dimension of v and u)
   int* flag_host = nullptr;  // mapped pinned
   int* flag_dev = nullptr;
-  int grid = 0;
+  int grid = 0;              // CTAs of the launch (all resident)
+  int occ = 0, nsm = 0;      // resident CTAs per SM at full occupancy, SM count
+  int cps = 0;               // CTAs per SM of the current grid (0: full occupancy)
   int work_gen = -1;         // generation of the work buffers captured in ptrs
   unsigned long long* trace = nullptr;   // tile timeline of the last profiled launch (3 per tile)
   bool traced = false;
@@ -660,10 +667,31 @@ struct PersCache {
   std::vector<PersPlan*> plans;
 };
 
-// Tile of the CTA kernel for R right-hand sides: rows * 1000 + columns (0:
-// the warp kernel, which suits few columns).  RS_SOLVE_TILE overrides it
-// ("TMxTN" with TM, TN in {32, 64}; "0" forces the warp kernel).
-int cta_tile(int R) {
+// Launch configurations chosen by the autotuner, shared by every handle of
+// the process: (mode, column bucket, complex, N) -> tile * 16 + cps, the
+// bucket being the column count rounded down to a power of two (a serving
+// loop's batches of varying width share one tuning).
+struct TuneKey {
+  int mode, R, cplx;
+  int64_t N;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(mode, R, cplx, N) < std::tie(o.mode, o.R, o.cplx, o.N);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+
+// Candidate tiles of the CTA kernel for R right-hand sides, as rows * 1000 +
+// columns (0: the warp kernel, which suits few columns).  The first solve of
+// a plan with several candidates times each and keeps the fastest (the
+// summation order inside a tile is the same for every shape, so so are the
+// results).  RS_SOLVE_TILE fixes the choice ("TMxTN" with TM, TN in
+// {32, 64}; "0" forces the warp kernel).
+// A launch configuration is tile * 16 + cps, cps the CTAs per SM (0: as
+// many as fit).  Few columns use the warp kernel, whose dependency chain is
+// the whole cost: fewer resident warps poll the dependency counters less
+// and can shorten it, so its candidates vary cps.
+std::vector<int> launch_configs(int R) {
   static const int forced = [] {
     const char* e = getenv("RS_SOLVE_TILE");
     if (!e) return -1;
@@ -671,10 +699,11 @@ int cta_tile(int R) {
     if (sscanf(e, "%dx%d", &tm, &tn) == 2 && (tm == 32 || tm == 64) && (tn == 32 || tn == 64)) return tm * 1000 + tn;
     return 0;
   }();
-  if (forced == 0) return 0;
-  if (forced > 0) return R < 16 ? 0 : forced;
-  if (R < 32) return 0;
-  return R >= 64 ? 32064 : 32032;
+  if (forced == 0) return {0 * 16 + 0};
+  if (forced > 0) return {(R < 16 ? 0 : forced) * 16};
+  if (R < 32) return {0 * 16 + 0, 0 * 16 + 3, 0 * 16 + 2};
+  if (R < 64) return {32032 * 16, 64032 * 16};
+  return {32064 * 16, 32032 * 16, 64064 * 16};
 }
 
 int ct_for(bool cplx, int prec, int R) {
@@ -698,15 +727,19 @@ int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X
   constexpr int TMv = TN ? TM : 32, TNv = TN ? TN : 32;
   const size_t smem = TN ? CtaSmem<S, TMv, TNv>::bytes : sizeof(S) * 32 * CT * P_WARPS;
   const int nt = TN ? C_NT : P_NT;
-  const void* fn = TN ? (const void*)k_solve_cta<S, SIO, TMv, TNv> : (const void*)k_solve_pers<S, SIO, CT>;
+  const void* fn = TN ? (const void*)k_solve_cta<S, SIO, TMv, TNv> : (const void*)k_solve_pers<S, SIO, CT, false>;
   if (smem > 48 * 1024) RS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  if (P->grid == 0) {
-    int dev = 0, nsm = 0, occ = 0;
+  if (P->occ == 0) {
+    int dev = 0;
     RS_CUDA(cudaGetDevice(&dev));
-    RS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, smem));
+    RS_CUDA(cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, dev));
+    RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P->occ, fn, nt, smem));
+    P->occ = std::max(P->occ, 1);
+  }
+  {
     const int per_block = TN ? 1 : P_WARPS;   // tiles a block works on at once
-    P->grid = std::max(1, std::min(nsm * std::max(occ, 1), div_up(P->ntiles, per_block)));
+    const int cps = P->cps > 0 ? std::min(P->cps, P->occ) : P->occ;
+    P->grid = std::max(1, std::min(P->nsm * cps, div_up(P->ntiles, per_block)));
   }
   if (++P->epoch > (1 << 20) || P->dirty) {   // counters restart (overflow guard, or after a timeout)
     RS_CUDA(cudaMemsetAsync(P->counters, 0, sizeof(int) * (2 + 2 * (size_t)P->nbox), st));
@@ -734,7 +767,7 @@ int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X
   pl.dn_cnt = P->counters + 2 + P->nbox;
   pl.trace = nullptr;
   P->traced = false;
-  if (prof_on()) {   // tile timeline for rs_profile_tiles
+  if (prof_tiles_on()) {   // tile timeline for rs_profile_tiles
     if (!P->trace) {
       RS_CUDA(cudaMalloc((void**)&P->trace, sizeof(unsigned long long) * 3 * (size_t)P->ntiles));
       P->mem.push_back(P->trace);
@@ -744,10 +777,15 @@ int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X
   }
   *P->flag_host = 0;
   prof_begin(prec_cat(P->prec), st);
-  if constexpr (TN > 0)
+  if constexpr (TN > 0) {
     k_solve_cta<S, SIO, TMv, TNv><<<P->grid, C_NT, smem, st>>>(pl, B, ldb, X, ldx, sub, wait_epoch, P->flag_dev);
-  else
-    k_solve_pers<S, SIO, CT><<<P->grid, P_NT, smem, st>>>(pl, B, ldb, X, ldx, sub, R, wait_epoch, P->flag_dev);
+  } else {
+    if (pl.trace)
+      k_solve_pers<S, SIO, CT, true><<<P->grid, P_NT, smem, st>>>(pl, B, ldb, X, ldx, sub, R, wait_epoch, P->flag_dev);
+    else
+      k_solve_pers<S, SIO, CT, false><<<P->grid, P_NT, smem, st>>>(pl, B, ldb, X, ldx, sub, R, wait_epoch,
+                                                                   P->flag_dev);
+  }
   RS_CHECK_LAUNCH();
   double sS = sizeof(S), fac = 0.0;
   for (auto& lv : h->lv) fac += (double)lv.usz + (double)lv.lsz;
@@ -799,13 +837,13 @@ static int refresh_ptrs(Handle* h, PersPlan* P, cudaStream_t st) {
   return RS_OK;
 }
 
-// Tile list and counters for (precision, R); built once per handle.
-static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out) {
+// Tile list and counters for (precision, R, tile); built once per handle.
+static int get_plan(Handle* h, int prec, int R, int tile, cudaStream_t st, PersPlan** out) {
   if (!h->pers) h->pers = new PersCache();
   PersCache* c = (PersCache*)h->pers;
   RS_TRY(ensure_work_pub(h, prec, R, st));
   for (PersPlan* P : c->plans)
-    if (P->prec == prec && P->R == R) {
+    if (P->prec == prec && P->R == R && (P->TN ? P->TM * 1000 + P->TN : 0) == tile) {
       if (P->work_gen != h->work[prec].gen) RS_TRY(refresh_ptrs(h, P, st));
       *out = P;
       return RS_OK;
@@ -815,7 +853,6 @@ static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out)
   P->prec = prec;
   P->R = R;
   P->CT = ct_for(h->cplx, prec, R);
-  const int tile = cta_tile(R);
   P->TN = tile % 1000;
   P->TM = tile ? tile / 1000 : 32;
   const int L = h->L;
@@ -914,10 +951,8 @@ static int get_plan(Handle* h, int prec, int R, cudaStream_t st, PersPlan** out)
 }
 
 template <class S, class SIO>
-static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO* X, int64_t ldx, cudaStream_t st,
-                     const SIO* sub = nullptr) {
-  PersPlan* P = nullptr;
-  RS_TRY(get_plan(h, prec, R, st, &P));
+static int launch_plan(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X, int64_t ldx,
+                       const SIO* sub, cudaStream_t st) {
   const int tile = P->TN ? P->TM * 1000 + P->TN : 0;
   switch (tile) {
     case 32032: RS_TRY((launch_pers<S, SIO, 1, 32, 32>(h, P, B, ldb, R, X, ldx, sub, st))); break;
@@ -937,6 +972,70 @@ static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO*
   }
   h->pers_last = P;
   return RS_OK;
+}
+
+template <class S, class SIO>
+static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO* X, int64_t ldx, cudaStream_t st,
+                     const SIO* sub = nullptr) {
+  int bucket = 1;
+  while (bucket * 2 <= R) bucket *= 2;
+  const TuneKey key{prec, bucket, h->cplx ? 1 : 0, h->N};
+  int known = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) known = it->second;
+  }
+  const std::vector<int> cand = launch_configs(R);
+  PersPlan* P = nullptr;
+  // Repeating the launch is only harmless when the output overwrites neither
+  // input (in-place solves and the in-place residual update are not tuned;
+  // the update borrows the FP32 solve's choice).
+  const bool aliased = (const void*)X == (const void*)B || (sub && (const void*)X == (const void*)sub);
+  if (known < 0 && aliased && prec == MODE_FWD_F32) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(TuneKey{RS_PREC_FP32, bucket, key.cplx, key.N});
+    if (it != g_tuned.end()) known = it->second;
+  }
+  if (known >= 0 || cand.size() == 1 || aliased) {
+    const int cfg = known >= 0 ? known : cand[0];
+    RS_TRY(get_plan(h, prec, R, cfg / 16, st, &P));
+    P->cps = cfg % 16;
+    return launch_plan<S, SIO>(h, P, B, ldb, R, X, ldx, sub, st);
+  }
+  // autotune: time the second of two launches of each candidate (the first
+  // pays one-time costs); the outputs agree bit for bit
+  cudaEvent_t e0, e1;
+  RS_CUDA(cudaEventCreate(&e0));
+  RS_CUDA(cudaEventCreate(&e1));
+  int best = cand[0];
+  float best_ms = 1e30f;
+  int rc = RS_OK;
+  for (int cfg : cand) {
+    if ((rc = get_plan(h, prec, R, cfg / 16, st, &P)) != RS_OK) break;
+    P->cps = cfg % 16;
+    if ((rc = launch_plan<S, SIO>(h, P, B, ldb, R, X, ldx, sub, st)) != RS_OK) break;
+    cudaEventRecord(e0, st);
+    if ((rc = launch_plan<S, SIO>(h, P, B, ldb, R, X, ldx, sub, st)) != RS_OK) break;
+    cudaEventRecord(e1, st);
+    float ms = 0;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(RS_ERR_CUDA, "solve: autotuning timing failed");
+      break;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cfg;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == RS_OK) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = best;
+  }
+  return rc;
 }
 
 int solve_pers_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, void* d_X, int64_t ldx,
@@ -968,8 +1067,10 @@ int tile_trace(Handle* h, int prec, int R, int64_t cap, int* kind, int* depth, i
   PersPlan* P = nullptr;
   if (c)
     for (PersPlan* q : c->plans)
-      if (q->prec == prec && q->R == R) P = q;
-  if (!P || !P->traced) return fail(RS_ERR_STATE, "rs_profile_tiles: no profiled launch of this plan");
+      if (q->prec == prec && q->R == R && q->traced) P = q;
+  PersPlan* last = (PersPlan*)h->pers_last;
+  if (last && last->prec == prec && last->R == R && last->traced) P = last;
+  if (!P) return fail(RS_ERR_STATE, "rs_profile_tiles: no profiled launch of this plan");
   std::vector<unsigned long long> tr(3 * (size_t)P->ntiles);
   RS_CUDA(cudaDeviceSynchronize());
   RS_CUDA(cudaMemcpy(tr.data(), P->trace, sizeof(unsigned long long) * tr.size(), cudaMemcpyDeviceToHost));

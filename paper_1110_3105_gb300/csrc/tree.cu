@@ -252,6 +252,31 @@ __global__ void k_permute_points(const double* pts, const int* perm, int64_t n, 
   for (int d = 0; d < dim; ++d) out[d * n + i] = pts[src * dim + d];
 }
 
+// Box count of one depth: last exclusive prefix + last flag.
+__global__ void k_count(const int* flags, const int64_t* excl, int n, int64_t* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = excl[n - 1] + flags[n - 1];
+}
+
+// Pinned host staging for the device -> host copies of a build (one per
+// host thread, grown as needed and kept).
+struct PinnedStage {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+static thread_local PinnedStage tl_stage;
+static int stage_reserve(size_t bytes, void** out) {
+  if (bytes > tl_stage.cap) {
+    if (tl_stage.p) cudaFreeHost(tl_stage.p);
+    tl_stage.p = nullptr;
+    tl_stage.cap = 0;
+    const size_t want = std::max<size_t>(bytes, 4u << 20);
+    RS_CUDA(cudaMallocHost(&tl_stage.p, want));
+    tl_stage.cap = want;
+  }
+  *out = tl_stage.p;
+  return RS_OK;
+}
+
 __global__ void k_iota(int* a, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = i;
@@ -296,20 +321,32 @@ int build_tree(Handle* h, const double* d_pts_in, cudaStream_t st) {
   int* svals;
   RS_TRY(dalloc_t(h, &skeys, n));
   RS_TRY(dalloc_t(h, &svals, n));
-  RS_CUDA(cudaMemcpyAsync(skeys, keys, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
-  RS_CUDA(cudaMemcpyAsync(svals, vals, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
-  RS_TRY(radix_sort_pairs(skeys, svals, keys2, vals2, n, dim * nbits, st));
+  // Depth from the occupancy of every depth's boxes: sort by the top key bits
+  // first (the depths whose prefixes they hold), all bits only if no depth
+  // up to there is fine enough.
   int* maxocc;
   RS_TRY(dalloc_t(h, &maxocc, nbits + 1));
-  RS_CUDA(cudaMemsetAsync(maxocc, 0, sizeof(int) * (nbits + 1), st));
-  k_level_occupancy<<<nb, NT, 0, st>>>(skeys, n, dim, nbits, maxocc);
-  RS_CHECK_LAUNCH();
   std::vector<int> occ(nbits + 1);
-  RS_CUDA(cudaMemcpyAsync(occ.data(), maxocc, sizeof(int) * (nbits + 1), cudaMemcpyDeviceToHost, st));
-  RS_CUDA(cudaStreamSynchronize(st));
   int L = -1;
-  for (int l = 0; l <= nbits; ++l)
-    if (occ[l] <= h->leaf) { L = l; break; }
+  const int top_levels = std::min(nbits, 32 / dim);
+  for (int pass = 0; pass < 2 && L < 0; ++pass) {
+    const int lv_top = pass == 0 ? top_levels : nbits;
+    if (pass == 1 && top_levels == nbits) break;
+    RS_CUDA(cudaMemcpyAsync(skeys, keys, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
+    RS_CUDA(cudaMemcpyAsync(svals, vals, sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+    if (lv_top < nbits) {
+      k_shift_keys<<<nb, NT, 0, st>>>(skeys, n, dim * (nbits - lv_top));
+      RS_CHECK_LAUNCH();
+    }
+    RS_TRY(radix_sort_pairs(skeys, svals, keys2, vals2, n, dim * lv_top, st));
+    RS_CUDA(cudaMemsetAsync(maxocc, 0, sizeof(int) * (nbits + 1), st));
+    k_level_occupancy<<<nb, NT, 0, st>>>(skeys, n, dim, lv_top, maxocc);
+    RS_CHECK_LAUNCH();
+    RS_CUDA(cudaMemcpyAsync(occ.data(), maxocc, sizeof(int) * (lv_top + 1), cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaStreamSynchronize(st));
+    for (int l = 0; l <= lv_top; ++l)
+      if (occ[l] <= h->leaf) { L = l; break; }
+  }
   if (L < 0) return fail(RS_ERR_ARG, "rs_build: more than leaf=%d coincident points", h->leaf);
   h->L = L;
 
@@ -323,20 +360,36 @@ int build_tree(Handle* h, const double* d_pts_in, cudaStream_t st) {
   k_permute_points<<<nb, NT, 0, st>>>(d_pts_in, vals, n, dim, h->pts);
   RS_CHECK_LAUNCH();
 
-  // box tables for every depth
+  // box tables for every depth: start flags and their scans for all depths,
+  // then one host read of the box counts
   h->lv.assign(L + 1, Level());
   int *flags, *pbox_prev = nullptr;
-  int64_t* excl;
-  RS_TRY(dalloc_t(h, &flags, n));
-  RS_TRY(dalloc_t(h, &excl, n));
+  int64_t *excl, *counts;
+  RS_TRY(dalloc_t(h, &flags, (size_t)n * (L + 1)));
+  RS_TRY(dalloc_t(h, &excl, (size_t)n * (L + 1)));
+  RS_TRY(dalloc_t(h, &counts, L + 1));
+  for (int l = 0; l <= L; ++l) {
+    k_box_flags<<<nb, NT, 0, st>>>(keys, n, dim * (L - l), flags + (size_t)l * n);
+    RS_CHECK_LAUNCH();
+    RS_TRY(scan_i32_to_i64(flags + (size_t)l * n, excl + (size_t)l * n, n, nullptr, st));
+    k_count<<<1, 32, 0, st>>>(flags + (size_t)l * n, excl + (size_t)l * n, n, counts + l);
+    RS_CHECK_LAUNCH();
+  }
+  std::vector<int64_t> nboxes(L + 1);
+  RS_CUDA(cudaMemcpyAsync(nboxes.data(), counts, sizeof(int64_t) * (L + 1), cudaMemcpyDeviceToHost, st));
+  RS_CUDA(cudaStreamSynchronize(st));
+  size_t host_ints = 0;
+  for (int l = 0; l <= L; ++l) host_ints += (size_t)nboxes[l] * 30;
+  void* pin = nullptr;
+  RS_TRY(stage_reserve(sizeof(int) * std::max<size_t>(1, host_ints), &pin));
+  int* hp = (int*)pin;
   for (int l = 0; l <= L; ++l) {
     Level& lv = h->lv[l];
     lv.depth = l;
     int sh = dim * (L - l);
-    k_box_flags<<<nb, NT, 0, st>>>(keys, n, sh, flags);
-    RS_CHECK_LAUNCH();
-    int64_t nbox = 0;
-    RS_TRY(scan_i32_to_i64(flags, excl, n, &nbox, st));
+    const int64_t nbox = nboxes[l];
+    const int* fl = flags + (size_t)l * n;
+    const int64_t* ex = excl + (size_t)l * n;
     lv.nbox = (int)nbox;
     int* pbox;
     RS_TRY(dalloc_t(h, &pbox, n));
@@ -348,7 +401,7 @@ int build_tree(Handle* h, const double* d_pts_in, cudaStream_t st) {
     RS_TRY(dalloc_t(h, &lv.coll, nbox * 27));
     RS_TRY(dalloc_t(h, &lv.coords, nbox * dim));
     RS_TRY(dalloc_t(h, &lv.keys, nbox));
-    k_box_begin<<<nb, NT, 0, st>>>(flags, excl, n, lv.begin, pbox);
+    k_box_begin<<<nb, NT, 0, st>>>(fl, ex, n, lv.begin, pbox);
     RS_CHECK_LAUNCH();
     int bb = div_up(nbox, NT);
     k_box_info<<<bb, NT, 0, st>>>(keys, lv.begin, (int)nbox, dim, sh, lv.keys, lv.coords, pbox_prev, lv.parent);
@@ -362,17 +415,24 @@ int build_tree(Handle* h, const double* d_pts_in, cudaStream_t st) {
     k_colleagues<<<bb, NT, 0, st>>>(lv.keys, lv.coords, (int)nbox, dim, l, lv.ncoll, lv.coll);
     RS_CHECK_LAUNCH();
     pbox_prev = pbox;
-    // host copies for sizing and inspection
-    lv.h_begin.resize(nbox);
-    lv.h_parent.resize(nbox);
-    lv.h_ncoll.resize(nbox);
-    lv.h_coll.resize((size_t)nbox * 27);
-    RS_CUDA(cudaMemcpyAsync(lv.h_begin.data(), lv.begin, sizeof(int) * nbox, cudaMemcpyDeviceToHost, st));
-    RS_CUDA(cudaMemcpyAsync(lv.h_parent.data(), lv.parent, sizeof(int) * nbox, cudaMemcpyDeviceToHost, st));
-    RS_CUDA(cudaMemcpyAsync(lv.h_ncoll.data(), lv.ncoll, sizeof(int) * nbox, cudaMemcpyDeviceToHost, st));
-    RS_CUDA(cudaMemcpyAsync(lv.h_coll.data(), lv.coll, sizeof(int) * nbox * 27, cudaMemcpyDeviceToHost, st));
+    // host copies for sizing and inspection, staged in pinned memory
+    RS_CUDA(cudaMemcpyAsync(hp, lv.begin, sizeof(int) * nbox, cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaMemcpyAsync(hp + nbox, lv.parent, sizeof(int) * nbox, cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaMemcpyAsync(hp + 2 * nbox, lv.ncoll, sizeof(int) * nbox, cudaMemcpyDeviceToHost, st));
+    RS_CUDA(cudaMemcpyAsync(hp + 3 * nbox, lv.coll, sizeof(int) * nbox * 27, cudaMemcpyDeviceToHost, st));
+    hp += 30 * nbox;
   }
   RS_CUDA(cudaStreamSynchronize(st));
+  hp = (int*)pin;
+  for (int l = 0; l <= L; ++l) {
+    Level& lv = h->lv[l];
+    const int64_t nbox = lv.nbox;
+    lv.h_begin.assign(hp, hp + nbox);
+    lv.h_parent.assign(hp + nbox, hp + 2 * nbox);
+    lv.h_ncoll.assign(hp + 2 * nbox, hp + 3 * nbox);
+    lv.h_coll.assign(hp + 3 * nbox, hp + 30 * nbox);
+    hp += 30 * nbox;
+  }
 
   // leaf active sets: identity
   Level& leaf = h->lv[L];
