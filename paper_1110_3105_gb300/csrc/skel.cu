@@ -24,6 +24,7 @@
 #include <cmath>
 #include <vector>
 
+#include <cooperative_groups.h>
 #include <cuda/atomic>
 #include <type_traits>
 
@@ -400,6 +401,12 @@ struct IdArgs {
   const int64_t* toff;
   int* kout;
   int* lperm;
+  // near-field blocks shared by colleague pairs (k_near_pairs): for box b's
+  // colleague slot s, the block G(I_j, I_b) starts at pair_base[27 b + s] of
+  // pairs, stored for the lower-numbered box of the pair (n_j x n_b
+  // column-major when j > b, its transpose when j < b); null: evaluate
+  const int64_t* pair_base;
+  const void* pairs;
   int smem_path;         // 1: M in shared memory
   int qr_df;             // 1: double-float QR (real kernels, rs_id_arith)
   int mmax, nmax;
@@ -413,14 +420,18 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
   const int n = a.n[b];
   const int m = a.mrows[b];
   const int64_t off = a.off[b];
-  // shared layout: [M (smem path)] | u[mmax] | nrm[2 nmax] | proxy xyz[3 nproxy] | piv[nmax] | rowid[mmax]
+  // shared layout: [M (smem path)] | u[mmax] | nrm[2 nmax] | proxy xyz[3 nproxy] | rbase[mmax] (int64) |
+  // piv[nmax] | rowid[mmax] | rstride[mmax]
   S* Ms = reinterpret_cast<S*>(smem);
   size_t msz = a.smem_path ? (size_t)a.mmax * a.nmax : 0;
   S* u = Ms + msz;
   double* nrm = reinterpret_cast<double*>(u + a.mmax);
   double* pxy = nrm + 2 * a.nmax;
-  int* piv = reinterpret_cast<int*>(pxy + 3 * a.geo.nproxy);
+  int64_t* rbase = reinterpret_cast<int64_t*>(pxy + 3 * a.geo.nproxy);
+  int* piv = reinterpret_cast<int*>(rbase + a.mmax);
   int* rowid = piv + a.nmax;
+  int* rstride = rowid + a.mmax;
+  const S* pairs = reinterpret_cast<const S*>(a.pairs);
   S* M = a.smem_path ? Ms : Mws + a.moff[b];
   const int ld = m;
   const int nc = a.ncoll[b];
@@ -440,7 +451,16 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
     int j = 0;
     while (cstart[j + 1] <= r) ++j;
     int c = a.coll[b * 27 + j];
-    rowid[r] = a.act[a.off[c] + (r - cstart[j])];
+    const int q = r - cstart[j];
+    rowid[r] = a.act[a.off[c] + q];
+    rstride[r] = 0;   // 0: evaluate the entry
+    if (pairs) {      // row q of colleague c in the shared block of the pair
+      const int64_t base = a.pair_base[b * 27 + j];
+      if (base >= 0) {
+        if (c > b) { rbase[r] = base + q; rstride[r] = a.n[c]; }
+        else { rbase[r] = base + (int64_t)q * n; rstride[r] = 1; }
+      }
+    }
   }
   __syncthreads();
 
@@ -455,7 +475,7 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
     int pc = a.act[off + c];
     S v;
     if (r < nnear) {
-      v = offdiag_entry<S>(a.kp, a.pts, rowid[r], pc);
+      v = rstride[r] ? pairs[rbase[r] + (int64_t)c * rstride[r]] : offdiag_entry<S>(a.kp, a.pts, rowid[r], pc);
     } else if (r < nnear + a.geo.nproxy) {
       v = green_at_s2<S>(a.kp, dist2_to(a.pts, pc, pxy + 3 * (r - nnear)));
     } else {
@@ -500,6 +520,24 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
   }
   for (int c = threadIdx.x; c < n; c += NT) a.lperm[off + c] = piv[c];
   if (threadIdx.x == 0) a.kout[b] = k;
+}
+
+// Near-field kernel blocks of one depth, once per colleague pair (i, j), i < j:
+// G(I_j, I_i) (n_j x n_i, column-major) at base[p]; the two boxes read it
+// directly and transposed (k_id), halving the near-field evaluations.
+template <class S>
+__global__ void k_near_pairs(KParams kp, Pts pts, const int* n, const int64_t* off, const int* act, const int* pi,
+                             const int* pj, const int64_t* base, S* out) {
+  const int p = blockIdx.x;
+  const int i = pi[p], j = pj[p];
+  const int ni = n[i], nj = n[j];
+  const int* ai = act + off[i];
+  const int* aj = act + off[j];
+  S* o = out + base[p];
+  for (int e = threadIdx.x; e < ni * nj; e += blockDim.x) {
+    const int a = e % nj, c = e / nj;
+    o[e] = offdiag_entry<S>(kp, pts, aj[a], ai[c]);
+  }
 }
 
 // ---------------------------------------------------------- big-box ID
@@ -1352,6 +1390,97 @@ __global__ void __launch_bounds__(BB_NT) k_bb_gj_coop(BigArgs g, S* ws, Dims dim
   for (int e = tid; e < nc * m; e += BB_NT) M[(size_t)c_beg * m + e] = Ms[e];
 }
 
+// All pivot steps of one box in one thread-block cluster: the cluster's CTAs
+// split the box's columns (cw each) and keep them in shared memory; per step
+// the owner of the pivot column finds the pivot row and publishes the
+// column's multipliers in its shared memory, one hardware cluster barrier
+// later every CTA reads them over distributed shared memory and updates its
+// own columns (the arithmetic of bb_gj_body).  The publication buffer
+// alternates between two halves so one barrier per step suffices.  Shared
+// layout per CTA: own columns [cw][m] | multipliers [m] | 2 x ([m] + inv, p).
+template <class S, class Dims>
+__global__ void __launch_bounds__(BB_NT) k_bb_gj_cluster(BigArgs g, S* ws, Dims dims, int nsteps, int cw, int* bad) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char bb_smem[];
+  __shared__ int s_p;
+  __shared__ double s_best;
+  __shared__ S newj[64];
+  const int crank = (int)cl.block_rank();
+  const int b = blockIdx.x / (int)cl.num_blocks();
+  int m;
+  S *M, *pb_in, *pb_out;
+  int* piv;
+  dims(ws, g, b, 0, m, M, pb_in, pb_out, piv);
+  const int c_beg = crank * cw, nc = max(0, min(m, c_beg + cw) - c_beg);
+  S* Ms = reinterpret_cast<S*>(bb_smem);     // own columns
+  S* ml = Ms + (size_t)cw * nsteps;          // this step's multipliers (local copy)
+  S* pub = ml + nsteps;                      // 2 halves of nsteps + 2 scalars (inv, p)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int e = tid; e < nc * m; e += BB_NT) Ms[e] = M[(size_t)c_beg * m + e];
+  __syncthreads();
+  bool failed = false;   // uniform over the cluster (every CTA reads the same published pivot)
+  for (int j = 0; j < m; ++j) {
+    const int owner = j / cw;
+    S* half = pub + (size_t)(j & 1) * (nsteps + 2);
+    if (crank == owner) {   // pivot search and publication
+      const S* colj = Ms + (size_t)(j - c_beg) * m;
+      if (warp == 0) {
+        double best = -1.0;
+        int bi = j;
+        for (int r = j + lane; r < m; r += 32) {
+          double v = abs2(colj[r]);
+          if (v > best) { best = v; bi = r; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          double ob = __shfl_xor_sync(0xffffffffu, best, o);
+          int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { s_p = bi; s_best = best; }
+      }
+      __syncthreads();
+      const int p = s_p;
+      const bool ok = s_best > 0.0 && isfinite(s_best);
+      for (int r = tid; r < m; r += BB_NT) half[r] = colj[r == j ? p : (r == p ? j : r)];
+      if (tid == 0) {
+        half[nsteps] = ok ? S(1.0) / colj[p] : S(0.0);
+        reinterpret_cast<int*>(half + nsteps + 1)[0] = ok ? p : -1;
+        if (ok) piv[j] = p;
+        else atomicOr(bad, 1);
+      }
+    }
+    cl.sync();
+    // multipliers, 1 / pivot and the pivot row from the owner's shared memory
+    const S* rhalf = cl.map_shared_rank(half, owner);
+    for (int r = tid; r < m; r += BB_NT) ml[r] = rhalf[r];
+    const S inv = rhalf[nsteps];
+    const int p = reinterpret_cast<const int*>(rhalf + nsteps + 1)[0];
+    if (p < 0) failed = true;
+    __syncthreads();
+    if (!failed && nc > 0) {
+      for (int q = tid; q < nc; q += BB_NT) {
+        const int c = c_beg + q;
+        newj[q] = c == j ? inv : Ms[(size_t)q * m + p] * inv;   // row p moves to row j
+      }
+      __syncthreads();
+      for (int e = tid; e < nc * m; e += BB_NT) {
+        const int r = e % m, q = e / m, c = c_beg + q;
+        if (r == j) continue;
+        S* col = Ms + (size_t)q * m;
+        const S old = c == j ? S(0.0) : (r == p ? col[j] : col[r]);
+        col[r] = old - ml[r] * newj[q];
+      }
+      __syncthreads();
+      for (int q = tid; q < nc; q += BB_NT) Ms[(size_t)q * m + j] = newj[q];
+      __syncthreads();
+    }
+  }
+  cl.sync();   // no CTA leaves while another may still read its shared memory
+  for (int e = tid; e < nc * m; e += BB_NT) M[(size_t)c_beg * m + e] = Ms[e];
+}
+
 // Final column order of a Gauss-Jordan inverse: position c holds column idx[c].
 template <class S, class Dims>
 __global__ void k_bb_unscramble(BigArgs g, S* ws, Dims dims, S* dst_base, int dst_kind, int* idx_ws, int maxm) {
@@ -1696,7 +1825,7 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
   IdArgs a = a0;
   size_t sb = sizeof(S);
   size_t extra = (size_t)a.mmax * sb + 2 * (size_t)a.nmax * sizeof(double) + 3 * (size_t)a.geo.nproxy * sizeof(double) +
-                 (size_t)a.nmax * sizeof(int) + (size_t)a.mmax * sizeof(int) + 64;
+                 (size_t)a.mmax * sizeof(int64_t) + (size_t)a.nmax * sizeof(int) + 2 * (size_t)a.mmax * sizeof(int) + 64;
   size_t mbytes = (size_t)a.mmax * a.nmax * sb;
   const size_t limit = 200 * 1024;
   S* Mws = nullptr;
@@ -1715,20 +1844,98 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
     RS_CUDA(cudaMallocAsync((void**)&Mws, sb * std::max<int64_t>(1, acc), st));
   }
   RS_CUDA(cudaFuncSetAttribute(k_id<S, ID_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // near-field blocks of every colleague pair, evaluated once (the kernels
+  // are symmetric: G(x, y) = G(y, x))
+  std::vector<int> pi, pj;
+  std::vector<int64_t> pbase, slot_base((size_t)lv.nbox * 27, -1);
+  int64_t pacc = 0;
+  for (int i = 0; i < lv.nbox; ++i)
+    for (int si = 0; si < lv.h_ncoll[i]; ++si) {
+      const int j = lv.h_coll[(size_t)i * 27 + si];
+      if (j <= i) continue;
+      pi.push_back(i);
+      pj.push_back(j);
+      pbase.push_back(pacc);
+      slot_base[(size_t)i * 27 + si] = pacc;
+      for (int sj = 0; sj < lv.h_ncoll[j]; ++sj)
+        if (lv.h_coll[(size_t)j * 27 + sj] == i) slot_base[(size_t)j * 27 + sj] = pacc;
+      pacc += (int64_t)lv.h_n[i] * lv.h_n[j];
+    }
+  S* pairs = nullptr;
   prof_begin(P_ID, st);
+  if (!pi.empty()) {
+    int *dpi, *dpj;
+    int64_t *dpb, *dsb;
+    RS_TRY(upload(h, &dpi, pi, st));
+    RS_TRY(upload(h, &dpj, pj, st));
+    RS_TRY(upload(h, &dpb, pbase, st));
+    RS_TRY(upload(h, &dsb, slot_base, st));
+    RS_CUDA(cudaMallocAsync((void**)&pairs, sb * (size_t)pacc, st));
+    k_near_pairs<S><<<(unsigned)pi.size(), 128, 0, st>>>(a.kp, a.pts, a.n, a.off, a.act, dpi, dpj, dpb, pairs);
+    RS_CHECK_LAUNCH();
+    a.pair_base = dsb;
+    a.pairs = pairs;
+  }
   k_id<S, ID_NT><<<lv.nbox, ID_NT, smem, st>>>(a, Mws, (S*)lv.T);
   RS_CHECK_LAUNCH();
   prof_end(P_ID, st, 0.0, 0.0);
   if (Mws) RS_CUDA(cudaFreeAsync(Mws, st));
+  if (pairs) RS_CUDA(cudaFreeAsync(pairs, st));
   (void)msum;
   return RS_OK;
 }
 
 // The nsteps Gauss-Jordan steps of every box: one cooperative launch when the
 // grid fits on the GPU at once, else one launch per step.
+// Cluster of cs CTAs per box with cw = ceil(nsteps / cs) <= 64 columns each,
+// when its shared memory fits; returns false if no cluster shape fits.
+template <class S, class Dims>
+int run_gj_cluster(BigArgs g, S* ws, Dims dims, int nsteps, int nb, int* bad, cudaStream_t st, bool* done) {
+  *done = false;
+  for (int cs : {16, 8}) {
+    const int cw = div_up(nsteps, cs);
+    if (cw > 64) continue;
+    const size_t smem = sizeof(S) * ((size_t)cw * nsteps + nsteps + 2 * ((size_t)nsteps + 2));
+    if (smem > (size_t)max_dyn_smem()) continue;
+    auto kern = k_bb_gj_cluster<S, Dims>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (cs > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb * cs);
+    cfg.blockDim = dim3(BB_NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    RS_CUDA(cudaLaunchKernelEx(&cfg, kern, g, ws, dims, nsteps, cw, bad));
+    RS_CHECK_LAUNCH();
+    *done = true;
+    return RS_OK;
+  }
+  return RS_OK;
+}
+
 template <class S, class Dims>
 int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int ncb, size_t smem, int* bad,
                  cudaStream_t st) {
+  if (nb >= 2) {   // one cluster per box; a single box (the root) spreads over more SMs cooperatively
+    bool done = false;
+    RS_TRY((run_gj_cluster<S, Dims>(g, ws, dims, nsteps, nb, bad, st, &done)));
+    if (done) return RS_OK;
+  }
   const size_t csmem = sizeof(S) * (size_t)(BB_CB + 1) * nsteps;   // own columns + pivot column (m <= nsteps)
   const bool co_ok = csmem <= (size_t)max_dyn_smem();
   if (co_ok)
