@@ -102,6 +102,22 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(ms: float, dist, device: str) -> float:
+    """The slowest rank's time (each rank solves its own replica problem; the
+    job is done when the last one is)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(ws: int, nrhs: int, steps: int, ms: float) -> float:
+    """Whole-job RHS/s: every rank solves nrhs columns per step (weak scaling)."""
+    return ws * nrhs * steps / (ms / 1e3)
+
+
 def workload_inputs():
     w = ri.WORKLOADS[WORKLOAD]
     pts, h = ri.starfish(w["n"])
@@ -267,13 +283,9 @@ def run_ours(args, ws, rank, local):
     launches = rs.rs_launch_count() - launches0
     prof = rs.rs_profile_read()
     rs.rs_profile_enable(False)
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     ms_step = ms / args.steps
-    value = ws * NRHS * args.steps / (ms / 1e3)
+    value = replica_throughput(ws, NRHS, args.steps, ms)
 
     # breakdown on the resident factorization (outside the timed region)
     H = rs.rs_build(P, "laplace2d", h, w["eps"], w["leaf"], w["nproxy"], stream=stream)
