@@ -532,53 +532,89 @@ __global__ void __launch_bounds__(C_NT) k_solve_cta(Plan<S> p, const SIO* B, int
     const int64_t in0 = down ? p.bt.skoff[g] : off;
     const int r0 = tl.r0;
     const bool busy = wrow < rows - r0;    // warp-uniform
-    // the tile's columns in blocks of TN; a single-chunk factor block is
-    // staged once for all of them
-    for (int c0 = tl.c0; c0 < tl.c1; c0 += TN) {
-    const int cw = min(TN, tl.c1 - c0);
+    // Stages (column block, k chunk) in order; float tiles load the next
+    // stage's factor and input values into registers while the current one
+    // is computed (software pipelining), the others load at staging time.  A
+    // single-chunk factor block is staged once for all column blocks.
+    constexpr bool PF = std::is_same<S, float>::value;
+    constexpr int AN = C_TM * C_TK / C_NT, BN = C_TK * TN / C_NT;
+    const int nkc = (K + C_TK - 1) / C_TK;
+    const int ncb = (tl.c1 - tl.c0 + TN - 1) / TN;
+    const int nstage = ncb * (nkc > 0 ? nkc : 1);
+    const int ia = tid % C_TM, ka = tid / C_TM;   // A element (row ia, chunk rows ka + k AN-stride)
+    const int kb = tid % C_TK, jb = tid / C_TK;   // B element (chunk row kb, columns jb + j * (C_NT / C_TK))
+    int64_t bsrc_k0 = -1;                         // chunk start the B source index below belongs to
+    int64_t bsrc = 0;
+    S aR[PF ? AN : 1], bR[PF ? BN : 1];
+    auto a_needed = [&](int st) { return nkc > 1 || st / nkc == 0; };
+    auto b_source = [&](int k0) {   // input row of this thread's chunk row
+      if (bsrc_k0 != k0) {
+        bsrc_k0 = k0;
+        const int kk = k0 + kb;
+        bsrc = kk < K ? (leaf_in ? (int64_t)p.perm[off + kk] : in0 + kk) : -1;
+      }
+      return bsrc;
+    };
+    auto a_val = [&](int k0, int q) -> S {
+      const int kk = ka + q * (C_NT / C_TM);
+      return (r0 + ia < rows && k0 + kk < K) ? ldro(A + (r0 + ia) + (size_t)(k0 + kk) * rows) : S(0.0);
+    };
+    auto b_val = [&](int c0, int64_t src, int q) -> S {
+      const int j = jb + q * (C_NT / C_TK);
+      if (src < 0 || c0 + j >= tl.c1) return S(0.0);
+      return leaf_in ? in_cv<S, SIO>(B[src + (int64_t)(c0 + j) * ldb]) : ldcg(vin + (int64_t)(c0 + j) * ldin + src);
+    };
+    auto prefetch = [&](int st) {
+      if constexpr (PF) {
+        const int k0 = (st % nkc) * C_TK, c0 = tl.c0 + (st / nkc) * TN;
+        if (a_needed(st)) {
+#pragma unroll
+          for (int q = 0; q < AN; ++q) aR[q] = a_val(k0, q);
+        }
+        const int64_t src = b_source(k0);
+#pragma unroll
+        for (int q = 0; q < BN; ++q) bR[q] = b_val(c0, src, q);
+      }
+    };
     S acc[RPT][CPT];
+    if (nkc > 0) prefetch(0);
+    for (int st = 0; st < nstage; ++st) {
+      const int cb = nkc > 0 ? st / nkc : st, kc = nkc > 0 ? st % nkc : 0;
+      const int c0 = tl.c0 + cb * TN;
+      const int cw = min(TN, tl.c1 - c0);
+      if (kc == 0) {
 #pragma unroll
-    for (int a = 0; a < RPT; ++a)
+        for (int a = 0; a < RPT; ++a)
 #pragma unroll
-      for (int b = 0; b < CPT; ++b) acc[a][b] = S(0.0);
-
-    for (int k0 = 0; k0 < K; k0 += C_TK) {
-      const int kn = min(C_TK, K - k0);
-      __syncthreads();   // the previous chunk (or tile) is done with As / Bs
-      if (K > C_TK || c0 == tl.c0) {
-        const int i = tid % C_TM;
-        const bool oki = r0 + i < rows;
-        const S* Ai = A + (r0 + i) + (size_t)k0 * rows;
-#pragma unroll 8
-        for (int kk = tid / C_TM; kk < C_TK; kk += C_NT / C_TM)
-          As[kk * C_TM + i] = (oki && kk < kn) ? ldro(Ai + (size_t)kk * rows) : S(0.0);
+          for (int b = 0; b < CPT; ++b) acc[a][b] = S(0.0);
       }
-      {
-        const int kk = tid % C_TK;
-        const bool okk = kk < kn;
-        int64_t src = 0;
-        if (okk) src = leaf_in ? (int64_t)p.perm[off + k0 + kk] : in0 + k0 + kk;
-#pragma unroll 8
-        for (int j = tid / C_TK; j < TN; j += C_NT / C_TK) {
-          S v = S(0.0);
-          if (okk && j < cw)
-            v = leaf_in ? in_cv<S, SIO>(B[src + (int64_t)(c0 + j) * ldb]) : ldcg(vin + (int64_t)(c0 + j) * ldin + src);
-          Bs[kk * BP + j] = v;
+      if (nkc > 0) {
+        const int k0 = kc * C_TK, kn = min(C_TK, K - k0);
+        __syncthreads();   // the previous stage (or tile) is done with As / Bs
+        if (a_needed(st)) {
+#pragma unroll
+          for (int q = 0; q < AN; ++q) As[(ka + q * (C_NT / C_TM)) * C_TM + ia] = PF ? aR[q] : a_val(k0, q);
+        }
+        {
+          const int64_t src = PF ? 0 : b_source(k0);
+#pragma unroll
+          for (int q = 0; q < BN; ++q) Bs[kb * BP + jb + q * (C_NT / C_TK)] = PF ? bR[q] : b_val(c0, src, q);
+        }
+        __syncthreads();
+        if (st + 1 < nstage) prefetch(st + 1);   // in flight while this stage computes
+        if (busy) {
+          for (int kk = 0; kk < kn; ++kk) {
+            S a[RPT], b[CPT];
+            Lds<S, RPT>::run(As + kk * C_TM + ty * RPT, a);
+            Lds<S, CPT>::run(Bs + kk * BP + tx * CPT, b);
+#pragma unroll
+            for (int x = 0; x < RPT; ++x)
+#pragma unroll
+              for (int y = 0; y < CPT; ++y) mac(acc[x][y], a[x], b[y]);
+          }
         }
       }
-      __syncthreads();
-      if (busy) {
-        for (int kk = 0; kk < kn; ++kk) {
-          S a[RPT], b[CPT];
-          Lds<S, RPT>::run(As + kk * C_TM + ty * RPT, a);
-          Lds<S, CPT>::run(Bs + kk * BP + tx * CPT, b);
-#pragma unroll
-          for (int x = 0; x < RPT; ++x)
-#pragma unroll
-            for (int y = 0; y < CPT; ++y) mac(acc[x][y], a[x], b[y]);
-        }
-      }
-    }
+      if (nkc > 0 && kc < nkc - 1) continue;
     __syncthreads();   // every thread is done reading As / Bs
     S* Os = Bs;
     if (busy) {
@@ -625,7 +661,7 @@ __global__ void __launch_bounds__(C_NT) k_solve_cta(Plan<S> p, const SIO* B, int
         }
       }
     }
-    }   // column blocks
+    }   // stages
     // every thread's stores of this tile precede the barrier; thread 0's
     // release add publishes them to the waiter that acquires the counter
     __syncthreads();
