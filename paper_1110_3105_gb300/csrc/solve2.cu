@@ -129,6 +129,16 @@ __device__ inline void signal(int* cnt) {
   if ((threadIdx.x & 31) == 0) atomicAdd(cnt, 1);
 }
 
+// Ask L2 for the lines of a factor column segment (rows r, stride ld, count
+// q) while a tile still waits for its inputs: the rows come from HBM once
+// the wait ends instead of on the tile's critical path.
+template <class S>
+__device__ __forceinline__ void prefetch_rows(const S* col, size_t ld, int count) {
+  for (int q = 0; q < count; ++q) asm volatile("prefetch.global.L2 [%0];" ::"l"(col + (size_t)q * ld));
+}
+// Whether a dependency counter has reached its target (one lane's look).
+__device__ __forceinline__ bool ready(const int* cnt, int target) { return ld_acquire(cnt) >= target; }
+
 template <class S> __device__ inline S ldcg(const S* p) { return __ldcg(p); }
 template <> __device__ inline c128 ldcg<c128>(const c128* p) {
   double2 t = __ldcg(reinterpret_cast<const double2*>(p));
@@ -289,7 +299,14 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
 
     if (tl.kind != T_DOWN) {
       // ---- up / root tile: rows of U b, U = [calD ; calR] ((n+k) x n)
-      if (p.bt.up_need[g] > 0 && !wait_at_least(&p.up_cnt[g], epoch * p.bt.up_need[g], flag, p.dflag)) return;
+      if (p.bt.up_need[g] > 0) {
+        const int target = epoch * p.bt.up_need[g];
+        int wait = 0;
+        if (lane == 0) wait = !ready(&p.up_cnt[g], target);
+        if (__shfl_sync(0xffffffffu, wait, 0) && CT == 1 && tl.r0 + lane < n + k)
+          prefetch_rows(p.U[d] + p.bt.uoff[g] + tl.r0 + lane, (size_t)(n + k), n);
+        if (!wait_at_least(&p.up_cnt[g], target, flag, p.dflag)) return;
+      }
       if (TR && lane == 0) p.trace[3 * (size_t)t + 1] = gtime();
       const int rows = n + k;
       const int r = tl.r0 + lane;
@@ -353,7 +370,14 @@ __global__ void __launch_bounds__(P_NT) k_solve_pers(Plan<S> p, const SIO* B, in
     } else {
       // ---- down tile: rows of u + calL x_parent (n x k)
       const int par = p.bt.parent[g];
-      if (!wait_at_least(&p.dn_cnt[par], epoch * p.bt.dn_need[par], flag, p.dflag)) return;
+      {
+        const int target = epoch * p.bt.dn_need[par];
+        int wait = 0;
+        if (lane == 0) wait = !ready(&p.dn_cnt[par], target);
+        if (__shfl_sync(0xffffffffu, wait, 0) && CT == 1 && tl.r0 + lane < n)
+          prefetch_rows(p.Lf[d] + p.bt.loff[g] + tl.r0 + lane, (size_t)n, k);
+        if (!wait_at_least(&p.dn_cnt[par], target, flag, p.dflag)) return;
+      }
       if (TR && lane == 0) p.trace[3 * (size_t)t + 1] = gtime();
       const int r = tl.r0 + lane;
       const S* Lb = p.Lf[d] + p.bt.loff[g];
