@@ -1764,8 +1764,9 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
   const int ncb = div_up(maxn, BI_CB);
   const size_t id_smem = sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax;
   RS_CUDA(cudaFuncSetAttribute(k_bbid_step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)id_smem));
-  // cooperative launch: CB = 8, 4 or 2 columns per CTA, the widest whose
-  // column cache fits in shared memory and whose grid fits on the GPU at once
+  // cooperative launch: CB columns per CTA (8 first; then 16 or 32 when the
+  // grid is too large to be resident at once, 4 or 2 when the column cache is
+  // too large for shared memory)
   bool coop_done = false;
   auto try_coop = [&](auto cbc) -> int {
     constexpr int CB = decltype(cbc)::value;
@@ -1788,7 +1789,9 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
     return RS_OK;
   };
   RS_TRY(try_coop(std::integral_constant<int, 8>{}));
-  RS_TRY(try_coop(std::integral_constant<int, 4>{}));
+  RS_TRY(try_coop(std::integral_constant<int, 16>{}));   // fewer CTAs when the grid does not fit
+  RS_TRY(try_coop(std::integral_constant<int, 32>{}));
+  RS_TRY(try_coop(std::integral_constant<int, 4>{}));    // less shared memory per CTA
   RS_TRY(try_coop(std::integral_constant<int, 2>{}));
   if (!coop_done) {
     // one launch per step; every 8 steps, stop early once every box of the
