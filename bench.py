@@ -52,7 +52,9 @@ def peaks():
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per
 # kernel category, from the ncu captures summarised in profiles/ (the leaf-level
 # launch of the bench workload); None where no capture of the current kernel exists.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"id": (48085248 + 571392,
+                      "k_id leaf-level launch (profiles/k_id_leaf_laplace2d_starfish_131072.md): "
+                      "dram__bytes_read.sum + dram__bytes_write.sum")}
 
 # FP64 FMA throughput of GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 # = 1.26 TFLOP/s nominal; a dependent-chain-free probe measured 1.195 TFLOP/s.
