@@ -1104,6 +1104,16 @@ __device__ void gj_inplace(S* A, int n, S* mult, int* piv, int* bad) {
   }
 }
 
+// Entry e of the upper triangle of an n x n matrix, column by column:
+// (r, c) with r <= c, e = c (c + 1) / 2 + r.
+__device__ __forceinline__ void tri_index(int e, int& r, int& c) {
+  int cc = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while ((cc + 1) * (cc + 2) / 2 <= e) ++cc;
+  while (cc * (cc + 1) / 2 > e) --cc;
+  c = cc;
+  r = e - cc * (cc + 1) / 2;
+}
+
 // The block elimination of k_factor with every intermediate in shared
 // memory: [D^-1 (n x n) | X (n x k) | (PX)^-1 (k x k) | mult (n) | piv (n)].
 template <class S, int NT>
@@ -1156,39 +1166,40 @@ __global__ void __launch_bounds__(NT) k_factor_smem(FaArgs a, const S* Tpool, co
     X[e] = s;
   }
   __syncthreads();
-  // Y = P X, then Lambda = Y^-1 in place
-  for (int e = tid; e < k * k; e += NT) {
-    int i = e % k, c = e / k;
+  // Y = P X = P D^-1 P^T (symmetric: one triangle, mirrored), then
+  // Lambda = Y^-1 in place
+  for (int e = tid; e < k * (k + 1) / 2; e += NT) {
+    int i, c;
+    tri_index(e, i, c);
     S s = X[lp[i] + c * n];
     for (int q = 0; q < nr; ++q) s += T[i + (size_t)q * k] * X[lp[k + q] + c * n];
-    Y[e] = s;
+    Y[i + c * k] = s;
+    Y[c + i * k] = s;
   }
   __syncthreads();
   gj_inplace<S, NT>(Y, k, mult, piv, a.bad);
   S* Lo = Lampool + a.lamoff[b];
   for (int e = tid; e < k * k; e += NT) Lo[e] = Y[e];
-  // calL = X Lambda -> global; calR = Lambda X^T -> rows n.. of U
+  // calL = X Lambda -> global; calR = Lambda X^T = calL^T (Lambda is
+  // symmetric) -> rows n.. of U
   S* Lf = Lpool + a.loff[b];
   for (int e = tid; e < n * k; e += NT) {
     int r = e % n, c = e / n;
     S s = S(0.0);
     for (int q = 0; q < k; ++q) s += X[r + q * n] * Y[q + c * k];
     Lf[e] = s;
+    U[n + c + (size_t)r * ldu] = s;
   }
-  for (int e = tid; e < k * n; e += NT) {
-    int i = e % k, c = e / k;
-    S s = S(0.0);
-    for (int q = 0; q < k; ++q) s += Y[i + q * k] * X[c + q * n];
-    U[n + i + (size_t)c * ldu] = s;
-  }
-  // calD = D^-1 - calL X^T = D^-1 - X Lambda X^T: form W = X Lambda in the Y
-  // slot is not possible (k x k), so reuse the global calL just written.
+  // calD = D^-1 - calL X^T = D^-1 - X Lambda X^T (symmetric: one triangle,
+  // mirrored), reading back the calL just written
   __syncthreads();
-  for (int e = tid; e < n * n; e += NT) {
-    int r = e % n, c = e / n;
-    S s = Dv[e];
+  for (int e = tid; e < n * (n + 1) / 2; e += NT) {
+    int r, c;
+    tri_index(e, r, c);
+    S s = Dv[r + c * n];
     for (int q = 0; q < k; ++q) s -= Lf[r + (size_t)q * n] * X[c + q * n];
     U[r + (size_t)c * ldu] = s;
+    U[c + (size_t)r * ldu] = s;
   }
 }
 
