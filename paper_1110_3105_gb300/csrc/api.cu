@@ -67,6 +67,10 @@ int dalloc(Handle* h, void** p, size_t bytes) {
                   cudaGetErrorString(e));
     }
     h->allocs.push_back(*q);
+    if (h->fst) {   // the factorization stream may use the block as well
+      RS_CUDA(cudaEventRecord(h->aev, h->bst));
+      RS_CUDA(cudaStreamWaitEvent(h->fst, h->aev, 0));
+    }
     return RS_OK;
   };
   if (bytes > kChunk / 4) return take(p, bytes);   // large tables get their own block
@@ -304,13 +308,21 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
   h->eps = eps;
   h->leaf = leaf;
 
-  cudaEvent_t e0, e1;
+  cudaEvent_t e0, e1, ej;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  cudaEventCreateWithFlags(&ej, cudaEventDisableTiming);
   cudaEventRecord(e0, st);
   h->bst = st;
   int rc = RS_OK;
+  cudaStream_t fs = nullptr;
   do {
+    if (cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->aev, cudaEventDisableTiming) != cudaSuccess) {
+      rc = fail(RS_ERR_CUDA, "rs_build: stream creation failed");
+      break;
+    }
+    h->fst = fs;
     if ((rc = dalloc_t(h, &h->status, 4)) != RS_OK) break;
     if (cudaMemsetAsync(h->status, 0, sizeof(int) * 4, st) != cudaSuccess) { rc = fail(RS_ERR_CUDA, "memset"); break; }
     const double* dp = pts;
@@ -324,12 +336,32 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
       dp = tmp;
     }
     if ((rc = build_tree(h, dp, st)) != RS_OK) break;
-    for (int d = h->L; d >= 1 && rc == RS_OK; --d) rc = skeletonize_level(h, d, st);
+    // fs starts after everything queued on st so far (tree, status words)
+    if (cudaEventRecord(ej, st) != cudaSuccess || cudaStreamWaitEvent(fs, ej, 0) != cudaSuccess) {
+      rc = fail(RS_ERR_CUDA, "rs_build: stream ordering failed");
+      break;
+    }
+    for (int d = h->L; d >= 1 && rc == RS_OK; --d) rc = skeletonize_level(h, d, st, fs);
     if (rc != RS_OK) break;
-    if ((rc = factor_root(h, st)) != RS_OK) break;
+    if ((rc = factor_root(h, st, fs)) != RS_OK) break;
+    if (cudaEventRecord(ej, fs) != cudaSuccess || cudaStreamWaitEvent(st, ej, 0) != cudaSuccess) {
+      rc = fail(RS_ERR_CUDA, "rs_build: stream ordering failed");
+      break;
+    }
+    h->fst = nullptr;
+    if ((rc = check_factor_status(h, st)) != RS_OK) break;
     if ((rc = make_fp32_copies(h, st)) != RS_OK) break;
     if ((rc = make_fwd_blocks(h, st)) != RS_OK) break;
   } while (0);
+  h->fst = nullptr;
+  if (fs) {
+    cudaStreamSynchronize(fs);
+    cudaStreamDestroy(fs);
+  }
+  if (h->aev) {
+    cudaEventDestroy(h->aev);
+    h->aev = nullptr;
+  }
   cudaEventRecord(e1, st);
   cudaError_t se = cudaStreamSynchronize(st);
   if (rc == RS_OK && se != cudaSuccess) rc = fail(RS_ERR_CUDA, "rs_build: %s", cudaGetErrorString(se));
@@ -337,6 +369,7 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaEventDestroy(ej);
   if (rc != RS_OK) {
     std::string keep = rs::g_err;
     destroy(h);

@@ -122,6 +122,9 @@ struct Handle {
   std::vector<Level> lv;       // index = depth
   std::vector<void*> allocs;   // pool blocks owned by the handle (freed by rs_free)
   cudaStream_t bst = nullptr;  // stream of the build (allocations are ordered on it)
+  cudaStream_t fst = nullptr;  // during the build: the factorization stream, which runs
+                               // behind the skeletonization on bst
+  cudaEvent_t aev = nullptr;   // orders fst after a new device block taken on bst
   char* arena_cur = nullptr;   // bump pointer into the current block
   size_t arena_left = 0;
   double build_ms = 0;
@@ -161,8 +164,13 @@ template <class T> int dalloc_t(Handle* h, T** p, size_t count) {
 int build_tree(Handle* h, const double* d_pts_in, cudaStream_t st);
 
 // Skeletonization + factorization of one depth (skel.cu).
-int skeletonize_level(Handle* h, int depth, cudaStream_t st);
-int factor_root(Handle* h, cudaStream_t st);
+// The skeletonization of a depth runs on st; its factorization is queued on
+// fs behind it (fs waits for the depth's ID on st and runs the depths in
+// order), so the IDs of the next depths overlap the factorizations.
+int skeletonize_level(Handle* h, int depth, cudaStream_t st, cudaStream_t fs);
+int factor_root(Handle* h, cudaStream_t st, cudaStream_t fs);
+// After fs has been joined into st: the factorizations' status words.
+int check_factor_status(Handle* h, cudaStream_t st);
 int make_fp32_copies(Handle* h, cudaStream_t st);
 
 // Solve / forward operator (solve.cu).

@@ -1729,12 +1729,12 @@ bool coop_fits(const void* kern, int grid, int nt, size_t smem) {
   return coop && grid <= occ * nsm;
 }
 
-// Arrival counter of a grid barrier (zeroed, stream ordered); the give-up
-// flag is the handle's status word 1.
-int make_bar(Handle* h, GridBar* gb, cudaStream_t st) {
+// Arrival counter of a grid barrier (zeroed, stream ordered); `flag` is the
+// status word set when a wait gives up.
+int make_bar(GridBar* gb, int* flag, cudaStream_t st) {
   RS_CUDA(cudaMallocAsync((void**)&gb->count, sizeof(unsigned int), st));
   RS_CUDA(cudaMemsetAsync(gb->count, 0, sizeof(unsigned int), st));
-  gb->flag = h->status + 1;
+  gb->flag = flag;
   return RS_OK;
 }
 
@@ -1788,7 +1788,7 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
     RS_CUDA(cudaFuncSetAttribute(k_bbid_coop<S, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)co_smem));
     if (!coop_fits((const void*)k_bbid_coop<S, CB>, nb * ncbc, BI_NT, co_smem)) return RS_OK;
     GridBar gb{};
-    RS_TRY(make_bar(h, &gb, st));
+    RS_TRY(make_bar(&gb, h->status + 1, st));
     int nsteps = maxkmax, ncbv = ncbc, nbv = nb;
     int* lp = a.lperm;
     void* args[] = {&a, &g, &Mws, &nsteps, &ncbv, &nbv, &lp, &gb};
@@ -1956,7 +1956,7 @@ int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int
     RS_CUDA(cudaFuncSetAttribute(k_bb_gj_coop<S, Dims>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
   if (co_ok && coop_fits((const void*)k_bb_gj_coop<S, Dims>, nb * ncb, BB_NT, csmem)) {
     GridBar gb{};
-    RS_TRY(make_bar(h, &gb, st));
+    RS_TRY(make_bar(&gb, bad + 1, st));   // the status word after the singularity flag
     void* args[] = {&g, &ws, &dims, &nsteps, &ncb, &bad, &gb};
     RS_CUDA(cudaLaunchCooperativeKernel((const void*)k_bb_gj_coop<S, Dims>, dim3(nb * ncb), dim3(BB_NT), args, csmem,
                                         st));
@@ -2094,7 +2094,9 @@ int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t 
   return RS_OK;
 }
 
-// Status words: [0] a singular or non-finite pivot, [1] a grid barrier gave up.
+// Status words: [0] a singular or non-finite pivot, [1] a grid barrier gave
+// up, both in the skeletonization; [2], [3] the same in the factorization
+// (which runs on its own stream and is checked once at the end).
 int check_bad(Handle* h, cudaStream_t st, const char* where) {
   int bad[2] = {0, 0};
   RS_CUDA(cudaMemcpyAsync(bad, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -2134,11 +2136,67 @@ int alloc_factors(Handle* h, Level& lv, cudaStream_t st) {
   return RS_OK;
 }
 
+// fs waits for the work queued on st so far.
+int follow(cudaStream_t fs, cudaStream_t st) {
+  cudaEvent_t ev;
+  RS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(fs, ev, 0);
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) return fail(RS_ERR_CUDA, "stream ordering: %s", cudaGetErrorString(e));
+  return RS_OK;
+}
+
 }  // namespace
 
-// Skeletonize and factor every box of depth `depth` (1 <= depth <= L); fills
-// the active sets of depth-1.
-int skeletonize_level(Handle* h, int depth, cudaStream_t st) {
+int check_factor_status(Handle* h, cudaStream_t st) {
+  int bad[2] = {0, 0};
+  RS_CUDA(cudaMemcpyAsync(bad, h->status + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  RS_CUDA(cudaStreamSynchronize(st));
+  if (bad[1]) return fail(RS_ERR_TIMEOUT, "rs_build: a grid barrier wait ran out during factorization");
+  if (bad[0]) return fail(RS_ERR_SINGULAR, "rs_build: singular block during factorization");
+  return RS_OK;
+}
+
+namespace {
+
+// The factorization of one depth (or the root, k = 0) on fs, after the
+// skeletonization work queued on st.
+int factor_level(Handle* h, Level& lv, const Level* child, const int* lperm, const int64_t* toff, bool leaf,
+                 cudaStream_t st, cudaStream_t fs) {
+  FaArgs f{};
+  f.kp = h->kp;
+  f.pts = make_pts(h);
+  f.leaf_level = leaf;
+  f.n = lv.n;
+  f.k = lv.k;
+  f.off = lv.off;
+  f.act = lv.act;
+  f.owner = lv.owner;
+  if (child) {
+    f.cskoff = child->skoff;
+    f.ck = child->k;
+    f.clamoff = child->lamoff;
+  }
+  f.lperm = lperm;
+  f.toff = toff;
+  f.uoff = lv.uoff;
+  f.loff = lv.loff;
+  f.lamoff = lv.lamoff;
+  f.bad = h->status + 2;
+  f.fu32 = (float*)lv.FU32;
+  f.fudf = (dfloat*)lv.FUdf;
+  RS_TRY(follow(fs, st));
+  if (h->cplx) RS_TRY(run_factor<c128>(h, lv, f, child, fs));
+  else RS_TRY(run_factor<double>(h, lv, f, child, fs));
+  return RS_OK;
+}
+
+}  // namespace
+
+// Skeletonize every box of depth `depth` (1 <= depth <= L) on st and queue
+// its factorization on fs; fills the active sets of depth-1.
+int skeletonize_level(Handle* h, int depth, cudaStream_t st, cudaStream_t fs) {
   Level& lv = h->lv[depth];
   const int nbox = lv.nbox;
   // active sets of the leaves come from the tree
@@ -2228,34 +2286,10 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st) {
   lv.h_skoff = skoff;
   RS_TRY(upload(h, &lv.skoff, skoff, st));
 
-  // factor
+  // factor (on fs, overlapping the next depths' skeletonization)
   RS_TRY(alloc_factors(h, lv, st));
-  FaArgs f{};
-  f.kp = h->kp;
-  f.pts = make_pts(h);
-  f.leaf_level = depth == h->L;
-  f.n = lv.n;
-  f.k = lv.k;
-  f.off = lv.off;
-  f.act = lv.act;
-  f.owner = lv.owner;
   const Level* child = depth < h->L ? &h->lv[depth + 1] : nullptr;
-  if (child) {
-    f.cskoff = child->skoff;
-    f.ck = child->k;
-    f.clamoff = child->lamoff;
-  }
-  f.lperm = lv.lperm;
-  f.toff = lv.toff;
-  f.uoff = lv.uoff;
-  f.loff = lv.loff;
-  f.lamoff = lv.lamoff;
-  f.bad = h->status;
-  f.fu32 = (float*)lv.FU32;
-  f.fudf = (dfloat*)lv.FUdf;
-  if (h->cplx) RS_TRY(run_factor<c128>(h, lv, f, child, st));
-  else RS_TRY(run_factor<double>(h, lv, f, child, st));
-  RS_TRY(check_bad(h, st, "factorization"));
+  RS_TRY(factor_level(h, lv, child, lv.lperm, lv.toff, depth == h->L, st, fs));
 
   // active sets of depth-1: skeletons of the children, in child order
   Level& up = h->lv[depth - 1];
@@ -2279,7 +2313,7 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st) {
 
 // Root: calS assembled like any upper-level block (or A itself when the tree
 // has a single box), inverted densely.
-int factor_root(Handle* h, cudaStream_t st) {
+int factor_root(Handle* h, cudaStream_t st, cudaStream_t fs) {
   Level& lv = h->lv[0];
   if (h->L == 0) {
     lv.h_n.assign(1, (int)h->N);
@@ -2294,35 +2328,10 @@ int factor_root(Handle* h, cudaStream_t st) {
   std::vector<int> k0(1, 0);
   RS_TRY(upload(h, &lv.k, k0, st));
   RS_TRY(alloc_factors(h, lv, st));
-  FaArgs f{};
-  f.kp = h->kp;
-  f.pts = make_pts(h);
-  f.leaf_level = h->L == 0;
-  f.n = lv.n;
-  f.k = lv.k;
-  f.off = lv.off;
-  f.act = lv.act;
-  f.owner = lv.owner;
   const Level* child = h->L > 0 ? &h->lv[1] : nullptr;
-  if (child) {
-    f.cskoff = child->skoff;
-    f.ck = child->k;
-    f.clamoff = child->lamoff;
-  }
   int* dummy_perm;
   RS_TRY(dalloc_t(h, &dummy_perm, std::max<int64_t>(1, lv.ntot)));
-  f.lperm = dummy_perm;
-  f.toff = nullptr;
-  f.uoff = lv.uoff;
-  f.loff = lv.loff;
-  f.lamoff = lv.lamoff;
-  f.bad = h->status;
-  f.fu32 = (float*)lv.FU32;
-  f.fudf = (dfloat*)lv.FUdf;
-  if (h->cplx) RS_TRY(run_factor<c128>(h, lv, f, child, st));
-  else RS_TRY(run_factor<double>(h, lv, f, child, st));
-  RS_TRY(check_bad(h, st, "root factorization"));
-  return RS_OK;
+  return factor_level(h, lv, child, dummy_perm, nullptr, h->L == 0, st, fs);
 }
 
 int make_fp32_copies(Handle* h, cudaStream_t st) {
