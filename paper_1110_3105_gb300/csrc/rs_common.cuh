@@ -103,6 +103,13 @@ template <class S> __device__ inline S warp_sum(S v) {
   for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
   return v;
 }
+// Sum over aligned groups of G lanes (G a power of two <= 32); every lane of
+// a group gets its group's sum.  All 32 lanes must take part.
+template <int G, class S> __device__ inline S group_sum(S v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += shfl_xor(v, o);
+  return v;
+}
 
 // ----------------------------------------------------------- point clouds
 // Points are stored per axis (structure of arrays) in tree order.

@@ -111,6 +111,8 @@ __device__ int cpqr(S* M, int m, int n, int ld, double eps, int* piv, double* nr
   __shared__ double s_rjj, s_r00;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = NT / 32;
+  constexpr int QG = 8, QCW = 32 / QG;
+  const int gl = lane & (QG - 1), grp = lane / QG;
   constexpr double kTol = 1.49e-8;   // sqrt of the double unit roundoff
   double* nref = nrm + n;
   for (int c = tid; c < n; c += NT) piv[c] = c;
@@ -185,26 +187,34 @@ __device__ int cpqr(S* M, int m, int n, int ld, double eps, int* piv, double* nr
     for (int r = j + tid; r < m; r += NT) u[r - j] = (r == j) ? alpha - beta : M[r + (size_t)j * ld];
     const double f = 1.0 / (rjj * (rjj + aa));
     __syncthreads();
-    for (int c = j + 1 + warp; c < n; c += NW) {
-      S* col = M + (size_t)c * ld;
+    // Trailing columns: a group of QG lanes per column (QCW columns per warp),
+    // each lane a strided share of the rows, so the dot product's reduction
+    // is log2(QG) shuffles shared by QCW columns.
+    for (int cb = j + 1 + warp * QCW; cb < n; cb += NW * QCW) {
+      const int c = cb + grp;
+      const bool act = c < n;
+      S* col = M + (size_t)(act ? c : j) * ld;
       S s = S(0.0);
-      for (int r = j + lane; r < m; r += 32) s += conj_(u[r - j]) * col[r];
-      s = warp_sum(s);
-      s = shfl(s, 0);
+      if (act)
+        for (int r = j + gl; r < m; r += QG) s += conj_(u[r - j]) * col[r];
+      s = group_sum<QG>(s);
       const S fs = scal(s, f);
-      for (int r = j + lane; r < m; r += 32) col[r] = col[r] - u[r - j] * fs;
+      if (act)
+        for (int r = j + gl; r < m; r += QG) col[r] = col[r] - u[r - j] * fs;
       __syncwarp();
       int again = 0;
-      if (lane == 0) {
+      if (act && gl == 0) {   // row j of the column was updated by this lane
         const double left = nrm[c] - abs2(col[j]);
         if (left <= kTol * nref[c]) again = 1;
         else nrm[c] = left;
       }
-      if (__shfl_sync(0xffffffffu, again, 0)) {   // too much cancelled: recompute
+      again = __shfl_sync(0xffffffffu, again, grp * QG);
+      if (__any_sync(0xffffffffu, again)) {   // too much cancelled: recompute
         double s2 = 0.0;
-        for (int r = j + 1 + lane; r < m; r += 32) s2 += abs2(col[r]);
-        s2 = warp_sum(s2);
-        if (lane == 0) nrm[c] = nref[c] = s2;
+        if (again)
+          for (int r = j + 1 + gl; r < m; r += QG) s2 += abs2(col[r]);
+        s2 = group_sum<QG>(s2);
+        if (again && gl == 0) nrm[c] = nref[c] = s2;
       }
     }
     if (tid == 0) M[j + (size_t)j * ld] = beta;
@@ -410,6 +420,7 @@ struct IdArgs {
   int smem_path;         // 1: M in shared memory
   int qr_df;             // 1: double-float QR (real kernels, rs_id_arith)
   int mmax, nmax;
+  int64_t mnmax;         // max over boxes of m n (the shared M, leading dimension m)
 };
 
 template <class S, int NT>
@@ -423,7 +434,7 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
   // shared layout: [M (smem path)] | u[mmax] | nrm[2 nmax] | proxy xyz[3 nproxy] | rbase[mmax] (int64) |
   // piv[nmax] | rowid[mmax] | rstride[mmax]
   S* Ms = reinterpret_cast<S*>(smem);
-  size_t msz = a.smem_path ? (size_t)a.mmax * a.nmax : 0;
+  size_t msz = a.smem_path ? (size_t)a.mnmax : 0;
   S* u = Ms + msz;
   double* nrm = reinterpret_cast<double*>(u + a.mmax);
   double* pxy = nrm + 2 * a.nmax;
@@ -1716,6 +1727,18 @@ int max_dyn_smem() {
   return v;
 }
 
+int num_sms() {
+  static const int v = [] {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 132;
+    }
+    return nsm;
+  }();
+  return v;
+}
+
 // Whether `grid` CTAs of `kern` can all be resident at once (the condition
 // of a cooperative launch).
 bool coop_fits(const void* kern, int grid, int nt, size_t smem) {
@@ -1840,8 +1863,11 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
   size_t sb = sizeof(S);
   size_t extra = (size_t)a.mmax * sb + 2 * (size_t)a.nmax * sizeof(double) + 3 * (size_t)a.geo.nproxy * sizeof(double) +
                  (size_t)a.mmax * sizeof(int64_t) + (size_t)a.nmax * sizeof(int) + 2 * (size_t)a.mmax * sizeof(int) + 64;
-  size_t mbytes = (size_t)a.mmax * a.nmax * sb;
-  const size_t limit = 200 * 1024;
+  int64_t mnmax = 0;
+  for (int b = 0; b < lv.nbox; ++b) mnmax = std::max<int64_t>(mnmax, (int64_t)mrows[b] * lv.h_n[b]);
+  a.mnmax = mnmax;
+  size_t mbytes = (size_t)mnmax * sb;
+  const size_t limit = (size_t)max_dyn_smem();
   S* Mws = nullptr;
   a.smem_path = (mbytes + extra <= limit) ? 1 : 0;
   if (!a.smem_path && a.geo.nproxy <= 256 && sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax <= 200 * 1024)
@@ -2051,7 +2077,10 @@ int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t 
     size_t n = lv.h_n[b], k = lv.h_k[b];
     sm_need = std::max(sm_need, sizeof(S) * (n * n + n * k + k * k + n) + sizeof(int) * n + 16);
   }
-  const bool smem_path = sm_need <= 200 * 1024;
+  // one CTA per box in shared memory when the boxes fit and are enough to
+  // spread over the SMs; a few large boxes take several CTAs each
+  const bool few = 2 * lv.nbox < num_sms() && lv.maxn >= 64 && sizeof(S) * (size_t)lv.maxn <= 200 * 1024;
+  const bool smem_path = sm_need <= 200 * 1024 && !few;
   double fl0 = 0.0, by0 = 0.0;
   for (int b = 0; b < lv.nbox; ++b) {
     double n = lv.h_n[b], k = lv.h_k[b];
