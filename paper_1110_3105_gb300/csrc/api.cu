@@ -315,9 +315,14 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
   cudaEventRecord(e0, st);
   h->bst = st;
   int rc = RS_OK;
-  cudaStream_t fs = nullptr;
+  // the skeletonization (the critical path) runs on a high-priority stream
+  // `is`, the factorization behind it on a low-priority stream fs
+  cudaStream_t fs = nullptr, is = nullptr;
   do {
-    if (cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking) != cudaSuccess ||
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&fs, cudaStreamNonBlocking, least) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&is, cudaStreamNonBlocking, greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->aev, cudaEventDisableTiming) != cudaSuccess) {
       rc = fail(RS_ERR_CUDA, "rs_build: stream creation failed");
       break;
@@ -336,28 +341,35 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
       dp = tmp;
     }
     if ((rc = build_tree(h, dp, st)) != RS_OK) break;
-    // fs starts after everything queued on st so far (tree, status words)
-    if (cudaEventRecord(ej, st) != cudaSuccess || cudaStreamWaitEvent(fs, ej, 0) != cudaSuccess) {
+    // is and fs start after everything queued on st so far (tree, status
+    // words); allocations are ordered on is from here on
+    if (cudaEventRecord(ej, st) != cudaSuccess || cudaStreamWaitEvent(fs, ej, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(is, ej, 0) != cudaSuccess) {
       rc = fail(RS_ERR_CUDA, "rs_build: stream ordering failed");
       break;
     }
-    for (int d = h->L; d >= 1 && rc == RS_OK; --d) rc = skeletonize_level(h, d, st, fs);
+    h->bst = is;
+    for (int d = h->L; d >= 1 && rc == RS_OK; --d) rc = skeletonize_level(h, d, is, fs);
     if (rc != RS_OK) break;
-    if ((rc = factor_root(h, st, fs)) != RS_OK) break;
-    if (cudaEventRecord(ej, fs) != cudaSuccess || cudaStreamWaitEvent(st, ej, 0) != cudaSuccess) {
+    if ((rc = factor_root(h, is, fs)) != RS_OK) break;
+    if (cudaEventRecord(ej, fs) != cudaSuccess || cudaStreamWaitEvent(st, ej, 0) != cudaSuccess ||
+        cudaEventRecord(ej, is) != cudaSuccess || cudaStreamWaitEvent(st, ej, 0) != cudaSuccess) {
       rc = fail(RS_ERR_CUDA, "rs_build: stream ordering failed");
       break;
     }
     h->fst = nullptr;
+    h->bst = st;
     if ((rc = check_factor_status(h, st)) != RS_OK) break;
     if ((rc = make_fp32_copies(h, st)) != RS_OK) break;
     if ((rc = make_fwd_blocks(h, st)) != RS_OK) break;
   } while (0);
   h->fst = nullptr;
-  if (fs) {
-    cudaStreamSynchronize(fs);
-    cudaStreamDestroy(fs);
-  }
+  h->bst = st;
+  for (cudaStream_t x : {fs, is})
+    if (x) {
+      cudaStreamSynchronize(x);
+      cudaStreamDestroy(x);
+    }
   if (h->aev) {
     cudaEventDestroy(h->aev);
     h->aev = nullptr;

@@ -822,6 +822,169 @@ __global__ void __launch_bounds__(BI_NT) k_bbid_coop(IdArgs a, BigId g, S* Mws, 
   }
 }
 
+// The pivoted QR of every box of a level on a thread-block cluster of CTAs
+// (one cluster per box).  CTA q keeps the box's physical columns
+// [q cw, q cw + cw) in shared memory for the whole factorization.  Each step:
+// every CTA publishes its best trailing column (exact norm, lowest position on
+// ties), all CTAs read the candidates through distributed shared memory and
+// agree on the pivot; the CTA that owns the pivot column publishes the
+// Householder vector; every CTA applies it to its own columns and recomputes
+// their trailing norms.  Two cluster barriers per step and no grid-wide
+// barrier.  Output as the cooperative kernel: rows 0..k-1 of the columns in
+// Mws, R_jj in rdiag, the rank in kk, the column order in lperm.
+template <class S>
+__global__ void __launch_bounds__(BI_NT) k_bbid_cluster(IdArgs a, BigId g, S* Mws, int cw, int* lperm) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char bc_smem[];
+  __shared__ double s_rjj, s_r00, s_f;
+  __shared__ int s_p, s_stop, s_owner;
+  const int cs = (int)cl.num_blocks(), q = (int)cl.block_rank();
+  const int b = blockIdx.x / cs;
+  const int n = a.n[b], m = g.m[b];
+  const int kmax = min(m, n);
+  const int c_beg = q * cw, nc = max(0, min(n, c_beg + cw) - c_beg);
+  // Ms[cw][m] | u[mmax] | nrm[cw] | candv[2] | fpub[2] | pos[nmax] | posof[cw] | candp[2]
+  S* Ms = reinterpret_cast<S*>(bc_smem);
+  S* u = Ms + (size_t)cw * a.mmax;
+  double* nrm = reinterpret_cast<double*>(u + a.mmax);
+  double* candv = nrm + cw;
+  double* fpub = candv + 2;
+  int* pos = reinterpret_cast<int*>(fpub + 2);
+  int* posof = pos + a.nmax;
+  int* candp = posof + cw;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = BI_NT / 32, QG = 8, QCW = 32 / QG;
+  const int gl = lane & (QG - 1), grp = lane / QG;
+  const S* src = Mws + g.moff[b] + (size_t)c_beg * m;
+  for (int e = tid; e < nc * m; e += BI_NT) Ms[e] = src[e];
+  for (int i = tid; i < n; i += BI_NT) pos[i] = i;
+  for (int i = tid; i < nc; i += BI_NT) posof[i] = c_beg + i;
+  __syncthreads();
+  for (int cb = warp * QCW; cb < nc; cb += NW * QCW) {   // exact column norms
+    const int c = cb + grp;
+    const bool act = c < nc;
+    double s2 = 0.0;
+    if (act)
+      for (int r = gl; r < m; r += QG) s2 += abs2(Ms[(size_t)c * m + r]);
+    s2 = group_sum<QG>(s2);
+    if (act && gl == 0) nrm[c] = s2;
+  }
+  __syncthreads();
+  auto better = [](double v, int p, double bv, int bp) { return v > bv || (v == bv && p < bp); };
+  int j = 0;
+  for (; j < kmax; ++j) {
+    if (warp == 0) {   // this CTA's candidate
+      double best = -1.0;
+      int bp = n;
+      for (int i = lane; i < nc; i += 32) {
+        const int ps = posof[i];
+        if (ps >= j && better(nrm[i], ps, best, bp)) { best = nrm[i]; bp = ps; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (better(ob, op, best, bp)) { best = ob; bp = op; }
+      }
+      if (lane == 0) {
+        candv[j & 1] = best;
+        candp[j & 1] = bp;
+      }
+    }
+    cl.sync();
+    if (warp == 0) {   // the cluster's pivot (the same in every CTA)
+      double best = -1.0;
+      int bp = n;
+      if (lane < cs) {
+        best = cl.map_shared_rank(candv, lane)[j & 1];
+        bp = cl.map_shared_rank(candp, lane)[j & 1];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (better(ob, op, best, bp)) { best = ob; bp = op; }
+      }
+      if (lane == 0) {
+        const double rjj = sqrt(fmax(best, 0.0));
+        const double r00 = j == 0 ? rjj : s_r00;
+        const int stop = j == 0 ? !(rjj > 0.0) : (rjj <= a.eps * r00);
+        s_rjj = rjj;
+        s_r00 = r00;
+        s_stop = stop;
+        if (!stop) {   // exchange positions j and bp
+          const int pc = pos[bp], cj = pos[j];
+          pos[j] = pc;
+          pos[bp] = cj;
+          if (cj >= c_beg && cj < c_beg + nc) posof[cj - c_beg] = bp;
+          if (pc >= c_beg && pc < c_beg + nc) posof[pc - c_beg] = j;
+          s_p = pc;
+          s_owner = pc / cw;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;   // uniform over the cluster
+    const int pc = s_p, owner = s_owner;
+    const double rjj = s_rjj;
+    if (q == owner) {   // Householder reflector of the pivot column, rows j..m-1
+      const S* col = Ms + (size_t)(pc - c_beg) * m;
+      const S alpha = col[j];
+      const double aa = sqrt(abs2(alpha));
+      const S phase = aa > 0.0 ? scal(alpha, 1.0 / aa) : S(1.0);
+      const S beta = scal(phase, -rjj);
+      for (int r = j + tid; r < m; r += BI_NT) u[r - j] = r == j ? alpha - beta : col[r];
+      if (tid == 0) {
+        fpub[j & 1] = 1.0 / (rjj * (rjj + aa));
+        reinterpret_cast<S*>(g.rdiag)[g.noff[b] + j] = beta;
+      }
+    }
+    cl.sync();
+    if (q != owner) {
+      const S* ru = cl.map_shared_rank(u, owner);
+      for (int r = tid; r < m - j; r += BI_NT) u[r] = ru[r];
+    }
+    if (tid == 0) s_f = cl.map_shared_rank(fpub, owner)[j & 1];
+    __syncthreads();
+    const double f = s_f;
+    for (int cb = warp * QCW; cb < nc; cb += NW * QCW) {   // own unpivoted columns
+      const int c = cb + grp;
+      const bool act = c < nc && posof[c] > j;
+      S* col = Ms + (size_t)(act ? c : 0) * m;
+      S sd = S(0.0);
+      if (act)
+        for (int r = j + gl; r < m; r += QG) sd += conj_(u[r - j]) * col[r];
+      sd = group_sum<QG>(sd);
+      const S fs = scal(sd, f);
+      double s2 = 0.0;
+      if (act)
+        for (int r = j + gl; r < m; r += QG) {
+          const S v = col[r] - u[r - j] * fs;
+          col[r] = v;
+          if (r > j) s2 += abs2(v);
+        }
+      s2 = group_sum<QG>(s2);
+      if (act && gl == 0) nrm[c] = s2;
+    }
+    __syncthreads();
+  }
+  const int k = j;
+  S* dst = Mws + g.moff[b] + (size_t)c_beg * m;
+  for (int e = tid; e < nc * k; e += BI_NT) {
+    const int c = e / k, r = e % k;
+    dst[(size_t)c * m + r] = Ms[(size_t)c * m + r];
+  }
+  if (q == 0) {
+    for (int i = tid; i < n; i += BI_NT) lperm[a.off[b] + i] = pos[i];
+    if (tid == 0) {
+      g.kk[b] = k;
+      g.r00[b] = s_r00;
+    }
+  }
+  cl.sync();   // no CTA leaves while another may still read its shared memory
+}
+
 // 1 if some box of the level is still pivoting at step j.
 __global__ void k_bbid_active(BigId g, const int* n, int nb, int j, int* out) {
   __shared__ int any;
@@ -1230,6 +1393,9 @@ struct BigArgs {
 
 constexpr int BB_NT = 128;
 constexpr int BB_CB = 8;   // columns per CTA in a pivot step
+constexpr int UNS_CB = 16; // columns per CTA of the final column permutation
+constexpr int GJB_NT = 256;          // threads of the blocked Gauss-Jordan kernels
+constexpr int GJB_APPLY_MAXC = 32;   // columns per CTA of k_gjb_apply, at most (shared memory permitting)
 
 template <class S>
 __device__ inline S* bb_A(S* ws, const BigArgs& g, int b) { return ws + g.bo[b]; }
@@ -1330,6 +1496,145 @@ __device__ void bb_gj_body(const BigArgs& g, S* ws, const Dims& dims, int j, int
     const int c = c_beg + cl;
     M[j + (size_t)c * m] = newj[cl];
     if (c == j + 1) pb_out[j] = newj[cl];
+  }
+}
+
+// Blocked form of the same in-place Gauss-Jordan for one large box (the
+// root): the m steps in panels of GJB columns.  k_gjb_panel runs a panel's
+// steps on the panel columns alone (one CTA).  For any other column a, the
+// panel's steps amount to a -> Pi a + V (Pi a)[panel rows], with Pi the
+// panel's row exchanges in order and V = (panel after its steps) - (identity
+// columns of the panel rows) -- the in-place panel holds the panel's
+// transformation applied to the unit vectors it replaced.  k_gjb_apply does
+// that rank-GJB update for all other columns at once.  Two launches per panel
+// instead of a barrier per step.
+constexpr int GJB = 16;
+
+// Magnitude key of a pivot candidate: |x| as ordered bits for real entries
+// (integer compares), |x|^2 for complex ones.
+__device__ inline double piv_key(double x) { return fabs(x); }
+__device__ inline double piv_key(c128 x) { return abs2(x); }
+
+template <class S, class Dims>
+__global__ void __launch_bounds__(GJB_NT) k_gjb_panel(BigArgs g, S* ws, Dims dims, int c0, int in_smem, int* bad) {
+  extern __shared__ __align__(16) unsigned char gp_smem[];
+  __shared__ int s_p, s_fail;
+  __shared__ S s_inv;
+  __shared__ S newj[GJB], rowj[GJB];
+  int m;
+  S *M, *pb_in, *pb_out;
+  int* piv;
+  dims(ws, g, 0, 0, m, M, pb_in, pb_out, piv);
+  const int bw = min(GJB, m - c0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  S* mult = reinterpret_cast<S*>(gp_smem);                  // m entries
+  S* P = in_smem ? mult + m : M + (size_t)c0 * m;           // the panel, ld m
+  if (in_smem)
+    for (int e = tid; e < bw * m; e += GJB_NT) P[e] = M[(size_t)c0 * m + e];
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  for (int jj = 0; jj < bw; ++jj) {
+    const int j = c0 + jj;
+    const S* colj = P + (size_t)jj * m;
+    if (warp == 0) {   // pivot: largest magnitude in rows j..m-1, lowest row on ties
+      long long best = -1;
+      int bi = j;
+      for (int r = j + lane; r < m; r += 32) {
+        const long long v = __double_as_longlong(piv_key(colj[r]));
+        if (v > best) { best = v; bi = r; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        const double bv = __longlong_as_double(best);
+        s_p = bi;
+        if (!(bv > 0.0) || !isfinite(bv)) s_fail = 1;
+        else s_inv = S(1.0) / colj[bi];
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    const int p = s_p;
+    const S inv = s_inv;
+    for (int r = tid; r < m; r += GJB_NT) mult[r] = colj[r == j ? p : (r == p ? j : r)];
+    for (int cl = tid; cl < bw; cl += GJB_NT) {
+      newj[cl] = cl == jj ? inv : P[p + (size_t)cl * m] * inv;
+      rowj[cl] = P[j + (size_t)cl * m];
+    }
+    if (tid == 0) piv[j] = p;
+    __syncthreads();
+    for (int r = tid; r < m; r += GJB_NT) {
+      const S mr = mult[r];
+      for (int cl = 0; cl < bw; ++cl) {
+        S* col = P + (size_t)cl * m;
+        if (r == j) {
+          col[j] = newj[cl];
+          continue;
+        }
+        const S old = cl == jj ? S(0.0) : (r == p ? rowj[cl] : col[r]);
+        col[r] = old - mr * newj[cl];
+      }
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (tid == 0) atomicOr(bad, 1);
+    return;
+  }
+  if (in_smem)
+    for (int e = tid; e < bw * m; e += GJB_NT) M[(size_t)c0 * m + e] = P[e];
+}
+
+// The panel's steps on cpb columns per CTA outside the panel [c0, c0 + bw):
+// the row exchanges, then the rank-bw update with V read from the panel.
+template <class S, class Dims>
+__global__ void __launch_bounds__(GJB_NT) k_gjb_apply(BigArgs g, S* ws, Dims dims, int c0, int cpb, const int* bad) {
+  extern __shared__ __align__(16) unsigned char ga_smem[];
+  __shared__ int sp[GJB];
+  int m;
+  S *M, *pb_in, *pb_out;
+  int* piv;
+  dims(ws, g, 0, 0, m, M, pb_in, pb_out, piv);
+  if (*bad) return;
+  const int bw = min(GJB, m - c0);
+  const int q0 = blockIdx.x * cpb;
+  const int nc = min(cpb, m - bw - q0);
+  if (nc <= 0) return;
+  S* A = reinterpret_cast<S*>(ga_smem);   // nc columns, ld m
+  const int tid = threadIdx.x;
+  auto colof = [&](int cl) { const int q = q0 + cl; return q < c0 ? q : q + bw; };
+  for (int e = tid; e < nc * m; e += GJB_NT) A[e] = M[(e % m) + (size_t)colof(e / m) * m];
+  for (int i = tid; i < bw; i += GJB_NT) sp[i] = piv[c0 + i];
+  __syncthreads();
+  for (int cl = tid; cl < nc; cl += GJB_NT) {   // row exchanges in step order
+    S* col = A + (size_t)cl * m;
+    for (int i = 0; i < bw; ++i) {
+      const int j = c0 + i, p = sp[i];
+      if (p <= j || p >= m) continue;
+      const S t = col[j];
+      col[j] = col[p];
+      col[p] = t;
+    }
+  }
+  __syncthreads();
+  const S* Pan = M + (size_t)c0 * m;
+  for (int r = tid; r < m; r += GJB_NT) {
+    S pr[GJB];
+#pragma unroll
+    for (int i = 0; i < GJB; ++i) pr[i] = i < bw ? Pan[r + (size_t)i * m] : S(0.0);
+    const bool in_panel = r >= c0 && r < c0 + bw;
+    for (int cl = 0; cl < nc; ++cl) {
+      const S* col = A + (size_t)cl * m;
+      S v = in_panel ? S(0.0) : col[r];
+#pragma unroll
+      for (int i = 0; i < GJB; ++i)
+        if (i < bw) v += pr[i] * col[c0 + i];
+      M[r + (size_t)colof(cl) * m] = v;
+    }
   }
 }
 
@@ -1505,26 +1810,34 @@ __global__ void __launch_bounds__(BB_NT) k_bb_gj_cluster(BigArgs g, S* ws, Dims 
 
 // Final column order of a Gauss-Jordan inverse: position c holds column idx[c].
 template <class S, class Dims>
-__global__ void k_bb_unscramble(BigArgs g, S* ws, Dims dims, S* dst_base, int dst_kind, int* idx_ws, int maxm) {
-  const int b = blockIdx.x;
+__global__ void k_bb_unscramble(BigArgs g, S* ws, Dims dims, S* dst_base, int dst_kind, int ucb) {
+  // grid: boxes x ucb column blocks of UNS_CB columns; shared: piv | idx (2 maxm ints)
+  extern __shared__ int us_smem[];
+  const int b = blockIdx.x / ucb, c0 = (blockIdx.x % ucb) * UNS_CB;
   int m;
   S *M, *pb_in, *pb_out;
   int* piv;
   dims(ws, g, b, 0, m, M, pb_in, pb_out, piv);
-  int* idx = idx_ws + (size_t)b * maxm;
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < m; ++c) idx[c] = c;
+  if (c0 >= m) return;
+  int* sp = us_smem;
+  int* idx = us_smem + m;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) {
+    sp[c] = piv[c];
+    idx[c] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)   // the row exchanges, last first, give the column order
     for (int j = m - 1; j >= 0; --j) {
-      int q = piv[j], t = idx[j];
+      const int q = sp[j], t = idx[j];
       idx[j] = idx[q];
       idx[q] = t;
     }
-  }
   __syncthreads();
   S* dst = dims.dest(ws, g, b, dst_base, dst_kind);
-  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
-    int r = (int)(e % m), c = (int)(e / m);
-    dst[e] = M[r + (size_t)idx[c] * m];
+  const int nc = min(UNS_CB, m - c0);
+  for (int e = threadIdx.x; e < nc * m; e += blockDim.x) {
+    const int r = e % m, c = c0 + e / m;
+    dst[r + (size_t)c * m] = M[r + (size_t)idx[c] * m];
   }
 }
 
@@ -1761,6 +2074,79 @@ int make_bar(GridBar* gb, int* flag, cudaStream_t st) {
   return RS_OK;
 }
 
+// Cluster launch of nb boxes, one cluster of cs CTAs per box, each CTA with
+// cw = ceil(width / cs) columns.  Picks cs from {16, 8, 4, 2} to minimise
+// waves x (cw + 4): the co-resident cluster count comes from the occupancy
+// API (clusters of 16 CTAs are few per GPC), the 4 stands for the fixed
+// per-step cost of the barriers.  Returns false when no size fits.
+template <class Kern, class SmemOf>
+bool pick_cluster(Kern kern, int nb, int width, int nt, SmemOf smem_of, cudaStream_t st, int* cs_out, int* cw_out,
+                  size_t* smem_out) {
+  double best = 0.0;
+  bool found = false;
+  for (int cs : {16, 8, 4, 2}) {
+    const int cw = div_up(width, cs);
+    const size_t smem = smem_of(cw);
+    if (smem > (size_t)max_dyn_smem()) continue;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        (cs > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb * cs);
+    cfg.blockDim = dim3(nt);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl < 1) {
+      cudaGetLastError();
+      continue;
+    }
+    const double cost = (double)div_up(nb, ncl) * (cw + 4);
+    if (!found || cost < best) {
+      found = true;
+      best = cost;
+      *cs_out = cs;
+      *cw_out = cw;
+      *smem_out = smem;
+    }
+  }
+  if (found) {   // leave the chosen size's attribute set
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem_out) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+  }
+  return found;
+}
+
+template <class Kern, class... Args>
+int launch_cluster(Kern kern, int nb, int cs, int nt, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nb * cs);
+  cfg.blockDim = dim3(nt);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  RS_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+  RS_CHECK_LAUNCH();
+  return RS_OK;
+}
+
 template <class S>
 int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cudaStream_t st) {
   const int nb = lv.nbox;
@@ -1798,10 +2184,24 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
   const int ncb = div_up(maxn, BI_CB);
   const size_t id_smem = sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax;
   RS_CUDA(cudaFuncSetAttribute(k_bbid_step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)id_smem));
-  // cooperative launch: CB columns per CTA (8 first; then 16 or 32 when the
-  // grid is too large to be resident at once, 4 or 2 when the column cache is
-  // too large for shared memory)
+  // first choice: one thread-block cluster per box, its columns resident in
+  // the CTAs' shared memory
   bool coop_done = false;
+  {
+    int cs = 0, cw = 0;
+    size_t smem = 0;
+    auto smem_of = [&](int w) {
+      return sizeof(S) * ((size_t)w * a.mmax + a.mmax) + sizeof(double) * ((size_t)w + 4) +
+             sizeof(int) * ((size_t)a.nmax + w + 2);
+    };
+    if (pick_cluster(k_bbid_cluster<S>, nb, maxn, BI_NT, smem_of, st, &cs, &cw, &smem)) {
+      RS_TRY(launch_cluster(k_bbid_cluster<S>, nb, cs, BI_NT, smem, st, a, g, Mws, cw, a.lperm));
+      coop_done = true;
+    }
+  }
+  // else a cooperative launch: CB columns per CTA (8 first; then 16 or 32 when
+  // the grid is too large to be resident at once, 4 or 2 when the column
+  // cache is too large for shared memory)
   auto try_coop = [&](auto cbc) -> int {
     constexpr int CB = decltype(cbc)::value;
     if (coop_done) return RS_OK;
@@ -1870,6 +2270,7 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
   const size_t limit = (size_t)max_dyn_smem();
   S* Mws = nullptr;
   a.smem_path = (mbytes + extra <= limit) ? 1 : 0;
+  // boxes too large for one CTA: several CTAs per box
   if (!a.smem_path && a.geo.nproxy <= 256 && sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax <= 200 * 1024)
     return run_id_big<S>(h, lv, a, mrows, st);
   size_t smem = a.smem_path ? mbytes + extra : extra;
@@ -1932,45 +2333,45 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
 template <class S, class Dims>
 int run_gj_cluster(BigArgs g, S* ws, Dims dims, int nsteps, int nb, int* bad, cudaStream_t st, bool* done) {
   *done = false;
-  for (int cs : {16, 8}) {
-    const int cw = div_up(nsteps, cs);
-    if (cw > 64) continue;
-    const size_t smem = sizeof(S) * ((size_t)cw * nsteps + nsteps + 2 * ((size_t)nsteps + 2));
-    if (smem > (size_t)max_dyn_smem()) continue;
-    auto kern = k_bb_gj_cluster<S, Dims>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        (cs > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
-      cudaGetLastError();
-      continue;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nb * cs);
-    cfg.blockDim = dim3(BB_NT);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess || nclusters < 1) {
-      cudaGetLastError();
-      continue;
-    }
-    RS_CUDA(cudaLaunchKernelEx(&cfg, kern, g, ws, dims, nsteps, cw, bad));
-    RS_CHECK_LAUNCH();
-    *done = true;
-    return RS_OK;
-  }
+  int cs = 0, cw = 0;
+  size_t smem = 0;
+  auto smem_of = [&](int w) -> size_t {
+    if (w > 64) return ~(size_t)0;   // k_bb_gj_cluster keeps at most 64 columns' multipliers
+    return sizeof(S) * ((size_t)w * nsteps + nsteps + 2 * ((size_t)nsteps + 2));
+  };
+  if (!pick_cluster(k_bb_gj_cluster<S, Dims>, nb, nsteps, BB_NT, smem_of, st, &cs, &cw, &smem)) return RS_OK;
+  RS_TRY(launch_cluster(k_bb_gj_cluster<S, Dims>, nb, cs, BB_NT, smem, st, g, ws, dims, nsteps, cw, bad));
+  *done = true;
   return RS_OK;
 }
 
 template <class S, class Dims>
 int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int ncb, size_t smem, int* bad,
                  cudaStream_t st) {
+  if (nb == 1 && nsteps >= 128) {   // one large box: blocked, two launches per panel of GJB steps
+    const int m = nsteps;
+    const size_t psmem = sizeof(S) * (size_t)m * (GJB + 1);
+    const int in_smem = psmem <= (size_t)max_dyn_smem() ? 1 : 0;
+    const size_t pa_smem = in_smem ? psmem : sizeof(S) * (size_t)m;
+    RS_CUDA(cudaFuncSetAttribute(k_gjb_panel<S, Dims>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pa_smem));
+    // columns per CTA: enough CTAs for two per SM, within shared memory
+    const int nout = m - std::min(GJB, m);
+    int cpb = std::max(1, nout / (2 * num_sms()));
+    cpb = std::min(cpb, std::min(GJB_APPLY_MAXC, (int)((size_t)max_dyn_smem() / (sizeof(S) * (size_t)m))));
+    if (cpb < 1) return fail(RS_ERR_ARG, "root block too large for the blocked inversion (m=%d)", m);
+    const size_t ap_smem = sizeof(S) * (size_t)m * cpb;
+    RS_CUDA(cudaFuncSetAttribute(k_gjb_apply<S, Dims>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ap_smem));
+    for (int c0 = 0; c0 < m; c0 += GJB) {
+      k_gjb_panel<S, Dims><<<1, GJB_NT, pa_smem, st>>>(g, ws, dims, c0, in_smem, bad);
+      RS_CHECK_LAUNCH();
+      const int no = m - std::min(GJB, m - c0);
+      if (no > 0) {
+        k_gjb_apply<S, Dims><<<div_up(no, cpb), GJB_NT, ap_smem, st>>>(g, ws, dims, c0, cpb, bad);
+        RS_CHECK_LAUNCH();
+      }
+    }
+    return RS_OK;
+  }
   if (nb >= 2) {   // one cluster per box; a single box (the root) spreads over more SMs cooperatively
     bool done = false;
     RS_TRY((run_gj_cluster<S, Dims>(g, ws, dims, nsteps, nb, bad, st, &done)));
@@ -2020,10 +2421,8 @@ int run_factor_big(Handle* h, Level& lv, FaArgs a, const Level* child, double by
   RS_TRY(upload(h, &dbo, bo, st));
   g.bo = dbo;
   S* ws = nullptr;
-  int* idx = nullptr;
   const int maxn = lv.maxn;
   RS_CUDA(cudaMallocAsync((void**)&ws, sizeof(S) * std::max<int64_t>(1, acc), st));
-  RS_CUDA(cudaMallocAsync((void**)&idx, sizeof(int) * (size_t)nb * maxn, st));
   const S* cL = child ? (const S*)child->Lam : nullptr;
   double fl = 0.0;
   for (int b = 0; b < nb; ++b) {
@@ -2037,7 +2436,9 @@ int run_factor_big(Handle* h, Level& lv, FaArgs a, const Level* child, double by
   const int ncb = div_up(maxn, BB_CB);
   const size_t gj_smem = sizeof(S) * (size_t)maxn;
   RS_TRY((run_gj_steps<S, DimsD>(h, g, ws, DimsD{}, maxn, nb, ncb, gj_smem, a.bad, st)));
-  k_bb_unscramble<S, DimsD><<<nb, BB_NT, 0, st>>>(g, ws, DimsD{}, (S*)nullptr, 0, idx, maxn);
+  const int ucb = div_up(maxn, UNS_CB);
+  const size_t us_smem = 2 * sizeof(int) * (size_t)maxn;
+  k_bb_unscramble<S, DimsD><<<nb * ucb, BB_NT, us_smem, st>>>(g, ws, DimsD{}, (S*)nullptr, 0, ucb);
   RS_CHECK_LAUNCH();
   if (lv.maxk > 0) {
     k_bb_X<S><<<nb * maxk, BB_NT, 0, st>>>(a, g, (const S*)lv.T, ws, maxk);
@@ -2048,7 +2449,7 @@ int run_factor_big(Handle* h, Level& lv, FaArgs a, const Level* child, double by
     DimsY dy{lv.lamoff};
     const size_t gy_smem = sizeof(S) * (size_t)maxk;
     RS_TRY((run_gj_steps<S, DimsY>(h, g, ws, dy, maxk, nb, nck, gy_smem, a.bad, st)));
-    k_bb_unscramble<S, DimsY><<<nb, BB_NT, 0, st>>>(g, ws, dy, (S*)lv.Lam, 1, idx, maxn);
+    k_bb_unscramble<S, DimsY><<<nb * ucb, BB_NT, us_smem, st>>>(g, ws, dy, (S*)lv.Lam, 1, ucb);
     RS_CHECK_LAUNCH();
   }
   const size_t pr_smem = sizeof(S) * (size_t)std::max(1, maxk);
@@ -2057,7 +2458,6 @@ int run_factor_big(Handle* h, Level& lv, FaArgs a, const Level* child, double by
   RS_CHECK_LAUNCH();
   prof_end(P_FACTOR, st, by, fl);
   RS_CUDA(cudaFreeAsync(ws, st));
-  RS_CUDA(cudaFreeAsync(idx, st));
   return RS_OK;
 }
 
