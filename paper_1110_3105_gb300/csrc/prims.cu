@@ -103,7 +103,7 @@ int scan_impl(const In* d_in, int64_t* d_out, int64_t n, int64_t* total, cudaStr
 }
 
 // ------------------------------------------------------------ radix sort
-constexpr int RS_TILE = 1024;      // elements per warp tile (32 chunks of 32)
+constexpr int RS_TILE = 256;       // elements per warp tile (8 chunks of 32)
 constexpr int RS_WARPS = 4;        // warps (tiles) per block
 
 __global__ void k_radix_hist(const uint64_t* keys, int n, int shift, int ntiles, int* counts) {

@@ -826,31 +826,33 @@ __global__ void __launch_bounds__(BI_NT) k_bbid_coop(IdArgs a, BigId g, S* Mws, 
 // (one cluster per box).  CTA q keeps the box's physical columns
 // [q cw, q cw + cw) in shared memory for the whole factorization.  Each step:
 // every CTA publishes its best trailing column (exact norm, lowest position on
-// ties), all CTAs read the candidates through distributed shared memory and
-// agree on the pivot; the CTA that owns the pivot column publishes the
-// Householder vector; every CTA applies it to its own columns and recomputes
-// their trailing norms.  Two cluster barriers per step and no grid-wide
-// barrier.  Output as the cooperative kernel: rows 0..k-1 of the columns in
+// ties) with that column's row-j entry; after one cluster barrier all CTAs
+// read the candidates through distributed shared memory, agree on the pivot
+// and form the same reflector coefficients, copy the pivot column from its
+// owner (which does not change it this step), apply the reflector to their
+// own columns and recompute their trailing norms.  One cluster barrier per
+// step and no grid-wide barrier.  Output as the cooperative kernel: rows 0..k-1 of the columns in
 // Mws, R_jj in rdiag, the rank in kk, the column order in lperm.
 template <class S>
 __global__ void __launch_bounds__(BI_NT) k_bbid_cluster(IdArgs a, BigId g, S* Mws, int cw, int* lperm) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char bc_smem[];
-  __shared__ double s_rjj, s_r00, s_f;
+  __shared__ double s_r00, s_f;
+  __shared__ S s_u0;
   __shared__ int s_p, s_stop, s_owner;
   const int cs = (int)cl.num_blocks(), q = (int)cl.block_rank();
   const int b = blockIdx.x / cs;
   const int n = a.n[b], m = g.m[b];
   const int kmax = min(m, n);
   const int c_beg = q * cw, nc = max(0, min(n, c_beg + cw) - c_beg);
-  // Ms[cw][m] | u[mmax] | nrm[cw] | candv[2] | fpub[2] | pos[nmax] | posof[cw] | candp[2]
+  // Ms[cw][m] | u[mmax] | canda[2] | nrm[cw] | candv[2] | pos[nmax] | posof[cw] | candp[2]
   S* Ms = reinterpret_cast<S*>(bc_smem);
   S* u = Ms + (size_t)cw * a.mmax;
-  double* nrm = reinterpret_cast<double*>(u + a.mmax);
+  S* canda = u + a.mmax;
+  double* nrm = reinterpret_cast<double*>(canda + 2);
   double* candv = nrm + cw;
-  double* fpub = candv + 2;
-  int* pos = reinterpret_cast<int*>(fpub + 2);
+  int* pos = reinterpret_cast<int*>(candv + 2);
   int* posof = pos + a.nmax;
   int* candp = posof + cw;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -876,76 +878,74 @@ __global__ void __launch_bounds__(BI_NT) k_bbid_cluster(IdArgs a, BigId g, S* Mw
   for (; j < kmax; ++j) {
     if (warp == 0) {   // this CTA's candidate
       double best = -1.0;
-      int bp = n;
+      int bp = n, bi = 0;
       for (int i = lane; i < nc; i += 32) {
         const int ps = posof[i];
-        if (ps >= j && better(nrm[i], ps, best, bp)) { best = nrm[i]; bp = ps; }
+        if (ps >= j && better(nrm[i], ps, best, bp)) { best = nrm[i]; bp = ps; bi = i; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const double ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-        if (better(ob, op, best, bp)) { best = ob; bp = op; }
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (better(ob, op, best, bp)) { best = ob; bp = op; bi = oi; }
       }
       if (lane == 0) {
         candv[j & 1] = best;
         candp[j & 1] = bp;
+        canda[j & 1] = nc > 0 ? Ms[(size_t)bi * m + j] : S(0.0);
       }
     }
     cl.sync();
-    if (warp == 0) {   // the cluster's pivot (the same in every CTA)
+    if (warp == 0) {   // the cluster's pivot and reflector (the same in every CTA)
       double best = -1.0;
-      int bp = n;
+      int bp = n, br = 0;
       if (lane < cs) {
         best = cl.map_shared_rank(candv, lane)[j & 1];
         bp = cl.map_shared_rank(candp, lane)[j & 1];
+        br = lane;
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const double ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-        if (better(ob, op, best, bp)) { best = ob; bp = op; }
+        const int orr = __shfl_xor_sync(0xffffffffu, br, o);
+        if (better(ob, op, best, bp)) { best = ob; bp = op; br = orr; }
       }
       if (lane == 0) {
         const double rjj = sqrt(fmax(best, 0.0));
         const double r00 = j == 0 ? rjj : s_r00;
         const int stop = j == 0 ? !(rjj > 0.0) : (rjj <= a.eps * r00);
-        s_rjj = rjj;
         s_r00 = r00;
         s_stop = stop;
-        if (!stop) {   // exchange positions j and bp
-          const int pc = pos[bp], cj = pos[j];
+        if (!stop) {
+          // Householder reflector H = I - f u u^H of the pivot column (rows
+          // j..m-1): beta = -phase(alpha) rjj, u = x - beta e_1
+          const S alpha = cl.map_shared_rank(canda, br)[j & 1];
+          const double aa = sqrt(abs2(alpha));
+          const S phase = aa > 0.0 ? scal(alpha, 1.0 / aa) : S(1.0);
+          const S beta = scal(phase, -rjj);
+          s_u0 = alpha - beta;
+          s_f = 1.0 / (rjj * (rjj + aa));
+          const int pc = pos[bp], cj = pos[j];   // exchange positions j and bp
           pos[j] = pc;
           pos[bp] = cj;
           if (cj >= c_beg && cj < c_beg + nc) posof[cj - c_beg] = bp;
           if (pc >= c_beg && pc < c_beg + nc) posof[pc - c_beg] = j;
           s_p = pc;
           s_owner = pc / cw;
+          if (q == pc / cw) reinterpret_cast<S*>(g.rdiag)[g.noff[b] + j] = beta;
         }
       }
     }
     __syncthreads();
     if (s_stop) break;   // uniform over the cluster
     const int pc = s_p, owner = s_owner;
-    const double rjj = s_rjj;
-    if (q == owner) {   // Householder reflector of the pivot column, rows j..m-1
-      const S* col = Ms + (size_t)(pc - c_beg) * m;
-      const S alpha = col[j];
-      const double aa = sqrt(abs2(alpha));
-      const S phase = aa > 0.0 ? scal(alpha, 1.0 / aa) : S(1.0);
-      const S beta = scal(phase, -rjj);
-      for (int r = j + tid; r < m; r += BI_NT) u[r - j] = r == j ? alpha - beta : col[r];
-      if (tid == 0) {
-        fpub[j & 1] = 1.0 / (rjj * (rjj + aa));
-        reinterpret_cast<S*>(g.rdiag)[g.noff[b] + j] = beta;
-      }
+    {   // u from the pivot column, which its owner leaves unchanged this step
+      const S* pcol = cl.map_shared_rank(Ms + (size_t)(pc - owner * cw) * m, owner);
+      for (int r = j + 1 + tid; r < m; r += BI_NT) u[r - j] = pcol[r];
+      if (tid == 0) u[0] = s_u0;
     }
-    cl.sync();
-    if (q != owner) {
-      const S* ru = cl.map_shared_rank(u, owner);
-      for (int r = tid; r < m - j; r += BI_NT) u[r] = ru[r];
-    }
-    if (tid == 0) s_f = cl.map_shared_rank(fpub, owner)[j & 1];
     __syncthreads();
     const double f = s_f;
     for (int cb = warp * QCW; cb < nc; cb += NW * QCW) {   // own unpivoted columns
@@ -2191,7 +2191,7 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
     int cs = 0, cw = 0;
     size_t smem = 0;
     auto smem_of = [&](int w) {
-      return sizeof(S) * ((size_t)w * a.mmax + a.mmax) + sizeof(double) * ((size_t)w + 4) +
+      return sizeof(S) * ((size_t)w * a.mmax + a.mmax + 2) + sizeof(double) * ((size_t)w + 2) +
              sizeof(int) * ((size_t)a.nmax + w + 2);
     };
     if (pick_cluster(k_bbid_cluster<S>, nb, maxn, BI_NT, smem_of, st, &cs, &cw, &smem)) {

@@ -58,17 +58,40 @@ __global__ void k_bbox_partial(const double* pts, int64_t n, int dim, double* pa
 }
 
 // Root box from the partials: out = {c0, c1, c2, a, nonfinite flag}.
+// One CTA of BB_NT threads: strided partial reductions, then a tree.
 __global__ void k_root_box(const double* part, int nblk, int dim, double* out) {
-  if (threadIdx.x != 0) return;
+  __shared__ double smin[3][BB_NT], smax[3][BB_NT];
+  __shared__ int sbad;
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   int bad = 0;
-  for (int b = 0; b < nblk; ++b)
+  if (threadIdx.x == 0) sbad = 0;
+  for (int b = threadIdx.x; b < nblk; b += BB_NT)
     for (int d = 0; d < 3; ++d) {
       lo[d] = fmin(lo[d], part[b * 6 + d]);
-      double h = part[b * 6 + 3 + d];
+      const double h = part[b * 6 + 3 + d];
       if (isnan(h)) bad = 1;
       hi[d] = fmax(hi[d], h);
     }
+  for (int d = 0; d < 3; ++d) {
+    smin[d][threadIdx.x] = lo[d];
+    smax[d][threadIdx.x] = hi[d];
+  }
+  __syncthreads();
+  if (bad) sbad = 1;
+  for (int o = BB_NT / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+      for (int d = 0; d < 3; ++d) {
+        smin[d][threadIdx.x] = fmin(smin[d][threadIdx.x], smin[d][threadIdx.x + o]);
+        smax[d][threadIdx.x] = fmax(smax[d][threadIdx.x], smax[d][threadIdx.x + o]);
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = smin[d][0];
+    hi[d] = smax[d][0];
+  }
+  bad = sbad;
   double ext = 0.0;
   for (int d = 0; d < dim; ++d) {
     out[d] = __dmul_rn(__dadd_rn(lo[d], hi[d]), 0.5);
@@ -299,7 +322,7 @@ int build_tree(Handle* h, const double* d_pts_in, cudaStream_t st) {
   RS_TRY(dalloc_t(h, &box, 8));
   k_bbox_partial<<<nblk, BB_NT, 0, st>>>(d_pts_in, n, dim, part);
   RS_CHECK_LAUNCH();
-  k_root_box<<<1, 32, 0, st>>>(part, nblk, dim, box);
+  k_root_box<<<1, BB_NT, 0, st>>>(part, nblk, dim, box);
   RS_CHECK_LAUNCH();
   double hbox[5];
   RS_CUDA(cudaMemcpyAsync(hbox, box, sizeof(hbox), cudaMemcpyDeviceToHost, st));
