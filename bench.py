@@ -52,7 +52,7 @@ def peaks():
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per
 # kernel category, from the ncu captures summarised in profiles/ (the leaf-level
 # launch of the bench workload); None where no capture of the current kernel exists.
-NCU_TRAFFIC = {"id": (48085248 + 571392,
+NCU_TRAFFIC = {"id": (48086272 + 795648,
                       "k_id leaf-level launch (profiles/k_id_leaf_laplace2d_starfish_131072.md): "
                       "dram__bytes_read.sum + dram__bytes_write.sum")}
 
