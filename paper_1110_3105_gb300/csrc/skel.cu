@@ -1305,8 +1305,11 @@ __global__ void __launch_bounds__(NT) k_factor_smem(FaArgs a, const S* Tpool, co
   S* mult = Y + (size_t)k * k;
   int* piv = reinterpret_cast<int*>(mult + n);
 
-  for (int e = tid; e < n * n; e += NT) {
-    int r = e % n, c = e / n;
+  // D is symmetric (the kernels are, and so are the children's Lambda blocks
+  // up to rounding): one triangle, mirrored
+  for (int e = tid; e < n * (n + 1) / 2; e += NT) {
+    int r, c;
+    tri_index(e, r, c);
     int pr = a.act[off + r], pc = a.act[off + c];
     S v;
     if (a.leaf_level) {
@@ -1321,8 +1324,13 @@ __global__ void __launch_bounds__(NT) k_factor_smem(FaArgs a, const S* Tpool, co
         v = offdiag_entry<S>(a.kp, a.pts, pr, pc);
       }
     }
-    Dv[e] = v;
-    emit_fwd<S>(a, b, n, k, r, c, v, !a.leaf_level && a.owner[off + r] == a.owner[off + c]);
+    const bool same = !a.leaf_level && a.owner[off + r] == a.owner[off + c];
+    Dv[r + c * n] = v;
+    emit_fwd<S>(a, b, n, k, r, c, v, same);
+    if (r != c) {
+      Dv[c + r * n] = v;
+      emit_fwd<S>(a, b, n, k, c, r, v, same);
+    }
   }
   __syncthreads();
   gj_inplace<S, NT>(Dv, n, mult, piv, a.bad);    // Dv = D^-1
@@ -1524,7 +1532,8 @@ __global__ void __launch_bounds__(GJB_NT) k_gjb_panel(BigArgs g, S* ws, Dims dim
   int m;
   S *M, *pb_in, *pb_out;
   int* piv;
-  dims(ws, g, 0, 0, m, M, pb_in, pb_out, piv);
+  dims(ws, g, blockIdx.x, 0, m, M, pb_in, pb_out, piv);   // one CTA per box
+  if (c0 >= m) return;
   const int bw = min(GJB, m - c0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   S* mult = reinterpret_cast<S*>(gp_smem);                  // m entries
@@ -1591,17 +1600,19 @@ __global__ void __launch_bounds__(GJB_NT) k_gjb_panel(BigArgs g, S* ws, Dims dim
 
 // The panel's steps on cpb columns per CTA outside the panel [c0, c0 + bw):
 // the row exchanges, then the rank-bw update with V read from the panel.
+// Grid: boxes x apb column blocks.
 template <class S, class Dims>
-__global__ void __launch_bounds__(GJB_NT) k_gjb_apply(BigArgs g, S* ws, Dims dims, int c0, int cpb, const int* bad) {
+__global__ void __launch_bounds__(GJB_NT) k_gjb_apply(BigArgs g, S* ws, Dims dims, int c0, int cpb, int apb,
+                                                      const int* bad) {
   extern __shared__ __align__(16) unsigned char ga_smem[];
   __shared__ int sp[GJB];
   int m;
   S *M, *pb_in, *pb_out;
   int* piv;
-  dims(ws, g, 0, 0, m, M, pb_in, pb_out, piv);
-  if (*bad) return;
+  dims(ws, g, blockIdx.x / apb, 0, m, M, pb_in, pb_out, piv);
+  if (*bad || c0 >= m) return;
   const int bw = min(GJB, m - c0);
-  const int q0 = blockIdx.x * cpb;
+  const int q0 = (blockIdx.x % apb) * cpb;
   const int nc = min(cpb, m - bw - q0);
   if (nc <= 0) return;
   S* A = reinterpret_cast<S*>(ga_smem);   // nc columns, ld m
@@ -2348,34 +2359,35 @@ int run_gj_cluster(BigArgs g, S* ws, Dims dims, int nsteps, int nb, int* bad, cu
 template <class S, class Dims>
 int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int ncb, size_t smem, int* bad,
                  cudaStream_t st) {
-  if (nb == 1 && nsteps >= 128) {   // one large box: blocked, two launches per panel of GJB steps
-    const int m = nsteps;
+  if (nb >= 2) {   // one cluster per box when the columns fit
+    bool done = false;
+    RS_TRY((run_gj_cluster<S, Dims>(g, ws, dims, nsteps, nb, bad, st, &done)));
+    if (done) return RS_OK;
+  }
+  if (nsteps >= 128) {   // the root, or boxes too large for a cluster: blocked, two launches per panel
+    const int m = nsteps;   // the largest box
     const size_t psmem = sizeof(S) * (size_t)m * (GJB + 1);
     const int in_smem = psmem <= (size_t)max_dyn_smem() ? 1 : 0;
     const size_t pa_smem = in_smem ? psmem : sizeof(S) * (size_t)m;
     RS_CUDA(cudaFuncSetAttribute(k_gjb_panel<S, Dims>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pa_smem));
     // columns per CTA: enough CTAs for two per SM, within shared memory
     const int nout = m - std::min(GJB, m);
-    int cpb = std::max(1, nout / (2 * num_sms()));
+    int cpb = std::max(1, nb * nout / (2 * num_sms()));
     cpb = std::min(cpb, std::min(GJB_APPLY_MAXC, (int)((size_t)max_dyn_smem() / (sizeof(S) * (size_t)m))));
     if (cpb < 1) return fail(RS_ERR_ARG, "root block too large for the blocked inversion (m=%d)", m);
     const size_t ap_smem = sizeof(S) * (size_t)m * cpb;
     RS_CUDA(cudaFuncSetAttribute(k_gjb_apply<S, Dims>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ap_smem));
     for (int c0 = 0; c0 < m; c0 += GJB) {
-      k_gjb_panel<S, Dims><<<1, GJB_NT, pa_smem, st>>>(g, ws, dims, c0, in_smem, bad);
+      k_gjb_panel<S, Dims><<<nb, GJB_NT, pa_smem, st>>>(g, ws, dims, c0, in_smem, bad);
       RS_CHECK_LAUNCH();
       const int no = m - std::min(GJB, m - c0);
       if (no > 0) {
-        k_gjb_apply<S, Dims><<<div_up(no, cpb), GJB_NT, ap_smem, st>>>(g, ws, dims, c0, cpb, bad);
+        const int apb = div_up(no, cpb);
+        k_gjb_apply<S, Dims><<<nb * apb, GJB_NT, ap_smem, st>>>(g, ws, dims, c0, cpb, apb, bad);
         RS_CHECK_LAUNCH();
       }
     }
     return RS_OK;
-  }
-  if (nb >= 2) {   // one cluster per box; a single box (the root) spreads over more SMs cooperatively
-    bool done = false;
-    RS_TRY((run_gj_cluster<S, Dims>(g, ws, dims, nsteps, nb, bad, st, &done)));
-    if (done) return RS_OK;
   }
   const size_t csmem = sizeof(S) * (size_t)(BB_CB + 1) * nsteps;   // own columns + pivot column (m <= nsteps)
   const bool co_ok = csmem <= (size_t)max_dyn_smem();
