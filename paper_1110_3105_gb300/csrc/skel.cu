@@ -1598,6 +1598,125 @@ __global__ void __launch_bounds__(GJB_NT) k_gjb_panel(BigArgs g, S* ws, Dims dim
     for (int e = tid; e < bw * m; e += GJB_NT) M[(size_t)c0 * m + e] = P[e];
 }
 
+// The panel steps of k_gjb_panel on a thread-block cluster per box: CTA q
+// keeps rows [q rpc, q rpc + rpc) of the panel in shared memory.  A step:
+// every CTA publishes its largest candidate (magnitude bits, lowest row on
+// ties); after a cluster barrier all CTAs agree on the pivot row p and read
+// rows p and j of the panel from their owners; after a second barrier (no
+// row is changed while it may be read) each CTA applies the step to its rows.
+template <class S, class Dims>
+__global__ void __launch_bounds__(GJB_NT) k_gjb_panel_cl(BigArgs g, S* ws, Dims dims, int c0, int rpc, int* bad) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char gc_smem[];
+  __shared__ long long s_key[GJB_NT / 32];
+  __shared__ int s_row[GJB_NT / 32];
+  __shared__ long long cand_k[2];
+  __shared__ int cand_r[2];
+  __shared__ int s_p, s_fail;
+  __shared__ S rowp[GJB], rowj[GJB], newj[GJB];
+  const int cs = (int)cl.num_blocks(), q = (int)cl.block_rank();
+  int m;
+  S *M, *pb_in, *pb_out;
+  int* piv;
+  dims(ws, g, blockIdx.x / cs, 0, m, M, pb_in, pb_out, piv);
+  if (c0 >= m) return;   // uniform over the cluster (same box)
+  const int bw = min(GJB, m - c0);
+  const int r0 = q * rpc, nr = max(0, min(m, r0 + rpc) - r0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  S* P = reinterpret_cast<S*>(gc_smem);   // [bw][rpc]: column cl of the panel, local rows
+  for (int e = tid; e < bw * nr; e += GJB_NT) {
+    const int c = e / nr, rl = e % nr;
+    P[(size_t)c * rpc + rl] = M[(r0 + rl) + (size_t)(c0 + c) * m];
+  }
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  for (int jj = 0; jj < bw; ++jj) {
+    const int j = c0 + jj;
+    const S* colj = P + (size_t)jj * rpc;
+    {   // this CTA's candidate among its rows >= j
+      long long best = -1;
+      int bi = m;
+      for (int rl = tid; rl < nr; rl += GJB_NT) {
+        if (r0 + rl < j) continue;
+        const long long v = __double_as_longlong(piv_key(colj[rl]));
+        if (v > best) { best = v; bi = r0 + rl; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { s_key[warp] = best; s_row[warp] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        long long bk = s_key[0];
+        int br = s_row[0];
+        for (int w = 1; w < GJB_NT / 32; ++w)
+          if (s_key[w] > bk || (s_key[w] == bk && s_row[w] < br)) { bk = s_key[w]; br = s_row[w]; }
+        cand_k[jj & 1] = bk;
+        cand_r[jj & 1] = br;
+      }
+    }
+    cl.sync();
+    if (warp == 0) {   // the pivot (the same in every CTA) and rows p, j
+      long long best = -1;
+      int bi = m;
+      if (lane < cs) {
+        best = cl.map_shared_rank(cand_k, lane)[jj & 1];
+        bi = cl.map_shared_rank(cand_r, lane)[jj & 1];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      const double bv = __longlong_as_double(best);
+      const bool ok = bv > 0.0 && isfinite(bv) && bi < m;
+      if (lane == 0) {
+        s_fail = ok ? 0 : 1;
+        s_p = bi;
+      }
+      if (ok && lane < bw) {
+        const int op = bi / rpc, oj = j / rpc;
+        rowp[lane] = cl.map_shared_rank(P, op)[(size_t)lane * rpc + (bi - op * rpc)];
+        rowj[lane] = cl.map_shared_rank(P, oj)[(size_t)lane * rpc + (j - oj * rpc)];
+      }
+    }
+    cl.sync();   // rows p and j have been read everywhere
+    if (s_fail) break;   // uniform over the cluster
+    const int p = s_p;
+    const S inv = S(1.0) / rowp[jj];
+    if (tid < bw) newj[tid] = tid == jj ? inv : rowp[tid] * inv;
+    if (q == 0 && tid == 0) piv[j] = p;
+    __syncthreads();
+    for (int rl = tid; rl < nr; rl += GJB_NT) {
+      const int r = r0 + rl;
+      if (r == j) {
+        for (int c = 0; c < bw; ++c) P[(size_t)c * rpc + rl] = newj[c];
+        continue;
+      }
+      const S mr = r == p ? rowj[jj] : colj[rl];
+      for (int c = 0; c < bw; ++c) {
+        S* pc = P + (size_t)c * rpc + rl;
+        const S old = c == jj ? S(0.0) : (r == p ? rowj[c] : *pc);
+        *pc = old - mr * newj[c];
+      }
+    }
+    __syncthreads();
+  }
+  if (s_fail) {
+    if (q == 0 && tid == 0) atomicOr(bad, 1);
+    return;
+  }
+  for (int e = tid; e < bw * nr; e += GJB_NT) {
+    const int c = e / nr, rl = e % nr;
+    M[(r0 + rl) + (size_t)(c0 + c) * m] = P[(size_t)c * rpc + rl];
+  }
+}
+
 // The panel's steps on cpb columns per CTA outside the panel [c0, c0 + bw):
 // the row exchanges, then the rank-bw update with V read from the panel.
 // Grid: boxes x apb column blocks.
@@ -2366,6 +2485,14 @@ int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int
   }
   if (nsteps >= 128) {   // the root, or boxes too large for a cluster: blocked, two launches per panel
     const int m = nsteps;   // the largest box
+    // panel steps on a cluster per box (rows split over its CTAs), else one CTA
+    int pcs = 0, prpc = 0;
+    size_t pc_smem = 0;
+    {
+      auto smem_of = [&](int rows) { return sizeof(S) * (size_t)rows * GJB; };
+      int cw = 0;
+      if (pick_cluster(k_gjb_panel_cl<S, Dims>, nb, m, GJB_NT, smem_of, st, &pcs, &cw, &pc_smem)) prpc = cw;
+    }
     const size_t psmem = sizeof(S) * (size_t)m * (GJB + 1);
     const int in_smem = psmem <= (size_t)max_dyn_smem() ? 1 : 0;
     const size_t pa_smem = in_smem ? psmem : sizeof(S) * (size_t)m;
@@ -2378,8 +2505,12 @@ int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int
     const size_t ap_smem = sizeof(S) * (size_t)m * cpb;
     RS_CUDA(cudaFuncSetAttribute(k_gjb_apply<S, Dims>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ap_smem));
     for (int c0 = 0; c0 < m; c0 += GJB) {
-      k_gjb_panel<S, Dims><<<nb, GJB_NT, pa_smem, st>>>(g, ws, dims, c0, in_smem, bad);
-      RS_CHECK_LAUNCH();
+      if (prpc > 0) {
+        RS_TRY(launch_cluster(k_gjb_panel_cl<S, Dims>, nb, pcs, GJB_NT, pc_smem, st, g, ws, dims, c0, prpc, bad));
+      } else {
+        k_gjb_panel<S, Dims><<<nb, GJB_NT, pa_smem, st>>>(g, ws, dims, c0, in_smem, bad);
+        RS_CHECK_LAUNCH();
+      }
       const int no = m - std::min(GJB, m - c0);
       if (no > 0) {
         const int apb = div_up(no, cpb);
