@@ -2667,16 +2667,9 @@ int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t 
 }
 
 // Status words: [0] a singular or non-finite pivot, [1] a grid barrier gave
-// up, both in the skeletonization; [2], [3] the same in the factorization
-// (which runs on its own stream and is checked once at the end).
-int check_bad(Handle* h, cudaStream_t st, const char* where) {
-  int bad[2] = {0, 0};
-  RS_CUDA(cudaMemcpyAsync(bad, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-  RS_CUDA(cudaStreamSynchronize(st));
-  if (bad[1]) return fail(RS_ERR_TIMEOUT, "rs_build: a grid barrier wait ran out during %s", where);
-  if (bad[0]) return fail(RS_ERR_SINGULAR, "rs_build: singular block during %s", where);
-  return RS_OK;
-}
+// up, both in the skeletonization (checked per depth with the ranks); [2],
+// [3] the same in the factorization (which runs on its own stream and is
+// checked once at the end).
 
 // Sizes and offsets of the factor pools of a level (host), then allocate.
 int alloc_factors(Handle* h, Level& lv, cudaStream_t st) {
@@ -2832,12 +2825,16 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st, cudaStream_t fs) {
   a.qr_df = h->id_df && !h->cplx;
   if (h->cplx) RS_TRY(run_id<c128>(h, lv, a, mrows, msum, st));
   else RS_TRY(run_id<double>(h, lv, a, mrows, msum, st));
-  RS_TRY(check_bad(h, st, "skeletonization"));
 
-  // ranks -> skeleton offsets in the parent depth
+  // ranks -> skeleton offsets in the parent depth (one synchronisation for
+  // the ranks and the skeletonization's status words)
   lv.h_k.resize(nbox);
+  int bad[2] = {0, 0};
   RS_CUDA(cudaMemcpyAsync(lv.h_k.data(), lv.k, sizeof(int) * nbox, cudaMemcpyDeviceToHost, st));
+  RS_CUDA(cudaMemcpyAsync(bad, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   RS_CUDA(cudaStreamSynchronize(st));
+  if (bad[1]) return fail(RS_ERR_TIMEOUT, "rs_build: a grid barrier wait ran out during skeletonization");
+  if (bad[0]) return fail(RS_ERR_SINGULAR, "rs_build: singular block during skeletonization");
   if (prof_on()) {
     double fl = 0.0, by = 0.0;
     for (int b = 0; b < nbox; ++b) {
