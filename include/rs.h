@@ -54,7 +54,8 @@ enum rs_status {
 enum rs_kernel {
   RS_LAPLACE2D = 0,   /* G = -(1/2 pi) log r          (eq. 2d-laplace)   */
   RS_HELMHOLTZ2D = 1, /* G = (i/4) H0^(1)(k r)         (eq. 2d-helmholtz) */
-  RS_LAPLACE3D = 2    /* G = 1 / (4 pi r)              (eq. 3d-laplace)   */
+  RS_LAPLACE3D = 2,   /* G = 1 / (4 pi r)              (eq. 3d-laplace)   */
+  RS_HELMHOLTZ3D = 3  /* G = e^{i k r} / (4 pi r)      (eq. 3d-helmholtz) */
 };
 
 enum rs_precision {
@@ -80,7 +81,7 @@ enum rs_id_arith {
 
 typedef struct {
   int kernel_id;      /* enum rs_kernel */
-  double k_wave;      /* Helmholtz wavenumber k (ignored otherwise) */
+  double k_wave;      /* Helmholtz wavenumber k > 0 (ignored otherwise) */
   double weight;      /* w > 0 */
   int proxy_n;        /* > 0; 3D needs 6 g^2 */
   double proxy_ratio; /* > 1 */
@@ -103,7 +104,9 @@ typedef struct {
 
 /* Build the compressed inverse.
  *   pts    dim x N column-major (point i at pts[i*dim .. i*dim+dim-1]), host
- *          or device; N >= 1; dim 2 or 3 (3 only with RS_LAPLACE3D).
+ *          or device; N >= 1; dim 3 with RS_LAPLACE3D and RS_HELMHOLTZ3D,
+ *          dim 2 with the 2D kernels.  The Helmholtz kernels build and solve
+ *          in complex arithmetic (interleaved re, im).
  *   eps    relative ID precision (Sec. 2.2), 0 < eps < 1.
  *   leaf   maximum points per leaf box, >= 1.
  * Errors: RS_ERR_ARG (bad sizes, parameters), RS_ERR_NAN (non-finite point),
@@ -285,9 +288,9 @@ const char* rs_last_error(void);
 const char* rs_version(void);
 
 /* The Green's function exactly as the library evaluates it (eqs. 2d-laplace,
- * 3d-laplace, 2d-helmholtz; no quadrature weight), at n squared distances
- * s2 > 0 (host array): out[n] for the real kernels, interleaved (re, im)
- * out[2 n] for Helmholtz (host).  For verification of the device evaluation
+ * 3d-laplace, 2d-helmholtz, 3d-helmholtz; no quadrature weight), at n squared
+ * distances s2 > 0 (host array): out[n] for the real kernels, interleaved
+ * (re, im) out[2 n] for the Helmholtz kernels (host).  For verification of the device evaluation
  * (2D Laplace uses a table-driven logarithm, Tang 1990); synchronous. */
 int rs_green(int kernel_id, double k_wave, const double* s2, int64_t n, double* out);
 

@@ -10,7 +10,8 @@ the GPU library: it reads inputs only from the seeded generators in
 Modules
   tree     quadtree / octree with contiguous index blocks (Sec. 2.1, Ex. 1;
            Sec. 6 opening paragraph)
-  kernels  Green's functions (eqs. 2d-laplace, 3d-laplace, 2d-helmholtz) and
+  kernels  Green's functions (eqs. 2d-laplace, 3d-laplace, 2d-helmholtz,
+           3d-helmholtz) and
            the system matrix A = I + w K with K_ii = 0
   interp   interpolative decomposition by column-pivoted Householder QR with
            adaptive rank (Sec. 2.2, Def. 2.3)

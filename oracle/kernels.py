@@ -6,6 +6,7 @@ Green's functions (Sec. 2, Example 1 and 2; Sec. 6.1.2):
   laplace2d    G = -(1/2 pi) log|x - y|          (eq. 2d-laplace)
   laplace3d    G = 1 / (4 pi |x - y|)             (eq. 3d-laplace)
   helmholtz2d  G = (i/4) H0^(1)(k |x - y|)        (eq. 2d-helmholtz)
+  helmholtz3d  G = exp(i k |x - y|) / (4 pi |x - y|) (eq. 3d-helmholtz)
 System matrix: A = I + w K with K_ij = G(x_i, x_j) for i != j and K_ii = 0
 (punctured trapezoid / one-point rule, the configuration the workloads
 state; w = h for curves, 4 pi / N on the sphere).
@@ -17,25 +18,32 @@ Proxy surfaces (Sec. 3.2, Fig. proxy-comp; count per Sec. 6 opening):
   3D  a g x g grid of cell centres on each of the 6 faces of a cube of
       half-width ratio * s / 2 (6 g^2 = n_p points), faces in the order
       -x, +x, -y, +y, -z, +z.
-H0^(1) is taken from scipy.special.hankel1, a library primitive.
+H0^(1) is taken from scipy.special.hankel1, a library primitive; the 3D
+kernel is numpy's complex exponential.
 
 Pins: tests/test_oracle_solver.py checks the Laplace 2D kernel through the
 closed-form spectrum of A on the unit circle (eigenvalue 1 - ln(N)/N for the
 constant mode, and its continuum limit 1 + 1/(2m)); the Helmholtz kernel
 through the continuum limit 1 + (i pi / 2) J_m(k) H_m^(1)(k) on the circle;
 the 3D kernel through the single-layer eigenvalue 1 + 1/(2l+1) of the
-spherical harmonics on the sphere.
+spherical harmonics on the sphere; the 3D Helmholtz kernel through the
+Helmholtz equation itself (a finite-difference Laplacian of G plus k^2 G
+vanishes away from the source, for e^{+ikr} only with the outgoing
+behaviour r (dG/dr - i k G) -> 0), its small-k expansion
+1/(4 pi r) + i k/(4 pi) - k^2 r/(8 pi) + ..., and the single-layer
+eigenvalue 1 + i k j_l(k) h_l^(1)(k) of the spherical harmonics on the unit
+sphere.
 """
 from __future__ import annotations
 
 import numpy as np
 from scipy.special import hankel1
 
-KINDS = ("laplace2d", "helmholtz2d", "laplace3d")
+KINDS = ("laplace2d", "helmholtz2d", "laplace3d", "helmholtz3d")
 
 
 def is_complex(kind: str) -> bool:
-    return kind == "helmholtz2d"
+    return kind in ("helmholtz2d", "helmholtz3d")
 
 
 def green(kind: str, X: np.ndarray, Y: np.ndarray, kwave: float = 0.0) -> np.ndarray:
@@ -49,6 +57,8 @@ def green(kind: str, X: np.ndarray, Y: np.ndarray, kwave: float = 0.0) -> np.nda
             return 1.0 / (4.0 * np.pi * r)
         if kind == "helmholtz2d":
             return 0.25j * hankel1(0, kwave * r)
+        if kind == "helmholtz3d":
+            return np.exp(1j * kwave * r) / (4.0 * np.pi * r)
     raise ValueError(kind)
 
 

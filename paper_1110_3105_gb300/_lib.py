@@ -15,9 +15,11 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librs.so")
 
-RS_LAPLACE2D, RS_HELMHOLTZ2D, RS_LAPLACE3D = 0, 1, 2
+RS_LAPLACE2D, RS_HELMHOLTZ2D, RS_LAPLACE3D, RS_HELMHOLTZ3D = 0, 1, 2, 3
 RS_PREC_FP64, RS_PREC_FP32 = 0, 1
-KERNELS = {"laplace2d": RS_LAPLACE2D, "helmholtz2d": RS_HELMHOLTZ2D, "laplace3d": RS_LAPLACE3D}
+KERNELS = {"laplace2d": RS_LAPLACE2D, "helmholtz2d": RS_HELMHOLTZ2D, "laplace3d": RS_LAPLACE3D,
+           "helmholtz3d": RS_HELMHOLTZ3D}
+COMPLEX_KERNELS = ("helmholtz2d", "helmholtz3d")
 STATUS = {0: "RS_OK", -1: "RS_ERR_ARG", -2: "RS_ERR_OOM", -3: "RS_ERR_CUDA", -4: "RS_ERR_SINGULAR",
           -5: "RS_ERR_TIMEOUT", -6: "RS_ERR_NAN", -7: "RS_ERR_STATE"}
 
@@ -189,7 +191,7 @@ def rs_build(points, kernel: str, weight: float, eps: float, leaf: int, proxy_n:
     rc = _lib.rs_build(ptr, n, dim, ctypes.byref(p), float(eps), int(leaf), _stream(stream), ctypes.byref(out))
     del keep
     _check(rc)
-    return Handle(out.value, n, kernel == "helmholtz2d")
+    return Handle(out.value, n, kernel in COMPLEX_KERNELS)
 
 
 def rs_solve(h: Handle, B, X, precision: int = RS_PREC_FP64, stream=None):
@@ -314,7 +316,7 @@ def rs_green(kernel: str, s2, k_wave: float = 0.0) -> np.ndarray:
     """The device evaluation of G at squared distances s2 (no weight)."""
     lib = load()
     s2 = np.ascontiguousarray(np.asarray(s2, dtype=np.float64))
-    cplx = kernel == "helmholtz2d"
+    cplx = kernel in COMPLEX_KERNELS
     out = np.zeros(2 * s2.size if cplx else s2.size, dtype=np.float64)
     _check(lib.rs_green(KERNELS[kernel], float(k_wave), s2.ctypes.data, s2.size, out.ctypes.data))
     return out.view(np.complex128) if cplx else out

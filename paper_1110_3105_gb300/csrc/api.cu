@@ -126,8 +126,8 @@ static int log_table(const double** out) {
 __global__ void k_green(rs::KParams kp, const double* s2, int64_t n, double* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  if (kp.kind == RS_HELMHOLTZ2D) {
-    const rs::c128 g = rs::green_cplx(kp.kwave, sqrt(s2[i]));
+  if (kp.kind == RS_HELMHOLTZ2D || kp.kind == RS_HELMHOLTZ3D) {
+    const rs::c128 g = rs::green_cplx(kp.kind, kp.kwave, sqrt(s2[i]));
     out[2 * i] = g.re;
     out[2 * i + 1] = g.im;
   } else {
@@ -221,7 +221,7 @@ const char* rs_last_error(void) { return rs::g_err.c_str(); }
 
 int rs_green(int kernel_id, double k_wave, const double* s2, int64_t n, double* out) {
   rs::g_err.clear();
-  if (kernel_id < RS_LAPLACE2D || kernel_id > RS_LAPLACE3D || n < 0 || (n > 0 && (!s2 || !out)))
+  if (kernel_id < RS_LAPLACE2D || kernel_id > RS_HELMHOLTZ3D || n < 0 || (n > 0 && (!s2 || !out)))
     return fail(RS_ERR_ARG, "rs_green: bad arguments");
   if (n == 0) return RS_OK;
   rs::KParams kp{};
@@ -229,7 +229,7 @@ int rs_green(int kernel_id, double k_wave, const double* s2, int64_t n, double* 
   kp.w = 1.0;
   kp.kwave = k_wave;
   RS_TRY(log_table(&kp.logtab));
-  const int64_t nout = kernel_id == RS_HELMHOLTZ2D ? 2 * n : n;
+  const int64_t nout = (kernel_id == RS_HELMHOLTZ2D || kernel_id == RS_HELMHOLTZ3D) ? 2 * n : n;
   double *ds = nullptr, *dout = nullptr;
   int rc = RS_OK;
   if (cudaMalloc((void**)&ds, sizeof(double) * n) || cudaMalloc((void**)&dout, sizeof(double) * nout)) {
@@ -258,9 +258,10 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
   if (!pts || !params) return fail(RS_ERR_ARG, "rs_build: null pointer argument");
   if (n < 1 || n > (int64_t)1 << 30) return fail(RS_ERR_ARG, "rs_build: N=%lld out of range", (long long)n);
   if (dim != 2 && dim != 3) return fail(RS_ERR_ARG, "rs_build: dim must be 2 or 3");
-  if (params->kernel_id < RS_LAPLACE2D || params->kernel_id > RS_LAPLACE3D)
+  if (params->kernel_id < RS_LAPLACE2D || params->kernel_id > RS_HELMHOLTZ3D)
     return fail(RS_ERR_ARG, "rs_build: unknown kernel_id %d", params->kernel_id);
-  if ((params->kernel_id == RS_LAPLACE3D) != (dim == 3))
+  const bool helm = params->kernel_id == RS_HELMHOLTZ2D || params->kernel_id == RS_HELMHOLTZ3D;
+  if ((params->kernel_id == RS_LAPLACE3D || params->kernel_id == RS_HELMHOLTZ3D) != (dim == 3))
     return fail(RS_ERR_ARG, "rs_build: kernel %d does not match dim %d", params->kernel_id, dim);
   if (!(eps > 0.0 && eps < 1.0)) return fail(RS_ERR_ARG, "rs_build: eps must be in (0, 1)");
   if (leaf < 1) return fail(RS_ERR_ARG, "rs_build: leaf must be >= 1");
@@ -273,7 +274,7 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
     int g = (int)std::lround(std::sqrt(params->proxy_n / 6.0));
     if (6 * g * g != params->proxy_n) return fail(RS_ERR_ARG, "rs_build: 3D proxy_n must be 6 g^2");
   }
-  if (params->kernel_id == RS_HELMHOLTZ2D && !(params->k_wave > 0.0))
+  if (helm && !(params->k_wave > 0.0))
     return fail(RS_ERR_ARG, "rs_build: Helmholtz needs k_wave > 0");
 
   cudaStream_t st = (cudaStream_t)stream;
@@ -301,7 +302,7 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
       return rc0;
     }
   }
-  h->cplx = params->kernel_id == RS_HELMHOLTZ2D;
+  h->cplx = helm;
   h->nproxy = params->proxy_n;
   h->ratio = params->proxy_ratio;
   h->id_df = params->id_arith == RS_ID_DFLOAT;

@@ -129,7 +129,7 @@ __device__ inline double dist(const Pts& p, int i, int j) { return sqrt(dist2(p,
 
 // Kernel parameters shared by every device routine.
 struct KParams {
-  int kind;       // RS_LAPLACE2D / RS_HELMHOLTZ2D / RS_LAPLACE3D
+  int kind;       // RS_LAPLACE2D / RS_HELMHOLTZ2D / RS_LAPLACE3D / RS_HELMHOLTZ3D
   double w;       // quadrature weight in A = I + w K
   double kwave;   // Helmholtz wavenumber
   const double* logtab;   // device table of log_tab (see below)
@@ -165,8 +165,8 @@ __device__ __forceinline__ double log_tab(const double* tab, double x) {
   return fma((double)e, ln2.x, li.x + fma((double)e, ln2.y, l1p));
 }
 
-// Green's functions: eq. 2d-laplace, eq. 3d-laplace, eq. 2d-helmholtz.
-// H0^(1) = J0 + i Y0 from CUDA's math library.
+// Green's functions: eq. 2d-laplace, eq. 3d-laplace, eq. 2d-helmholtz,
+// eq. 3d-helmholtz.  H0^(1) = J0 + i Y0, cos and sin from CUDA's math library.
 __device__ inline double green_real(int kind, double r) {
   if (kind == RS_LAPLACE3D) return 1.0 / (4.0 * M_PI * r);
   return -log(r) * (1.0 / (2.0 * M_PI));
@@ -177,8 +177,14 @@ __device__ inline double green_real_s2(const KParams& kp, double s) {
   if (kp.kind == RS_LAPLACE3D) return rsqrt(s) * (1.0 / (4.0 * M_PI));
   return -log_tab(kp.logtab, s) * (1.0 / (4.0 * M_PI));
 }
-__device__ inline c128 green_cplx(double kwave, double r) {
-  double kr = kwave * r;
+__device__ inline c128 green_cplx(int kind, double kwave, double r) {
+  const double kr = kwave * r;
+  if (kind == RS_HELMHOLTZ3D) {   // e^{i k r} / (4 pi r)
+    double s, c;
+    sincos(kr, &s, &c);
+    const double f = 1.0 / (4.0 * M_PI * r);
+    return c128(c * f, s * f);
+  }
   return c128(-0.25 * y0(kr), 0.25 * j0(kr));   // (i/4)(J0 + i Y0)
 }
 // w G(x_i, x_j) for distinct points.
@@ -187,7 +193,7 @@ template <> __device__ inline double offdiag_entry<double>(const KParams& kp, co
   return kp.w * green_real_s2(kp, dist2(p, i, j));
 }
 template <> __device__ inline c128 offdiag_entry<c128>(const KParams& kp, const Pts& p, int i, int j) {
-  c128 g = green_cplx(kp.kwave, dist(p, i, j));
+  c128 g = green_cplx(kp.kind, kp.kwave, dist(p, i, j));
   return c128(kp.w * g.re, kp.w * g.im);
 }
 // A_ij = delta_ij + w G(x_i, x_j) with K_ii = 0.
@@ -200,7 +206,7 @@ template <class S> __device__ inline S system_entry(const KParams& kp, const Pts
 template <class S> __device__ inline S green_at(const KParams& kp, double r);
 template <> __device__ inline double green_at<double>(const KParams& kp, double r) { return kp.w * green_real(kp.kind, r); }
 template <> __device__ inline c128 green_at<c128>(const KParams& kp, double r) {
-  c128 g = green_cplx(kp.kwave, r);
+  c128 g = green_cplx(kp.kind, kp.kwave, r);
   return c128(kp.w * g.re, kp.w * g.im);
 }
 // The same from the squared distance.

@@ -47,3 +47,15 @@ def test_laplace3d_and_helmholtz():
     href = 0.25j * (j0(kr) + 1j * y0(kr))
     # CUDA j0 / y0 against scipy: a few units of 1e-13 absolute
     assert np.max(np.abs(h - href) / np.maximum(1.0, np.abs(href))) <= 1e-12
+
+
+def test_helmholtz3d():
+    import paper_1110_3105_gb300 as rs
+    rng = np.random.default_rng(8)
+    s = 10.0 ** rng.uniform(-10, 2, 50000)
+    k = 10.0
+    g = rs.rs_green("helmholtz3d", s, k_wave=k)
+    r = np.sqrt(s)
+    ref = np.exp(1j * k * r) / (4 * np.pi * r)
+    # CUDA sincos and the reference each round a few times; kr up to 1e2
+    assert np.max(np.abs(g - ref) / np.abs(ref)) <= 1e-14

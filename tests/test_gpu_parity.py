@@ -79,6 +79,7 @@ SOLVE_CASES = [
     ("laplace2d", "starfish", 8192, 1e-10, 64, 64),
     ("helmholtz2d", "starfish", 4096, 1e-9, 64, 64),
     ("laplace3d", "sphere", 4096, 1e-6, 128, 216),
+    ("helmholtz3d", "sphere", 2048, 1e-6, 128, 216),
 ]
 
 
@@ -87,10 +88,10 @@ def built(request):
     rs = rs_mod()
     kind, geom, n, eps, leaf, nproxy = request.param
     pts, w = ri.geometry(geom, n)
-    kw = 10.0 if kind == "helmholtz2d" else 0.0
+    kw = 10.0 if kind.startswith("helmholtz") else 0.0   # 3D: k = 10 is omega = 3.18 on the unit sphere (Sec. 6.2)
     F = _oracle(kind, pts, w, eps, leaf, nproxy, kw)
     H = rs.rs_build(pts, kind, w, eps, leaf, nproxy, k_wave=kw)
-    yield dict(kind=kind, n=n, eps=eps, F=F, H=H, pts=pts, w=w, kw=kw, cplx=kind == "helmholtz2d")
+    yield dict(kind=kind, n=n, eps=eps, F=F, H=H, pts=pts, w=w, kw=kw, cplx=kind.startswith("helmholtz"))
     H.free()
 
 

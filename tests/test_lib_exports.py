@@ -68,3 +68,11 @@ def test_build_parameter_validation(lib):
         rc = _lib._lib.rs_build(pts.ctypes.data, 100, 2, ctypes.byref(p), 1e-9, 64, None, ctypes.byref(out))
         assert rc == -1, field
         assert out.value is None
+    # kernel / dimension mismatches and a Helmholtz kernel without a wavenumber
+    for kid, dim, kwave in ((3, 2, 10.0), (2, 2, 0.0), (1, 3, 10.0), (3, 3, 0.0), (1, 2, 0.0)):
+        kw = dict(good, kernel_id=kid, k_wave=kwave, proxy_n=216 if dim == 3 else 64)
+        p = _lib.rs_params(**kw)
+        q = np.asfortranarray(np.random.default_rng(1).random((dim, 100)))
+        rc = _lib._lib.rs_build(q.ctypes.data, 100, dim, ctypes.byref(p), 1e-9, 64, None, ctypes.byref(out))
+        assert rc == -1, (kid, dim, kwave)
+        assert out.value is None

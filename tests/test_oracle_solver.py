@@ -3,16 +3,19 @@
 Pins: Sec. 5 error bound (||A - A_RS|| / ||A|| within 10 eps for a
 second-kind operator), Sec. 4.3 (the telescoping inverse is one ordering of
 Gaussian elimination on the compressed matrix), and closed-form spectra of
-A = I + h K on the unit circle (circulant) and the sphere.
+A = I + h K on the unit circle (circulant) and the sphere; the 3D Helmholtz
+kernel (eq. 3d-helmholtz) by the Helmholtz equation, the outgoing radiation
+condition and its small-wavenumber expansion.
 """
 import math
 
 import numpy as np
 import pytest
-from scipy.special import hankel1, jv
+from scipy.special import hankel1, jv, spherical_jn, spherical_yn
 
 import rs_inputs as ri
 from oracle import dense, rskel
+from oracle.kernels import green
 
 
 def _build(kind, pts, w, eps, leaf, nproxy, kwave=0.0):
@@ -25,6 +28,7 @@ CASES = [
     ("laplace2d", "starfish", 2048, 1e-10, 64, 64),
     ("helmholtz2d", "starfish", 1024, 1e-9, 64, 64),
     ("laplace3d", "sphere", 1500, 1e-6, 128, 216),
+    ("helmholtz3d", "sphere", 1500, 1e-6, 128, 216),
 ]
 
 
@@ -32,10 +36,10 @@ CASES = [
 def case(request):
     kind, geom, n, eps, leaf, nproxy = request.param
     pts, w = ri.geometry(geom, n)
-    kw = 10.0 if kind == "helmholtz2d" else 0.0
+    kw = 10.0 if kind.startswith("helmholtz") else 0.0
     F = _build(kind, pts, w, eps, leaf, nproxy, kw)
     A = dense.dense_matrix(kind, pts, w, kw)
-    dt = np.complex128 if kind == "helmholtz2d" else np.float64
+    dt = np.complex128 if kind.startswith("helmholtz") else np.float64
     ARS = F.apply(np.eye(n, dtype=dt))
     return dict(kind=kind, n=n, eps=eps, F=F, A=A, ARS=ARS, dt=dt)
 
@@ -122,3 +126,46 @@ def test_sphere_single_layer_eigenvalue():
         # S Y_l = Y_l / (2l + 1) on the unit sphere; the punctured rule drops
         # about 1/sqrt(N) of the self cell
         assert abs(lam - (1 + 1 / (2 * l + 1))) < 2.0 / np.sqrt(n)
+
+
+def test_helmholtz3d_kernel_pins():
+    """G = e^{ikr}/(4 pi r): (Laplacian + k^2) G = 0 off the source (second
+    differences, O(h^2)); r (dG/dr - i k G) -> 0 (outgoing; the incoming
+    e^{-ikr} leaves k/(2 pi)); G = 1/(4 pi r) + i k/(4 pi) - k^2 r/(8 pi) + O(k^3 r^2)."""
+    k = 7.0
+    y = np.zeros((3, 1))
+    x0 = np.array([0.3, -0.2, 0.5])
+    for hstep in (1e-2, 5e-3):
+        g0 = green("helmholtz3d", x0[:, None], y, k)[0, 0]
+        lap = 0.0
+        for d in range(3):
+            e = np.zeros(3)
+            e[d] = hstep
+            gp = green("helmholtz3d", (x0 + e)[:, None], y, k)[0, 0]
+            gm = green("helmholtz3d", (x0 - e)[:, None], y, k)[0, 0]
+            lap += (gp - 2 * g0 + gm) / hstep**2
+        assert abs(lap + k * k * g0) < 2.0 * hstep**2 * abs(k**4 * g0) + 1e-9
+    for r in (50.0, 500.0):
+        dr = 1e-5   # k dr small: central-difference error (k dr)^2 / 6
+        p = lambda t: np.array([[t], [0.0], [0.0]])
+        g = green("helmholtz3d", p(r), y, k)[0, 0]
+        dg = (green("helmholtz3d", p(r + dr), y, k)[0, 0] - green("helmholtz3d", p(r - dr), y, k)[0, 0]) / (2 * dr)
+        assert abs(r * (dg - 1j * k * g)) < 2.0 / (4 * np.pi * r) + 1e-6
+    kk, r = 1e-3, 0.5
+    g = green("helmholtz3d", np.array([[r], [0.0], [0.0]]), y, kk)[0, 0]
+    ser = 1 / (4 * np.pi * r) + 1j * kk / (4 * np.pi) - kk * kk * r / (8 * np.pi)
+    assert abs(g - ser) < kk**3 * r * r / (4 * np.pi) + 1e-15
+
+
+def test_sphere_helmholtz_single_layer_eigenvalue():
+    """On the unit sphere the single layer of eq. 3d-helmholtz maps Y_l to
+    i k j_l(k) h_l^(1)(k) Y_l; A = I + w K approximates I + S, to the same
+    1/sqrt(N) self-cell error as the Laplace case."""
+    n, k = 1500, 10.0
+    pts, w = ri.fibonacci_sphere(n)
+    F = _build("helmholtz3d", pts, w, 1e-6, 128, 216, k)
+    for l, Y in ((0, np.ones(n)), (1, pts[2].copy())):
+        x = F.solve(Y.astype(np.complex128))
+        lam = (Y @ Y) / (Y @ x)
+        cont = 1 + 1j * k * spherical_jn(l, k) * (spherical_jn(l, k) + 1j * spherical_yn(l, k))
+        assert abs(lam - cont) < 2.0 / np.sqrt(n), (l, lam, cont)
