@@ -153,6 +153,9 @@ WORKLOADS = {
                                        eps=1e-9, leaf=64, nproxy=64, kwave=10.0),
     "laplace3d_sphere_32768": dict(geom="sphere", n=32768, kernel="laplace3d",
                                    eps=1e-6, leaf=128, nproxy=216),
+    # 3D Helmholtz on the unit sphere, k = 10 (omega = k diam / 2 pi = 3.18)
+    "helmholtz3d_sphere_8192": dict(geom="sphere", n=8192, kernel="helmholtz3d",
+                                    eps=1e-6, leaf=128, nproxy=216, kwave=10.0),
 }
 
 
