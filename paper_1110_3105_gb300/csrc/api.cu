@@ -483,9 +483,10 @@ int rs_solve_refined(rs_handle h, const void* B, int64_t ldb, int nrhs, void* X,
     if ((rc = colnorm2_device(h, b, nrhs, nrm + nrhs, st)) != RS_OK) break;
     if ((rc = solve_pers_device(h, RS_PREC_FP32, b, N, nrhs, x, N, st)) != RS_OK) break;
     cudaMemcpyAsync(hb.data(), nrm + nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
-    // Real kernels: r_0 = b - A x_0 with double-float products; later
-    // residuals by the update r_{j+1} = r_j - A d_j (float products on the
-    // small correction).  Complex kernels: every residual in FP64.
+    // r_0 = b - A x_0 with double-float products (complex kernels: complex
+    // double); later residuals by the update r_{j+1} = r_j - A d_j (float /
+    // complex float products on the small correction), all from the stored
+    // forward factors.
     const bool dfp = df_supported(h);
     bool first = true;
     for (;;) {

@@ -1,4 +1,4 @@
-// Forward operator for the refinement residual (real kernels).
+// Forward operator for the refinement residual.
 //
 // The residual r = b - A_RS x of the refinement (forward operator of eq.
 // multilevel-compression, applied as in Sec. 3.3) must be accurate to far
@@ -17,7 +17,10 @@
 // coordinates (FP64 evaluation) and stored as float and double-float.
 //
 // The float mode serves the cheap update r_{j+1} = r_j - A d_j of the
-// refinement, whose correction d_j is already ~1e-7 of x.
+// refinement, whose correction d_j is already ~1e-7 of x.  Complex kernels
+// store the same factors as complex float and complex double (the residual
+// then runs in FP64 complex arithmetic on the same persistent kernel, with
+// the kernel blocks read instead of re-evaluated from the coordinates).
 #include <algorithm>
 #include <vector>
 
@@ -41,61 +44,77 @@ struct FwdTab {
 //        written by the factorization while it assembles its block (skel.cu:
 //        emit_fwd); rows n.. hold the projection P = [I T] Pi;
 //   FL = P^T (n x k).
-// Stored as float and as double-float.
-__global__ void k_fwd_factors(FwdTab t, const double* T, const int64_t* uoff, const int64_t* loff, float* FU32,
-                              dfloat* FUdf, float* FL32, dfloat* FLdf) {
+// Stored as float and as double-float (real), complex float and complex
+// double (complex).
+template <class S> __device__ __forceinline__ void put_lo(void* p, int64_t i, S v);
+template <> __device__ __forceinline__ void put_lo<double>(void* p, int64_t i, double v) {
+  static_cast<float*>(p)[i] = f64_to_f32_rn(v);
+}
+template <> __device__ __forceinline__ void put_lo<c128>(void* p, int64_t i, c128 v) {
+  static_cast<c64*>(p)[i] = c64(f64_to_f32_rn(v.re), f64_to_f32_rn(v.im));
+}
+template <class S> __device__ __forceinline__ void put_hi(void* p, int64_t i, S v);
+template <> __device__ __forceinline__ void put_hi<double>(void* p, int64_t i, double v) {
+  static_cast<dfloat*>(p)[i] = f64_to_df(v);
+}
+template <> __device__ __forceinline__ void put_hi<c128>(void* p, int64_t i, c128 v) { static_cast<c128*>(p)[i] = v; }
+
+template <class S>
+__global__ void k_fwd_factors(FwdTab t, const S* T, const int64_t* uoff, const int64_t* loff, void* FUlo, void* FUhi,
+                              void* FLlo, void* FLhi) {
   extern __shared__ int inv[];   // position within I -> index in the ID order
   const int b = blockIdx.x;
   const int n = t.n[b], k = t.k ? t.k[b] : 0, rows = n + k;
   if (k == 0) return;
   const int64_t off = t.off[b];
   const int* lp = t.lperm + off;
-  const double* Tb = T + t.toff[b];
+  const S* Tb = T + t.toff[b];
   for (int q = threadIdx.x; q < n; q += blockDim.x) inv[lp[q]] = q;
   __syncthreads();
-  auto pval = [&](int a, int c) -> double {   // P[a, c]
+  auto pval = [&](int a, int c) -> S {   // P[a, c]
     int q = inv[c];
-    return q < k ? (q == a ? 1.0 : 0.0) : Tb[a + (size_t)(q - k) * k];
+    return q < k ? S(q == a ? 1.0 : 0.0) : Tb[a + (size_t)(q - k) * k];
   };
-  float* U32 = FU32 + uoff[b];
-  dfloat* Udf = FUdf + uoff[b];
+  const int64_t ub = uoff[b], lb = loff[b];
   for (int64_t e = threadIdx.x; e < (int64_t)k * n; e += blockDim.x) {
     const int a = (int)(e % k), c = (int)(e / k);
-    const double v = pval(a, c);
-    const int64_t i = n + a + (int64_t)c * rows;
-    U32[i] = f64_to_f32_rn(v);
-    Udf[i] = f64_to_df(v);
+    const S v = pval(a, c);
+    const int64_t i = ub + n + a + (int64_t)c * rows;
+    put_lo<S>(FUlo, i, v);
+    put_hi<S>(FUhi, i, v);
   }
-  float* L32 = FL32 + loff[b];
-  dfloat* Ldf = FLdf + loff[b];
   for (int64_t e = threadIdx.x; e < (int64_t)n * k; e += blockDim.x) {
     const int r = (int)(e % n), a = (int)(e / n);
-    const double v = pval(a, r);
-    L32[e] = f64_to_f32_rn(v);
-    Ldf[e] = f64_to_df(v);
+    const S v = pval(a, r);
+    put_lo<S>(FLlo, lb + e, v);
+    put_hi<S>(FLhi, lb + e, v);
   }
 }
 
 }  // namespace
 
 // Build-time: the projection rows of the forward factors of every depth
-// (real kernels; the factors were allocated with the level's pools).
-int make_fwd_blocks(Handle* h, cudaStream_t st) {
-  if (h->cplx) return RS_OK;
+// (the factors were allocated with the level's pools).
+template <class S>
+int fwd_blocks(Handle* h, cudaStream_t st) {
   for (int d = 1; d <= h->L; ++d) {
     Level& lv = h->lv[d];
     FwdTab t{lv.n, lv.k, lv.off, lv.skoff, lv.lperm, lv.toff};
     const size_t smem = sizeof(int) * (size_t)std::max(1, lv.maxn);
-    RS_CUDA(cudaFuncSetAttribute(k_fwd_factors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_fwd_factors<<<lv.nbox, 256, smem, st>>>(t, (const double*)lv.T, lv.uoff, lv.loff, (float*)lv.FU32,
-                                              (dfloat*)lv.FUdf, (float*)lv.FL32, (dfloat*)lv.FLdf);
+    RS_CUDA(cudaFuncSetAttribute(k_fwd_factors<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_fwd_factors<S><<<lv.nbox, 256, smem, st>>>(t, (const S*)lv.T, lv.uoff, lv.loff, lv.FU32, lv.FUdf, lv.FL32,
+                                                 lv.FLdf);
     RS_CHECK_LAUNCH();
   }
   return RS_OK;
 }
 
-// The double-float residual covers the real kernels (forward factors exist).
-bool df_supported(const Handle* h) { return !h->cplx; }
+int make_fwd_blocks(Handle* h, cudaStream_t st) {
+  return h->cplx ? fwd_blocks<c128>(h, st) : fwd_blocks<double>(h, st);
+}
+
+// The stored forward factors exist for every kernel.
+bool df_supported(const Handle*) { return true; }
 
 // r = b - A_RS x with double-float products (full), or r = r - A_RS d with
 // float products (update): the forward operator runs on the persistent

@@ -19,7 +19,8 @@
 //       Lam at lamoff[b]: k x k   = Lambda (read by the parent's assembly)
 //     float copies U32 / Lf32 for the mixed-precision solve
 //     forward factors FU32/FUdf ((n+k) x n = [D ; P] at uoff) and FL32/FLdf
-//       (n x k = P^T at loff), float and double-float (real kernels)
+//       (n x k = P^T at loff): float and double-float (real kernels),
+//       complex float and complex double (complex kernels)
 //   the root is depth 0 with k = 0, so its U holds calS^{-1}.
 #pragma once
 
@@ -91,7 +92,7 @@ struct Level {
   void* U32 = nullptr;
   void* Lf32 = nullptr;
   // forward operator in the solve's two-pass form (fwd2.cu): FU = [D ; P]
-  // ((n+k) x n at uoff) and FL = P^T (n x k at loff), in float and double-float
+  // ((n+k) x n at uoff) and FL = P^T (n x k at loff), low and high precision
   void* FU32 = nullptr;
   void* FL32 = nullptr;
   void* FUdf = nullptr;
@@ -189,9 +190,10 @@ bool df_supported(const Handle* h);
 int residual_df(Handle* h, const double* b, const double* x, double* r, int R, bool full, cudaStream_t st);
 
 // Persistent single-launch solve (solve2.cu).  Besides RS_PREC_FP64 and
-// RS_PREC_FP32 it runs the forward operator (real kernels) from the forward
-// factors, in float or double-float arithmetic, and then writes
-// X = sub - A_RS B.
+// RS_PREC_FP32 it runs the forward operator from the forward factors and
+// then writes X = sub - A_RS B: MODE_FWD_F32 in float (complex float),
+// MODE_FWD_DF in double-float for real kernels and complex double for
+// complex ones.
 enum { MODE_FWD_F32 = 2, MODE_FWD_DF = 3 };
 int solve_pers_device_sub(Handle* h, int mode, const double* d_B, int64_t ldb, int nrhs, double* d_X, int64_t ldx,
                           const double* d_sub, cudaStream_t st);

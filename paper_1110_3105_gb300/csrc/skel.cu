@@ -1102,22 +1102,29 @@ struct FaArgs {
   const int64_t* loff;
   const int64_t* lamoff;
   int* bad;
-  float* fu32;            // forward-operator rows [D ; P] (real kernels; null otherwise)
+  // forward-operator rows [D ; P]: real kernels float (fu32) and double-float
+  // (fudf); complex kernels complex float and complex double in the same slots
+  float* fu32;
   dfloat* fudf;
 };
 
 // The forward operator's D block shares the assembled block's entries: the
 // same at the leaves; above, zero inside one child's block (where the
-// assembled block holds the child's Lambda).  Written while assembling, as
-// float and double-float, into rows 0..n-1 of FU ((n+k) x n at uoff).
+// assembled block holds the child's Lambda).  Written while assembling into
+// rows 0..n-1 of FU ((n+k) x n at uoff): float and double-float for real
+// kernels, complex float and complex double for complex ones.
 template <class S>
 __device__ __forceinline__ void emit_fwd(const FaArgs& a, int b, int n, int k, int r, int c, S v, bool same_child) {
+  if (!a.fu32) return;
+  const int64_t i = a.uoff[b] + r + (int64_t)c * (n + k);
   if constexpr (std::is_same<S, double>::value) {
-    if (!a.fu32) return;
     const double f = (a.leaf_level || !same_child) ? v : 0.0;
-    const int64_t i = a.uoff[b] + r + (int64_t)c * (n + k);
     a.fu32[i] = f64_to_f32_rn(f);
     a.fudf[i] = f64_to_df(f);
+  } else {
+    const S f = (a.leaf_level || !same_child) ? v : S(0.0);
+    reinterpret_cast<c64*>(a.fu32)[i] = c64(f64_to_f32_rn(f.re), f64_to_f32_rn(f.im));
+    reinterpret_cast<c128*>(a.fudf)[i] = f;
   }
 }
 
@@ -2691,11 +2698,13 @@ int alloc_factors(Handle* h, Level& lv, cudaStream_t st) {
   RS_TRY(dalloc(h, &lv.U, sb * std::max<int64_t>(1, us)));
   RS_TRY(dalloc(h, &lv.Lf, sb * std::max<int64_t>(1, ls)));
   RS_TRY(dalloc(h, &lv.Lam, sb * std::max<int64_t>(1, lams)));
-  if (!h->cplx) {   // forward-operator factors of the refinement residual (fwd2.cu)
-    RS_TRY(dalloc(h, &lv.FU32, sizeof(float) * std::max<int64_t>(1, us)));
-    RS_TRY(dalloc(h, &lv.FUdf, sizeof(dfloat) * std::max<int64_t>(1, us)));
-    RS_TRY(dalloc(h, &lv.FL32, sizeof(float) * std::max<int64_t>(1, ls)));
-    RS_TRY(dalloc(h, &lv.FLdf, sizeof(dfloat) * std::max<int64_t>(1, ls)));
+  {   // forward-operator factors of the refinement residual (fwd2.cu): float
+      // and double-float (real), complex float and complex double (complex)
+    const size_t lo = h->cplx ? sizeof(c64) : sizeof(float), hi = h->cplx ? sizeof(c128) : sizeof(dfloat);
+    RS_TRY(dalloc(h, &lv.FU32, lo * std::max<int64_t>(1, us)));
+    RS_TRY(dalloc(h, &lv.FUdf, hi * std::max<int64_t>(1, us)));
+    RS_TRY(dalloc(h, &lv.FL32, lo * std::max<int64_t>(1, ls)));
+    RS_TRY(dalloc(h, &lv.FLdf, hi * std::max<int64_t>(1, ls)));
   }
   h->factor_scalars += us + ls;
   return RS_OK;

@@ -1110,8 +1110,12 @@ int solve_pers_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrh
 
 int solve_pers_device_sub(Handle* h, int mode, const double* d_B, int64_t ldb, int nrhs, double* d_X, int64_t ldx,
                           const double* d_sub, cudaStream_t st) {
-  if (h->cplx || (mode != MODE_FWD_F32 && mode != MODE_FWD_DF))
-    return fail(RS_ERR_ARG, "forward operator: real kernels only");
+  if (mode != MODE_FWD_F32 && mode != MODE_FWD_DF) return fail(RS_ERR_ARG, "forward operator: bad mode");
+  if (h->cplx) {   // the buffers hold complex double values
+    const c128 *B = (const c128*)d_B, *sub = (const c128*)d_sub;
+    if (mode == MODE_FWD_DF) return pers_impl<c128, c128>(h, mode, B, ldb, nrhs, (c128*)d_X, ldx, st, sub);
+    return pers_impl<c64, c128>(h, mode, B, ldb, nrhs, (c128*)d_X, ldx, st, sub);
+  }
   if (mode == MODE_FWD_DF) return pers_impl<dfloat, double>(h, mode, d_B, ldb, nrhs, d_X, ldx, st, d_sub);
   return pers_impl<float, double>(h, mode, d_B, ldb, nrhs, d_X, ldx, st, d_sub);
 }
