@@ -484,7 +484,7 @@ int rs_solve_refined(rs_handle h, const void* B, int64_t ldb, int nrhs, void* X,
     if ((rc = solve_pers_device(h, RS_PREC_FP32, b, N, nrhs, x, N, st)) != RS_OK) break;
     cudaMemcpyAsync(hb.data(), nrm + nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
     // r_0 = b - A x_0 with double-float products (complex kernels: complex
-    // double); later residuals by the update r_{j+1} = r_j - A d_j (float /
+    // double-float); later residuals by the update r_{j+1} = r_j - A d_j (float /
     // complex float products on the small correction), all from the stored
     // forward factors.
     const bool dfp = df_supported(h);

@@ -18,9 +18,8 @@
 //
 // The float mode serves the cheap update r_{j+1} = r_j - A d_j of the
 // refinement, whose correction d_j is already ~1e-7 of x.  Complex kernels
-// store the same factors as complex float and complex double (the residual
-// then runs in FP64 complex arithmetic on the same persistent kernel, with
-// the kernel blocks read instead of re-evaluated from the coordinates).
+// store the same factors as complex float and complex double-float (each
+// part a double-float), on the same persistent kernel.
 #include <algorithm>
 #include <vector>
 
@@ -45,7 +44,7 @@ struct FwdTab {
 //        emit_fwd); rows n.. hold the projection P = [I T] Pi;
 //   FL = P^T (n x k).
 // Stored as float and as double-float (real), complex float and complex
-// double (complex).
+// double-float (complex).
 template <class S> __device__ __forceinline__ void put_lo(void* p, int64_t i, S v);
 template <> __device__ __forceinline__ void put_lo<double>(void* p, int64_t i, double v) {
   static_cast<float*>(p)[i] = f64_to_f32_rn(v);
@@ -57,7 +56,9 @@ template <class S> __device__ __forceinline__ void put_hi(void* p, int64_t i, S 
 template <> __device__ __forceinline__ void put_hi<double>(void* p, int64_t i, double v) {
   static_cast<dfloat*>(p)[i] = f64_to_df(v);
 }
-template <> __device__ __forceinline__ void put_hi<c128>(void* p, int64_t i, c128 v) { static_cast<c128*>(p)[i] = v; }
+template <> __device__ __forceinline__ void put_hi<c128>(void* p, int64_t i, c128 v) {
+  static_cast<cdfloat*>(p)[i] = cdfloat(f64_to_df(v.re), f64_to_df(v.im));
+}
 
 template <class S>
 __global__ void k_fwd_factors(FwdTab t, const S* T, const int64_t* uoff, const int64_t* loff, void* FUlo, void* FUhi,

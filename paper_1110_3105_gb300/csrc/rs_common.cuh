@@ -255,6 +255,22 @@ __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
   return df_renorm(dfloat(t, __fadd_rn(a.lo, __fadd_rn(err, b.lo))));
 }
 
+// Complex double-float: real and imaginary parts each a double-float.
+struct cdfloat {
+  dfloat re, im;
+  cdfloat() = default;
+  __host__ __device__ cdfloat(dfloat r, dfloat i) : re(r), im(i) {}
+  __device__ explicit cdfloat(double x) : re(x), im(0.0f, 0.0f) {}
+};
+__device__ __forceinline__ cdfloat operator+(cdfloat a, cdfloat b) { return cdfloat(a.re + b.re, a.im + b.im); }
+// s += a * b (four double-float products)
+__device__ __forceinline__ void cdf_fma(cdfloat& s, cdfloat a, cdfloat b) {
+  df_fma(s.re, a.re, b.re);
+  df_fma(s.re, dfloat(-a.im.hi, -a.im.lo), b.im);
+  df_fma(s.im, a.re, b.im);
+  df_fma(s.im, a.im, b.re);
+}
+
 
 // ------------------------------------------------- conversions off the FP64 pipe
 // Double <-> float conversions issue on the FP64 pipe, which on this GPU runs

@@ -20,7 +20,7 @@
 //     float copies U32 / Lf32 for the mixed-precision solve
 //     forward factors FU32/FUdf ((n+k) x n = [D ; P] at uoff) and FL32/FLdf
 //       (n x k = P^T at loff): float and double-float (real kernels),
-//       complex float and complex double (complex kernels)
+//       complex float and complex double-float (complex kernels)
 //   the root is depth 0 with k = 0, so its U holds calS^{-1}.
 #pragma once
 
@@ -192,8 +192,7 @@ int residual_df(Handle* h, const double* b, const double* x, double* r, int R, b
 // Persistent single-launch solve (solve2.cu).  Besides RS_PREC_FP64 and
 // RS_PREC_FP32 it runs the forward operator from the forward factors and
 // then writes X = sub - A_RS B: MODE_FWD_F32 in float (complex float),
-// MODE_FWD_DF in double-float for real kernels and complex double for
-// complex ones.
+// MODE_FWD_DF in double-float (complex double-float).
 enum { MODE_FWD_F32 = 2, MODE_FWD_DF = 3 };
 int solve_pers_device_sub(Handle* h, int mode, const double* d_B, int64_t ldb, int nrhs, double* d_X, int64_t ldx,
                           const double* d_sub, cudaStream_t st);

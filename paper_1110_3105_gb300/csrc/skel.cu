@@ -1103,7 +1103,8 @@ struct FaArgs {
   const int64_t* lamoff;
   int* bad;
   // forward-operator rows [D ; P]: real kernels float (fu32) and double-float
-  // (fudf); complex kernels complex float and complex double in the same slots
+  // (fudf); complex kernels complex float and complex double-float in the
+  // same slots
   float* fu32;
   dfloat* fudf;
 };
@@ -1112,7 +1113,7 @@ struct FaArgs {
 // same at the leaves; above, zero inside one child's block (where the
 // assembled block holds the child's Lambda).  Written while assembling into
 // rows 0..n-1 of FU ((n+k) x n at uoff): float and double-float for real
-// kernels, complex float and complex double for complex ones.
+// kernels, complex float and complex double-float for complex ones.
 template <class S>
 __device__ __forceinline__ void emit_fwd(const FaArgs& a, int b, int n, int k, int r, int c, S v, bool same_child) {
   if (!a.fu32) return;
@@ -1124,7 +1125,7 @@ __device__ __forceinline__ void emit_fwd(const FaArgs& a, int b, int n, int k, i
   } else {
     const S f = (a.leaf_level || !same_child) ? v : S(0.0);
     reinterpret_cast<c64*>(a.fu32)[i] = c64(f64_to_f32_rn(f.re), f64_to_f32_rn(f.im));
-    reinterpret_cast<c128*>(a.fudf)[i] = f;
+    reinterpret_cast<cdfloat*>(a.fudf)[i] = cdfloat(f64_to_df(f.re), f64_to_df(f.im));
   }
 }
 
@@ -2699,8 +2700,8 @@ int alloc_factors(Handle* h, Level& lv, cudaStream_t st) {
   RS_TRY(dalloc(h, &lv.Lf, sb * std::max<int64_t>(1, ls)));
   RS_TRY(dalloc(h, &lv.Lam, sb * std::max<int64_t>(1, lams)));
   {   // forward-operator factors of the refinement residual (fwd2.cu): float
-      // and double-float (real), complex float and complex double (complex)
-    const size_t lo = h->cplx ? sizeof(c64) : sizeof(float), hi = h->cplx ? sizeof(c128) : sizeof(dfloat);
+      // and double-float (real), complex float and complex double-float (complex)
+    const size_t lo = h->cplx ? sizeof(c64) : sizeof(float), hi = h->cplx ? sizeof(cdfloat) : sizeof(dfloat);
     RS_TRY(dalloc(h, &lv.FU32, lo * std::max<int64_t>(1, us)));
     RS_TRY(dalloc(h, &lv.FUdf, hi * std::max<int64_t>(1, us)));
     RS_TRY(dalloc(h, &lv.FL32, lo * std::max<int64_t>(1, ls)));

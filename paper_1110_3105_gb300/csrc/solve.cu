@@ -299,7 +299,7 @@ __global__ void k_axpy(S* x, const S* d, int64_t cnt) {
 // ------------------------------------------------------------------- host
 size_t sbytes(bool cplx, int prec) {
   if (prec == RS_PREC_FP64) return cplx ? sizeof(c128) : sizeof(double);
-  if (prec == MODE_FWD_DF) return cplx ? sizeof(c128) : sizeof(dfloat);
+  if (prec == MODE_FWD_DF) return cplx ? sizeof(cdfloat) : sizeof(dfloat);
   return cplx ? sizeof(c64) : sizeof(float);
 }
 

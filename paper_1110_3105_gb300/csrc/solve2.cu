@@ -152,6 +152,10 @@ template <> __device__ inline dfloat ldcg<dfloat>(const dfloat* p) {
   float2 t = __ldcg(reinterpret_cast<const float2*>(p));
   return dfloat(t.x, t.y);
 }
+template <> __device__ inline cdfloat ldcg<cdfloat>(const cdfloat* p) {
+  float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+  return cdfloat(dfloat(t.x, t.y), dfloat(t.z, t.w));
+}
 
 // Read-only (non-coherent) loads for the factors, which no kernel writes
 // during a solve.
@@ -167,6 +171,10 @@ template <> __device__ inline c64 ldro<c64>(const c64* p) {
 template <> __device__ inline dfloat ldro<dfloat>(const dfloat* p) {
   float2 t = __ldg(reinterpret_cast<const float2*>(p));
   return dfloat(t.x, t.y);
+}
+template <> __device__ inline cdfloat ldro<cdfloat>(const cdfloat* p) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  return cdfloat(dfloat(t.x, t.y), dfloat(t.z, t.w));
 }
 
 template <class D, class S> __device__ inline D cv(S v) { return D(v); }
@@ -242,11 +250,22 @@ struct StageRow<dfloat, CT> {
   }
 };
 
+template <int CT>
+struct StageRow<cdfloat, CT> {
+  __device__ static void fma(cdfloat* acc, cdfloat a, const cdfloat* row) {
+#pragma unroll
+    for (int c = 0; c < CT; ++c) cdf_fma(acc[c], a, row[c]);
+  }
+};
+
 // Right-hand-side entries into the working type (integer-instruction
 // conversions for float and double-float, see rs_common.cuh).
 template <class S, class SIO> __device__ __forceinline__ S in_cv(SIO v) { return cv<S, SIO>(v); }
 template <> __device__ __forceinline__ float in_cv<float, double>(double v) { return f64_to_f32_rn(v); }
 template <> __device__ __forceinline__ dfloat in_cv<dfloat, double>(double v) { return f64_to_df(v); }
+template <> __device__ __forceinline__ cdfloat in_cv<cdfloat, c128>(c128 v) {
+  return cdfloat(f64_to_df(v.re), f64_to_df(v.im));
+}
 
 // Leaf output: the value itself, or sub - value (forward operator used for a
 // residual b - A x).  In float and double-float the subtraction is done in
@@ -262,6 +281,13 @@ template <> __device__ __forceinline__ double out_cv<float, double>(const double
 template <> __device__ __forceinline__ double out_cv<dfloat, double>(const double* sub, int64_t i, dfloat y) {
   if (sub) return f32_to_f64((f64_to_df(sub[i]) + (-y)).hi);
   return __dadd_rn(f32_to_f64(y.hi), f32_to_f64(y.lo));
+}
+template <> __device__ __forceinline__ c128 out_cv<cdfloat, c128>(const c128* sub, int64_t i, cdfloat y) {
+  if (sub) {
+    const c128 s = sub[i];
+    return c128(f32_to_f64((f64_to_df(s.re) + (-y.re)).hi), f32_to_f64((f64_to_df(s.im) + (-y.im)).hi));
+  }
+  return c128(__dadd_rn(f32_to_f64(y.re.hi), f32_to_f64(y.re.lo)), __dadd_rn(f32_to_f64(y.im.hi), f32_to_f64(y.im.lo)));
 }
 
 template <class S, int CT>
@@ -444,6 +470,7 @@ template <int TM, int TN> struct CtaShape {
 
 template <class S> __device__ __forceinline__ void mac(S& acc, S a, S b) { acc += a * b; }
 template <> __device__ __forceinline__ void mac<dfloat>(dfloat& acc, dfloat a, dfloat b) { df_fma(acc, a, b); }
+template <> __device__ __forceinline__ void mac<cdfloat>(cdfloat& acc, cdfloat a, cdfloat b) { cdf_fma(acc, a, b); }
 
 // N consecutive elements from 16-byte aligned shared memory.
 template <class S, int N> struct Lds {
@@ -1113,7 +1140,7 @@ int solve_pers_device_sub(Handle* h, int mode, const double* d_B, int64_t ldb, i
   if (mode != MODE_FWD_F32 && mode != MODE_FWD_DF) return fail(RS_ERR_ARG, "forward operator: bad mode");
   if (h->cplx) {   // the buffers hold complex double values
     const c128 *B = (const c128*)d_B, *sub = (const c128*)d_sub;
-    if (mode == MODE_FWD_DF) return pers_impl<c128, c128>(h, mode, B, ldb, nrhs, (c128*)d_X, ldx, st, sub);
+    if (mode == MODE_FWD_DF) return pers_impl<cdfloat, c128>(h, mode, B, ldb, nrhs, (c128*)d_X, ldx, st, sub);
     return pers_impl<c64, c128>(h, mode, B, ldb, nrhs, (c128*)d_X, ldx, st, sub);
   }
   if (mode == MODE_FWD_DF) return pers_impl<dfloat, double>(h, mode, d_B, ldb, nrhs, d_X, ldx, st, d_sub);
