@@ -487,14 +487,10 @@ int rs_solve_refined(rs_handle h, const void* B, int64_t ldb, int nrhs, void* X,
     // double-float); later residuals by the update r_{j+1} = r_j - A d_j (float /
     // complex float products on the small correction), all from the stored
     // forward factors.
-    const bool dfp = df_supported(h);
     bool first = true;
     for (;;) {
-      if (!dfp || first) {
-        if (dfp) rc = residual_df(h, (const double*)b, (const double*)x, (double*)r, nrhs, true, st);
-        else rc = residual_device(h, b, x, r, nrhs, nullptr, st);
-        if (rc != RS_OK) break;
-      }
+      if (first && (rc = residual_df(h, (const double*)b, (const double*)x, (double*)r, nrhs, true, st)) != RS_OK)
+        break;
       first = false;
       if ((rc = colnorm2_device(h, r, nrhs, nrm, st)) != RS_OK) break;
       cudaMemcpyAsync(hr.data(), nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
@@ -510,8 +506,7 @@ int rs_solve_refined(rs_handle h, const void* B, int64_t ldb, int nrhs, void* X,
       if (rc != RS_OK || done || its >= max_it) break;
       if ((rc = solve_pers_device(h, RS_PREC_FP32, r, N, nrhs, d, N, st)) != RS_OK) break;
       if ((rc = axpy_lowp_device(h, x, d, nrhs, st)) != RS_OK) break;
-      if (dfp && (rc = residual_df(h, (const double*)r, (const double*)d, (double*)r, nrhs, false, st)) != RS_OK)
-        break;
+      if ((rc = residual_df(h, (const double*)r, (const double*)d, (double*)r, nrhs, false, st)) != RS_OK) break;
       ++its;
     }
     if (rc != RS_OK) break;

@@ -114,12 +114,12 @@ int make_fwd_blocks(Handle* h, cudaStream_t st) {
   return h->cplx ? fwd_blocks<c128>(h, st) : fwd_blocks<double>(h, st);
 }
 
-// The stored forward factors exist for every kernel.
-bool df_supported(const Handle*) { return true; }
 
 // r = b - A_RS x with double-float products (full), or r = r - A_RS d with
-// float products (update): the forward operator runs on the persistent
-// two-pass kernel with the forward factors, subtracting its result from b.
+// float products (update), complex variants for complex kernels (the buffers
+// then hold complex double values): the forward operator runs on the
+// persistent two-pass kernel with the forward factors, subtracting its
+// result from b.
 int residual_df(Handle* h, const double* b, const double* x, double* r, int R, bool full, cudaStream_t st) {
   return solve_pers_device_sub(h, full ? MODE_FWD_DF : MODE_FWD_F32, x, h->N, R, r, h->N, b, st);
 }

@@ -179,14 +179,10 @@ int solve_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, vo
                  cudaStream_t st);
 int matvec_device(Handle* h, const void* d_X, int64_t ldx, int nrhs, void* d_Y, int64_t ldy,
                   cudaStream_t st);
-// r = b - A_RS x (all device, caller order, ld = N); colnorm: per column ||r||^2 (device, R doubles)
-int residual_device(Handle* h, const void* d_b, const void* d_x, void* d_r, int nrhs, double* d_rnorm2,
-                    cudaStream_t st);
 int colnorm2_device(Handle* h, const void* d_v, int nrhs, double* d_out, cudaStream_t st);
 int axpy_lowp_device(Handle* h, void* d_x, const void* d_d, int nrhs, cudaStream_t st);
-// Double-float forward operator (fwd2.cu).
+// Forward operator of the refinement from the stored forward factors (fwd2.cu).
 int make_fwd_blocks(Handle* h, cudaStream_t st);
-bool df_supported(const Handle* h);
 int residual_df(Handle* h, const double* b, const double* x, double* r, int R, bool full, cudaStream_t st);
 
 // Persistent single-launch solve (solve2.cu).  Besides RS_PREC_FP64 and

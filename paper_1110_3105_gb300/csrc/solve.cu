@@ -263,17 +263,6 @@ __global__ void k_fwd_down(FwdView fv, const S* T, const S* ypar, S* y, int R) {
   }
 }
 
-// r[perm[i] + c*N] = b[perm[i] + c*N] - y[i*R + c]   (caller order, ld = N)
-template <class S>
-__global__ void k_residual_out(const S* b, const S* y, const int* perm, int64_t N, int R, S* r) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * R) return;
-  int64_t i = e / R;
-  int c = (int)(e % R);
-  int64_t g = perm[i] + (int64_t)c * N;
-  r[g] = b[g] - y[e];
-}
-
 // out[c] = sum_i |v[i + c*N]|^2, one block per column (fixed order).
 template <class S>
 __global__ void k_colnorm2(const S* v, int64_t N, double* out) {
@@ -468,21 +457,7 @@ int matvec_impl(Handle* h, const S* X, int64_t ldx, int R, S* Y, int64_t ldy, cu
   return RS_OK;
 }
 
-template <class S>
-int residual_impl(Handle* h, const S* b, const S* x, S* r, int R, double* rn2, cudaStream_t st) {
-  RS_TRY(ensure_fwd(h, R, st));
-  int nb = div_up(h->N * R, 256);
-  k_perm_in<S, S><<<nb, 256, 0, st>>>(x, h->N, h->perm, h->N, R, (S*)h->fz[h->L]);
-  RS_CHECK_LAUNCH();
-  RS_TRY(forward_tree<S>(h, R, st));
-  k_residual_out<S><<<nb, 256, 0, st>>>(b, (const S*)h->fy[h->L], h->perm, h->N, R, r);
-  RS_CHECK_LAUNCH();
-  if (rn2) {
-    k_colnorm2<S><<<R, SV_NT, 0, st>>>(r, h->N, rn2);
-    RS_CHECK_LAUNCH();
-  }
-  return RS_OK;
-}
+
 
 }  // namespace
 
@@ -503,13 +478,6 @@ int solve_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, vo
 int matvec_device(Handle* h, const void* d_X, int64_t ldx, int nrhs, void* d_Y, int64_t ldy, cudaStream_t st) {
   if (h->cplx) return matvec_impl<c128>(h, (const c128*)d_X, ldx, nrhs, (c128*)d_Y, ldy, st);
   return matvec_impl<double>(h, (const double*)d_X, ldx, nrhs, (double*)d_Y, ldy, st);
-}
-
-int residual_device(Handle* h, const void* d_b, const void* d_x, void* d_r, int nrhs, double* d_rnorm2,
-                    cudaStream_t st) {
-  if (h->cplx)
-    return residual_impl<c128>(h, (const c128*)d_b, (const c128*)d_x, (c128*)d_r, nrhs, d_rnorm2, st);
-  return residual_impl<double>(h, (const double*)d_b, (const double*)d_x, (double*)d_r, nrhs, d_rnorm2, st);
 }
 
 int colnorm2_device(Handle* h, const void* d_v, int nrhs, double* d_out, cudaStream_t st) {
