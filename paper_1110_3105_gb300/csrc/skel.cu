@@ -1609,9 +1609,12 @@ __global__ void __launch_bounds__(GJB_NT) k_gjb_panel(BigArgs g, S* ws, Dims dim
 // The panel steps of k_gjb_panel on a thread-block cluster per box: CTA q
 // keeps rows [q rpc, q rpc + rpc) of the panel in shared memory.  A step:
 // every CTA publishes its largest candidate (magnitude bits, lowest row on
-// ties); after a cluster barrier all CTAs agree on the pivot row p and read
-// rows p and j of the panel from their owners; after a second barrier (no
-// row is changed while it may be read) each CTA applies the step to its rows.
+// ties) with a copy of that row, and the owner of row j a copy of row j
+// (both double-buffered by step parity); after one cluster barrier all CTAs
+// agree on the pivot row p, read the two copies from their owners and apply
+// the step to their own rows.  The copies are never written while they may
+// be read: a CTA writes the same parity again only two steps later, after
+// the next barrier, by which time every CTA has read them.
 template <class S, class Dims>
 __global__ void __launch_bounds__(GJB_NT) k_gjb_panel_cl(BigArgs g, S* ws, Dims dims, int c0, int rpc, int* bad) {
   namespace cg = cooperative_groups;
@@ -1623,6 +1626,7 @@ __global__ void __launch_bounds__(GJB_NT) k_gjb_panel_cl(BigArgs g, S* ws, Dims 
   __shared__ int cand_r[2];
   __shared__ int s_p, s_fail;
   __shared__ S rowp[GJB], rowj[GJB], newj[GJB];
+  __shared__ S pub_p[2][GJB], pub_j[2][GJB];   // copies of the candidate row and of row j
   const int cs = (int)cl.num_blocks(), q = (int)cl.block_rank();
   int m;
   S *M, *pb_in, *pb_out;
@@ -1666,6 +1670,12 @@ __global__ void __launch_bounds__(GJB_NT) k_gjb_panel_cl(BigArgs g, S* ws, Dims 
         cand_k[jj & 1] = bk;
         cand_r[jj & 1] = br;
       }
+      __syncthreads();
+      const int br = cand_r[jj & 1];
+      if (tid < bw) {
+        if (br < m) pub_p[jj & 1][tid] = P[(size_t)tid * rpc + (br - r0)];
+        if (j >= r0 && j < r0 + nr) pub_j[jj & 1][tid] = P[(size_t)tid * rpc + (j - r0)];
+      }
     }
     cl.sync();
     if (warp == 0) {   // the pivot (the same in every CTA) and rows p, j
@@ -1689,11 +1699,11 @@ __global__ void __launch_bounds__(GJB_NT) k_gjb_panel_cl(BigArgs g, S* ws, Dims 
       }
       if (ok && lane < bw) {
         const int op = bi / rpc, oj = j / rpc;
-        rowp[lane] = cl.map_shared_rank(P, op)[(size_t)lane * rpc + (bi - op * rpc)];
-        rowj[lane] = cl.map_shared_rank(P, oj)[(size_t)lane * rpc + (j - oj * rpc)];
+        rowp[lane] = cl.map_shared_rank(&pub_p[0][0], op)[(jj & 1) * GJB + lane];
+        rowj[lane] = cl.map_shared_rank(&pub_j[0][0], oj)[(jj & 1) * GJB + lane];
       }
     }
-    cl.sync();   // rows p and j have been read everywhere
+    __syncthreads();
     if (s_fail) break;   // uniform over the cluster
     const int p = s_p;
     const S inv = S(1.0) / rowp[jj];
@@ -1715,6 +1725,7 @@ __global__ void __launch_bounds__(GJB_NT) k_gjb_panel_cl(BigArgs g, S* ws, Dims 
     }
     __syncthreads();
   }
+  cl.sync();   // no CTA leaves while another may still read its row copies
   if (s_fail) {
     if (q == 0 && tid == 0) atomicOr(bad, 1);
     return;
