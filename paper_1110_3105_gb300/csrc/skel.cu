@@ -2475,10 +2475,9 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
   return RS_OK;
 }
 
-// The nsteps Gauss-Jordan steps of every box: one cooperative launch when the
-// grid fits on the GPU at once, else one launch per step.
-// Cluster of cs CTAs per box with cw = ceil(nsteps / cs) <= 64 columns each,
-// when its shared memory fits; returns false if no cluster shape fits.
+// The Gauss-Jordan steps of every box on one thread-block cluster per box:
+// cs CTAs with cw = ceil(nsteps / cs) <= 64 columns each, when their shared
+// memory fits (cs from pick_cluster); *done = false if no cluster shape fits.
 template <class S, class Dims>
 int run_gj_cluster(BigArgs g, S* ws, Dims dims, int nsteps, int nb, int* bad, cudaStream_t st, bool* done) {
   *done = false;
@@ -2494,6 +2493,10 @@ int run_gj_cluster(BigArgs g, S* ws, Dims dims, int nsteps, int nb, int* bad, cu
   return RS_OK;
 }
 
+// The nsteps in-place Gauss-Jordan steps of every box of a level: a cluster
+// per box when the columns fit; else (the root, or boxes too large for a
+// cluster) the blocked form; else one cooperative launch when the grid is
+// resident at once, else one launch per step.
 template <class S, class Dims>
 int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int ncb, size_t smem, int* bad,
                  cudaStream_t st) {
@@ -2561,8 +2564,10 @@ int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int
   return RS_OK;
 }
 
-// Big boxes (n <= 512): many CTAs per box; the pivot steps in one
-// cooperative launch (or one launch per step).
+// Big boxes (few of them, or too large for one CTA's shared memory): several
+// CTAs per box -- assembly, the two Gauss-Jordan inversions (run_gj_steps:
+// clusters, blocked for the root and the largest boxes, cooperative or
+// per-step launches as fallbacks) and the products.
 template <class S>
 int run_factor_big(Handle* h, Level& lv, FaArgs a, const Level* child, double by, cudaStream_t st) {
   const int nb = lv.nbox;
