@@ -76,3 +76,25 @@ def test_build_parameter_validation(lib):
         rc = _lib._lib.rs_build(q.ctypes.data, 100, dim, ctypes.byref(p), 1e-9, 64, None, ctypes.byref(out))
         assert rc == -1, (kid, dim, kwave)
         assert out.value is None
+
+
+def test_handle_and_argument_errors(lib):
+    """Null handles, bad sizes and bad kernel ids are rejected with RS_ERR_ARG
+    and a message, before any device work."""
+    import numpy as np
+    from paper_1110_3105_gb300 import _lib
+    _lib.load()
+    L = _lib._lib
+    x = np.zeros(4)
+    assert L.rs_solve(None, 0, x.ctypes.data, 4, 1, x.ctypes.data, 4, None) == -1
+    assert b"null handle" in L.rs_last_error()
+    assert L.rs_solve_refined(None, x.ctypes.data, 4, 1, x.ctypes.data, 4, 1e-10, 8, None, None, None) == -1
+    assert L.rs_matvec(None, x.ctypes.data, 4, 1, x.ctypes.data, 4, None) == -1
+    assert L.rs_stats(None, None) == -1
+    out = ctypes.c_void_p()
+    assert L.rs_server_create(0, 0, ctypes.byref(out)) == -1 and out.value is None
+    s2 = np.ones(3)
+    g = np.zeros(6)
+    assert L.rs_green(9, 0.0, s2.ctypes.data, 3, g.ctypes.data) == -1
+    assert L.rs_green(0, 0.0, s2.ctypes.data, -1, g.ctypes.data) == -1
+    assert L.rs_version().startswith(b"rs-gb300")
