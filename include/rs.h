@@ -24,7 +24,7 @@
  *     keeps.  A handle owns all device memory it allocates until rs_free.
  *   - Vectors are N x nrhs, column-major with leading dimension ld >= N, in
  *     the caller's original point order.  Real kernels use double, the
- *     Helmholtz kernel interleaved double complex (re, im).
+ *     Helmholtz kernels interleaved double complex (re, im).
  *   - stream: a cudaStream_t (NULL = legacy default stream).  Calls are
  *     stream-ordered; a call returns after its results are complete and, for
  *     host outputs, copied back.
@@ -144,10 +144,11 @@ int rs_solve_noalloc(rs_handle h, int precision, const void* B, int64_t ldb, int
                      void* X, int64_t ldx, void* stream);
 
 /* Mixed-precision solve with iterative refinement: x0 = FP32 solve of b;
- * repeat r = b - A_RS x in FP64 (forward operator of eq.
- * multilevel-compression with its kernel blocks evaluated on the fly from the
- * coordinates), x += FP32 solve of r, until every column has
- * ||r|| <= tol ||b|| or max_it corrections were applied.
+ * r0 = b - A_RS x0 (forward operator of eq. multilevel-compression from its
+ * stored blocks, double-float products -- about 48 significant bits; complex
+ * kernels: complex double-float); then repeat x += FP32 solve of r and
+ * r -= A_RS d (float products on the small correction) until every column
+ * has ||r|| <= tol ||b|| or max_it corrections were applied.
  *   its_out     (host, may be NULL) corrections applied
  *   relres_out  (host, may be NULL, nrhs entries) final ||r||/||b|| per column
  * Returns RS_OK even when tol was not met; check relres_out. */
@@ -205,8 +206,8 @@ int rs_profile_record(int i, int* cat, double* ms, double* bytes, double* flops)
 int rs_profile_record_start(int i, double* start_ms);
 /* Tile timeline of the last persistent solve launch made while
  * rs_profile_enable(2) was on, for the plan of `mode` (RS_PREC_FP64 or RS_PREC_FP32 solve; 2: float
- * and 3: double-float forward operator of the refinement residual, real
- * kernels) and nrhs columns.  Each tile is a block of one box's product at
+ * and 3: double-float forward operator of the refinement residual) and nrhs
+ * columns.  Each tile is a block of one box's product at
  * one tree depth (kind 0 upward, 1 root, 2 downward); per tile: kind, depth,
  * first row, column count, and the times in microseconds from the earliest
  * claim at which it was claimed by a CTA or warp, its dependencies were met
