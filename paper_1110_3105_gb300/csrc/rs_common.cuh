@@ -1,8 +1,9 @@
 // Shared device/host definitions for the recursive-skeletonization library.
 //
 // Scalar types: the real kernels (2D/3D Laplace) run in double (build) and
-// float (mixed-precision solve); the Helmholtz kernel in complex<double> and
-// complex<float>.  The complex type is a plain two-field struct with the
+// float (mixed-precision solve); the Helmholtz kernels (2D and 3D) in
+// complex<double> and complex<float>; double-float pairs (and complex pairs
+// of them) carry the refinement residual.  The complex type is a plain two-field struct with the
 // operators the kernels need, interleaved (re, im) like C99 double complex.
 #pragma once
 

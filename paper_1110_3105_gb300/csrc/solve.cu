@@ -7,7 +7,8 @@
 //            in the parent's active vector at skoff_i
 //   root     x_0 = calS^-1 c (the root's U holds calS^-1, k = 0)
 //   downward for depth 1..L:  x_i = u_i + calL_i x_parent[skoff_i ...]
-// Forward operator A_RS (eq. multilevel-compression, Sec. 3.3), FP64:
+// Forward operator A_RS (eq. multilevel-compression, Sec. 3.3), FP64 (the
+// rs_matvec path, an independent check of the refinement's residual):
 //   upward   z_parent[skoff_i + a] = (P_i z_i)[a] = z_i[sk_a] + sum_e T[a,e] z_i[rd_e]
 //            y_i = D^(l)_i z_i with the kernel block evaluated on the fly from
 //            the coordinates (leaf: A(I_i, I_i); above: w G between skeletons
