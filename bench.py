@@ -53,6 +53,10 @@ def peaks():
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per
 # kernel category, from the ncu captures summarised in profiles/ (the leaf-level
 # launch of the bench workload); None where no capture of the current kernel exists.
+# FP64 pipe utilisation of the same launch (sm__inst_executed_pipe_fp64, % of
+# peak sustained active): the ID's algorithmic flops exclude the fill and the
+# pivoting arithmetic, so its roofline fraction reads far below the pipe.
+NCU_FP64_PIPE = {"id": 0.875}
 NCU_TRAFFIC = {"id": (48086272 + 795648,
                       "k_id leaf-level launch (profiles/k_id_leaf_laplace2d_starfish_131072.md): "
                       "dram__bytes_read.sum + dram__bytes_write.sum")}
@@ -373,7 +377,8 @@ def run_ours(args, ws, rank, local):
     roof = {"bound": bound, "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": traffic[0] if traffic else None,
             "traffic_source": traffic[1] if traffic else None, "peak_source": peak_src,
-            "launches": dom["launches"], "avg_launch_ms": dom["ms"] / dom["launches"]}
+            "launches": dom["launches"], "avg_launch_ms": dom["ms"] / dom["launches"],
+            "ncu_fp64_pipe_active": NCU_FP64_PIPE.get(dom_name)}
     kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                    "GB_s": v["bytes"] / v["ms"] / 1e6 if v["ms"] else 0.0,
                    "GFLOP_s": v["flops"] / v["ms"] / 1e6 if v["ms"] else 0.0} for k, v in prof.items()}
