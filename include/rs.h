@@ -126,7 +126,9 @@ int rs_solve(rs_handle h, int precision, const void* B, int64_t ldb, int nrhs,
  * the device and stall other streams' work) or a process whose device-memory
  * budget is fixed at start-up.  Same arguments and result as rs_solve, except:
  *   - B and X must be device memory (RS_ERR_ARG otherwise: host buffers would
- *     need a staging allocation);
+ *     need a staging allocation), and the current device must be the one the
+ *     handle was built on (RS_ERR_ARG otherwise: the scratch array used is
+ *     the current device's);
  *   - the per-level solve vectors live in one static device array of
  *     RS_NOALLOC_SCRATCH_BYTES that every GPU which loads the library holds
  *     until the process exits; a solve needing more (about 2 * nrhs * scalar
@@ -278,6 +280,33 @@ int rs_server_destroy(rs_server s);
  *              RS_ERR_TIMEOUT; the next solve restarts its counters;
  *   "off" / NULL  disarm. */
 int rs_set_fault(const char* spec);
+
+/* Build-path override and path counters, for tests (the paper has no
+ * counterpart: these select among this library's own kernels, all of which
+ * compute the same ID and block elimination).  The multi-CTA forms of the ID
+ * and of the Gauss-Jordan steps normally run only on boxes too large for
+ * one CTA's shared memory (the top levels of the 3D workloads); the
+ * override sends small problems through them too, so that they can be
+ * compared with the oracle at sizes it finishes quickly.
+ * rs_set_path(spec): comma-separated tokens, cumulative; NULL, "" or "off"
+ * restores the normal selection:
+ *   "id:big"      every ID level on the multi-CTA form (cluster first)
+ *   "id:coop"     ... skipping the thread-block-cluster form
+ *   "id:step"     ... skipping the cooperative form too (a launch per pivot step)
+ *   "factor:big"  every factorization level on the multi-CTA form
+ *   "gj:blocked"  Gauss-Jordan steps without the cluster form
+ *   "gj:coop"     ... and without the blocked form
+ *   "gj:step"     ... and without the cooperative form
+ * A form whose launch does not fit the device falls through to the next, as
+ * in the normal selection.  RS_ERR_ARG for an unknown token.
+ * rs_path_counts(counts, cap, reset): level launches per form since the last
+ * reset, in the order ID {one CTA, cluster, cooperative, per step},
+ * factorization {one CTA, multi-CTA, generic}, Gauss-Jordan {cluster,
+ * blocked, cooperative, per step}; fills min(cap, total) entries of counts
+ * (host), clears them if reset != 0, and returns the total number of
+ * counters (11).  Process-wide. */
+int rs_set_path(const char* spec);
+int rs_path_counts(int64_t* counts, int cap, int reset);
 
 /* Release every resource of the handle.  NULL is accepted. */
 int rs_free(rs_handle h);

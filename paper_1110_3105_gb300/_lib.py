@@ -77,6 +77,8 @@ _PROTOS = {
     "rs_server_reset_stats": (ctypes.c_int, [_P]),
     "rs_server_handle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
     "rs_server_destroy": (ctypes.c_int, [_P]),
+    "rs_set_path": (ctypes.c_int, [ctypes.c_char_p]),
+    "rs_path_counts": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "rs_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "rs_profile_ncat": (ctypes.c_int, []),
     "rs_launch_count": (ctypes.c_int64, []),
@@ -390,6 +392,25 @@ class Server:
             self.destroy()
         except Exception:
             pass
+
+
+PATH_NAMES = ("id_cta", "id_cluster", "id_coop", "id_step", "factor_smem", "factor_big", "factor_generic",
+              "gj_cluster", "gj_blocked", "gj_coop", "gj_step")
+
+
+def rs_set_path(spec):
+    """Build-path override for tests: e.g. "id:step,gj:coop"; None or "off" restores the selection."""
+    _check(load().rs_set_path(None if spec is None else spec.encode()))
+
+
+def rs_path_counts(reset: bool = False) -> dict:
+    """Level launches per build form since the last reset: {name: count}."""
+    lib = load()
+    out = np.zeros(len(PATH_NAMES), dtype=np.int64)
+    n = lib.rs_path_counts(out.ctypes.data, len(PATH_NAMES), 1 if reset else 0)
+    if n < 0:
+        _check(n)
+    return dict(zip(PATH_NAMES, (int(v) for v in out)))
 
 
 def rs_set_fault(spec):

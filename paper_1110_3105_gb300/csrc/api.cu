@@ -47,6 +47,13 @@ static std::atomic<int> g_fault_wait{0};
 
 bool take_wait_fault() { return g_fault_wait.exchange(0) != 0; }
 
+static std::atomic<int> g_path_force{0};
+static std::atomic<long long> g_path_count[PATH_N];
+int path_force() { return g_path_force.load(); }
+void path_count(int which) {
+  if (which >= 0 && which < PATH_N) g_path_count[which].fetch_add(1);
+}
+
 // Handle memory is carved out of chunks taken from the stream-ordered pool
 // (whose memory the library keeps cached), so a build makes a handful of
 // allocation calls instead of one per table, and a rebuild reuses the memory
@@ -290,6 +297,11 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
     cudaGetLastError();
   }
   rs_handle_s* h = new rs_handle_s();
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(RS_ERR_CUDA, "rs_build: no current CUDA device");
+  }
   h->dim = dim;
   h->N = n;
   h->kp.kind = params->kernel_id;
@@ -425,6 +437,17 @@ int rs_solve_noalloc(rs_handle h, int precision, const void* B, int64_t ldb, int
     return fail(RS_ERR_ARG, "rs_solve_noalloc: bad precision");
   if (!is_device_ptr(B) || !is_device_ptr(X))
     return fail(RS_ERR_ARG, "rs_solve_noalloc: B and X must be device memory (host buffers would need staging)");
+  {
+    // the scratch array's address is looked up for the current device, the
+    // factors live on the handle's: the two must be the same GPU
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RS_ERR_CUDA, "rs_solve_noalloc: no current CUDA device");
+    }
+    if (dev != h->device)
+      return fail(RS_ERR_ARG, "rs_solve_noalloc: current device %d is not the handle's device %d", dev, h->device);
+  }
   cudaStream_t st = (cudaStream_t)stream;
   int rc = solve_noalloc_device(h, precision, B, ldb, nrhs, X, ldx, st);
   cudaError_t e = cudaStreamSynchronize(st);
@@ -609,6 +632,51 @@ int rs_set_fault(const char* spec) {
     return RS_OK;
   }
   return fail(RS_ERR_ARG, "rs_set_fault: unknown fault '%s'", spec);
+}
+
+int rs_set_path(const char* spec) {
+  rs::g_err.clear();
+  if (!spec || !*spec) {
+    g_path_force = 0;
+    return RS_OK;
+  }
+  static const std::pair<const char*, int> names[] = {
+      {"off", 0},
+      {"id:big", PF_ID_BIG},
+      {"id:coop", PF_ID_BIG | PF_ID_NOCLUSTER},
+      {"id:step", PF_ID_BIG | PF_ID_NOCLUSTER | PF_ID_NOCOOP},
+      {"factor:big", PF_FACTOR_BIG},
+      {"gj:blocked", PF_GJ_NOCLUSTER},
+      {"gj:coop", PF_GJ_NOCLUSTER | PF_GJ_NOBLOCKED},
+      {"gj:step", PF_GJ_NOCLUSTER | PF_GJ_NOBLOCKED | PF_GJ_NOCOOP}};
+  int f = 0;
+  std::string s(spec);
+  size_t pos = 0;
+  while (pos <= s.size()) {
+    size_t e = s.find(',', pos);
+    if (e == std::string::npos) e = s.size();
+    const std::string tok = s.substr(pos, e - pos);
+    bool found = false;
+    for (auto& nm : names)
+      if (tok == nm.first) {
+        f |= nm.second;
+        found = true;
+      }
+    if (!found) return fail(RS_ERR_ARG, "rs_set_path: unknown path '%s'", tok.c_str());
+    pos = e + 1;
+  }
+  g_path_force = f;
+  return RS_OK;
+}
+
+int rs_path_counts(int64_t* counts, int cap, int reset) {
+  rs::g_err.clear();
+  if (cap < 0 || (cap > 0 && !counts)) return fail(RS_ERR_ARG, "rs_path_counts: bad output");
+  for (int i = 0; i < PATH_N; ++i) {
+    const long long v = reset ? g_path_count[i].exchange(0) : g_path_count[i].load();
+    if (i < cap) counts[i] = v;
+  }
+  return PATH_N;
 }
 
 int rs_free(rs_handle h) {

@@ -106,6 +106,7 @@ struct Level {
 };
 
 struct Handle {
+  int device = -1;             // CUDA device the handle was built on (its memory lives there)
   int dim = 2;
   int64_t N = 0;
   KParams kp{};
@@ -154,6 +155,27 @@ struct Handle {
 
 // fault injection (api.cu): true once after rs_set_fault("wait")
 bool take_wait_fault();
+
+// Build-path selection override (rs_set_path, for tests that reach the
+// multi-CTA fallbacks on small problems) and per-path launch counters
+// (rs_path_counts).  The override only removes choices: every path it
+// leaves is one the production selection can take.
+enum PathForce {
+  PF_ID_BIG = 1,          // every ID level on the multi-CTA path (run_id_big)
+  PF_ID_NOCLUSTER = 2,    // ... without the thread-block-cluster form
+  PF_ID_NOCOOP = 4,       // ... and without the cooperative form (one launch per pivot step)
+  PF_FACTOR_BIG = 8,      // every factorization level on the multi-CTA path
+  PF_GJ_NOCLUSTER = 16,   // Gauss-Jordan steps without the cluster form
+  PF_GJ_NOBLOCKED = 32,   // ... without the blocked form
+  PF_GJ_NOCOOP = 64       // ... without the cooperative form
+};
+enum PathId {
+  PATH_ID_CTA, PATH_ID_CLUSTER, PATH_ID_COOP, PATH_ID_STEP,
+  PATH_FAC_SMEM, PATH_FAC_BIG, PATH_FAC_GENERIC,
+  PATH_GJ_CLUSTER, PATH_GJ_BLOCKED, PATH_GJ_COOP, PATH_GJ_STEP, PATH_N
+};
+int path_force();
+void path_count(int which);
 
 // allocation helper: records in h->allocs
 int dalloc(Handle* h, void** p, size_t bytes);

@@ -2343,8 +2343,10 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
       return sizeof(S) * ((size_t)w * a.mmax + a.mmax + 2) + sizeof(double) * ((size_t)w + 2) +
              sizeof(int) * ((size_t)a.nmax + w + 2);
     };
-    if (pick_cluster(k_bbid_cluster<S>, nb, maxn, BI_NT, smem_of, st, &cs, &cw, &smem)) {
+    if (!(path_force() & PF_ID_NOCLUSTER) &&
+        pick_cluster(k_bbid_cluster<S>, nb, maxn, BI_NT, smem_of, st, &cs, &cw, &smem)) {
       RS_TRY(launch_cluster(k_bbid_cluster<S>, nb, cs, BI_NT, smem, st, a, g, Mws, cw, a.lperm));
+      path_count(PATH_ID_CLUSTER);
       coop_done = true;
     }
   }
@@ -2353,7 +2355,7 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
   // cache is too large for shared memory)
   auto try_coop = [&](auto cbc) -> int {
     constexpr int CB = decltype(cbc)::value;
-    if (coop_done) return RS_OK;
+    if (coop_done || (path_force() & PF_ID_NOCOOP)) return RS_OK;
     const int ncbc = div_up(maxn, CB);
     const size_t co_smem = ((id_smem + 15) & ~(size_t)15) + sizeof(S) * (size_t)CB * a.mmax;
     if (co_smem > (size_t)max_dyn_smem()) return RS_OK;
@@ -2368,6 +2370,7 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
                                         st));
     RS_CHECK_LAUNCH();
     RS_CUDA(cudaFreeAsync(gb.count, st));
+    path_count(PATH_ID_COOP);
     coop_done = true;
     return RS_OK;
   };
@@ -2381,6 +2384,7 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
     // level has found its rank
     int* d_active = nullptr;
     int h_active = 1;
+    path_count(PATH_ID_STEP);
     RS_CUDA(cudaMallocAsync((void**)&d_active, sizeof(int), st));
     for (int j = 0; j < maxkmax; ++j) {
       k_bbid_step<S><<<nb * ncb, BI_NT, id_smem, st>>>(a, g, Mws, j, ncb, a.lperm);
@@ -2420,8 +2424,9 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
   S* Mws = nullptr;
   a.smem_path = (mbytes + extra <= limit) ? 1 : 0;
   // boxes too large for one CTA: several CTAs per box
-  if (!a.smem_path && a.geo.nproxy <= 256 && sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax <= 200 * 1024)
-    return run_id_big<S>(h, lv, a, mrows, st);
+  const bool big_ok =
+      a.geo.nproxy <= 256 && sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax <= 200 * 1024;
+  if (big_ok && (!a.smem_path || (path_force() & PF_ID_BIG))) return run_id_big<S>(h, lv, a, mrows, st);
   size_t smem = a.smem_path ? mbytes + extra : extra;
   if (smem > 227 * 1024) return fail(RS_ERR_ARG, "box too large for shared staging (m=%d n=%d)", a.mmax, a.nmax);
   if (!a.smem_path) {
@@ -2468,6 +2473,7 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
   }
   k_id<S, ID_NT><<<lv.nbox, ID_NT, smem, st>>>(a, Mws, (S*)lv.T);
   RS_CHECK_LAUNCH();
+  path_count(PATH_ID_CTA);
   prof_end(P_ID, st, 0.0, 0.0);
   if (Mws) RS_CUDA(cudaFreeAsync(Mws, st));
   if (pairs) RS_CUDA(cudaFreeAsync(pairs, st));
@@ -2489,6 +2495,7 @@ int run_gj_cluster(BigArgs g, S* ws, Dims dims, int nsteps, int nb, int* bad, cu
   };
   if (!pick_cluster(k_bb_gj_cluster<S, Dims>, nb, nsteps, BB_NT, smem_of, st, &cs, &cw, &smem)) return RS_OK;
   RS_TRY(launch_cluster(k_bb_gj_cluster<S, Dims>, nb, cs, BB_NT, smem, st, g, ws, dims, nsteps, cw, bad));
+  path_count(PATH_GJ_CLUSTER);
   *done = true;
   return RS_OK;
 }
@@ -2500,13 +2507,15 @@ int run_gj_cluster(BigArgs g, S* ws, Dims dims, int nsteps, int nb, int* bad, cu
 template <class S, class Dims>
 int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int ncb, size_t smem, int* bad,
                  cudaStream_t st) {
-  if (nb >= 2) {   // one cluster per box when the columns fit
+  const int force = path_force();
+  if (nb >= 2 && !(force & PF_GJ_NOCLUSTER)) {   // one cluster per box when the columns fit
     bool done = false;
     RS_TRY((run_gj_cluster<S, Dims>(g, ws, dims, nsteps, nb, bad, st, &done)));
     if (done) return RS_OK;
   }
-  if (nsteps >= 128) {   // the root, or boxes too large for a cluster: blocked, two launches per panel
+  if (nsteps >= 128 && !(force & PF_GJ_NOBLOCKED)) {   // the root, or boxes too large for a cluster: blocked
     const int m = nsteps;   // the largest box
+    path_count(PATH_GJ_BLOCKED);
     // panel steps on a cluster per box (rows split over its CTAs), else one CTA
     int pcs = 0, prpc = 0;
     size_t pc_smem = 0;
@@ -2546,7 +2555,8 @@ int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int
   const bool co_ok = csmem <= (size_t)max_dyn_smem();
   if (co_ok)
     RS_CUDA(cudaFuncSetAttribute(k_bb_gj_coop<S, Dims>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem));
-  if (co_ok && coop_fits((const void*)k_bb_gj_coop<S, Dims>, nb * ncb, BB_NT, csmem)) {
+  if (co_ok && !(force & PF_GJ_NOCOOP) && coop_fits((const void*)k_bb_gj_coop<S, Dims>, nb * ncb, BB_NT, csmem)) {
+    path_count(PATH_GJ_COOP);
     GridBar gb{};
     RS_TRY(make_bar(&gb, bad + 1, st));   // the status word after the singularity flag
     void* args[] = {&g, &ws, &dims, &nsteps, &ncb, &bad, &gb};
@@ -2557,6 +2567,7 @@ int run_gj_steps(Handle* h, BigArgs g, S* ws, Dims dims, int nsteps, int nb, int
     return RS_OK;
   }
   RS_CUDA(cudaFuncSetAttribute(k_bb_gj_step<S, Dims>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  path_count(PATH_GJ_STEP);
   for (int j = 0; j < nsteps; ++j) {
     k_bb_gj_step<S, Dims><<<nb * ncb, BB_NT, smem, st>>>(g, ws, dims, j, ncb, bad);
     RS_CHECK_LAUNCH();
@@ -2647,7 +2658,7 @@ int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t 
   // one CTA per box in shared memory when the boxes fit and are enough to
   // spread over the SMs; a few large boxes take several CTAs each
   const bool few = 2 * lv.nbox < num_sms() && lv.maxn >= 64 && sizeof(S) * (size_t)lv.maxn <= 200 * 1024;
-  const bool smem_path = sm_need <= 200 * 1024 && !few;
+  const bool smem_path = sm_need <= 200 * 1024 && !few && !(path_force() & PF_FACTOR_BIG);
   double fl0 = 0.0, by0 = 0.0;
   for (int b = 0; b < lv.nbox; ++b) {
     double n = lv.h_n[b], k = lv.h_k[b];
@@ -2663,10 +2674,15 @@ int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t 
     k_factor_smem<S, FA_SM_NT><<<lv.nbox, FA_SM_NT, sm_need, st>>>(a, (const S*)lv.T, cL, (S*)lv.U, (S*)lv.Lf,
                                                                     (S*)lv.Lam);
     RS_CHECK_LAUNCH();
+    path_count(PATH_FAC_SMEM);
     prof_end(P_FACTOR, st, by0, fl0);
     return RS_OK;
   }
-  if (sizeof(S) * (size_t)lv.maxn <= 200 * 1024) return run_factor_big<S>(h, lv, a, child, by0, st);
+  if (sizeof(S) * (size_t)lv.maxn <= 200 * 1024) {
+    path_count(PATH_FAC_BIG);
+    return run_factor_big<S>(h, lv, a, child, by0, st);
+  }
+  path_count(PATH_FAC_GENERIC);
   int64_t* dws;
   RS_TRY(upload(h, &dws, wsoff, st));
   a.wsoff = dws;

@@ -157,6 +157,51 @@ def test_fp32_solve_and_refinement(built):
     assert np.all(np.abs(true_rel - rel) <= 1e-12 + 1e-3 * true_rel), (true_rel, rel)
 
 
+def test_matvec_matches_oracle_apply(built):
+    """rs_matvec (FP64 forward operator, Sec. 3.3) against the oracle's own
+    compressed operator A_RS, column by column: the two compress A with their
+    own skeletons, each within eps of A (Def. 2.3), so they agree to 10 eps."""
+    rs = rs_mod()
+    n, eps = built["n"], built["eps"]
+    x = ri.rhs(n, 3, seed=31, complex_=built["cplx"])
+    y = np.zeros_like(x)
+    rs.rs_matvec(built["H"], x, y)
+    yo = built["F"].apply(x)
+    err = np.linalg.norm(y - yo, axis=0) / np.linalg.norm(yo, axis=0)
+    assert np.all(err <= 10 * eps), err
+
+
+def _check_refined_against_oracle(built, B, Xr, rel, tol):
+    """The refined solution against the oracle's FP64 solve (10 eps per
+    column); the residual of the GPU's X under the oracle's A_RS and under
+    the dense A (both within 10 eps: the GPU's operator differs from each by
+    at most that); and the library's reported residual against the oracle's
+    measurement of it (they may differ by the two operators' difference)."""
+    eps = built["eps"]
+    Xo = built["F"].solve(B)
+    err = np.linalg.norm(Xr - Xo, axis=0) / np.linalg.norm(Xo, axis=0)
+    assert np.all(err <= 10 * eps), err.max()
+    nb = np.linalg.norm(B, axis=0)
+    r_oracle = np.linalg.norm(built["F"].apply(Xr) - B, axis=0) / nb
+    assert np.all(r_oracle <= 10 * eps), r_oracle.max()
+    assert np.all(rel <= tol), rel.max()
+    assert np.all(np.abs(r_oracle - rel) <= 10 * eps), np.abs(r_oracle - rel).max()
+    if built["n"] <= 8192:
+        A = dense.dense_matrix(built["kind"], built["pts"], built["w"], built["kw"])
+        r_true = np.linalg.norm(A @ Xr - B, axis=0) / nb
+        assert np.all(r_true <= 10 * eps), r_true.max()
+
+
+def test_refined_matches_oracle(built):
+    rs = rs_mod()
+    n = built["n"]
+    B = ri.rhs(n, 5, seed=33, complex_=built["cplx"])
+    Xr = np.zeros_like(B)
+    its, rel = rs.rs_solve_refined(built["H"], B, Xr, tol=1e-10, max_it=8)
+    assert its >= 1
+    _check_refined_against_oracle(built, B, Xr, rel, 1e-10)
+
+
 @pytest.mark.parametrize("nrhs", [40, 70, 130])
 def test_many_rhs_tiles(built, nrhs):
     """Block-tiled multi-column solve (column blocks of 32/64/128 with a ragged
@@ -187,6 +232,7 @@ def test_many_rhs_tiles(built, nrhs):
     true_rel = np.linalg.norm(Y - B, axis=0) / np.linalg.norm(B, axis=0)
     assert np.all(true_rel <= 1e-10), true_rel.max()
     assert np.all(np.abs(true_rel - rel) <= 1e-12 + 1e-3 * true_rel)
+    _check_refined_against_oracle(built, B, Xr, rel, 1e-10)
 
 
 def test_device_pointers_same_as_host(built):

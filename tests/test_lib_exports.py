@@ -98,3 +98,14 @@ def test_handle_and_argument_errors(lib):
     assert L.rs_green(9, 0.0, s2.ctypes.data, 3, g.ctypes.data) == -1
     assert L.rs_green(0, 0.0, s2.ctypes.data, -1, g.ctypes.data) == -1
     assert L.rs_version().startswith(b"rs-gb300")
+
+
+def test_path_spec_validation(lib):
+    from paper_1110_3105_gb300 import _lib
+    _lib.load()
+    assert _lib._lib.rs_set_path(b"id:bogus") == -1
+    assert _lib._lib.rs_set_path(b"id:step,gj:coop") == 0
+    assert _lib._lib.rs_set_path(b"off") == 0
+    assert _lib._lib.rs_set_path(None) == 0
+    counts = _lib.rs_path_counts(reset=True)
+    assert len(counts) == 11 and all(v == 0 for v in counts.values())
