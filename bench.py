@@ -4,18 +4,25 @@ One step = one pass of the whole hot path over one batch of synthetic input:
 rs_build (tree, proxy compression + ID, block elimination, root) of the
 131072-point starfish 2D Laplace system (eps 1e-10, leaf 64, 64 proxies)
 followed by rs_solve_refined of a 256-column right-hand-side batch to
-relative residual <= 1e-10 (FP32 solves, FP64 residual of the compressed
-operator).  `value` = right-hand sides solved per second over whole steps.
+relative residual <= 1e-10 (FP32 solves, FP64-accurate residual of the
+compressed operator).  `value` = right-hand sides solved per second over
+whole steps.
 
-Also reported (same run): build time, the resident-factorization refined
-throughput, the plain FP64 one-RHS-at-a-time solve throughput, the roofline
-of the dominant kernel (CUDA events on the library's stream), clocks during
-the timed region, an end-to-end number through the C ABI with host buffers,
-and the CPU oracle timed on this host.
+Also reported (same run): build time; the solve phase by itself (one-RHS
+FP64 and FP32 solves and the 256-column FP32 solve, each against the HBM
+peak and its FMA peak, measured in this run); refined throughput at 1, 16
+and 256 columns; the plain FP64 one-RHS-at-a-time solve; the 4096-point
+circle (plain FP64, one RHS); a serving session on the mix of resident
+factorizations with admitted builds, at the offered rate and below
+capacity; the roofline of the dominant kernel (CUDA events on the
+library's stream); clocks during the timed region; an end-to-end number
+through the C ABI with host buffers; and the CPU oracle timed on this host
+(all cores and one core, full size).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Multi-GPU: launched under torchrun; each rank builds and solves its own
-replica (no collective on the data path); value = all ranks' RHS / max time.
+Multi-GPU: launched under torchrun; every rank holds its own replica of the
+factorization and solves its slice of one global batch of columns (no
+collective on the data path); value = all ranks' RHS / max time.
 """
 from __future__ import annotations
 
@@ -40,9 +47,12 @@ METRIC = "RHS solves/s at rel. residual<=1e-10 (served vs plain FP64); build s; 
 NRHS = 256
 TOL = 1e-10
 SERVE_COLS = 1024   # column cap of one served batch (continuous batching)
+DTYPE = "f64 build; f32 solves + double-float residual (refined to 1e-10)"
 
 
 def peaks():
+    """HBM and bf16 denominators: MEASURED_PEAKS.json (written on this pool's
+    GPUs before the run), else the fallback figures."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
@@ -50,21 +60,49 @@ def peaks():
     return dict(hbm=6800.0, bf16=1900.0, src="fallback")
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per
-# kernel category, from the ncu captures summarised in profiles/ (the leaf-level
-# launch of the bench workload); None where no capture of the current kernel exists.
-# FP64 pipe utilisation of the same launch (sm__inst_executed_pipe_fp64, % of
-# peak sustained active): the ID's algorithmic flops exclude the fill and the
-# pivoting arithmetic, so its roofline fraction reads far below the pipe.
-NCU_FP64_PIPE = {"id": 0.875}
-NCU_TRAFFIC = {"id": (48086272 + 795648,
-                      "k_id leaf-level launch (profiles/k_id_leaf_laplace2d_starfish_131072.md): "
-                      "dram__bytes_read.sum + dram__bytes_write.sum")}
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from an ncu summary in profiles/, if
+    the summary was captured on the current source of that kernel.  A
+    summary states it on a line
+      bench-traffic: kernel=<name> source=<file> sha256=<hex> dram_bytes=<int> launch=<what>
+    where sha256 is the hash of the source file at capture time; once the
+    file has changed, the counters no longer describe the kernel and the
+    traffic is reported as null."""
+    import glob
+    import hashlib
+    stale = None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            if not line.startswith("bench-traffic:"):
+                continue
+            kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+            if kv.get("kernel") != kernel:
+                continue
+            src = os.path.join(ROOT, kv.get("source", ""))
+            cur = hashlib.sha256(open(src, "rb").read()).hexdigest() if os.path.isfile(src) else None
+            where = f"{os.path.relpath(path, ROOT)} ({kv.get('launch', '')})"
+            if cur == kv.get("sha256"):
+                return int(kv["dram_bytes"]), f"ncu capture {where}, source unchanged since"
+            stale = f"ncu capture {where} predates the current {kv.get('source')}"
+    return None, stale or "no ncu capture of this kernel"
 
-# FP64 FMA throughput of GB300: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-# = 1.26 TFLOP/s nominal; a dependent-chain-free probe measured 1.195 TFLOP/s.
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
-FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
 
 
 class Clocks:
@@ -131,120 +169,238 @@ def workload_inputs():
     return w, pts, h
 
 
-def oracle_step_sample(n_sample: int) -> float:
-    """Seconds of one oracle step on a sample: build at n_sample + solve NRHS."""
+def oracle_steps(n: int, steps: int, workers: int) -> list:
+    """Seconds of each of `steps` oracle steps at N = n (build + NRHS-column
+    solve of the starfish workload), with the boxes of each level spread
+    over `workers` processes (1: one process).  Runs in a fresh interpreter
+    that never touches CUDA, so the oracle's worker processes can be forked;
+    BLAS is single-threaded so that the workers do not oversubscribe."""
     code = f"""
-import sys, time, numpy as np
+import sys, time
 sys.path.insert(0, {ROOT!r})
 import rs_inputs as ri
 from oracle import rskel
-pts, h = ri.starfish({n_sample})
-B = ri.rhs({n_sample}, {NRHS}, seed=1)
-t = time.perf_counter()
-F = rskel.build(pts, rskel.Params(kind='laplace2d', w=h, eps=1e-10, leaf=64, nproxy=64))
-X = F.solve(B)
-print(time.perf_counter() - t)
+pts, h = ri.starfish({n})
+B = ri.rhs({n}, {NRHS}, seed=1)
+bm = rskel.process_box_map({workers}) if {workers} > 1 else None
+for _ in range({steps}):
+    t = time.perf_counter()
+    F = rskel.build(pts, rskel.Params(kind='laplace2d', w=h, eps=1e-10, leaf=64, nproxy=64), bm)
+    X = F.solve(B)
+    print('STEP', time.perf_counter() - t, flush=True)
 """
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
-    return float(out.stdout.strip().splitlines()[-1])
+    return [float(l.split()[1]) for l in out.stdout.splitlines() if l.startswith("STEP")]
 
 
-def cpu_baseline(steps: int = 1):
-    """The oracle on this host: single thread, sample = 1/8 of the workload."""
-    w = ri.WORKLOADS[WORKLOAD]
-    n_sample = w["n"] // 8
-    ts = [oracle_step_sample(n_sample) for _ in range(steps)]
-    t = min(ts)
-    # The 2D build and solve are O(N) (Sec. 4, d = 1), so a step at full N
-    # costs N / n_sample times the sample's.
-    full = t * w["n"] / n_sample
-    return {"value": NRHS / full, "unit": "RHS/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle build + {NRHS}-column solve on the same starfish family at N={n_sample} "
-                      f"({t:.2f} s), scaled by N/{n_sample} (O(N) cost in 2D, Sec. 4); single thread",
-            "sample_s": t}
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline():
+    """The oracle on this host at the workload's full size: one step on all
+    cores (the boxes of a level over worker processes) and one step on one
+    core."""
+    n = ri.WORKLOADS[WORKLOAD]["n"]
+    cores = host_cores()
+    t_all = oracle_steps(n, 1, cores)[0]
+    t_one = oracle_steps(n, 1, 1)[0]
+    return {"value": NRHS / t_all, "unit": "RHS/s", "cores": cores, "kind": "oracle",
+            "sample": f"one full step at N={n}: oracle build (boxes of each level over {cores} processes) + "
+                      f"{NRHS}-column FP64 solve, {t_all:.2f} s",
+            "cpu_model": cpu_model(), "step_s": t_all,
+            "single_core": {"value": NRHS / t_one, "step_s": t_one, "cores": 1}}
 
 
 def run_reference(args, ws, rank):
+    """The oracle as the reference arm: each step is one full-size step on all
+    host cores (rank 0 only)."""
     if rank != 0:
         return
-    t_all = []
-    for _ in range(args.warmup):
-        oracle_step_sample(ri.WORKLOADS[WORKLOAD]["n"] // 8)
-    for _ in range(args.steps):
-        t_all.append(oracle_step_sample(ri.WORKLOADS[WORKLOAD]["n"] // 8))
     n = ri.WORKLOADS[WORKLOAD]["n"]
-    scale = n / (n // 8)
-    per_step = statistics.median(t_all) * scale
+    cores = host_cores()
+    t_all = oracle_steps(n, args.warmup + args.steps, cores)[args.warmup:]
+    per_step = sum(t_all) / len(t_all)
     value = NRHS / per_step
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "nrhs": NRHS, "tol": TOL},
-            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: oracle build + {NRHS}-column solve at N={n // 8} of the "
-                                       f"same starfish family, scaled by {scale:g} (O(N) in 2D)"},
+            "cpu_baseline": {"value": value, "unit": "RHS/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: the full oracle step at N={n} (build with the boxes of each "
+                                       f"level over {cores} processes + {NRHS}-column FP64 solve)",
+                             "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def serving_session(rs, torch, P, h, w, window_s=1.0, rate=2000.0, seed=7):
-    """Poisson arrivals (mean `rate` req/s, 1..64 columns each) for `window_s`
-    seconds against the resident factorization, plus one memory-admitted
-    build of a random starfish (serving mix form); returns RHS/s and
-    latency percentiles of the completed requests."""
-    n = w["n"]
-    H = rs.rs_build(P, "laplace2d", h, w["eps"], w["leaf"], w["nproxy"])
+SERVE_MIX = (("laplace2d_starfish_131072", 1e-10), ("helmholtz2d_starfish_65536", 1e-9),
+             ("laplace3d_sphere_32768", 1e-10))
+
+
+def _pinned(torch, n, cols, cplx, data=None):
+    dt = torch.complex128 if cplx else torch.float64
+    t = torch.empty((cols, n), dtype=dt).pin_memory()
+    if data is not None:
+        t.copy_(torch.from_numpy(np.ascontiguousarray(data.T)))
+    return t.t()   # n x cols, column-major, pinned
+
+
+def serving_session(rs, torch, resident, window_s, rate, seed, build_every_s=5.0, backlog_cols=64 * SERVE_COLS):
+    """The serving mix: the `resident` factorizations [(Handle, n, complex,
+    tol)] registered with one server; Poisson arrivals at `rate` requests/s
+    with U{1..64} columns each, each for a factorization drawn uniformly from
+    those resident so far; every `build_every_s` a new 2D Laplace build of a
+    random starfish (N in {8192 .. 65536}) is submitted, admitted by free
+    HBM, and joins the mix once built.  Arrivals that find more than
+    `backlog_cols` columns queued are shed (counted, not submitted).
+    Returns throughput, latency percentiles and the admission record."""
     S = rs.Server(max_cols=SERVE_COLS)
-    hid = S.add(H)
-    # warm the server's buffers (and the launch autotuner) with full batches
-    for cols in (SERVE_COLS, SERVE_COLS // 2):
-        Bw = torch.from_numpy(ri.rhs(n, cols, seed=900)).t().contiguous().pin_memory().t()
-        Xw = torch.empty((cols, n), dtype=torch.float64).pin_memory().t()
-        S.wait(S.submit(hid, Bw, Xw))
-    nb, arms, amp, rot = ri.serving_curve(seed, 0)
-    pts2, h2 = ri.starfish(16384, arms=arms, amp=amp, rotation=rot)
-    bt = S.submit_build(pts2, "laplace2d", h2, w["eps"], w["leaf"], w["nproxy"])
+    targets = []
+
+    def add_target(hid, n, cplx, tol):
+        B = _pinned(torch, n, 64, cplx, ri.rhs(n, 64, seed=901 + len(targets), complex_=cplx))
+        ring = [_pinned(torch, n, 64, cplx) for _ in range(4)]
+        targets.append((hid, n, cplx, tol, B, ring))
+
+    for H, n, cplx, tol in resident:
+        add_target(S.add(H), n, cplx, tol)
+    for hid, n, cplx, tol, B, ring in targets:   # warm the workers' buffers and the tile autotuner
+        Bw = _pinned(torch, n, SERVE_COLS, cplx, ri.rhs(n, SERVE_COLS, seed=900, complex_=cplx))
+        Xw = _pinned(torch, n, SERVE_COLS, cplx)
+        S.wait(S.submit(hid, Bw, Xw, tol=tol))
     S.reset_stats()
-    u = ri.uniform01(seed, 200000, stream=7)
-    gaps = -np.log(u) / rate
-    cols = 1 + (ri.uniform01(seed, 200000, stream=8) * 64).astype(int).clip(0, 63)
-    B = torch.from_numpy(ri.rhs(n, 64, seed=901)).t().contiguous().pin_memory().t()
-    ring = [torch.empty((64, n), dtype=torch.float64).pin_memory().t() for _ in range(8)]
-    tickets, i = [], 0
+    nreq = int(rate * window_s * 1.5) + 100
+    gaps = -np.log(ri.uniform01(seed, nreq, stream=7)) / rate
+    cols = 1 + (ri.uniform01(seed, nreq, stream=8) * 64).astype(int).clip(0, 63)
+    pick = ri.uniform01(seed, nreq, stream=9)
+    tickets, builds, built = [], [], []
+    submitted_cols = shed = shed_cols = offered_cols = 0
+    done_cols = 0
+    i, nb = 0, 0
     t0 = time.perf_counter()
-    t_next = t0
+    t_next, t_build, t_poll = t0, t0, t0
     while True:
         now = time.perf_counter()
         if now - t0 >= window_s:
             break
+        if now >= t_build:
+            n2, arms, amp, rot = ri.serving_curve(seed, nb)
+            pts2, h2 = ri.starfish(n2, arms=arms, amp=amp, rotation=rot)
+            builds.append((S.submit_build(pts2, "laplace2d", h2, 1e-10, 64, 64), n2))
+            nb += 1
+            t_build += build_every_s
+        if now >= t_poll:
+            done_cols = S.stats()["rhs"]
+            for bt in list(builds):
+                try:
+                    r = S.wait(bt[0], timeout_s=1e-4)
+                except rs.RSError as e:
+                    if e.code == -5:
+                        continue
+                    raise
+                builds.remove(bt)
+                built.append(r["status"])
+                if r["status"] == 0:
+                    add_target(r["result"], bt[1], False, 1e-10)
+            t_poll = now + 0.1
         if now < t_next:
             time.sleep(min(t_next - now, 0.0005))
             continue
         c = int(cols[i])
-        tickets.append(S.submit(hid, B[:, :c], ring[i % len(ring)][:, :c]))
+        offered_cols += c
+        if submitted_cols - done_cols > backlog_cols:
+            shed += 1
+            shed_cols += c
+        else:
+            hid, n, cplx, tol, B, ring = targets[min(len(targets) - 1, int(pick[i] * len(targets)))]
+            tickets.append(S.submit(hid, B[:, :c], ring[i % len(ring)][:, :c], tol=tol))
+            submitted_cols += c
         t_next += gaps[i]
         i += 1
-    offered = sum(int(cols[j]) for j in range(i)) / window_s
     worst, bad = 0.0, 0
     for t in tickets:
         r = S.wait(t)
         bad += r["status"] != 0
         worst = max(worst, r["relres"])
     st = S.stats()
-    rb = S.wait(bt)
+    for bt in builds:
+        built.append(S.wait(bt[0])["status"])
     S.destroy()
-    H.free()
     return {"rhs_per_s": st["rhs"] / st["elapsed_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "requests": st["requests"], "failed": bad, "mean_batch_cols": st["mean_batch_cols"],
-            "offered_rhs_per_s": offered, "arrival_rate_per_s": rate, "window_s": window_s,
-            "relres_max": worst, "admitted_build_status": rb["status"],
-            "note": "offered load above capacity: latency includes queueing"}
+            "offered_rhs_per_s": offered_cols / window_s, "arrival_rate_per_s": rate, "window_s": window_s,
+            "shed_requests": shed, "shed_rhs": shed_cols, "backlog_cap_cols": backlog_cols,
+            "relres_max": worst, "builds_submitted": nb, "builds_admitted": sum(1 for b in built if b == 0),
+            "builds_refused_oom": sum(1 for b in built if b == -2), "factorizations_served": len(targets),
+            "resident_gb": st["resident_bytes"] / 1e9}
+
+
+def serving(rs, torch, H2, n2, window_s, stream):
+    """Configs 2-4 resident (built here besides the benchmark's handle);
+    a session at the configuration's rate (2000 requests/s, ~65k RHS/s
+    offered), then one at 70% of the capacity that session measured."""
+    resident = [(H2, n2, False, 1e-10)]
+    own = []
+    for name, tol in SERVE_MIX[1:]:
+        wl = ri.WORKLOADS[name]
+        pts, wt = ri.geometry(wl["geom"], wl["n"])
+        H = rs.rs_build(pts, wl["kernel"], wt, wl["eps"], wl["leaf"], wl["nproxy"], k_wave=wl.get("kwave", 0.0))
+        own.append(H)
+        resident.append((H, wl["n"], wl["kernel"].startswith("helmholtz"), tol))
+    try:
+        sat = serving_session(rs, torch, resident, window_s, 2000.0, seed=7)
+        rate2 = 0.7 * sat["rhs_per_s"] / 32.5
+        below = serving_session(rs, torch, resident, max(10.0, window_s / 3), rate2, seed=8)
+    finally:
+        for H in own:
+            H.free()
+    return {"mix": [name for name, _ in SERVE_MIX] + ["new 2D Laplace builds, random starfish, N in 8192..65536"],
+            "at_config_rate": sat, "below_capacity": below}
+
+
+def solve_phase(rs, torch, H, B, n, stream, pk, fp64_peak, fp32_peak):
+    """The solve by itself on the resident factorization: device time per
+    launch from the library's CUDA-event profiler, algorithmic bytes = the
+    factors one solve reads (FP64 or FP32 copies) + B read and X written
+    (double), flops = 2 x stored scalars per column."""
+    st = H.stats()
+    scal = st["factor_scalars"]
+    out = {}
+    cases = (("r1_fp64", 1, rs.RS_PREC_FP64, 8, "solve_fp64"), ("r1_fp32", 1, rs.RS_PREC_FP32, 4, "solve_fp32"),
+             ("r16_fp64", 16, rs.RS_PREC_FP64, 8, "solve_fp64"), ("r256_fp32", NRHS, rs.RS_PREC_FP32, 4, "solve_fp32"))
+    for name, R, prec, sb, cat in cases:
+        b = B[:, :R].clone()
+        x = torch.zeros_like(b)
+        for _ in range(3):
+            rs.rs_solve(H, b, x, precision=prec, stream=stream)
+        torch.cuda.synchronize()
+        reps = 50 if R == 1 else 10
+        rs.rs_profile_enable(True)
+        for _ in range(reps):
+            rs.rs_solve(H, b, x, precision=prec, stream=stream)
+        torch.cuda.synchronize()
+        prof = rs.rs_profile_read()
+        rs.rs_profile_enable(False)
+        ms = prof[cat]["ms"] / prof[cat]["launches"]
+        by = scal * sb + 2.0 * n * R * 8
+        fl = 2.0 * scal * R
+        peak = fp64_peak if prec == rs.RS_PREC_FP64 else fp32_peak
+        out[name] = {"nrhs": R, "us_per_solve": ms * 1e3, "rhs_per_s": R / (ms * 1e-3),
+                     "bytes": by, "GB_s": by / ms / 1e6, "hbm_frac": by / ms / 1e6 / pk["hbm"],
+                     "GFLOP_s": fl / ms / 1e6, "fma_frac": fl / ms / 1e6 / peak,
+                     "fma_peak": "FP64" if prec == rs.RS_PREC_FP64 else "FP32"}
+    return out
 
 
 def run_ours(args, ws, rank, local):
     import torch
     import paper_1110_3105_gb300 as rs
+    from paper_1110_3105_gb300.replicas import column_range
 
     torch.cuda.set_device(local)
     dist = None
@@ -253,7 +409,9 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl")
     w, pts, h = workload_inputs()
     n = w["n"]
-    Bh = ri.rhs(n, NRHS, seed=100 + rank)
+    # this rank's slice of one global batch of ws x NRHS columns
+    c0, c1 = column_range(ws * NRHS, ws, rank)
+    Bh = ri.rhs_columns(n, c0, c1, seed=100)
     # device-resident inputs (point-major points, column-major B)
     P = torch.from_numpy(np.ascontiguousarray(pts.T)).cuda().t()
     B = torch.from_numpy(Bh).cuda().t().contiguous().t()
@@ -295,7 +453,10 @@ def run_ours(args, ws, rank, local):
     ms_step = ms / args.steps
     value = replica_throughput(ws, NRHS, args.steps, ms)
 
-    # breakdown on the resident factorization (outside the timed region)
+    # ---- outside the timed region: the parts of the path by themselves
+    fp64_peak = rs.rs_probe_fma_peak(rs.RS_PREC_FP64)
+    fp32_peak = rs.rs_probe_fma_peak(rs.RS_PREC_FP32)
+    pk = peaks()
     H = rs.rs_build(P, "laplace2d", h, w["eps"], w["leaf"], w["nproxy"], stream=stream)
     st = H.stats()
     torch.cuda.synchronize()
@@ -307,21 +468,28 @@ def run_ours(args, ws, rank, local):
         Ht = rs.rs_build(P, "laplace2d", h, w["eps"], w["leaf"], w["nproxy"], stream=stream, id_arith="dfloat")
         tbd.append(Ht.stats()["build_ms"])
         Ht.free()
-    rs.rs_solve_refined(H, B, X, tol=TOL, max_it=8, stream=stream)
-    torch.cuda.synchronize()
-    t = time.perf_counter()
-    reps = 3
-    for _ in range(reps):
-        its, rel = rs.rs_solve_refined(H, B, X, tol=TOL, max_it=8, stream=stream)
-    torch.cuda.synchronize()
-    refined_ms = (time.perf_counter() - t) / reps * 1e3
+    phase = solve_phase(rs, torch, H, B, n, stream, pk, fp64_peak, fp32_peak)
+    refined = {}
+    for R in (1, 16, NRHS):
+        b = B[:, :R].clone()
+        x = torch.zeros_like(b)
+        rs.rs_solve_refined(H, b, x, tol=TOL, max_it=8, stream=stream)
+        torch.cuda.synchronize()
+        reps = 20 if R < NRHS else 3
+        t = time.perf_counter()
+        for _ in range(reps):
+            its, rel = rs.rs_solve_refined(H, b, x, tol=TOL, max_it=8, stream=stream)
+        torch.cuda.synchronize()
+        rms = (time.perf_counter() - t) / reps * 1e3
+        refined[str(R)] = {"ms_per_batch": rms, "rhs_per_s": R / (rms / 1e3), "corrections": its,
+                           "relres_max": float(np.max(rel))}
     b1 = B[:, :1].clone()
     x1 = torch.zeros_like(b1)
     for _ in range(5):
         rs.rs_solve(H, b1, x1, stream=stream)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    nplain = 50
+    nplain = 100
     for _ in range(nplain):
         rs.rs_solve(H, b1, x1, stream=stream)
     torch.cuda.synchronize()
@@ -331,6 +499,7 @@ def run_ours(args, ws, rank, local):
     rs.rs_matvec(H, x1, y1, stream=stream)
     torch.cuda.synchronize()
     plain_rel = float(torch.linalg.norm(y1 - b1) / torch.linalg.norm(b1))
+    circle = config1(rs, torch, stream)
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     Bp = torch.empty((NRHS, n), dtype=torch.float64, pin_memory=True)
@@ -338,13 +507,12 @@ def run_ours(args, ws, rank, local):
     Bp = Bp.t()                                   # n x NRHS, column-major, pinned
     Xp = torch.empty((NRHS, n), dtype=torch.float64, pin_memory=True).t()
     pts_host = np.asfortranarray(pts)
-    H.free()
     Hh = rs.rs_build(pts_host, "laplace2d", h, w["eps"], w["leaf"], w["nproxy"])
     rs.rs_solve_refined(Hh, Bp, Xp, tol=TOL, max_it=8)
     Hh.free()
     torch.cuda.synchronize()
     t = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 5))
     for _ in range(e2e_steps):
         Hh = rs.rs_build(pts_host, "laplace2d", h, w["eps"], w["leaf"], w["nproxy"])
         rs.rs_solve_refined(Hh, Bp, Xp, tol=TOL, max_it=8)
@@ -352,33 +520,33 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t) / e2e_steps
 
-    serving = others = None
-    if not args.no_serve:
+    serve = others = None
+    if not args.no_serve and rank == 0:
         try:
-            serving = serving_session(rs, torch, P, h, w)
+            serve = serving(rs, torch, H, n, args.serve_window, stream)
         except Exception as e:   # keep the main measurement
-            serving = {"error": f"{type(e).__name__}: {e}"}
-    if rank == 0 and not args.no_serve:
+            serve = {"error": f"{type(e).__name__}: {e}"}
         try:
             others = other_configs(rs, torch, stream)
         except Exception as e:
             others = {"error": f"{type(e).__name__}: {e}"}
+    H.free()
 
     # roofline of the dominant kernel category in the timed region
-    pk = peaks()
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
     if dom["bytes"] > 0 and dom["flops"] / max(dom["bytes"], 1.0) < 0.5:
         bound, achieved, peak, unit = "hbm", dom["bytes"] / dom["ms"] / 1e6, pk["hbm"], "GB/s"
-        peak_src = f"{pk['src']} copy bandwidth"
+        peak_src = f"{pk['src']} copy bandwidth (MEASURED_PEAKS.json)"
     else:
-        bound, achieved, peak, unit = "alu", dom["flops"] / dom["ms"] / 1e6, FP64_PEAK_GFLOPS, "GFLOP/s"
-        peak_src = "FP64 FMA peak 152 SM x 2 FMA/clk x 2.07 GHz (derived)"
-    traffic = NCU_TRAFFIC.get(dom_name)
+        bound, achieved, peak, unit = "alu", dom["flops"] / dom["ms"] / 1e6, fp64_peak, "GFLOP/s"
+        peak_src = "FP64 FMA throughput measured in this run (rs_probe_fma_peak)"
+    kernel_of = {"id": "k_id", "factor": "k_factor_smem", "solve_fp32": "k_solve_cta", "residual": "k_solve_cta"}
+    traffic, traffic_src = ncu_traffic(kernel_of.get(dom_name, dom_name))
     roof = {"bound": bound, "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": traffic[0] if traffic else None,
-            "traffic_source": traffic[1] if traffic else None, "peak_source": peak_src,
+            "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src, "peak_source": peak_src,
             "launches": dom["launches"], "avg_launch_ms": dom["ms"] / dom["launches"],
-            "ncu_fp64_pipe_active": NCU_FP64_PIPE.get(dom_name)}
+            "work": "algorithmic flops of the pivoted QR and T (4mnk - 2k^2(m+n) + 4k^3/3 + k^2(n-k) per box)"
+                    if dom_name == "id" else "algorithmic bytes/flops counted from the block sizes"}
     kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                    "GB_s": v["bytes"] / v["ms"] / 1e6 if v["ms"] else 0.0,
                    "GFLOP_s": v["flops"] / v["ms"] / 1e6 if v["ms"] else 0.0} for k, v in prof.items()}
@@ -390,12 +558,15 @@ def run_ours(args, ws, rank, local):
     cpu = cpu_baseline() if ws == 1 and not args.no_cpu else None
     h2d = pts.size * 8 + n * NRHS * 8
     d2h = n * NRHS * 8
+    plain = 1e6 / plain_us
+    sat = serve.get("at_config_rate") if isinstance(serve, dict) else None
     line = {
         "metric": METRIC, "value": value, "unit": "RHS/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": DTYPE,
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "eps": w["eps"], "leaf": w["leaf"], "nproxy": w["nproxy"],
-                   "nrhs_per_step": NRHS, "tol": TOL,
+                   "nrhs_per_step": NRHS, "tol": TOL, "columns": [c0, c1],
                    "step": "rs_build + rs_solve_refined(256 columns)",
                    "l2": "inputs larger than L2: B is 268 MB and every step rebuilds 0.33 GB of factors"},
         "clocks": clocks,
@@ -403,25 +574,55 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": launches,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "peaks_measured": {"fp64_fma_gflops": fp64_peak, "fp32_fma_gflops": fp32_peak, "hbm_gbs": pk["hbm"],
+                           "hbm_source": pk["src"]},
         "build_ms": statistics.median(tb),
         "build_ms_dfloat_id": statistics.median(tbd),
-        "resident_refined_ms_per_batch": refined_ms,
-        "resident_refined_rhs_per_s": NRHS / (refined_ms / 1e3),
-        "plain_fp64_rhs_per_s": 1e6 / plain_us,
-        "batched_vs_plain": (NRHS / (refined_ms / 1e3)) / (1e6 / plain_us),
-        "serving": serving,
-        "served_vs_plain": (serving["rhs_per_s"] / (1e6 / plain_us)) if serving and "rhs_per_s" in serving else None,
+        "solve_phase": phase,
+        "refined": refined,
+        "resident_refined_rhs_per_s": refined[str(NRHS)]["rhs_per_s"],
+        "plain_fp64_rhs_per_s": plain,
+        "plain_fp64_relres": plain_rel,
+        "batched_vs_plain": refined[str(NRHS)]["rhs_per_s"] / plain,
+        "serving": serve,
+        "served_vs_plain": (sat["rhs_per_s"] / plain) if sat and "rhs_per_s" in sat else None,
         "refine_iterations": itss,
         "relres_max": max(rels),
-        "plain_fp64_relres": plain_rel,
         "factor_bytes": st["factor_bytes"],
         "top_skeletons": st["top_skeletons"],
+        "circle_4096": circle,
         "kernels": kernels,
         "other_configs": others,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def config1(rs, torch, stream):
+    """4096 points on the unit circle, eps 1e-9, plain FP64, one RHS: build
+    time and one-RHS solve time (device-resident)."""
+    wl = ri.WORKLOADS["laplace2d_circle_4096"]
+    pts, h = ri.circle(wl["n"])
+    P = torch.from_numpy(np.ascontiguousarray(pts.T)).cuda().t()
+    tb = []
+    for _ in range(3):
+        H = rs.rs_build(P, "laplace2d", h, wl["eps"], wl["leaf"], wl["nproxy"], stream=stream)
+        tb.append(H.stats()["build_ms"])
+        H.free()
+    H = rs.rs_build(P, "laplace2d", h, wl["eps"], wl["leaf"], wl["nproxy"], stream=stream)
+    b = torch.from_numpy(ri.rhs(wl["n"], 1, seed=0)).cuda()
+    x = torch.zeros_like(b)
+    for _ in range(5):
+        rs.rs_solve(H, b, x, stream=stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(100):
+        rs.rs_solve(H, b, x, stream=stream)
+    torch.cuda.synchronize()
+    us = (time.perf_counter() - t) / 100 * 1e6
+    H.free()
+    return {"build_ms": statistics.median(tb), "solve_us": us, "rhs_per_s": 1e6 / us}
 
 
 def other_configs(rs, torch, stream):
@@ -483,7 +684,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--no-serve", action="store_true", help="skip the serving session")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving sessions and the other workloads")
+    ap.add_argument("--serve-window", type=float, default=60.0, help="seconds of the serving session at the "
+                    "configuration's arrival rate (the session below capacity lasts a third of it)")
     ap.add_argument("--profile-step", action="store_true",
                     help="one warm-up step, then one step (build + refined solve) inside a profiler range: "
                          "the command profiled by ncu --profile-from-start off")

@@ -218,6 +218,25 @@ int rs_profile_record_start(int i, double* start_ms);
 int rs_profile_tiles(rs_handle h, int mode, int nrhs, int64_t cap, int* kind, int* depth, int* row0, int* ncol,
                      double* t_claim_us, double* t_start_us, double* t_end_us, int64_t* count);
 
+/* FMA throughput of the current device, measured (not the paper's: a
+ * roofline denominator for the FP64 and FP32 kernels): every thread runs 8
+ * independent multiply-add chains, 8 CTAs of 256 threads per SM; the best of
+ * three timed launches (CUDA events) after one warm-up.  precision
+ * RS_PREC_FP64 or RS_PREC_FP32; *gflops receives 2 x FMAs / s / 1e9.  Allocates
+ * and frees a small output buffer; synchronous. */
+int rs_probe_fma_peak(int precision, double* gflops);
+
+/* Self-test of the tensor-core building blocks the multi-column solve uses
+ * (the paper has no counterpart): one block product D = A B^T on the
+ * tensor cores (tcgen05.mma, cta_group::1, M = 128, operands staged in
+ * shared memory in the 128-byte-swizzled K-major layout, accumulator in
+ * tensor memory).  kind 0: A, B rounded to tf32, K = 32; kind 1: rounded to
+ * bf16, K = 64.  A: 128 x K, B: n x K, D: 128 x n, all row-major fp32 in
+ * DEVICE memory (caller-owned); n in {16, 32, ..., 256}.  Synchronous.
+ * RS_ERR_ARG for bad arguments, RS_ERR_TIMEOUT if the MMA completion wait
+ * ran out, RS_ERR_CUDA on a launch error. */
+int rs_tc_selftest(int kind, const float* A, const float* B, float* D, int n);
+
 /* Number of kernels the library has launched in this process so far. */
 int64_t rs_launch_count(void);
 
@@ -297,6 +316,12 @@ int rs_set_fault(const char* spec);
  *   "gj:blocked"  Gauss-Jordan steps without the cluster form
  *   "gj:coop"     ... and without the blocked form
  *   "gj:step"     ... and without the cooperative form
+ *   "tile:TMxTN"  every persistent solve of 16 or more columns on that tile
+ *                 shape (32x32, 32x64, 64x32, 64x64: CUDA-core tiles;
+ *                 128x64, 128x128, 128x256: tensor-core tiles, float
+ *                 arithmetic on real kernels only -- elsewhere 32x64 is
+ *                 used); "tile:warp" the warp kernel; by default the
+ *                 autotuner picks per (mode, column count)
  * A form whose launch does not fit the device falls through to the next, as
  * in the normal selection.  RS_ERR_ARG for an unknown token.
  * rs_path_counts(counts, cap, reset): level launches per form since the last

@@ -6,6 +6,11 @@ sum_j A_ij x_j = b_i; kernels from oracle.kernels).  Dense solves use
 numpy.linalg.solve (LU with partial pivoting, a library primitive): the
 brute-force Gaussian elimination the compressed inverse is compared with
 (Sec. 4.3 states the hand-rolled elimination is one ordering of it).
+
+Pins (tests/test_oracle_pins.py): norm2_est against the 2-norm from the
+singular value decomposition (LAPACK through numpy.linalg.norm(E, 2)) on
+random real and complex matrices and on A - A_RS, and against closed forms
+(a diagonal matrix, rank-one products u v^H).
 """
 from __future__ import annotations
 

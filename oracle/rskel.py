@@ -41,6 +41,13 @@ Pins (tests/test_oracle_solver.py): ||A - A_RS|| / ||A|| <= 10 eps against the
 dense matrix; the solve equals dense Gaussian elimination on A_RS to rounding
 and on A within 10 eps; closed-form circulant spectrum on the unit circle
 (Laplace and Helmholtz); sphere harmonics eigenvalues (3D, loose).
+(tests/test_oracle_pins.py): every box's proxy ID compresses the TRUE
+off-diagonal block row A(other boxes' active points, I) to eps, and its rank
+is at least that of the ID of that block itself (Sec. 3.2).
+
+build() takes an optional box_map to run the independent boxes of a level
+elsewhere; process_box_map spreads them over forked processes (the CPU
+baseline of the benchmark); the arithmetic is unchanged.
 """
 from __future__ import annotations
 
@@ -149,36 +156,44 @@ class Factorization:
         return np.vstack(rows)
 
     # -------------------------------------------------------------------- build
-    def build(self):
+    def _factor_box(self, depth, b, active_of):
+        """Compression and block elimination of box b at `depth` (its children,
+        if any, are done)."""
         tr, pr = self.tree, self.params
+        I = active_of[b]
+        M = self._compress_matrix(depth, b, I, active_of)
+        sk_loc, rd_loc, T = interp_decomp(M, pr.eps)
+        P = projection(sk_loc, rd_loc, T, len(I)).astype(self._dtype())
+        if depth == tr.L:
+            D = system_block(pr.kind, tr.points, I, I, pr.w, pr.kwave)
+            Dfwd = D
+        else:
+            D = self._blocks_from_children(depth, b, with_lambda=True)
+            Dfwd = self._blocks_from_children(depth, b, with_lambda=False)
+        # block elimination, eq. compressed-inverse (L = P^T, R = P)
+        DinvL = np.linalg.solve(D, P.T)              # D^-1 L
+        RDinv = np.linalg.solve(D.T, P.T).T          # R D^-1
+        Lam = np.linalg.inv(P @ DinvL)               # (R D^-1 L)^-1
+        Dinv = np.linalg.inv(D)
+        calD = Dinv - DinvL @ Lam @ RDinv
+        calL = DinvL @ Lam
+        calR = Lam @ RDinv
+        return BoxFactor(I, sk_loc, rd_loc, T, P, D, Lam, calD, calL, calR, m=M.shape[0]), Dfwd
+
+    def build(self, box_map=None):
+        """Level by level from the leaves.  box_map(f, items) -> list may run the
+        independent boxes of one level elsewhere (e.g. a process pool); the
+        default runs them in order.  The arithmetic is the same either way."""
+        tr = self.tree
         for depth in range(tr.L, 0, -1):
             lv = tr.levels[depth]
             active_of = [self._active(depth, b) for b in range(lv.nbox)]
-            facs, fwd = [], []
-            for b in range(lv.nbox):
-                I = active_of[b]
-                M = self._compress_matrix(depth, b, I, active_of)
-                sk_loc, rd_loc, T = interp_decomp(M, pr.eps)
-                P = projection(sk_loc, rd_loc, T, len(I)).astype(self._dtype())
-                if depth == tr.L:
-                    D = system_block(pr.kind, tr.points, I, I, pr.w, pr.kwave)
-                    Dfwd = D
-                else:
-                    D = self._blocks_from_children(depth, b, with_lambda=True)
-                    Dfwd = self._blocks_from_children(depth, b, with_lambda=False)
-                # block elimination, eq. compressed-inverse (L = P^T, R = P)
-                DinvL = np.linalg.solve(D, P.T)              # D^-1 L
-                RDinv = np.linalg.solve(D.T, P.T).T          # R D^-1
-                Lam = np.linalg.inv(P @ DinvL)               # (R D^-1 L)^-1
-                Dinv = np.linalg.inv(D)
-                calD = Dinv - DinvL @ Lam @ RDinv
-                calL = DinvL @ Lam
-                calR = Lam @ RDinv
-                facs.append(BoxFactor(I, sk_loc, rd_loc, T, P, D, Lam, calD, calL, calR,
-                                      m=M.shape[0]))
-                fwd.append(Dfwd)
-            self.boxes[depth] = facs
-            self.fwd_blocks[depth] = fwd
+            if box_map is None:
+                res = [self._factor_box(depth, b, active_of) for b in range(lv.nbox)]
+            else:
+                res = box_map(self, depth, active_of, range(lv.nbox))
+            self.boxes[depth] = [r[0] for r in res]
+            self.fwd_blocks[depth] = [r[1] for r in res]
         # root (depth 0)
         self.root_I = self._active(0, 0)
         if tr.L == 0:
@@ -281,7 +296,39 @@ class Factorization:
         return Y.reshape(np.shape(X)) if np.ndim(X) == 1 else Y
 
 
-def build(points: np.ndarray, params: Params) -> Factorization:
+def build(points: np.ndarray, params: Params, box_map=None) -> Factorization:
     """Tree + compression + factorization of A = I + w K on `points` (dim x N)."""
     tree = Tree(points, params.leaf)
-    return Factorization(tree, params).build()
+    return Factorization(tree, params).build(box_map)
+
+
+# ------------------------------------------------------- parallel box driver
+# The boxes of one level are independent once the level below is done (Sec.
+# 3.1: each box's ID and elimination read only its own and its colleagues'
+# active sets and its children's Lambda).  `process_box_map` runs them on a
+# pool of forked worker processes, one pool per level so that the workers see
+# the finished lower levels.  Only for processes that never initialise CUDA
+# (a fork after CUDA initialisation is unsafe).
+_POOL_STATE = None
+
+
+def _pool_worker(b):
+    fac, depth, active_of = _POOL_STATE
+    return fac._factor_box(depth, b, active_of)
+
+
+def process_box_map(workers: int):
+    import multiprocessing as mp
+
+    def box_map(fac, depth, active_of, boxes):
+        global _POOL_STATE
+        boxes = list(boxes)
+        if workers <= 1 or len(boxes) < 2:
+            return [fac._factor_box(depth, b, active_of) for b in boxes]
+        _POOL_STATE = (fac, depth, active_of)
+        try:
+            with mp.get_context("fork").Pool(min(workers, len(boxes))) as pool:
+                return pool.map(_pool_worker, boxes, chunksize=max(1, len(boxes) // (4 * workers)))
+        finally:
+            _POOL_STATE = None
+    return box_map

@@ -78,6 +78,8 @@ _PROTOS = {
     "rs_server_handle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
     "rs_server_destroy": (ctypes.c_int, [_P]),
     "rs_set_path": (ctypes.c_int, [ctypes.c_char_p]),
+    "rs_tc_selftest": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, ctypes.c_int]),
+    "rs_probe_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "rs_path_counts": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "rs_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "rs_profile_ncat": (ctypes.c_int, []),
@@ -322,6 +324,19 @@ def rs_green(kernel: str, s2, k_wave: float = 0.0) -> np.ndarray:
     out = np.zeros(2 * s2.size if cplx else s2.size, dtype=np.float64)
     _check(lib.rs_green(KERNELS[kernel], float(k_wave), s2.ctypes.data, s2.size, out.ctypes.data))
     return out.view(np.complex128) if cplx else out
+
+
+def rs_probe_fma_peak(precision: int = RS_PREC_FP64) -> float:
+    """Measured FMA throughput (GFLOP/s) of the current device."""
+    out = ctypes.c_double()
+    _check(load().rs_probe_fma_peak(int(precision), ctypes.byref(out)))
+    return out.value
+
+
+def rs_tc_selftest(kind: int, A, B, D):
+    """D = A B^T on the tensor cores (kind 0 tf32, 1 bf16); CUDA float32 tensors."""
+    _check(load().rs_tc_selftest(int(kind), A.data_ptr(), B.data_ptr(), D.data_ptr(), int(B.shape[0])))
+    return D
 
 
 def rs_launch_count() -> int:

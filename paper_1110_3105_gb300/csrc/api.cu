@@ -49,7 +49,9 @@ bool take_wait_fault() { return g_fault_wait.exchange(0) != 0; }
 
 static std::atomic<int> g_path_force{0};
 static std::atomic<long long> g_path_count[PATH_N];
+static std::atomic<int> g_solve_tile{-1};
 int path_force() { return g_path_force.load(); }
+int solve_tile_force() { return g_solve_tile.load(); }
 void path_count(int which) {
   if (which >= 0 && which < PATH_N) g_path_count[which].fetch_add(1);
 }
@@ -638,6 +640,7 @@ int rs_set_path(const char* spec) {
   rs::g_err.clear();
   if (!spec || !*spec) {
     g_path_force = 0;
+    g_solve_tile = -1;
     return RS_OK;
   }
   static const std::pair<const char*, int> names[] = {
@@ -649,7 +652,7 @@ int rs_set_path(const char* spec) {
       {"gj:blocked", PF_GJ_NOCLUSTER},
       {"gj:coop", PF_GJ_NOCLUSTER | PF_GJ_NOBLOCKED},
       {"gj:step", PF_GJ_NOCLUSTER | PF_GJ_NOBLOCKED | PF_GJ_NOCOOP}};
-  int f = 0;
+  int f = 0, tile = -1;
   std::string s(spec);
   size_t pos = 0;
   while (pos <= s.size()) {
@@ -657,6 +660,19 @@ int rs_set_path(const char* spec) {
     if (e == std::string::npos) e = s.size();
     const std::string tok = s.substr(pos, e - pos);
     bool found = false;
+    if (tok.rfind("tile:", 0) == 0) {
+      int tm = 0, tn = 0;
+      const std::string v = tok.substr(5);
+      if (v == "warp") tile = 0;
+      else if (sscanf(v.c_str(), "%dx%d", &tm, &tn) == 2 &&
+               (((tm == 32 || tm == 64) && (tn == 32 || tn == 64)) ||
+                (tm == 128 && (tn == 64 || tn == 128 || tn == 256))))
+        tile = tm * 1000 + tn;
+      else
+        return fail(RS_ERR_ARG, "rs_set_path: unknown tile '%s'", v.c_str());
+      pos = e + 1;
+      continue;
+    }
     for (auto& nm : names)
       if (tok == nm.first) {
         f |= nm.second;
@@ -666,6 +682,7 @@ int rs_set_path(const char* spec) {
     pos = e + 1;
   }
   g_path_force = f;
+  g_solve_tile = tile;
   return RS_OK;
 }
 

@@ -1,6 +1,7 @@
 // Launch profiler: CUDA events around each kernel launch, grouped by
 // category, with the launch's algorithmic bytes and flops counted on the
 // host from the known block sizes.  Off unless rs_profile_enable(1).
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -79,9 +80,64 @@ void prof_amend(int cat, double bytes, double flops) {
     }
 }
 
+// FMA throughput probe: every thread runs 8 independent FMA chains, so the
+// pipe (not the FMA latency) bounds the rate.
+template <class T>
+__global__ void __launch_bounds__(256) k_fma_probe(T mul, T add, int iters, T* out) {
+  T a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) a[i] = (T)(threadIdx.x + i);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = a[i] * mul + add;
+  }
+  T s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s += a[i];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <class T>
+int fma_probe(double* gflops) {
+  int dev = 0, nsm = 0;
+  RS_CUDA(cudaGetDevice(&dev));
+  RS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = nsm * 8, threads = 256, iters = sizeof(T) == 8 ? 1 << 12 : 1 << 15;
+  T* out = nullptr;
+  RS_CUDA(cudaMalloc((void**)&out, sizeof(T) * (size_t)blocks * threads));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int rc = RS_OK;
+  for (int rep = 0; rep < 4 && rc == RS_OK; ++rep) {
+    cudaEventRecord(e0);
+    k_fma_probe<T><<<blocks, threads>>>((T)0.999999, (T)1e-7, iters, out);
+    cudaEventRecord(e1);
+    float ms = 0;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(RS_ERR_CUDA, "rs_probe_fma_peak: probe launch failed");
+    } else if (rep > 0) {
+      best = std::min(best, ms);   // the first launch pays one-time costs
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (rc == RS_OK) *gflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e9;
+  return rc;
+}
+
 }  // namespace rs
 
 extern "C" {
+
+int rs_probe_fma_peak(int precision, double* gflops) {
+  if (!gflops || (precision != RS_PREC_FP64 && precision != RS_PREC_FP32))
+    return rs::fail(RS_ERR_ARG, "rs_probe_fma_peak: bad arguments");
+  return precision == RS_PREC_FP64 ? rs::fma_probe<double>(gflops) : rs::fma_probe<float>(gflops);
+}
 
 int rs_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(rs::g_mu);

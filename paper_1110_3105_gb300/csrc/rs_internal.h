@@ -176,6 +176,9 @@ enum PathId {
 };
 int path_force();
 void path_count(int which);
+// Solve tile override (rs_set_path "tile:..."): -1 = the autotuner's choice,
+// 0 = the warp kernel, else TM * 1000 + TN.
+int solve_tile_force();
 
 // allocation helper: records in h->allocs
 int dalloc(Handle* h, void** p, size_t bytes);

@@ -35,10 +35,11 @@ def splitmix64(counter: np.ndarray) -> np.ndarray:
         return z ^ (z >> np.uint64(31))
 
 
-def uniform01(seed: int, count: int, stream: int = 0) -> np.ndarray:
-    """`count` doubles in (0, 1], counter-based from (seed, stream)."""
+def uniform01(seed: int, count: int, stream: int = 0, offset: int = 0) -> np.ndarray:
+    """`count` doubles in (0, 1], counter-based from (seed, stream), starting
+    at position `offset` of the stream."""
     base = (np.uint64(seed) * np.uint64(0x100000001B3)) ^ (np.uint64(stream) << np.uint64(40))
-    ctr = np.arange(count, dtype=np.uint64) + base
+    ctr = np.arange(count, dtype=np.uint64) + base + np.uint64(offset)
     bits = splitmix64(ctr) >> np.uint64(11)
     return (bits.astype(np.float64) + 1.0) * (1.0 / 9007199254740992.0)
 
@@ -54,6 +55,26 @@ def normal(seed: int, shape, stream: int = 0) -> np.ndarray:
     z[0::2] = rad * np.cos(2.0 * np.pi * u2)
     z[1::2] = rad * np.sin(2.0 * np.pi * u2)
     return z[:count].reshape(shape)
+
+
+def normal_range(seed: int, start: int, count: int, stream: int = 0) -> np.ndarray:
+    """Elements [start, start + count) of the stream normal(seed, ...) makes."""
+    p0 = start // 2
+    p1 = (start + count + 1) // 2
+    u1 = uniform01(seed, p1 - p0, 2 * stream, offset=p0)
+    u2 = uniform01(seed, p1 - p0, 2 * stream + 1, offset=p0)
+    rad = np.sqrt(-2.0 * np.log(u1))
+    z = np.empty(2 * (p1 - p0))
+    z[0::2] = rad * np.cos(2.0 * np.pi * u2)
+    z[1::2] = rad * np.sin(2.0 * np.pi * u2)
+    return z[start - 2 * p0:start - 2 * p0 + count]
+
+
+def rhs_columns(n: int, c0: int, c1: int, seed: int = 0) -> np.ndarray:
+    """Columns [c0, c1) of rhs(n, nrhs, seed) for any nrhs >= c1 (real), so a
+    rank can make its slice of one global batch without the rest."""
+    z = normal_range(seed, c0 * n, (c1 - c0) * n, stream=0)
+    return np.asfortranarray(z.reshape(c1 - c0, n).T)
 
 
 def rhs(n: int, nrhs: int, seed: int = 0, complex_: bool = False) -> np.ndarray:

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _run(env_extra):
     env = dict(os.environ, **env_extra)
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
+                          "--warmup", "0"], capture_output=True, text=True, env=env, cwd=ROOT, timeout=900)
     assert out.returncode == 0, out.stderr[-2000:]
     return [l for l in out.stdout.splitlines() if l.startswith("{")]
 
@@ -27,7 +27,7 @@ def test_reference_arm_line():
     assert d["impl"] == "reference" and d["unit"] == "RHS/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["ms_per_step"] > 0 and d["steps"] == 1
     assert d["config"]["workload"] == "laplace2d_starfish_131072"
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 

@@ -24,15 +24,22 @@ CASES = {
     "sphere": ("laplace3d", "sphere", 4096, 1e-6, 128, 216),
     "starfish": ("laplace2d", "starfish", 4096, 1e-10, 64, 64),
 }
+CASE_NAMES = list(CASES)
 
-# spec -> (forms that must have run, forms that must not)
+# spec -> (per case: forms of which at least one must have run; forms that
+# must not have run).  A cooperative launch needs every CTA of the level
+# resident at once: the 3D leaf boxes' column caches are too large for that,
+# so there the selection falls through to the per-step launches.
 FORCED = [
-    ("id:coop", ["id_coop"], ["id_cta", "id_cluster"]),
-    ("id:step", ["id_step"], ["id_cta", "id_cluster", "id_coop"]),
-    ("id:big", ["id_cluster"], ["id_cta"]),
-    ("factor:big,gj:coop", ["factor_big", "gj_coop"], ["factor_smem", "gj_cluster", "gj_blocked"]),
-    ("factor:big,gj:step", ["factor_big", "gj_step"], ["factor_smem", "gj_cluster", "gj_blocked", "gj_coop"]),
-    ("factor:big,gj:blocked", ["factor_big"], ["factor_smem", "gj_cluster"]),
+    ("id:coop", {"starfish": ["id_coop"], "sphere": ["id_coop", "id_step"]}, ["id_cta", "id_cluster"]),
+    ("id:step", {"starfish": ["id_step"], "sphere": ["id_step"]}, ["id_cta", "id_cluster", "id_coop"]),
+    ("id:big", {"starfish": ["id_cluster", "id_coop", "id_step"], "sphere": ["id_cluster", "id_coop", "id_step"]},
+     ["id_cta"]),
+    ("factor:big,gj:coop", {"starfish": ["gj_coop"], "sphere": ["gj_coop", "gj_step"]},
+     ["factor_smem", "gj_cluster", "gj_blocked"]),
+    ("factor:big,gj:step", {"starfish": ["gj_step"], "sphere": ["gj_step"]},
+     ["factor_smem", "gj_cluster", "gj_blocked", "gj_coop"]),
+    ("factor:big,gj:blocked", {"starfish": ["factor_big"], "sphere": ["factor_big"]}, ["factor_smem", "gj_cluster"]),
 ]
 
 
@@ -45,7 +52,8 @@ def case(request):
     pts, w = ri.geometry(geom, n)
     F = rskel.build(pts, rskel.Params(kind=kind, w=w, eps=eps, leaf=leaf, nproxy=nproxy))
     B = ri.rhs(n, 3, seed=61)
-    return dict(rs=rs, kind=kind, n=n, eps=eps, leaf=leaf, nproxy=nproxy, pts=pts, w=w, F=F, B=B, Xo=F.solve(B))
+    return dict(name=request.param, rs=rs, kind=kind, n=n, eps=eps, leaf=leaf, nproxy=nproxy, pts=pts, w=w, F=F, B=B,
+                Xo=F.solve(B))
 
 
 @pytest.mark.parametrize("spec,must,mustnot", FORCED, ids=[f[0] for f in FORCED])
@@ -70,15 +78,15 @@ def test_forced_form_matches_oracle(case, spec, must, mustnot):
         assert np.all(err <= 10 * case["eps"]), (spec, counts, err)
     finally:
         H.free()
-    for name in must:
-        assert counts[name] > 0, (spec, counts)
+    assert any(counts[name] > 0 for name in must[case["name"]]), (spec, counts)
     for name in mustnot:
         assert counts[name] == 0, (spec, counts)
 
 
 def test_normal_selection_recorded(case):
-    """Without an override the small problems use the one-CTA forms below the
-    top levels; the counters say which forms ran."""
+    """Without an override: the 2D boxes all fit one CTA or a cluster; the 3D
+    sphere's top boxes (n ~ 500, m ~ 3000) fit neither, so its top ID level
+    runs one launch per pivot step.  The counters say which forms ran."""
     rs = case["rs"]
     rs.rs_set_path(None)
     rs.rs_path_counts(reset=True)
@@ -86,4 +94,7 @@ def test_normal_selection_recorded(case):
     H.free()
     counts = rs.rs_path_counts(reset=True)
     assert counts["id_cta"] + counts["id_cluster"] + counts["id_coop"] + counts["id_step"] >= 1
-    assert counts["id_coop"] == 0 and counts["id_step"] == 0, counts
+    if case["name"] == "starfish":
+        assert counts["id_coop"] == 0 and counts["id_step"] == 0, counts
+    else:
+        assert counts["id_step"] >= 1, counts

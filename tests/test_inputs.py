@@ -42,3 +42,10 @@ def test_starfish_equal_arclength():
     dr = -1.5 * np.sin(5 * tt)
     arcs = half * (np.sqrt(rr * rr + dr * dr) @ wg)
     assert np.max(np.abs(arcs - h)) < 1e-12
+
+
+def test_rhs_column_slices_match_the_batch():
+    for n in (7, 8, 131):
+        B = ri.rhs(n, 9, seed=4)
+        for c0, c1 in ((0, 9), (2, 5), (3, 4), (8, 9)):
+            assert np.array_equal(ri.rhs_columns(n, c0, c1, seed=4), B[:, c0:c1])

@@ -109,3 +109,13 @@ def test_path_spec_validation(lib):
     assert _lib._lib.rs_set_path(None) == 0
     counts = _lib.rs_path_counts(reset=True)
     assert len(counts) == 11 and all(v == 0 for v in counts.values())
+
+
+def test_tile_spec_validation(lib):
+    from paper_1110_3105_gb300 import _lib
+    _lib.load()
+    for good in (b"tile:128x128", b"tile:32x64", b"tile:warp", b"tile:128x256,id:big"):
+        assert _lib._lib.rs_set_path(good) == 0, good
+    for bad in (b"tile:128x32", b"tile:16x16", b"tile:"):
+        assert _lib._lib.rs_set_path(bad) == -1, bad
+    assert _lib._lib.rs_set_path(None) == 0
