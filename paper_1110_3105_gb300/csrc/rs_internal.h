@@ -150,6 +150,7 @@ struct Handle {
   double* colnorm = nullptr;    // 2 * R
   int ncolnorm = 0;
   void* pers = nullptr;         // persistent-solve plans (solve2.cu)
+  void* pers_tc = nullptr;      // tensor-core solve plans (solve_tc.cu)
   void* pers_last = nullptr;
 };
 
@@ -220,6 +221,15 @@ int solve_pers_device_sub(Handle* h, int mode, const double* d_B, int64_t ldb, i
 int solve_pers_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, void* d_X, int64_t ldx,
                       cudaStream_t st);
 int pers_check(Handle* h);
+// Tensor-core multi-column solve (solve_tc.cu): mode RS_PREC_FP32 or
+// MODE_FWD_F32 on real kernels, TN in {64, 128, 256} columns per unit.
+int solve_tc_run(Handle* h, int mode, int TN, const double* B, int64_t ldb, int R, double* X, int64_t ldx,
+                 const double* sub, cudaStream_t st);
+int tc_check(Handle* h);
+int tc_tile_trace(Handle* h, int mode, int R, int64_t cap, int* kind, int* depth, int* r0, int* ncol,
+                  double* t_claim, double* t_start, double* t_end, int64_t* count);
+void tc_forget_last(Handle* h);
+void free_tc(Handle* h);
 int tile_trace(Handle* h, int prec, int R, int64_t cap, int* kind, int* depth, int* r0, int* ncol, double* t_claim,
                double* t_start, double* t_end, int64_t* count);
 void free_pers(Handle* h);

@@ -41,6 +41,7 @@ namespace rs {
 namespace {
 
 constexpr int P_NT = 256;
+constexpr int TC_TM = 128;   // rows of a tensor-core tile (solve_tc.cu)
 constexpr int P_WARPS = P_NT / 32;
 constexpr int MAX_SPIN = 1 << 22;
 
@@ -726,222 +727,6 @@ __global__ void __launch_bounds__(C_NT) k_solve_cta(Plan<S> p, const SIO* B, int
 }
 
 
-// --------------------------------------------------------- tensor-core tiles
-// Many right-hand sides in float arithmetic (the FP32 solve and the float
-// forward operator of the refinement): the same tile list and dependency
-// counters, a tile being 128 rows x TN columns of one box's product computed
-// on the tensor cores (tcgen05.mma kind::tf32, accumulator in tensor memory).
-// Each operand is split into two tf32 values, a = hi + lo, and the product
-// is formed as hi*hi + hi*lo + lo*hi (three MMAs per K step), which carries
-// about fp32 accuracy (the dropped lo*lo term and the split are ~2^-22
-// relative).  Per 32-deep K chunk the CTA's threads stage the factor rows and
-// the input columns, split, in shared memory (128-byte-swizzled K-major
-// layout); one thread issues the 4 x 3 MMAs and commits them to an
-// mbarrier; the threads wait (bounded) and stage the next chunk.  After the
-// last chunk every thread reads its row of the accumulator from tensor
-// memory and stores it (coalesced along the rows, like the other kernels).
-constexpr int TC_NT = 256, TC_TM = 128, TC_KC = 32;
-constexpr int TC_MMA_POLLS = 1 << 24;
-
-template <int TN> struct TcSmem {
-  static constexpr size_t a_bytes = TC_TM * 128;      // one 128 x 32 fp32 operand
-  static constexpr size_t b_bytes = (size_t)TN * 128;  // TN x 32 fp32
-  static constexpr size_t bytes = 1024 + 2 * a_bytes + 2 * b_bytes;
-};
-
-template <int TN>
-__global__ void __launch_bounds__(TC_NT, 1) k_solve_tc(Plan<float> p, const double* B, int64_t ldb, double* X,
-                                                       int64_t ldx, const double* sub, int epoch, int* flag) {
-  extern __shared__ unsigned char tc_raw[];
-  __shared__ uint32_t s_taddr;
-  __shared__ __align__(8) uint64_t s_bar;
-  __shared__ int s_tile, s_ok;
-  const uint32_t raw = tc::smem_u32(tc_raw);
-  unsigned char* base = tc_raw + ((1024u - (raw & 1023u)) & 1023u);
-  unsigned char* Ahi = base;
-  unsigned char* Alo = Ahi + TcSmem<TN>::a_bytes;
-  unsigned char* Bhi = Alo + TcSmem<TN>::a_bytes;
-  unsigned char* Blo = Bhi + TcSmem<TN>::b_bytes;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (warp == 0) tc::tmem_alloc(&s_taddr, TN);
-  if (tid == 0) tc::mbar_init(&s_bar, 1);
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t taddr = s_taddr;
-  constexpr uint32_t IDESC = tc::idesc(tc::FMT_TF32, TC_TM, TN);
-  uint32_t phase = 0;
-  bool failed = false;
-  int next = 0;
-  if (tid == 0) next = atomicAdd(p.dispatch, 1);
-  for (;;) {
-    if (tid == 0) {
-      const int t = next;
-      int ok = 1;
-      if (t < p.ntiles) {
-        if (p.trace) p.trace[3 * (size_t)t] = gtime();
-        const Tile tl = p.tiles[t];
-        if (tl.kind != T_DOWN) {
-          if (p.bt.up_need[tl.g] > 0)
-            ok = spin_until(&p.up_cnt[tl.g], epoch * p.bt.up_need[tl.g], flag, p.dflag);
-        } else {
-          const int par = p.bt.parent[tl.g];
-          ok = spin_until(&p.dn_cnt[par], epoch * p.bt.dn_need[par], flag, p.dflag);
-        }
-        if (ok) next = atomicAdd(p.dispatch, 1);
-        if (p.trace) p.trace[3 * (size_t)t + 1] = gtime();
-      }
-      s_tile = t;
-      s_ok = ok;
-    }
-    __syncthreads();
-    const int t = s_tile;
-    if (t >= p.ntiles || !s_ok) break;
-    const Tile tl = p.tiles[t];
-    const int g = tl.g;
-    const int d = p.bt.depth[g];
-    const int n = p.bt.n[g], k = p.bt.k[g];
-    const int64_t off = p.bt.off[g];
-    const bool down = tl.kind == T_DOWN;
-    const int rows = down ? n : n + k;     // the root has k = 0
-    const int K = down ? k : n;
-    const float* A = down ? p.Lf[d] + p.bt.loff[g] : p.U[d] + p.bt.uoff[g];
-    const bool leaf_in = !down && d == p.L;
-    const float* vin = down ? p.u[d - 1] : (leaf_in ? nullptr : p.v[d]);
-    const int64_t ldin = down ? p.ldv[d - 1] : p.ldv[d];
-    const int64_t in0 = down ? p.bt.skoff[g] : off;
-    const int r0 = tl.r0;
-    const int nkc = (K + TC_KC - 1) / TC_KC;
-    for (int c0 = tl.c0; c0 < tl.c1 && !failed; c0 += TN) {
-      const int cw = min(TN, tl.c1 - c0);
-      for (int kc = 0; kc < nkc; ++kc) {
-        const int k0 = kc * TC_KC;
-        // factor rows r0..r0+127, columns k0..k0+31 (column-major source:
-        // consecutive threads read consecutive rows)
-        for (int e = tid; e < TC_TM * TC_KC; e += TC_NT) {
-          const int i = e % TC_TM, q = e / TC_TM;
-          const int r = r0 + i, kk = k0 + q;
-          const float a = (r < rows && kk < K) ? ldro(A + r + (size_t)kk * rows) : 0.0f;
-          float hi, lo;
-          tc::tf32_split(a, hi, lo);
-          const uint32_t o = tc::sw128_offset(i, q, 4);
-          *reinterpret_cast<float*>(Ahi + o) = hi;
-          *reinterpret_cast<float*>(Alo + o) = lo;
-        }
-        // input columns c0..c0+TN-1, rows k0..k0+31 (a warp reads 32
-        // consecutive rows of one column)
-        for (int e = tid; e < TN * TC_KC; e += TC_NT) {
-          const int q = e % TC_KC, j = e / TC_KC;
-          const int kk = k0 + q;
-          float b = 0.0f;
-          if (kk < K && j < cw) {
-            if (leaf_in) b = f64_to_f32_rn(B[(int64_t)p.perm[off + kk] + (int64_t)(c0 + j) * ldb]);
-            else b = ldcg(vin + (int64_t)(c0 + j) * ldin + in0 + kk);
-          }
-          float hi, lo;
-          tc::tf32_split(b, hi, lo);
-          const uint32_t o = tc::sw128_offset(j, q, 4);
-          *reinterpret_cast<float*>(Bhi + o) = hi;
-          *reinterpret_cast<float*>(Blo + o) = lo;
-        }
-        tc::fence_smem_to_async();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (tid == 0) {
-          const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo);
-          const uint32_t bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
-#pragma unroll
-          for (int ks = 0; ks < TC_KC / 8; ++ks) {
-            const uint32_t o = 32u * ks;
-            tc::mma_tf32(taddr, tc::desc_sw128(al + o), tc::desc_sw128(bh + o), IDESC, kc > 0 || ks > 0);
-            tc::mma_tf32(taddr, tc::desc_sw128(ah + o), tc::desc_sw128(bl + o), IDESC, true);
-            tc::mma_tf32(taddr, tc::desc_sw128(ah + o), tc::desc_sw128(bh + o), IDESC, true);
-          }
-          tc::mma_commit(&s_bar);
-        }
-        __syncwarp();
-        if (!tc::mbar_wait(&s_bar, phase, TC_MMA_POLLS)) failed = true;
-        phase ^= 1u;
-        tc::fence_after_sync();
-        if (__syncthreads_or(failed)) {
-          failed = true;
-          break;
-        }
-      }
-      if (failed) break;
-      // epilogue: warp w reads lanes 32 (w % 4) + lane, columns of its half
-      const int i = 32 * (warp & 3) + lane;
-      const int r = r0 + i;
-      const int jb = (warp >> 2) * (TN / 2);
-      const uint32_t lrow = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
-      for (int j0 = jb; j0 < jb + TN / 2; j0 += 16) {
-        float acc[16];
-        if (nkc > 0) {
-          tc::tmem_ld16(lrow + (uint32_t)j0, acc);
-          tc::tmem_ld_wait();
-        } else {
-#pragma unroll
-          for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
-        }
-        if (r >= rows || j0 >= cw) continue;
-        const int jn = min(16, cw - j0);
-        if (!down) {
-          if (r < n && tl.kind == T_ROOT && d == p.L) {   // single-box tree: the root is the answer
-            const int64_t dst = p.perm[off + r];
-            for (int q = 0; q < jn; ++q) {
-              const int64_t idx = dst + (int64_t)(c0 + j0 + q) * ldx;
-              X[idx] = out_cv<float, double>(sub, idx, acc[q]);
-            }
-          } else if (r < n) {
-            const int64_t ld = p.ldv[d];
-            float* uo = p.u[d] + (int64_t)(c0 + j0) * ld + off + r;
-            for (int q = 0; q < jn; ++q) uo[(int64_t)q * ld] = acc[q];
-          } else {
-            const int64_t ld = p.ldv[d - 1];
-            float* vo = p.v[d - 1] + (int64_t)(c0 + j0) * ld + p.bt.skoff[g] + (r - n);
-            for (int q = 0; q < jn; ++q) vo[(int64_t)q * ld] = acc[q];
-          }
-        } else {
-          const int64_t ld = p.ldv[d];
-          float* uo = p.u[d] + (int64_t)(c0 + j0) * ld + off + r;
-          if (d == p.L) {
-            const int64_t dst = p.perm[off + r];
-            for (int q = 0; q < jn; ++q) {
-              const int64_t idx = dst + (int64_t)(c0 + j0 + q) * ldx;
-              X[idx] = out_cv<float, double>(sub, idx, ldcg(uo + (int64_t)q * ld) + acc[q]);
-            }
-          } else {
-            for (int q = 0; q < jn; ++q) uo[(int64_t)q * ld] = ldcg(uo + (int64_t)q * ld) + acc[q];
-          }
-        }
-      }
-      // every thread is done reading the accumulator before the next MMAs
-      tc::fence_before_sync();
-      __syncthreads();
-      tc::fence_after_sync();
-    }
-    if (failed) break;
-    // every thread's stores of this tile precede the barrier; thread 0's
-    // release add publishes them to the waiter that acquires the counter
-    __syncthreads();
-    if (tid == 0) {
-      cuda::atomic_ref<int, cuda::thread_scope_device> c(tl.kind == T_UP ? p.up_cnt[p.bt.parent[g]] : p.dn_cnt[g]);
-      c.fetch_add(1, cuda::memory_order_release);
-      if (p.trace) p.trace[3 * (size_t)t + 2] = gtime();
-    }
-  }
-  if (failed && tid == 0) {   // an MMA never completed: raise both flags
-    atomicExch(p.dflag, 1);
-    atomicExch(flag, 1);
-  }
-  if (failed) tc::mbar_wait(&s_bar, phase ^ 1u, TC_MMA_POLLS);   // let a late MMA land before freeing
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  if (warp == 0) tc::tmem_free(taddr, TN);
-}
-
 // ------------------------------------------------------------------- host
 struct PersPlan {
   int prec = -1, R = 0, CT = 0;
@@ -1019,6 +804,18 @@ std::vector<int> launch_configs(int R, bool tc) {
   return c;
 }
 
+// The tensor cores accumulate a block product in fp32 one K step after
+// another: on blocks thousands deep (the 3D top levels) that loses about an
+// order of magnitude against the CUDA-core FMA chains (1e-5 against 1e-6
+// relative at N = 4096 on the sphere), which the refinement's float residual
+// update cannot afford.  Tensor-core tiles therefore serve trees whose
+// largest block is at most 320 deep (every 2D workload).
+bool tc_shallow(const Handle* h) {
+  int m = 0;
+  for (const auto& lv : h->lv) m = std::max(m, lv.maxn);
+  return m <= 320;
+}
+
 // Tensor-core tiles are candidates unless RS_SOLVE_TC=0.
 bool tc_enabled() {
   static const bool on = [] {
@@ -1043,29 +840,19 @@ int dev_upload(PersPlan* P, T** d, const std::vector<T>& v, cudaStream_t st) {
   return RS_OK;
 }
 
-// The tensor-core tiles exist for float arithmetic with double input and
-// output (the FP32 solve and the float forward operator of real kernels).
+// The tensor-core tiles (solve_tc.cu) exist for float arithmetic with
+// double input and output: the FP32 solve and the float forward operator of
+// real kernels.
 template <class S, class SIO> struct TcOk { static constexpr bool value = false; };
 template <> struct TcOk<float, double> { static constexpr bool value = true; };
-
-template <class S, class SIO, int TN>
-const void* tc_kernel() {
-  if constexpr (TcOk<S, SIO>::value) return (const void*)k_solve_tc<TN>;
-  return nullptr;
-}
 
 template <class S, class SIO, int CT, int TM, int TN>
 int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X, int64_t ldx, const SIO* sub,
                 cudaStream_t st) {
-  constexpr bool TCK = TM == TC_TM;
-  constexpr int TMv = TN ? (TCK ? 32 : TM) : 32, TNv = TN ? TN : 32;
-  const size_t smem = TCK ? TcSmem<TNv>::bytes : TN ? CtaSmem<S, TMv, TNv>::bytes : sizeof(S) * 32 * CT * P_WARPS;
-  const int nt = TCK ? TC_NT : TN ? C_NT : P_NT;
-  const void* fn = nullptr;
-  if constexpr (TCK) fn = tc_kernel<S, SIO, TNv>();
-  else if constexpr (TN > 0) fn = (const void*)k_solve_cta<S, SIO, TMv, TNv>;
-  else fn = (const void*)k_solve_pers<S, SIO, CT, false>;
-  if (!fn) return fail(RS_ERR_ARG, "solve: tensor-core tiles need float arithmetic on real kernels");
+  constexpr int TMv = TN ? TM : 32, TNv = TN ? TN : 32;
+  const size_t smem = TN ? CtaSmem<S, TMv, TNv>::bytes : sizeof(S) * 32 * CT * P_WARPS;
+  const int nt = TN ? C_NT : P_NT;
+  const void* fn = TN ? (const void*)k_solve_cta<S, SIO, TMv, TNv> : (const void*)k_solve_pers<S, SIO, CT, false>;
   if (smem > 48 * 1024) RS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (P->occ == 0) {
     int dev = 0;
@@ -1073,7 +860,6 @@ int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X
     RS_CUDA(cudaDeviceGetAttribute(&P->nsm, cudaDevAttrMultiProcessorCount, dev));
     RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P->occ, fn, nt, smem));
     P->occ = std::max(P->occ, 1);
-    if (TCK) P->occ = std::min(P->occ, 512 / TNv);   // every resident CTA holds TN tensor-memory columns
   }
   {
     const int per_block = TN ? 1 : P_WARPS;   // tiles a block works on at once
@@ -1116,10 +902,7 @@ int launch_pers(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R, SIO* X
   }
   *P->flag_host = 0;
   prof_begin(prec_cat(P->prec), st);
-  if constexpr (TCK) {
-    if constexpr (TcOk<S, SIO>::value)
-      k_solve_tc<TNv><<<P->grid, TC_NT, smem, st>>>(pl, B, ldb, X, ldx, sub, wait_epoch, P->flag_dev);
-  } else if constexpr (TN > 0) {
+  if constexpr (TN > 0) {
     k_solve_cta<S, SIO, TMv, TNv><<<P->grid, C_NT, smem, st>>>(pl, B, ldb, X, ldx, sub, wait_epoch, P->flag_dev);
   } else {
     if (pl.trace)
@@ -1143,6 +926,7 @@ int prec_cat(int prec) {
 }
 
 void free_pers(Handle* h) {
+  free_tc(h);
   PersCache* c = (PersCache*)h->pers;
   if (!c) return;
   for (PersPlan* P : c->plans) {
@@ -1301,9 +1085,6 @@ static int launch_plan(Handle* h, PersPlan* P, const SIO* B, int64_t ldb, int R,
     case 32064: RS_TRY((launch_pers<S, SIO, 1, 32, 64>(h, P, B, ldb, R, X, ldx, sub, st))); break;
     case 64032: RS_TRY((launch_pers<S, SIO, 1, 64, 32>(h, P, B, ldb, R, X, ldx, sub, st))); break;
     case 64064: RS_TRY((launch_pers<S, SIO, 1, 64, 64>(h, P, B, ldb, R, X, ldx, sub, st))); break;
-    case 128064: RS_TRY((launch_pers<S, SIO, 1, 128, 64>(h, P, B, ldb, R, X, ldx, sub, st))); break;
-    case 128128: RS_TRY((launch_pers<S, SIO, 1, 128, 128>(h, P, B, ldb, R, X, ldx, sub, st))); break;
-    case 128256: RS_TRY((launch_pers<S, SIO, 1, 128, 256>(h, P, B, ldb, R, X, ldx, sub, st))); break;
     case 0:
       switch (P->CT) {
         case 1: RS_TRY((launch_pers<S, SIO, 1, 32, 0>(h, P, B, ldb, R, X, ldx, sub, st))); break;
@@ -1331,15 +1112,29 @@ static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO*
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) known = it->second;
   }
-  const std::vector<int> cand = launch_configs(R, TcOk<S, SIO>::value && tc_enabled());
+  const bool tc = TcOk<S, SIO>::value && tc_enabled() && R <= 256 && tc_shallow(h);
+  const std::vector<int> cand = launch_configs(R, tc);
   PersPlan* P = nullptr;
+  // one launch of configuration cfg (tile * 16 + CTAs per SM): tensor-core
+  // tiles go to solve_tc.cu, the others to the persistent kernels here
+  auto run = [&](int cfg) -> int {
+    const int tile = cfg / 16;
+    if (tile / 1000 == TC_TM) {
+      if constexpr (TcOk<S, SIO>::value)
+        return solve_tc_run(h, prec, tile % 1000, (const double*)B, ldb, R, (double*)X, ldx, (const double*)sub, st);
+      return fail(RS_ERR_ARG, "solve: tensor-core tiles need float arithmetic on real kernels");
+    }
+    RS_TRY(get_plan(h, prec, R, tile, st, &P));
+    P->cps = cfg % 16;
+    tc_forget_last(h);
+    return launch_plan<S, SIO>(h, P, B, ldb, R, X, ldx, sub, st);
+  };
   {   // an override (rs_set_path "tile:...") replaces the tuned choice
     int f = solve_tile_force();
     if (f >= 0) {
-      if (R < 16 || (f / 1000 == TC_TM && !TcOk<S, SIO>::value)) f = f == 0 || R < 16 ? 0 : 32064;
-      RS_TRY(get_plan(h, prec, R, f, st, &P));
-      P->cps = 0;
-      return launch_plan<S, SIO>(h, P, B, ldb, R, X, ldx, sub, st);
+      if (R < 16 || (f / 1000 == TC_TM && !(TcOk<S, SIO>::value && R <= 256 && tc_shallow(h))))
+        f = f == 0 || R < 16 ? 0 : 32064;
+      return run(f * 16);
     }
   }
   // Repeating the launch is only harmless when the output overwrites neither
@@ -1351,12 +1146,8 @@ static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO*
     auto it = g_tuned.find(TuneKey{RS_PREC_FP32, bucket, key.cplx, key.N});
     if (it != g_tuned.end()) known = it->second;
   }
-  if (known >= 0 || cand.size() == 1 || aliased) {
-    const int cfg = known >= 0 ? known : cand[0];
-    RS_TRY(get_plan(h, prec, R, cfg / 16, st, &P));
-    P->cps = cfg % 16;
-    return launch_plan<S, SIO>(h, P, B, ldb, R, X, ldx, sub, st);
-  }
+  if (known >= 0 && (known / 16) / 1000 == TC_TM && !tc) known = -1;   // not available here
+  if (known >= 0 || cand.size() == 1 || aliased) return run(known >= 0 ? known : cand[0]);
   // autotune: time the second of two launches of each candidate (the first
   // pays one-time costs); the outputs agree bit for bit
   cudaEvent_t e0, e1;
@@ -1366,11 +1157,9 @@ static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO*
   float best_ms = 1e30f;
   int rc = RS_OK;
   for (int cfg : cand) {
-    if ((rc = get_plan(h, prec, R, cfg / 16, st, &P)) != RS_OK) break;
-    P->cps = cfg % 16;
-    if ((rc = launch_plan<S, SIO>(h, P, B, ldb, R, X, ldx, sub, st)) != RS_OK) break;
+    if ((rc = run(cfg)) != RS_OK) break;
     cudaEventRecord(e0, st);
-    if ((rc = launch_plan<S, SIO>(h, P, B, ldb, R, X, ldx, sub, st)) != RS_OK) break;
+    if ((rc = run(cfg)) != RS_OK) break;
     cudaEventRecord(e1, st);
     float ms = 0;
     if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
@@ -1389,6 +1178,9 @@ static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO*
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[key] = best;
   }
+  // the candidates do not all round alike (tensor-core and CUDA-core tiles):
+  // leave the chosen configuration's result in X
+  if (rc == RS_OK && best != cand.back()) rc = run(best);
   return rc;
 }
 
@@ -1421,6 +1213,7 @@ int solve_pers_device_sub(Handle* h, int mode, const double* d_B, int64_t ldb, i
 // earliest claim) it was claimed, its dependencies were met and it finished.
 int tile_trace(Handle* h, int prec, int R, int64_t cap, int* kind, int* depth, int* r0, int* ncol, double* t_claim,
                double* t_start, double* t_end, int64_t* count) {
+  if (tc_tile_trace(h, prec, R, cap, kind, depth, r0, ncol, t_claim, t_start, t_end, count) == RS_OK) return RS_OK;
   PersCache* c = (PersCache*)h->pers;
   PersPlan* P = nullptr;
   if (c)
@@ -1450,6 +1243,7 @@ int tile_trace(Handle* h, int prec, int R, int64_t cap, int* kind, int* depth, i
 }
 
 int pers_check(Handle* h) {
+  RS_TRY(tc_check(h));
   PersCache* c = (PersCache*)h->pers;
   if (!c) return RS_OK;
   int rc = RS_OK;

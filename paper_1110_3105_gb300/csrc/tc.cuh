@@ -99,10 +99,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int max_polls) {
-  for (int i = 0; i < max_polls; ++i)
+// Bounded wait for the phase with the given parity to complete: gives up
+// after max_polls polls or, if limit_ns > 0, once that much time has passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int max_polls, long long limit_ns = 0) {
+  unsigned long long t0 = 0;
+  if (limit_ns > 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (int i = 0; i < max_polls; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (limit_ns > 0 && (i & 255) == 255) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if ((long long)(t - t0) > limit_ns) return false;
+    }
+  }
   return false;
 }
 
