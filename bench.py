@@ -250,7 +250,23 @@ def _pinned(torch, n, cols, cplx, data=None):
     return t.t()   # n x cols, column-major, pinned
 
 
-def serving_session(rs, torch, resident, window_s, rate, seed, build_every_s=5.0, backlog_cols=64 * SERVE_COLS):
+def plain_fp64_rate(rs, torch, H, n, cplx, reps=20):
+    """The plain FP64 one-RHS-at-a-time solve rate (RHS/s, host-timed) on H."""
+    dt = torch.complex128 if cplx else torch.float64
+    b = torch.from_numpy(ri.rhs(n, 1, seed=5, complex_=cplx)).to(dtype=dt).cuda()
+    x = torch.zeros_like(b)
+    for _ in range(3):
+        rs.rs_solve(H, b, x)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        rs.rs_solve(H, b, x)
+    torch.cuda.synchronize()
+    return reps / (time.perf_counter() - t)
+
+
+def serving_session(rs, torch, resident, window_s, rate, seed, build_every_s=5.0, backlog_cols=64 * SERVE_COLS,
+                    only_first=False):
     """The serving mix: the `resident` factorizations [(Handle, n, complex,
     tol)] registered with one server; Poisson arrivals at `rate` requests/s
     with U{1..64} columns each, each for a factorization drawn uniformly from
@@ -258,17 +274,26 @@ def serving_session(rs, torch, resident, window_s, rate, seed, build_every_s=5.0
     random starfish (N in {8192 .. 65536}) is submitted, admitted by free
     HBM, and joins the mix once built.  Arrivals that find more than
     `backlog_cols` columns queued are shed (counted, not submitted).
-    Returns throughput, latency percentiles and the admission record."""
+    Returns throughput, latency percentiles and the admission record, and the
+    plain FP64 one-RHS-at-a-time rate of the same column mix: each
+    factorization's plain rate weighted by the columns it served (a
+    factorization built by the server is timed on it after the session).
+    only_first: every request goes to the first resident factorization and
+    no builds are submitted."""
     S = rs.Server(max_cols=SERVE_COLS)
     targets = []
+    plain = []   # per target: plain FP64 RHS/s (None: measure after the session)
 
-    def add_target(hid, n, cplx, tol):
+    def add_target(hid, n, cplx, tol, pr=None):
         B = _pinned(torch, n, 64, cplx, ri.rhs(n, 64, seed=901 + len(targets), complex_=cplx))
         ring = [_pinned(torch, n, 64, cplx) for _ in range(4)]
         targets.append((hid, n, cplx, tol, B, ring))
+        plain.append(pr)
 
-    for H, n, cplx, tol in resident:
-        add_target(S.add(H), n, cplx, tol)
+    for H, n, cplx, tol, pr in resident:
+        add_target(S.add(H), n, cplx, tol, pr)
+        if only_first:
+            break
     for hid, n, cplx, tol, B, ring in targets:   # warm the workers' buffers and the tile autotuner
         Bw = _pinned(torch, n, SERVE_COLS, cplx, ri.rhs(n, SERVE_COLS, seed=900, complex_=cplx))
         Xw = _pinned(torch, n, SERVE_COLS, cplx)
@@ -279,6 +304,7 @@ def serving_session(rs, torch, resident, window_s, rate, seed, build_every_s=5.0
     cols = 1 + (ri.uniform01(seed, nreq, stream=8) * 64).astype(int).clip(0, 63)
     pick = ri.uniform01(seed, nreq, stream=9)
     tickets, builds, built = [], [], []
+    served_cols = [0] * 64
     submitted_cols = shed = shed_cols = offered_cols = 0
     done_cols = 0
     i, nb = 0, 0
@@ -288,7 +314,7 @@ def serving_session(rs, torch, resident, window_s, rate, seed, build_every_s=5.0
         now = time.perf_counter()
         if now - t0 >= window_s:
             break
-        if now >= t_build:
+        if now >= t_build and not only_first:
             n2, arms, amp, rot = ri.serving_curve(seed, nb)
             pts2, h2 = ri.starfish(n2, arms=arms, amp=amp, rotation=rot)
             builds.append((S.submit_build(pts2, "laplace2d", h2, 1e-10, 64, 64), n2))
@@ -317,9 +343,11 @@ def serving_session(rs, torch, resident, window_s, rate, seed, build_every_s=5.0
             shed += 1
             shed_cols += c
         else:
-            hid, n, cplx, tol, B, ring = targets[min(len(targets) - 1, int(pick[i] * len(targets)))]
+            ti = min(len(targets) - 1, int(pick[i] * len(targets)))
+            hid, n, cplx, tol, B, ring = targets[ti]
             tickets.append(S.submit(hid, B[:, :c], ring[i % len(ring)][:, :c], tol=tol))
             submitted_cols += c
+            served_cols[ti] += c
         t_next += gaps[i]
         i += 1
     worst, bad = 0.0, 0
@@ -330,37 +358,46 @@ def serving_session(rs, torch, resident, window_s, rate, seed, build_every_s=5.0
     st = S.stats()
     for bt in builds:
         built.append(S.wait(bt[0])["status"])
+    for ti, (hid, n, cplx, tol, B, ring) in enumerate(targets):   # the server is idle now
+        if plain[ti] is None and served_cols[ti] > 0:
+            plain[ti] = plain_fp64_rate(rs, torch, S.handle(hid, n, cplx), n, cplx)
     S.destroy()
+    tot = sum(served_cols[:len(targets)])
+    plain_mix = tot / sum(served_cols[ti] / plain[ti] for ti in range(len(targets)) if served_cols[ti] > 0)
     return {"rhs_per_s": st["rhs"] / st["elapsed_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "requests": st["requests"], "failed": bad, "mean_batch_cols": st["mean_batch_cols"],
             "offered_rhs_per_s": offered_cols / window_s, "arrival_rate_per_s": rate, "window_s": window_s,
             "shed_requests": shed, "shed_rhs": shed_cols, "backlog_cap_cols": backlog_cols,
             "relres_max": worst, "builds_submitted": nb, "builds_admitted": sum(1 for b in built if b == 0),
             "builds_refused_oom": sum(1 for b in built if b == -2), "factorizations_served": len(targets),
-            "resident_gb": st["resident_bytes"] / 1e9}
+            "resident_gb": st["resident_bytes"] / 1e9, "plain_fp64_mix_rhs_per_s": plain_mix,
+            "served_vs_plain_same_mix": st["rhs"] / st["elapsed_s"] / plain_mix}
 
 
-def serving(rs, torch, H2, n2, window_s, stream):
+def serving(rs, torch, H2, n2, plain2, window_s, stream):
     """Configs 2-4 resident (built here besides the benchmark's handle);
     a session at the configuration's rate (2000 requests/s, ~65k RHS/s
-    offered), then one at 70% of the capacity that session measured."""
-    resident = [(H2, n2, False, 1e-10)]
+    offered), then one at 70% of the capacity that session measured; and a
+    session with the 131072-point factorization alone at the same rate."""
+    resident = [(H2, n2, False, 1e-10, plain2)]
     own = []
     for name, tol in SERVE_MIX[1:]:
         wl = ri.WORKLOADS[name]
         pts, wt = ri.geometry(wl["geom"], wl["n"])
+        cplx = wl["kernel"].startswith("helmholtz")
         H = rs.rs_build(pts, wl["kernel"], wt, wl["eps"], wl["leaf"], wl["nproxy"], k_wave=wl.get("kwave", 0.0))
         own.append(H)
-        resident.append((H, wl["n"], wl["kernel"].startswith("helmholtz"), tol))
+        resident.append((H, wl["n"], cplx, tol, plain_fp64_rate(rs, torch, H, wl["n"], cplx)))
     try:
         sat = serving_session(rs, torch, resident, window_s, 2000.0, seed=7)
         rate2 = 0.7 * sat["rhs_per_s"] / 32.5
         below = serving_session(rs, torch, resident, max(10.0, window_s / 3), rate2, seed=8)
+        alone = serving_session(rs, torch, resident, max(10.0, window_s / 3), 2000.0, seed=9, only_first=True)
     finally:
         for H in own:
             H.free()
     return {"mix": [name for name, _ in SERVE_MIX] + ["new 2D Laplace builds, random starfish, N in 8192..65536"],
-            "at_config_rate": sat, "below_capacity": below}
+            "at_config_rate": sat, "below_capacity": below, "laplace2d_starfish_131072_alone": alone}
 
 
 def solve_phase(rs, torch, H, B, n, stream, pk, fp64_peak, fp32_peak):
@@ -523,7 +560,7 @@ def run_ours(args, ws, rank, local):
     serve = others = None
     if not args.no_serve and rank == 0:
         try:
-            serve = serving(rs, torch, H, n, args.serve_window, stream)
+            serve = serving(rs, torch, H, n, 1e6 / plain_us, args.serve_window, stream)
         except Exception as e:   # keep the main measurement
             serve = {"error": f"{type(e).__name__}: {e}"}
         try:
@@ -585,7 +622,12 @@ def run_ours(args, ws, rank, local):
         "plain_fp64_relres": plain_rel,
         "batched_vs_plain": refined[str(NRHS)]["rhs_per_s"] / plain,
         "serving": serve,
-        "served_vs_plain": (sat["rhs_per_s"] / plain) if sat and "rhs_per_s" in sat else None,
+        # served rate over the plain FP64 one-at-a-time rate of the same
+        # request mix (each factorization's own plain rate, weighted by the
+        # columns it served); beside it the 131072-point factorization alone
+        "served_vs_plain": sat.get("served_vs_plain_same_mix") if sat else None,
+        "served_vs_plain_starfish_alone": (serve["laplace2d_starfish_131072_alone"]["served_vs_plain_same_mix"]
+                                           if sat else None),
         "refine_iterations": itss,
         "relres_max": max(rels),
         "factor_bytes": st["factor_bytes"],

@@ -388,6 +388,14 @@ class Server:
         self._keep.pop(ticket, None)
         return dict(status=st.value, latency_ms=lat.value, relres=rel.value, result=res.value)
 
+    def handle(self, hid: int, n: int, complex_: bool = False) -> Handle:
+        """Non-owning wrapper of the handle behind an id (e.g. one the server built)."""
+        out = ctypes.c_void_p()
+        _check(_lib.rs_server_handle(self._s, int(hid), ctypes.byref(out)))
+        h = Handle(out.value, n, complex_)
+        h.free = lambda: None   # the server owns it
+        return h
+
     def stats(self) -> dict:
         s = rs_server_stats_t()
         _check(_lib.rs_server_stats(self._s, ctypes.byref(s)))

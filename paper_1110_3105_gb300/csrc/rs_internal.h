@@ -222,7 +222,9 @@ int solve_pers_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrh
                       cudaStream_t st);
 int pers_check(Handle* h);
 // Tensor-core multi-column solve (solve_tc.cu): mode RS_PREC_FP32 or
-// MODE_FWD_F32 on real kernels, TN in {64, 128, 256} columns per unit.
+// MODE_FWD_F32 on real kernels, TN in {64, 128, 256} columns per unit, at
+// most TC_MAX_COLS columns per call.
+constexpr int TC_MAX_COLS = 1024;
 int solve_tc_run(Handle* h, int mode, int TN, const double* B, int64_t ldb, int R, double* X, int64_t ldx,
                  const double* sub, cudaStream_t st);
 int tc_check(Handle* h);

@@ -1112,7 +1112,7 @@ static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO*
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) known = it->second;
   }
-  const bool tc = TcOk<S, SIO>::value && tc_enabled() && R <= 256 && tc_shallow(h);
+  const bool tc = TcOk<S, SIO>::value && tc_enabled() && R <= TC_MAX_COLS && tc_shallow(h);
   const std::vector<int> cand = launch_configs(R, tc);
   PersPlan* P = nullptr;
   // one launch of configuration cfg (tile * 16 + CTAs per SM): tensor-core
@@ -1132,7 +1132,7 @@ static int pers_impl(Handle* h, int prec, const SIO* B, int64_t ldb, int R, SIO*
   {   // an override (rs_set_path "tile:...") replaces the tuned choice
     int f = solve_tile_force();
     if (f >= 0) {
-      if (R < 16 || (f / 1000 == TC_TM && !(TcOk<S, SIO>::value && R <= 256 && tc_shallow(h))))
+      if (R < 16 || (f / 1000 == TC_TM && !(TcOk<S, SIO>::value && R <= TC_MAX_COLS && tc_shallow(h))))
         f = f == 0 || R < 16 ? 0 : 32064;
       return run(f * 16);
     }

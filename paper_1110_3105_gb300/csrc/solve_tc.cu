@@ -448,7 +448,7 @@ __global__ void k_tma_ident(const int64_t* rb, const int* n, const int* c1, int6
 
 // ------------------------------------------------------------------ host
 // Per handle: the padded geometry (computed once), the vectors per column
-// bucket (64, 128 or 256 columns; shared by the two modes, which run one
+// bucket (64, 128, ..., 1024 columns; shared by the two modes, which run one
 // after the other on a stream), the factor rows per mode, and one plan (tile
 // list, counters, tensor maps) per (mode, column bucket, TN).  Every device
 // buffer comes from the stream-ordered pool and goes back with the handle.
@@ -958,13 +958,18 @@ int launch_tn(Handle* h, TCache* c, TPlan* P, const double* B, int64_t ldb, int 
 
 // Column buckets of the tensor-core plans: one plan serves every column
 // count up to its bucket.
-int tc_bucket(int R) { return R <= 64 ? 64 : R <= 128 ? 128 : 256; }
+int tc_bucket(int R) {
+  int b = 64;
+  while (b < R) b <<= 1;
+  return b;
+}
 
 int solve_tc_run(Handle* h, int mode, int TN, const double* B, int64_t ldb, int R, double* X, int64_t ldx,
                  const double* sub, cudaStream_t st) {
   if (h->cplx || (mode != RS_PREC_FP32 && mode != MODE_FWD_F32) || (TN != 64 && TN != 128 && TN != 256) || R < 1 ||
-      R > 256)
-    return fail(RS_ERR_ARG, "tensor-core solve: real kernels, float modes, TN in {64, 128, 256}, 1..256 columns");
+      R > TC_MAX_COLS)
+    return fail(RS_ERR_ARG, "tensor-core solve: real kernels, float modes, TN in {64, 128, 256}, 1..%d columns",
+                TC_MAX_COLS);
   if (!h->pers_tc) h->pers_tc = new TCache();
   TCache* c = (TCache*)h->pers_tc;
   const int Rb = std::max(tc_bucket(R), TN);
