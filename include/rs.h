@@ -79,6 +79,17 @@ enum rs_id_arith {
   RS_ID_DFLOAT = 1
 };
 
+/* Randomized ID (Sec. 2.2: the paper's ID compresses a random sample of a
+ * box's matrix instead of the matrix).  With id_oversample = p > 0, a box
+ * whose compressed matrix M (m x n) has m > n + p is compressed through the
+ * sample Omega M of n + p rows (the same pivoted QR and rank rule), Omega
+ * having independent N(0,1) entries: entry (i, r) is element r * 1024 + i of
+ * the normal stream 77 of id_seed (splitmix64 counters, Box-Muller pairs),
+ * the same numbers the package's input module draws.  Boxes compressed by
+ * the multi-CTA forms (too large for one CTA) keep the deterministic QR.
+ * Needs id_arith = RS_ID_FP64 and every box's n + p <= 1024; p = 0 keeps the
+ * deterministic ID.  The paper samples with a structured random transform;
+ * the Gaussian sample is the plain form of the same scheme. */
 typedef struct {
   int kernel_id;      /* enum rs_kernel */
   double k_wave;      /* Helmholtz wavenumber k > 0 (ignored otherwise) */
@@ -86,6 +97,8 @@ typedef struct {
   int proxy_n;        /* > 0; 3D needs 6 g^2 */
   double proxy_ratio; /* > 1 */
   int id_arith;       /* enum rs_id_arith */
+  int id_oversample;  /* randomized ID oversampling p (0: deterministic CPQR), 0..512 */
+  uint64_t id_seed;   /* seed of the randomized ID's sample */
 } rs_params;
 
 /* Summary of a built handle (Table solve-lap-2d fields plus timings). */
@@ -299,6 +312,35 @@ int rs_server_destroy(rs_server s);
  *              RS_ERR_TIMEOUT; the next solve restarts its counters;
  *   "off" / NULL  disarm. */
 int rs_set_fault(const char* spec);
+
+/* Recursive skeletonization as a preconditioner (Sec. 6.4): solve a system
+ * coupling npatch patches (scatterers) -- patch i's points X_i, its own
+ * matrix A_ii = I + w_i K(X_i, X_i) and the couplings A_ij = w_j K(X_i, X_j)
+ * (i != j), K_ii = 0 as everywhere -- by restarted GMRES(restart) with the
+ * block-diagonal preconditioner diag(A_ii^-1), each block applied by patch
+ * i's compressed inverse (FP64 solve).  The coupled matrix is applied densely
+ * from the coordinates on the device (the paper uses an FMM there; that is
+ * not part of this library), so n = sum of the patches' N should stay in the
+ * tens of thousands.
+ *   patches   npatch built handles (one per patch, same kernel, wavenumber
+ *             and dimension; each built on exactly its patch's points, with
+ *             its w); not modified
+ *   pts       dim x n, point-major (point q at pts[q*dim ..]), the patches'
+ *             points in patch order, each patch in the order it was built
+ *             with; host or device
+ *   B, X      n values (double, or interleaved complex for the Helmholtz
+ *             kernels) in the same order; host or device; X is written
+ *   tol       relative residual ||b - A x|| / ||b|| to reach (the true
+ *             residual of the coupled matrix, checked at the end)
+ *   max_it    total GMRES iterations allowed; restart: Krylov dimension
+ *             (1..200); precondition: 0 runs plain GMRES (for comparison)
+ *   its_out, relres_out (host, may be NULL): iterations used, final relative
+ *             residual.  Returns RS_OK even when tol was not met.
+ * Errors: RS_ERR_ARG (null or inconsistent arguments), RS_ERR_OOM,
+ * RS_ERR_CUDA, RS_ERR_TIMEOUT (a block solve's bounded wait ran out). */
+int rs_gmres_patches(int npatch, const rs_handle* patches, const double* pts, const void* B, void* X,
+                     double tol, int max_it, int restart, int precondition, int* its_out,
+                     double* relres_out, void* stream);
 
 /* Build-path override and path counters, for tests (the paper has no
  * counterpart: these select among this library's own kernels, all of which

@@ -7,6 +7,10 @@ numpy.linalg.solve (LU with partial pivoting, a library primitive): the
 brute-force Gaussian elimination the compressed inverse is compared with
 (Sec. 4.3 states the hand-rolled elimination is one ordering of it).
 
+coupled_matrix (several patches, Sec. 6.4) is pinned by its special cases:
+one patch is dense_matrix, equal weights give a (complex) symmetric matrix,
+a common translation of all patches leaves it unchanged.
+
 Pins (tests/test_oracle_pins.py): norm2_est against the 2-norm from the
 singular value decomposition (LAPACK through numpy.linalg.norm(E, 2)) on
 random real and complex matrices and on A - A_RS, and against closed forms
@@ -22,6 +26,17 @@ from .kernels import system_block
 def dense_matrix(kind: str, points: np.ndarray, w: float, kwave: float = 0.0) -> np.ndarray:
     idx = np.arange(points.shape[1])
     return system_block(kind, points, idx, idx, w, kwave)
+
+
+def coupled_matrix(kind: str, pts_list, w_list, kwave: float = 0.0) -> np.ndarray:
+    """The matrix coupling several patches (Sec. 6.4): block (i, j) is
+    delta_ij I + w_j K(X_i, X_j) with K_ii = 0 on the diagonal, i.e. every
+    column carries its own patch's weight."""
+    pts = np.hstack(pts_list)
+    n = pts.shape[1]
+    w = np.concatenate([np.full(p.shape[1], wj) for p, wj in zip(pts_list, w_list)])
+    idx = np.arange(n)
+    return system_block(kind, pts, idx, idx, 1.0, kwave) * w[None, :] + np.diag(1.0 - w)
 
 
 def dense_solve(A: np.ndarray, B: np.ndarray) -> np.ndarray:

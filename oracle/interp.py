@@ -22,7 +22,11 @@ Pins (tests/test_oracle_interp.py): skeleton columns reproduced exactly; an
 exactly rank-r matrix gives k = r with a residual at rounding level; the pivot
 order equals LAPACK's dgeqp3 (scipy.linalg.qr with pivoting) on matrices with
 well separated column norms; the ID error sits within a modest factor of
-sigma_{k+1} (Def. 2.3).
+sigma_{k+1} (Def. 2.3).  The randomized ID (interp_decomp_randomized): an
+exactly rank-r matrix again gives k = r and a rounding-level residual (the
+sample of a rank-r matrix has rank r with probability one), the sample is
+the product with the stated normal stream, and on kernel matrices its error
+stays within a modest factor of eps.
 """
 from __future__ import annotations
 
@@ -77,6 +81,38 @@ def interp_decomp(M: np.ndarray, eps: float):
         return sk, rd, np.zeros((0, M.shape[1]), dtype=R.dtype)
     T = solve_triangular(np.triu(R[:k, :k]), R[:k, k:], lower=False)
     return sk, rd, T
+
+
+# Randomized ID (the paper's own ID, Sec. 2.2: compression of a random
+# sample of the matrix's row space instead of the matrix itself).  The
+# sample is Y = Omega M with Omega an l x m matrix of independent N(0,1)
+# entries, l = n + p (p oversampling rows); the ID of Y (the same pivoted QR,
+# same rank rule) is taken as the ID of M: with probability close to one the
+# column relations of Y are those of M up to the precision asked for.  Used
+# only when it shrinks the matrix (m > l).  The paper samples with a
+# structured random transform; a Gaussian Omega is the plain form of the same
+# scheme.  Omega's entries are an input of the method: entry (i, r) is element
+# r * SKETCH_STRIDE + i of the counter-based normal stream `SKETCH_STREAM` of
+# the seed (rs_inputs), the same entries the GPU build draws.
+SKETCH_STRIDE = 1024
+SKETCH_STREAM = 77
+
+
+def sketch_matrix(seed: int, l: int, m: int) -> np.ndarray:
+    """Omega (l x m): entry (i, r) = normal stream element r * SKETCH_STRIDE + i."""
+    import rs_inputs
+    Z = rs_inputs.normal(seed, (m, SKETCH_STRIDE), stream=SKETCH_STREAM)
+    return Z[:, :l].T.copy()
+
+
+def interp_decomp_randomized(M: np.ndarray, eps: float, p: int, seed: int):
+    """Randomized ID of M: the ID of the sample Omega M (l = n + p rows)."""
+    m, n = M.shape
+    l = n + p
+    if m <= l:
+        return interp_decomp(M, eps)
+    Y = sketch_matrix(seed, l, m) @ M
+    return interp_decomp(Y, eps)
 
 
 def projection(sk, rd, T, n):

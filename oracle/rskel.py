@@ -55,7 +55,7 @@ import dataclasses
 
 import numpy as np
 
-from .interp import interp_decomp, projection
+from .interp import interp_decomp, interp_decomp_randomized, projection
 from .kernels import green, is_complex, offdiag_block, proxy_points, proxy_radius_2d, system_block
 from .tree import Tree
 
@@ -69,6 +69,8 @@ class Params:
     nproxy: int = 64
     ratio: float = 1.5
     kwave: float = 0.0
+    id_oversample: int = 0    # > 0: randomized ID with n + id_oversample sample rows (Sec. 2.2)
+    id_seed: int = 0
 
 
 @dataclasses.dataclass
@@ -162,7 +164,10 @@ class Factorization:
         tr, pr = self.tree, self.params
         I = active_of[b]
         M = self._compress_matrix(depth, b, I, active_of)
-        sk_loc, rd_loc, T = interp_decomp(M, pr.eps)
+        if pr.id_oversample > 0:
+            sk_loc, rd_loc, T = interp_decomp_randomized(M, pr.eps, pr.id_oversample, pr.id_seed)
+        else:
+            sk_loc, rd_loc, T = interp_decomp(M, pr.eps)
         P = projection(sk_loc, rd_loc, T, len(I)).astype(self._dtype())
         if depth == tr.L:
             D = system_block(pr.kind, tr.points, I, I, pr.w, pr.kwave)

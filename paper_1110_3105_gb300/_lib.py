@@ -32,7 +32,8 @@ class RSError(RuntimeError):
 
 class rs_params(ctypes.Structure):
     _fields_ = [("kernel_id", ctypes.c_int), ("k_wave", ctypes.c_double), ("weight", ctypes.c_double),
-                ("proxy_n", ctypes.c_int), ("proxy_ratio", ctypes.c_double), ("id_arith", ctypes.c_int)]
+                ("proxy_n", ctypes.c_int), ("proxy_ratio", ctypes.c_double), ("id_arith", ctypes.c_int),
+                ("id_oversample", ctypes.c_int), ("id_seed", ctypes.c_uint64)]
 
 
 class rs_stats_t(ctypes.Structure):
@@ -78,6 +79,9 @@ _PROTOS = {
     "rs_server_handle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
     "rs_server_destroy": (ctypes.c_int, [_P]),
     "rs_set_path": (ctypes.c_int, [ctypes.c_char_p]),
+    "rs_gmres_patches": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                        _P]),
     "rs_tc_selftest": (ctypes.c_int, [ctypes.c_int, _P, _P, _P, ctypes.c_int]),
     "rs_probe_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "rs_path_counts": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
@@ -175,9 +179,11 @@ ID_ARITH = {"fp64": 0, "dfloat": 1}
 
 
 def rs_build(points, kernel: str, weight: float, eps: float, leaf: int, proxy_n: int,
-             proxy_ratio: float = 1.5, k_wave: float = 0.0, stream=None, id_arith: str = "fp64") -> Handle:
+             proxy_ratio: float = 1.5, k_wave: float = 0.0, stream=None, id_arith: str = "fp64",
+             id_oversample: int = 0, id_seed: int = 0) -> Handle:
     """points: (dim, N) array (any order numpy, or a column-major torch tensor).
-    id_arith: "fp64" or "dfloat" (arithmetic of the ID's pivoted QR, rs_id_arith)."""
+    id_arith: "fp64" or "dfloat" (arithmetic of the ID's pivoted QR, rs_id_arith).
+    id_oversample > 0: randomized ID with n + id_oversample sample rows (seed id_seed)."""
     load()
     if hasattr(points, "data_ptr"):
         dim, n = points.shape
@@ -190,7 +196,7 @@ def rs_build(points, kernel: str, weight: float, eps: float, leaf: int, proxy_n:
         ptr = pts.ctypes.data
         keep = pts
     p = rs_params(KERNELS[kernel], float(k_wave), float(weight), int(proxy_n), float(proxy_ratio),
-                  ID_ARITH[id_arith])
+                  ID_ARITH[id_arith], int(id_oversample), int(id_seed))
     out = ctypes.c_void_p()
     rc = _lib.rs_build(ptr, n, dim, ctypes.byref(p), float(eps), int(leaf), _stream(stream), ctypes.byref(out))
     del keep
@@ -339,6 +345,23 @@ def rs_tc_selftest(kind: int, A, B, D):
     return D
 
 
+def rs_gmres_patches(handles, points, B, X, tol: float = 1e-10, max_it: int = 500, restart: int = 50,
+                     precondition: bool = True, stream=None):
+    """Block-diagonal RS-preconditioned GMRES on the system coupling the
+    patches (handles in patch order; points (dim, n) of all patches in the
+    same order; B, X length-n vectors).  Returns (iterations, relres)."""
+    lib = load()
+    arr = (ctypes.c_void_p * len(handles))(*[h.ptr for h in handles])
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).T)   # point-major
+    pb = B.data_ptr() if hasattr(B, "data_ptr") else np.asarray(B).ctypes.data
+    px = X.data_ptr() if hasattr(X, "data_ptr") else np.asarray(X).ctypes.data
+    its = ctypes.c_int()
+    rel = ctypes.c_double()
+    _check(lib.rs_gmres_patches(len(handles), arr, pts.ctypes.data, pb, px, float(tol), int(max_it), int(restart),
+                                1 if precondition else 0, ctypes.byref(its), ctypes.byref(rel), _stream(stream)))
+    return its.value, rel.value
+
+
 def rs_launch_count() -> int:
     return int(load().rs_launch_count())
 
@@ -372,7 +395,7 @@ class Server:
         pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).T)   # point-major
         n, dim = pts.shape
         p = rs_params(KERNELS[kernel], float(k_wave), float(weight), int(proxy_n), float(proxy_ratio),
-                      ID_ARITH[id_arith])
+                      ID_ARITH[id_arith], 0, 0)
         t = ctypes.c_int64()
         _check(_lib.rs_server_submit_build(self._s, pts.ctypes.data, n, dim, ctypes.byref(p), float(eps), int(leaf),
                                            ctypes.byref(t)))

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librs.so")
-SOURCES = ["prims.cu", "tree.cu", "skel.cu", "solve.cu", "api.cu", "prof.cu", "solve2.cu", "fwd2.cu", "server.cu", "tc_test.cu", "solve_tc.cu"]
+SOURCES = ["prims.cu", "tree.cu", "skel.cu", "solve.cu", "api.cu", "prof.cu", "solve2.cu", "fwd2.cu", "server.cu", "tc_test.cu", "solve_tc.cu", "gmres.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcompiler", "-Wall", "-Xcompiler", "-Wno-unused-function"]

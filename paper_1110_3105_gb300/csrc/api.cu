@@ -279,6 +279,10 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
   if (!(params->proxy_ratio > 1.0)) return fail(RS_ERR_ARG, "rs_build: proxy_ratio must be > 1");
   if (params->id_arith != RS_ID_FP64 && params->id_arith != RS_ID_DFLOAT)
     return fail(RS_ERR_ARG, "rs_build: unknown id_arith %d", params->id_arith);
+  if (params->id_oversample < 0 || params->id_oversample > 512)
+    return fail(RS_ERR_ARG, "rs_build: id_oversample must be in 0..512");
+  if (params->id_oversample > 0 && params->id_arith == RS_ID_DFLOAT)
+    return fail(RS_ERR_ARG, "rs_build: the randomized ID runs the FP64 pivoted QR (id_arith must be RS_ID_FP64)");
   if (dim == 3) {
     int g = (int)std::lround(std::sqrt(params->proxy_n / 6.0));
     if (6 * g * g != params->proxy_n) return fail(RS_ERR_ARG, "rs_build: 3D proxy_n must be 6 g^2");
@@ -320,6 +324,8 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
   h->nproxy = params->proxy_n;
   h->ratio = params->proxy_ratio;
   h->id_df = params->id_arith == RS_ID_DFLOAT;
+  h->id_p = params->id_oversample;
+  h->id_seed = params->id_seed;
   h->eps = eps;
   h->leaf = leaf;
 
@@ -634,6 +640,58 @@ int rs_set_fault(const char* spec) {
     return RS_OK;
   }
   return fail(RS_ERR_ARG, "rs_set_fault: unknown fault '%s'", spec);
+}
+
+// Points (dim x n, point-major, host or device) to per-axis device arrays.
+__global__ void k_pts_soa(const double* in, int dim, int64_t n, double* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int d = 0; d < dim; ++d) out[d * n + i] = in[i * dim + d];
+}
+
+int rs_gmres_patches(int npatch, const rs_handle* patches, const double* pts, const void* B, void* X, double tol,
+                     int max_it, int restart, int precondition, int* its_out, double* relres_out, void* stream) {
+  rs::g_err.clear();
+  if (npatch < 1 || !patches || !pts || !B || !X) return fail(RS_ERR_ARG, "rs_gmres_patches: null or empty argument");
+  if (!(tol > 0.0) || max_it < 1 || restart < 1 || restart > 200)
+    return fail(RS_ERR_ARG, "rs_gmres_patches: need tol > 0, max_it >= 1, 1 <= restart <= 200");
+  std::vector<Handle*> hs(npatch);
+  int64_t n = 0;
+  for (int i = 0; i < npatch; ++i) {
+    RS_TRY(check_handle(patches[i]));
+    hs[i] = patches[i];
+    const Handle* a = hs[0];
+    const Handle* b = hs[i];
+    if (b->kp.kind != a->kp.kind || b->kp.kwave != a->kp.kwave || b->dim != a->dim || b->cplx != a->cplx)
+      return fail(RS_ERR_ARG, "rs_gmres_patches: patches must share the kernel, wavenumber and dimension");
+    n += b->N;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int dim = hs[0]->dim;
+  const size_t sb = hs[0]->cplx ? sizeof(c128) : sizeof(double);
+  Staged sP, sB, sX;
+  double* soa = nullptr;
+  int rc = stage_in(pts, dim, dim, (int)n, sizeof(double), st, &sP);   // dim x n, one "column" per point
+  if (rc == RS_OK) rc = stage_in(B, n, n, 1, sb, st, &sB);
+  if (rc == RS_OK) rc = stage_out_alloc(X, n, n, 1, sb, st, &sX);
+  if (rc == RS_OK && cudaMallocAsync((void**)&soa, sizeof(double) * 3 * n, st) != cudaSuccess) {
+    cudaGetLastError();
+    rc = fail(RS_ERR_OOM, "rs_gmres_patches: point buffer allocation failed");
+  }
+  if (rc == RS_OK) {
+    k_pts_soa<<<(int)std::min<int64_t>(4096, (n + 255) / 256), 256, 0, st>>>((const double*)sP.d, dim, n, soa);
+    RS_CHECK_LAUNCH();
+    rc = gmres_patches_device(npatch, hs.data(), soa, sB.d, sX.d, tol, max_it, restart, precondition, its_out,
+                              relres_out, st);
+  }
+  if (rc == RS_OK) rc = stage_out_finish(X, n, n, 1, sb, st, &sX);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (soa) cudaFreeAsync(soa, st);
+  release(&sP, st);
+  release(&sB, st);
+  release(&sX, st);
+  cudaStreamSynchronize(st);
+  if (rc == RS_OK && e != cudaSuccess) rc = fail(RS_ERR_CUDA, "rs_gmres_patches: %s", cudaGetErrorString(e));
+  return rc;
 }
 
 int rs_set_path(const char* spec) {

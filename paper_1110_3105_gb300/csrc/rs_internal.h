@@ -116,6 +116,10 @@ struct Handle {
   int leaf = 64;
   bool cplx = false;
   bool id_df = false;          // double-float pivoted QR in the ID (real kernels)
+  int id_p = 0;                // randomized ID: oversampling rows of the sample (0: deterministic CPQR)
+  uint64_t id_seed = 0;        // seed of the sample's normal stream
+  double* sketch = nullptr;    // sketch table (SKETCH_STRIDE x sketch_m), from the handle's memory
+  int sketch_m = 0;
   int L = 0;
   double center[3] = {0, 0, 0};
   double half = 1.0;           // root half-width a
@@ -237,6 +241,11 @@ int tile_trace(Handle* h, int prec, int R, int64_t cap, int* kind, int* depth, i
 void free_pers(Handle* h);
 int prec_cat(int prec);
 int ensure_work_pub(Handle* h, int prec, int R, cudaStream_t st);
+// Block-diagonal preconditioned GMRES over several patches (gmres.cu); d_pts
+// per axis (x[n], y[n], z[n]) in the caller's order, b and x device vectors.
+int gmres_patches_device(int np, Handle* const* hs, const double* d_pts, const void* b, void* x, double tol,
+                         int max_it, int restart, int precondition, int* its_out, double* relres_out,
+                         cudaStream_t st);
 // Solve with the per-level vectors in the library's static device scratch.
 int solve_noalloc_device(Handle* h, int prec, const void* d_B, int64_t ldb, int nrhs, void* d_X, int64_t ldx,
                          cudaStream_t st);

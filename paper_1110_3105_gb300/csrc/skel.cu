@@ -419,9 +419,43 @@ struct IdArgs {
   const void* pairs;
   int smem_path;         // 1: M in shared memory
   int qr_df;             // 1: double-float QR (real kernels, rs_id_arith)
+  // randomized ID (Sec. 2.2): with sketch_p > 0 a box whose m exceeds
+  // n + sketch_p is compressed through its sample Omega M (n + sketch_p
+  // rows); Omega(i, r) = sketch[i + r * SKETCH_STRIDE]
+  const double* sketch;
+  int sketch_p;
   int mmax, nmax;
   int64_t mnmax;         // max over boxes of m n (the shared M, leading dimension m)
 };
+
+constexpr int SKETCH_STRIDE = 1024;   // rows of the sketch table (the largest sample)
+constexpr int SKETCH_STREAM = 77;
+
+// splitmix64 (Steele, Lea & Flood 2014) of one 64-bit counter.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = (x + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ double uniform01(uint64_t seed, uint64_t stream, uint64_t idx) {
+  const uint64_t base = (seed * 0x100000001B3ull) ^ (stream << 40);
+  return ((double)(splitmix64(idx + base) >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+}
+
+// The sketch table: entry e = r * SKETCH_STRIDE + i is element e of the
+// normal stream of the seed (Box-Muller on pairs of splitmix64 uniforms:
+// element 2p = rad cos(2 pi u2), 2p + 1 = rad sin(2 pi u2), rad =
+// sqrt(-2 log u1), u1 and u2 the p-th uniforms of streams 2 s and 2 s + 1).
+__global__ void k_sketch_table(uint64_t seed, int64_t count, double* out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t pi = (uint64_t)e >> 1;
+    const double u1 = uniform01(seed, 2 * SKETCH_STREAM, pi), u2 = uniform01(seed, 2 * SKETCH_STREAM + 1, pi);
+    const double rad = sqrt(-2.0 * log(u1));
+    const double ang = 2.0 * M_PI * u2;
+    out[e] = (e & 1) ? rad * sin(ang) : rad * cos(ang);
+  }
+}
 
 template <class S, int NT>
 __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
@@ -501,6 +535,25 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
   }
   __syncthreads();
 
+  // randomized ID: the pivoted QR of the sample Omega M (l = n + p rows)
+  // instead of M; the sample overwrites M's first l rows column by column
+  int mq = m;
+  if (a.sketch_p > 0 && m > n + a.sketch_p) {
+    const int l = n + a.sketch_p;
+    for (int c = 0; c < n; ++c) {
+      const S* col = M + (size_t)c * ld;
+      for (int i = threadIdx.x; i < l; i += NT) {
+        S acc = S(0.0);
+        for (int r = 0; r < m; ++r) acc += scal(col[r], a.sketch[i + (size_t)r * SKETCH_STRIDE]);
+        u[i] = acc;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < l; i += NT) M[i + (size_t)c * ld] = u[i];
+      __syncthreads();
+    }
+    mq = l;
+  }
+
   S* T = Tpool + a.toff[b];
   int k;
   bool done = false;
@@ -519,7 +572,7 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
       done = true;
     }
   if (!done) {
-    k = cpqr<S, NT>(M, m, n, ld, a.eps, piv, nrm, u);
+    k = cpqr<S, NT>(M, mq, n, ld, a.eps, piv, nrm, u);
     __syncthreads();
     back_substitute<S, NT>(M, k, n, ld);
     __syncthreads();
@@ -2296,8 +2349,45 @@ int launch_cluster(Kern kern, int nb, int cs, int nt, size_t smem, cudaStream_t 
   return RS_OK;
 }
 
+// Randomized ID on the multi-CTA path: column c of box b of the sample
+// Y = Omega M (l_b rows, compact with leading dimension l_b) from the filled
+// M (m_b rows, g.m / g.moff); boxes with l_b == m_b are copied.  The column's
+// squared norm and the box's rank bound are reset for the sample.
 template <class S>
-int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cudaStream_t st) {
+__global__ void __launch_bounds__(BI_NT) k_sketch_big(const double* sketch, BigId g, const int* n, const int* l,
+                                                      const int64_t* yoff, const S* Mws, S* Yws, int maxn) {
+  const int b = blockIdx.x / maxn, c = blockIdx.x % maxn;
+  if (c >= n[b]) return;
+  const int mb = g.m[b], lb = l[b];
+  const S* col = Mws + g.moff[b] + (size_t)c * mb;
+  S* out = Yws + yoff[b] + (size_t)c * lb;
+  double s2 = 0.0;
+  for (int i = threadIdx.x; i < lb; i += BI_NT) {
+    S acc = S(0.0);
+    if (lb == mb) {
+      acc = col[i];
+    } else {
+      for (int r = 0; r < mb; ++r) acc += scal(col[r], sketch[i + (size_t)r * SKETCH_STRIDE]);
+    }
+    out[i] = acc;
+    s2 += abs2(acc);
+  }
+  __shared__ double red[BI_NT];
+  red[threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = BI_NT / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    g.nrm[g.noff[b] + c] = red[0];
+    if (c == 0) g.kk[b] = min(lb, n[b]);
+  }
+}
+
+template <class S>
+int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows_in, cudaStream_t st) {
+  std::vector<int> mrows = mrows_in;
   const int nb = lv.nbox;
   std::vector<int64_t> moff(nb), noff(nb);
   int64_t macc = 0, nacc = 0;
@@ -2330,6 +2420,35 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows, cu
   prof_begin(P_ID, st);
   k_bbid_fill<S><<<nb * maxn, BI_NT, 0, st>>>(a, g, Mws, maxn);
   RS_CHECK_LAUNCH();
+  if (a.sketch_p > 0) {   // randomized ID: the QR below runs on the samples
+    std::vector<int> lrows(nb);
+    std::vector<int64_t> yoff(nb);
+    int64_t yacc = 0;
+    int lmax = 0;
+    for (int b = 0; b < nb; ++b) {
+      lrows[b] = mrows[b] > lv.h_n[b] + a.sketch_p ? lv.h_n[b] + a.sketch_p : mrows[b];
+      yoff[b] = yacc;
+      yacc += (int64_t)lrows[b] * lv.h_n[b];
+      lmax = std::max(lmax, lrows[b]);
+    }
+    int *dl;
+    int64_t* dyo;
+    RS_TRY(upload(h, &dl, lrows, st));
+    RS_TRY(upload(h, &dyo, yoff, st));
+    S* Yws = nullptr;
+    RS_CUDA(cudaMallocAsync((void**)&Yws, sizeof(S) * std::max<int64_t>(1, yacc), st));
+    k_sketch_big<S><<<nb * maxn, BI_NT, 0, st>>>(a.sketch, g, a.n, dl, dyo, Mws, Yws, maxn);
+    RS_CHECK_LAUNCH();
+    RS_CUDA(cudaFreeAsync(Mws, st));
+    Mws = Yws;
+    mrows = lrows;
+    g.m = dl;
+    g.moff = dyo;
+    a.mrows = dl;
+    a.mmax = lmax;
+    maxkmax = 0;
+    for (int b = 0; b < nb; ++b) maxkmax = std::max(maxkmax, std::min(lrows[b], lv.h_n[b]));
+  }
   const int ncb = div_up(maxn, BI_CB);
   const size_t id_smem = sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax;
   RS_CUDA(cudaFuncSetAttribute(k_bbid_step<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)id_smem));
@@ -2865,6 +2984,22 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st, cudaStream_t fs) {
   a.mmax = lv.maxm;
   a.nmax = lv.maxn;
   a.qr_df = h->id_df && !h->cplx;
+  a.sketch_p = 0;
+  a.sketch = nullptr;
+  if (h->id_p > 0) {   // randomized ID: the sketch table for this depth's largest m
+    if (lv.maxn + h->id_p > SKETCH_STRIDE)
+      return fail(RS_ERR_ARG, "rs_build: randomized ID needs n + oversampling <= %d (n = %d)", SKETCH_STRIDE, lv.maxn);
+    if (h->sketch_m < lv.maxm) {
+      const int64_t cnt = (int64_t)SKETCH_STRIDE * lv.maxm;
+      RS_TRY(dalloc(h, (void**)&h->sketch, sizeof(double) * cnt));
+      k_sketch_table<<<std::max<int64_t>(1, std::min<int64_t>(4096, (cnt + 255) / 256)), 256, 0, st>>>(h->id_seed, cnt,
+                                                                                                    h->sketch);
+      RS_CHECK_LAUNCH();
+      h->sketch_m = lv.maxm;
+    }
+    a.sketch = h->sketch;
+    a.sketch_p = h->id_p;
+  }
   if (h->cplx) RS_TRY(run_id<c128>(h, lv, a, mrows, msum, st));
   else RS_TRY(run_id<double>(h, lv, a, mrows, msum, st));
 

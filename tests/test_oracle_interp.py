@@ -68,3 +68,49 @@ def test_rank_zero_and_full():
     M = np.eye(6)[:, :4]
     sk, rd, T = interp_decomp(M, 1e-9)
     assert len(sk) == 4 and T.shape == (4, 0)
+
+
+# ------------------------------------------------------------ randomized ID
+def test_randomized_id_exact_rank():
+    """A rank-r matrix: the sample has rank r with probability one, so the
+    randomized ID finds k = r and reproduces M to rounding."""
+    from oracle import interp
+    rng = np.random.default_rng(3)
+    for m, n, r in ((300, 40, 7), (500, 90, 33)):
+        M = rng.standard_normal((m, r)) @ rng.standard_normal((r, n))
+        sk, rd, T = interp.interp_decomp_randomized(M, 1e-12, 8, seed=5)
+        assert len(sk) == r
+        P = interp.projection(sk, rd, T, n)
+        assert np.linalg.norm(M - M[:, sk] @ P) <= 1e-12 * np.linalg.norm(M)
+
+
+def test_sketch_is_the_stated_normal_stream():
+    """Omega's entry (i, r) is element r * SKETCH_STRIDE + i of the normal
+    stream (Box-Muller pairs of splitmix64 uniforms), independent of l, m."""
+    from oracle import interp
+    import rs_inputs as ri
+    O = interp.sketch_matrix(9, 12, 30)
+    O2 = interp.sketch_matrix(9, 5, 7)
+    assert np.array_equal(O[:5, :7], O2)
+    z = ri.normal_range(9, 17 * interp.SKETCH_STRIDE + 3, 1, stream=interp.SKETCH_STREAM)[0]
+    assert O[3, 17] == z
+
+
+def test_randomized_id_on_kernel_matrix():
+    """On a proxy-compression matrix of a box: the randomized ID compresses
+    it to a modest factor of eps (Def. 2.3), with a rank near the
+    deterministic one."""
+    import rs_inputs as ri
+    from oracle import interp, rskel
+    pts, h = ri.starfish(2048)
+    F = rskel.build(pts, rskel.Params(kind="laplace2d", w=h, eps=1e-10, leaf=64, nproxy=64))
+    L = F.tree.L
+    lv = F.tree.levels[L]
+    active = [F._active(L, b) for b in range(lv.nbox)]
+    for b in (0, lv.nbox // 2, lv.nbox - 1):
+        M = F._compress_matrix(L, b, active[b], active)
+        sk, rd, T = interp.interp_decomp_randomized(M, 1e-10, 8, seed=1)
+        P = interp.projection(sk, rd, T, M.shape[1])
+        assert np.linalg.norm(M - M[:, sk] @ P, 2) <= 100 * 1e-10 * np.linalg.norm(M, 2)
+        sk0, _, _ = interp.interp_decomp(M, 1e-10)
+        assert abs(len(sk) - len(sk0)) <= 4

@@ -78,3 +78,30 @@ def test_proxy_id_compresses_true_far_field(kind, geom, n, eps, leaf, nproxy):
             assert f.k >= len(sk_true), (depth, b, f.k, len(sk_true))
             checked += 1
     assert checked >= 8
+
+
+def _scatterer(n, center, scale=1.0 / 3.0, rotation=0.0):
+    """r = (2 + cos 3 theta) / 6 (the paper's scatterer, Sec. 6.4) = the
+    starfish with 3 arms, amplitude 1/2, scaled by 1/3; equal arc length."""
+    pts, h = ri.starfish(n, arms=3, amp=0.5, rotation=rotation)
+    return pts * scale + np.asarray(center, dtype=float)[:, None], h * scale
+
+
+def test_coupled_matrix_special_cases():
+    p1, w1 = _scatterer(96, (0.0, 0.0))
+    p2, w2 = _scatterer(80, (1.3, 0.2), rotation=0.4)
+    # one patch: the ordinary system matrix
+    assert np.array_equal(dense.coupled_matrix("laplace2d", [p1], [w1]), dense.dense_matrix("laplace2d", p1, w1))
+    for kind, kw in (("laplace2d", 0.0), ("helmholtz2d", 7.0)):
+        # equal weights: (complex) symmetric, since G(x, y) = G(y, x)
+        A = dense.coupled_matrix(kind, [p1, p2], [w1, w1], kw)
+        assert np.allclose(A, A.T, rtol=0, atol=1e-15 * np.abs(A).max())
+        # a common translation changes no distance
+        At = dense.coupled_matrix(kind, [p1 + 5.0, p2 + 5.0], [w1, w2], kw)
+        A2 = dense.coupled_matrix(kind, [p1, p2], [w1, w2], kw)
+        assert np.allclose(At, A2, rtol=1e-12, atol=1e-13)
+        # each column carries its own patch's weight
+        n1 = p1.shape[1]
+        A1 = dense.coupled_matrix(kind, [p1, p2], [1.0, 1.0], kw)
+        assert np.allclose(A2[:n1, n1:], w2 * A1[:n1, n1:])
+        assert np.allclose(A2[n1:, :n1], w1 * A1[n1:, :n1])

@@ -169,3 +169,22 @@ def test_sphere_helmholtz_single_layer_eigenvalue():
         lam = (Y @ Y) / (Y @ x)
         cont = 1 + 1j * k * spherical_jn(l, k) * (spherical_jn(l, k) + 1j * spherical_yn(l, k))
         assert abs(lam - cont) < 2.0 / np.sqrt(n), (l, lam, cont)
+
+
+@pytest.mark.parametrize("kind,geom,n,eps,leaf,nproxy", [
+    ("laplace2d", "starfish", 2048, 1e-10, 64, 64),
+    ("laplace3d", "sphere", 1500, 1e-6, 128, 216),
+], ids=lambda v: str(v))
+def test_randomized_build_compression_and_solve(kind, geom, n, eps, leaf, nproxy):
+    """The randomized-ID build (Sec. 2.2) meets the same bars as the
+    deterministic one: ||A - A_RS|| / ||A|| <= 10 eps and the solve equals
+    dense elimination on A within 10 eps."""
+    pts, w = ri.geometry(geom, n)
+    F = rskel.build(pts, rskel.Params(kind=kind, w=w, eps=eps, leaf=leaf, nproxy=nproxy, id_oversample=8, id_seed=3))
+    A = dense.dense_matrix(kind, pts, w)
+    ARS = F.apply(np.eye(n))
+    assert dense.norm2_est(A - ARS) / dense.norm2_est(A) <= 10 * eps
+    B = ri.rhs(n, 2, seed=12)
+    X = F.solve(B)
+    Xa = np.linalg.solve(A, B)
+    assert np.linalg.norm(X - Xa) / np.linalg.norm(Xa) <= 10 * eps
