@@ -557,7 +557,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t) / e2e_steps
 
-    serve = others = None
+    serve = others = fwd = None
     if not args.no_serve and rank == 0:
         try:
             serve = serving(rs, torch, H, n, 1e6 / plain_us, args.serve_window, stream)
@@ -567,6 +567,10 @@ def run_ours(args, ws, rank, local):
             others = other_configs(rs, torch, stream)
         except Exception as e:
             others = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            fwd = forward_apply(rs, torch, stream)
+        except Exception as e:
+            fwd = {"error": f"{type(e).__name__}: {e}"}
     H.free()
 
     # roofline of the dominant kernel category in the timed region
@@ -635,6 +639,7 @@ def run_ours(args, ws, rank, local):
         "circle_4096": circle,
         "kernels": kernels,
         "other_configs": others,
+        "forward_apply": fwd,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -665,6 +670,60 @@ def config1(rs, torch, stream):
     us = (time.perf_counter() - t) / 100 * 1e6
     H.free()
     return {"build_ms": statistics.median(tb), "solve_us": us, "rhs_per_s": 1e6 / us}
+
+
+# The paper's forward-apply tables (Sec. 6.1, Tables apply-lap-2ds and
+# apply-lap-3ds: one CPU core at 2.66 GHz, eps 1e-9): matrix-vector time in
+# seconds by N, for context beside rs_matvec's.
+PAPER_TMV = {"circle": {4096: 1.0e-3, 32768: 1.4e-2, 131072: 5.7e-2}, "sphere": {4096: 1.1e-2, 8192: 2.9e-2}}
+
+
+def forward_apply(rs, torch, stream):
+    """rs_matvec (the compressed forward operator of eq. multilevel-compression
+    applied in FP64, Sec. 3.3: the 'generalized FMM' use) on the shapes of the
+    paper's forward-apply tables: the unit circle (2D Laplace) and the unit
+    sphere (3D Laplace) at eps 1e-9.  Build time, one-RHS matvec time (CUDA
+    events around 20 applications on the stream) and the relative error of 64
+    sampled rows against the dense product."""
+    out = []
+    for geom, kind, n, leaf, nproxy in (("circle", "laplace2d", 4096, 64, 64), ("circle", "laplace2d", 32768, 64, 64),
+                                        ("circle", "laplace2d", 131072, 64, 64),
+                                        ("sphere", "laplace3d", 4096, 128, 216),
+                                        ("sphere", "laplace3d", 8192, 128, 216)):
+        pts, w = ri.geometry(geom, n)
+        H = rs.rs_build(pts, kind, w, 1e-9, leaf, nproxy, stream=stream)
+        st = H.stats()
+        x = torch.from_numpy(ri.rhs(n, 1, seed=4)).cuda()
+        y = torch.zeros_like(x)
+        for _ in range(3):
+            rs.rs_matvec(H, x, y, stream=stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps = 20
+        for _ in range(reps):
+            rs.rs_matvec(H, x, y, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mv_ms = e0.elapsed_time(e1) / reps
+        # Sec. 6.1's E on 64 sampled rows: (A x)_i = x_i + w sum_{j != i} G_ij x_j
+        # with G from the library's own Green's-function evaluation (rs_green)
+        rows = np.random.default_rng(n).choice(n, 64, replace=False)
+        xh, yh = x.cpu().numpy()[:, 0], y.cpu().numpy()[:, 0]
+        d = pts[:, rows][:, :, None] - pts[:, None, :]
+        s2 = np.einsum("dij,dij->ij", d, d)
+        s2[np.arange(64), rows] = 1.0
+        G = rs.rs_green(kind, s2.ravel()).reshape(64, n)
+        G[np.arange(64), rows] = 0.0
+        ya = xh[rows] + w * (G @ xh)
+        err = float(np.linalg.norm(yh[rows] - ya) / np.linalg.norm(ya))
+        out.append({"geometry": geom, "kernel": kind, "n": n, "eps": 1e-9, "build_ms": st["build_ms"],
+                    "top_skeletons": st["top_skeletons"], "factor_bytes": st["factor_bytes"],
+                    "matvec_ms": mv_ms, "rel_err_sampled_rows": err,
+                    "paper_tmv_ms_one_cpu_core": PAPER_TMV[geom].get(n, None) and PAPER_TMV[geom][n] * 1e3})
+        H.free()
+    return out
 
 
 def other_configs(rs, torch, stream):
