@@ -23,9 +23,10 @@ import numpy as np
 from .kernels import system_block
 
 
-def dense_matrix(kind: str, points: np.ndarray, w: float, kwave: float = 0.0) -> np.ndarray:
+def dense_matrix(kind: str, points: np.ndarray, w: float, kwave: float = 0.0, geom=None) -> np.ndarray:
+    """geom = (normals, curvature) in the same order as points (double layer)."""
     idx = np.arange(points.shape[1])
-    return system_block(kind, points, idx, idx, w, kwave)
+    return system_block(kind, points, idx, idx, w, kwave, geom)
 
 
 def coupled_matrix(kind: str, pts_list, w_list, kwave: float = 0.0) -> np.ndarray:

@@ -34,8 +34,10 @@ import numpy as np
 from scipy.linalg import solve_triangular
 
 
-def cpqr(M: np.ndarray, eps: float):
-    """Column-pivoted Householder QR stopped at relative precision eps.
+def cpqr(M: np.ndarray, eps: float, kmin: int = 0):
+    """Column-pivoted Householder QR stopped at relative precision eps, but
+    not before kmin steps (kmin > 0: the two-sided ID of a non-symmetric
+    kernel asks both sides for the same rank).
 
     Returns (R, piv, k): R holds the triangular factor in its first k rows,
     piv the column permutation, k the numerical rank.
@@ -53,7 +55,7 @@ def cpqr(M: np.ndarray, eps: float):
             r00 = rjj
             if r00 == 0.0:
                 break
-        elif rjj <= eps * r00:
+        elif rjj <= eps * r00 and (j >= kmin or rjj == 0.0):
             break
         R[:, [j, p]] = R[:, [p, j]]
         piv[[j, p]] = piv[[p, j]]
@@ -72,9 +74,10 @@ def cpqr(M: np.ndarray, eps: float):
     return R, piv, k
 
 
-def interp_decomp(M: np.ndarray, eps: float):
-    """ID of M to relative precision eps: returns (sk, rd, T) with local indices."""
-    R, piv, k = cpqr(M, eps)
+def interp_decomp(M: np.ndarray, eps: float, kmin: int = 0):
+    """ID of M to relative precision eps (rank at least kmin where M allows
+    it): returns (sk, rd, T) with local indices."""
+    R, piv, k = cpqr(M, eps, kmin)
     sk = piv[:k].copy()
     rd = piv[k:].copy()
     if k == 0:
@@ -105,14 +108,14 @@ def sketch_matrix(seed: int, l: int, m: int) -> np.ndarray:
     return Z[:, :l].T.copy()
 
 
-def interp_decomp_randomized(M: np.ndarray, eps: float, p: int, seed: int):
+def interp_decomp_randomized(M: np.ndarray, eps: float, p: int, seed: int, kmin: int = 0):
     """Randomized ID of M: the ID of the sample Omega M (l = n + p rows)."""
     m, n = M.shape
     l = n + p
     if m <= l:
-        return interp_decomp(M, eps)
+        return interp_decomp(M, eps, kmin)
     Y = sketch_matrix(seed, l, m) @ M
-    return interp_decomp(Y, eps)
+    return interp_decomp(Y, eps, kmin)
 
 
 def projection(sk, rd, T, n):

@@ -7,9 +7,17 @@ Green's functions (Sec. 2, Example 1 and 2; Sec. 6.1.2):
   laplace3d    G = 1 / (4 pi |x - y|)             (eq. 3d-laplace)
   helmholtz2d  G = (i/4) H0^(1)(k |x - y|)        (eq. 2d-helmholtz)
   helmholtz3d  G = exp(i k |x - y|) / (4 pi |x - y|) (eq. 3d-helmholtz)
+  laplace2d_dl K = dG/dnu_y = (1/2 pi) (x - y) . nu_y / |x - y|^2, the kernel
+               of the double-layer potential (eq. double-layer) with the 2D
+               Laplace G, nu_y the outward unit normal at the source
 System matrix: A = I + w K with K_ij = G(x_i, x_j) for i != j and K_ii = 0
 (punctured trapezoid / one-point rule, the configuration the workloads
-state; w = h for curves, 4 pi / N on the sphere).
+state; w = h for curves, 4 pi / N on the sphere).  The double-layer kernel
+is smooth on a smooth curve: K_ii is its limit -kappa_i / (4 pi) (kappa the
+curvature), and the trapezoid rule is used as it stands.  The second-kind
+equation -sigma/2 + D sigma = f (eq. 2k-integral-eqn) times -2 is
+A sigma = -2 f with w = -2 h.  The double-layer kernel is not symmetric
+(K(x, y) != K(y, x)): the row and column skeletons of a box differ.
 
 Proxy surfaces (Sec. 3.2, Fig. proxy-comp; count per Sec. 6 opening):
   2D  n_p points on a circle of radius ratio * (sqrt(2)/2) * s around the box
@@ -39,11 +47,24 @@ from __future__ import annotations
 import numpy as np
 from scipy.special import hankel1
 
-KINDS = ("laplace2d", "helmholtz2d", "laplace3d", "helmholtz3d")
+KINDS = ("laplace2d", "helmholtz2d", "laplace3d", "helmholtz3d", "laplace2d_dl")
 
 
 def is_complex(kind: str) -> bool:
     return kind in ("helmholtz2d", "helmholtz3d")
+
+
+def is_symmetric(kind: str) -> bool:
+    return kind != "laplace2d_dl"
+
+
+def green_dl(X: np.ndarray, Y: np.ndarray, NY: np.ndarray) -> np.ndarray:
+    """dG/dnu_y (x_i, y_j) for G = -(1/2 pi) log|x - y|: targets X (2, m),
+    sources Y (2, n) with unit normals NY (2, n); x != y assumed."""
+    diff = X[:, :, None] - Y[:, None, :]
+    r2 = np.sum(diff * diff, axis=0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.einsum("dij,dj->ij", diff, NY) / (2.0 * np.pi * r2)
 
 
 def green(kind: str, X: np.ndarray, Y: np.ndarray, kwave: float = 0.0) -> np.ndarray:
@@ -62,21 +83,38 @@ def green(kind: str, X: np.ndarray, Y: np.ndarray, kwave: float = 0.0) -> np.nda
     raise ValueError(kind)
 
 
-def system_block(kind, pts, I, J, w, kwave=0.0) -> np.ndarray:
-    """A(I, J) = delta_ij + w G(x_i, x_j), with the diagonal term K_ii = 0."""
+def kernel_block(kind, pts, I, J, kwave=0.0, geom=None) -> np.ndarray:
+    """K(x_i, y_j) for targets I and sources J (indices into pts); geom =
+    (normals 2 x N, curvature N) for the double-layer kernel."""
     I = np.asarray(I)
     J = np.asarray(J)
-    G = green(kind, pts[:, I], pts[:, J], kwave)
+    if kind == "laplace2d_dl":
+        nrm, _ = geom
+        return green_dl(pts[:, I], pts[:, J], nrm[:, J])
+    return green(kind, pts[:, I], pts[:, J], kwave)
+
+
+def system_block(kind, pts, I, J, w, kwave=0.0, geom=None) -> np.ndarray:
+    """A(I, J) = delta_ij + w K(x_i, x_j); K_ii = 0, or for the double layer
+    its limit -kappa_i / (4 pi)."""
+    I = np.asarray(I)
+    J = np.asarray(J)
+    G = kernel_block(kind, pts, I, J, kwave, geom)
     same = I[:, None] == J[None, :]
     G[same] = 0.0
     A = w * G
-    A[same] = 1.0
+    if kind == "laplace2d_dl":
+        _, curv = geom
+        ii, jj = np.nonzero(same)
+        A[ii, jj] = 1.0 - w * curv[I[ii]] / (4.0 * np.pi)
+    else:
+        A[same] = 1.0
     return A
 
 
-def offdiag_block(kind, pts, I, J, w, kwave=0.0) -> np.ndarray:
-    """w G(x_i, x_j) between two disjoint point sets."""
-    return w * green(kind, pts[:, np.asarray(I)], pts[:, np.asarray(J)], kwave)
+def offdiag_block(kind, pts, I, J, w, kwave=0.0, geom=None) -> np.ndarray:
+    """w K(x_i, y_j) between two disjoint point sets (targets I, sources J)."""
+    return w * kernel_block(kind, pts, I, J, kwave, geom)
 
 
 def proxy_points(dim: int, center: np.ndarray, side: float, nproxy: int,

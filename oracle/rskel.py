@@ -1,10 +1,18 @@
 """Oracle: recursive skeletonization -- compression, inverse, solve, apply.
 
-Test infrastructure (see the package header).  Symmetric kernels only (all
-three Green's functions give A = A^T), so each box needs a single ID whose
-projection P serves as both R_i = P and L_i = P^T (Sec. 3.1 with identical
-row and column skeletons; complex symmetric Helmholtz uses the transpose,
-not the conjugate transpose).
+Test infrastructure (see the package header).  Symmetric kernels (the four
+Green's functions give A = A^T) need a single ID per box whose projection P
+serves as both R_i = P and L_i = P^T (Sec. 3.1 with identical row and column
+skeletons; complex symmetric Helmholtz uses the transpose, not the conjugate
+transpose).  The double-layer kernel is not symmetric: each box gets a
+column ID of its off-diagonal block column (R_i = P_i, column skeletons) and
+a row ID of its off-diagonal block row (L_i = Q_i^T, row skeletons), as the
+one-level scheme of Sec. 3.1 states it; the two are taken at the same rank
+k_i = max(row rank, column rank) (the pivoted QR of the side with the lower
+rank runs on to k_i steps), the equal-dimension case in which Sec. 3.4
+writes the block elimination.  A box then carries a row active set
+(targets) and a column active set (sources) of equal size: its points at the
+leaves, above them the children's row and column skeletons.
 
 Build, level by level from the leaves (Sec. 3.1, the two-step multilevel
 procedure; depth L of the tree is compression level 1, depth 1 is level
@@ -15,6 +23,12 @@ lambda, depth 0 the root):
   boxes (the near neighbours) plus the proxy surface, each scaled by w;
   2D Laplace adds one constant row when |log rho| < 0.1 (the single layer on
   a circle of radius 1 cannot make constants);
+  double layer, column ID: the colleagues' row active points and the proxy
+  points as targets of the box's sources (the field the box sends out);
+  row ID: the transpose of the box's targets against the colleagues' column
+  active points and against single-layer charges on the proxy circle plus a
+  constant (the fields the box receives from far away: harmonic inside the
+  circle, so single-layer charges on it and a constant represent them);
   ID of that matrix (interp.interp_decomp) -> skeletons, P;
   diagonal block D_i: at the leaves A(I_i, I_i); above, the children's
   Lambda on the diagonal and w G between skeletons of different children
@@ -35,7 +49,7 @@ Forward apply of the compressed matrix (eq. multilevel-compression, Sec. 3.3):
            is A(I_i, I_i) at the leaves and the sibling blocks (zero blocks
            on the children) above
   top      S z on the root's active set (sibling blocks of the depth-1 boxes)
-  downward y_i = D^(l)_i z_i + P_i^T y_parent[slots of i]
+  downward y_i = D^(l)_i z_i + Q_i^T y_parent[slots of i]   (Q_i = P_i if symmetric)
 
 Pins (tests/test_oracle_solver.py): ||A - A_RS|| / ||A|| <= 10 eps against the
 dense matrix; the solve equals dense Gaussian elimination on A_RS to rounding
@@ -56,7 +70,8 @@ import dataclasses
 import numpy as np
 
 from .interp import interp_decomp, interp_decomp_randomized, projection
-from .kernels import green, is_complex, offdiag_block, proxy_points, proxy_radius_2d, system_block
+from .kernels import (green, green_dl, is_complex, is_symmetric, offdiag_block, proxy_points, proxy_radius_2d,
+                      system_block)
 from .tree import Tree
 
 
@@ -71,25 +86,37 @@ class Params:
     kwave: float = 0.0
     id_oversample: int = 0    # > 0: randomized ID with n + id_oversample sample rows (Sec. 2.2)
     id_seed: int = 0
+    normals: np.ndarray | None = None     # (2, N) outward unit normals (double layer), input order
+    curvature: np.ndarray | None = None   # (N,) curvature (double layer), input order
 
 
 @dataclasses.dataclass
 class BoxFactor:
-    I: np.ndarray            # active point ids (tree order positions)
-    sk_loc: np.ndarray       # skeleton positions within I (pivot order)
+    I: np.ndarray            # column active point ids (tree order positions)
+    sk_loc: np.ndarray       # column skeleton positions within I (pivot order)
     rd_loc: np.ndarray       # redundant positions within I
     T: np.ndarray            # k x (n - k) interpolation matrix
-    P: np.ndarray            # k x n projection (R_i = P, L_i = P^T)
+    P: np.ndarray            # k x n column projection (R_i = P)
     D: np.ndarray            # n x n diagonal block of the inverse recursion
     Lam: np.ndarray          # k x k
     calD: np.ndarray         # n x n
     calL: np.ndarray         # n x k
     calR: np.ndarray         # k x n
     m: int = 0               # rows of the compressed matrix
+    # row side (L_i = Q^T); the same objects as the column side for symmetric kernels
+    Ir: np.ndarray = None    # row active point ids
+    skr_loc: np.ndarray = None
+    rdr_loc: np.ndarray = None
+    Tr: np.ndarray = None
+    Q: np.ndarray = None     # k x n row projection
 
     @property
     def sk(self):
         return self.I[self.sk_loc]
+
+    @property
+    def skr(self):
+        return self.Ir[self.skr_loc]
 
     @property
     def n(self):
@@ -104,6 +131,9 @@ class Factorization:
     def __init__(self, tree: Tree, params: Params):
         self.tree = tree
         self.params = params
+        self.geom = None      # (normals, curvature) in tree order (double layer)
+        if params.normals is not None:
+            self.geom = (np.asarray(params.normals)[:, tree.perm], np.asarray(params.curvature)[tree.perm])
         self.boxes = {}       # depth -> list[BoxFactor] for depths L..1
         self.root_I = None    # active set of the root
         self.calS = None      # root diagonal block (dense)
@@ -130,60 +160,100 @@ class Factorization:
                 if a == c:
                     if with_lambda:
                         D[ra, rc] = fa.Lam
-                else:
-                    D[ra, rc] = offdiag_block(pr.kind, tr.points, fa.sk, fc.sk, pr.w, pr.kwave)
+                else:   # rows: row skeletons of child a; columns: column skeletons of child c
+                    D[ra, rc] = offdiag_block(pr.kind, tr.points, fa.skr, fc.sk, pr.w, pr.kwave, self.geom)
         return D
 
     def _active(self, depth, b):
+        """(row active set, column active set) of box b."""
         tr = self.tree
         lv = tr.levels[depth]
         if depth == tr.L:
-            return np.arange(lv.begin[b], lv.end[b])
+            I = np.arange(lv.begin[b], lv.end[b])
+            return I, I
         kids = range(lv.child_begin[b], lv.child_end[b])
-        return np.concatenate([self.boxes[depth + 1][c].sk for c in kids])
+        fs = [self.boxes[depth + 1][c] for c in kids]
+        I = np.concatenate([f.sk for f in fs])
+        return (I if is_symmetric(self.params.kind) else np.concatenate([f.skr for f in fs])), I
+
+    def _proxy(self, depth, b):
+        tr, pr = self.tree, self.params
+        side = tr.box_side(depth)
+        return proxy_points(tr.dim, tr.box_center(depth, b), side, pr.nproxy, pr.ratio), side
 
     def _compress_matrix(self, depth, b, I, active_of):
-        """Rows: near-neighbour active points and proxy points (Sec. 3.2)."""
+        """Column compression of box b: rows = near-neighbour (row) active
+        points and proxy points as targets of the box's sources I (Sec. 3.2)."""
         tr, pr = self.tree, self.params
         lv = tr.levels[depth]
-        near = [active_of[c] for c in lv.colleagues[b]]
+        near = [active_of[c][0] for c in lv.colleagues[b]]
         near = np.concatenate(near) if near else np.zeros(0, dtype=np.int64)
-        center = tr.box_center(depth, b)
-        side = tr.box_side(depth)
-        prox = proxy_points(tr.dim, center, side, pr.nproxy, pr.ratio)
-        rows = [offdiag_block(pr.kind, tr.points, near, I, pr.w, pr.kwave)]
-        rows.append(pr.w * green(pr.kind, prox, tr.points[:, I], pr.kwave))
+        prox, side = self._proxy(depth, b)
+        rows = [offdiag_block(pr.kind, tr.points, near, I, pr.w, pr.kwave, self.geom)]
+        if pr.kind == "laplace2d_dl":
+            rows.append(pr.w * green_dl(prox, tr.points[:, I], self.geom[0][:, I]))
+        else:
+            rows.append(pr.w * green(pr.kind, prox, tr.points[:, I], pr.kwave))
         if pr.kind == "laplace2d" and abs(np.log(proxy_radius_2d(side, pr.ratio))) < 0.1:
             rows.append(pr.w * np.ones((1, len(I))))
         return np.vstack(rows)
+
+    def _compress_matrix_rows(self, depth, b, Ir, active_of):
+        """Row compression of box b (non-symmetric kernels), transposed:
+        rows = the colleagues' column active points and single-layer charges
+        on the proxy circle plus a constant, as sources acting on the box's
+        targets Ir (Sec. 3.2)."""
+        tr, pr = self.tree, self.params
+        lv = tr.levels[depth]
+        near = [active_of[c][1] for c in lv.colleagues[b]]
+        near = np.concatenate(near) if near else np.zeros(0, dtype=np.int64)
+        prox, _ = self._proxy(depth, b)
+        rows = [offdiag_block(pr.kind, tr.points, Ir, near, pr.w, pr.kwave, self.geom).T,
+                pr.w * green("laplace2d", tr.points[:, Ir], prox).T,
+                pr.w * np.ones((1, len(Ir)))]
+        return np.vstack(rows)
+
+    def _id(self, M, kmin=0):
+        pr = self.params
+        if pr.id_oversample > 0:
+            return interp_decomp_randomized(M, pr.eps, pr.id_oversample, pr.id_seed, kmin)
+        return interp_decomp(M, pr.eps, kmin)
 
     # -------------------------------------------------------------------- build
     def _factor_box(self, depth, b, active_of):
         """Compression and block elimination of box b at `depth` (its children,
         if any, are done)."""
         tr, pr = self.tree, self.params
-        I = active_of[b]
+        Ir, I = active_of[b]
         M = self._compress_matrix(depth, b, I, active_of)
-        if pr.id_oversample > 0:
-            sk_loc, rd_loc, T = interp_decomp_randomized(M, pr.eps, pr.id_oversample, pr.id_seed)
-        else:
-            sk_loc, rd_loc, T = interp_decomp(M, pr.eps)
+        sk_loc, rd_loc, T = self._id(M)
+        if is_symmetric(pr.kind):
+            skr_loc, rdr_loc, Tr = sk_loc, rd_loc, T
+        else:   # row ID at the column rank, then the column ID again if the row rank is higher
+            Mr = self._compress_matrix_rows(depth, b, Ir, active_of)
+            skr_loc, rdr_loc, Tr = self._id(Mr, kmin=len(sk_loc))
+            if len(skr_loc) > len(sk_loc):
+                sk_loc, rd_loc, T = self._id(M, kmin=len(skr_loc))
+            if len(skr_loc) != len(sk_loc):
+                raise ValueError("row and column ranks differ: a block of rank below the other side's")
         P = projection(sk_loc, rd_loc, T, len(I)).astype(self._dtype())
+        Q = P if is_symmetric(pr.kind) else projection(skr_loc, rdr_loc, Tr, len(Ir)).astype(self._dtype())
         if depth == tr.L:
-            D = system_block(pr.kind, tr.points, I, I, pr.w, pr.kwave)
+            D = system_block(pr.kind, tr.points, Ir, I, pr.w, pr.kwave, self.geom)
             Dfwd = D
         else:
             D = self._blocks_from_children(depth, b, with_lambda=True)
             Dfwd = self._blocks_from_children(depth, b, with_lambda=False)
-        # block elimination, eq. compressed-inverse (L = P^T, R = P)
-        DinvL = np.linalg.solve(D, P.T)              # D^-1 L
+        # block elimination, eq. compressed-inverse (L = Q^T, R = P)
+        DinvL = np.linalg.solve(D, Q.T)              # D^-1 L
         RDinv = np.linalg.solve(D.T, P.T).T          # R D^-1
         Lam = np.linalg.inv(P @ DinvL)               # (R D^-1 L)^-1
         Dinv = np.linalg.inv(D)
         calD = Dinv - DinvL @ Lam @ RDinv
         calL = DinvL @ Lam
         calR = Lam @ RDinv
-        return BoxFactor(I, sk_loc, rd_loc, T, P, D, Lam, calD, calL, calR, m=M.shape[0]), Dfwd
+        return BoxFactor(I, sk_loc, rd_loc, T, P, D, Lam, calD, calL, calR, m=M.shape[0],
+                         Ir=Ir, skr_loc=skr_loc, rdr_loc=rdr_loc, Tr=Tr, Q=Q), Dfwd
 
     def build(self, box_map=None):
         """Level by level from the leaves.  box_map(f, items) -> list may run the
@@ -200,9 +270,10 @@ class Factorization:
             self.boxes[depth] = [r[0] for r in res]
             self.fwd_blocks[depth] = [r[1] for r in res]
         # root (depth 0)
-        self.root_I = self._active(0, 0)
+        pr = self.params
+        self.root_Ir, self.root_I = self._active(0, 0)
         if tr.L == 0:
-            self.calS = system_block(pr.kind, tr.points, self.root_I, self.root_I, pr.w, pr.kwave)
+            self.calS = system_block(pr.kind, tr.points, self.root_Ir, self.root_I, pr.w, pr.kwave, self.geom)
             self.fwd_blocks[0] = [self.calS]
         else:
             self.calS = self._blocks_from_children(0, 0, with_lambda=True)
@@ -293,7 +364,7 @@ class Factorization:
                 nxt = []
                 for b, f in enumerate(fs):
                     p, sl = self._child_slots(depth, b)
-                    nxt.append(yD[depth][b] + f.P.T @ ys[p][sl])
+                    nxt.append(yD[depth][b] + f.Q.T @ ys[p][sl])
                 ys = nxt
             yt = np.concatenate(ys)
         Y = np.empty_like(yt)

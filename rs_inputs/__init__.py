@@ -11,7 +11,10 @@ workloads here use):
   * starfish r(theta) = 1 + amp*cos(arms*theta), N points equispaced in arc
     length starting at theta = 0, weight h = L / N with L the perimeter;
   * Fibonacci sphere z_i = 1 - (2i+1)/N, phi_i = i*pi*(3 - sqrt 5),
-    weight w = 4 pi / N.
+    weight w = 4 pi / N;
+  * ellipse with semi-axes a = 2, b = 1 (aspect ratio 2, Sec. 6.2), N points
+    equispaced in arc length, weight h = L / N, with outward unit normals and
+    curvature (the double-layer kernel needs both).
 
 Random numbers come from splitmix64 (Steele, Lea & Flood, OOPSLA 2014) as a
 counter-based generator, mapped to N(0,1) with the Box-Muller transform, so
@@ -145,6 +148,53 @@ def starfish(n: int, arms: int = 5, amp: float = 0.3, rotation: float = 0.0):
     return np.vstack([r * np.cos(ang), r * np.sin(ang)]), length / n
 
 
+def ellipse(n: int, a: float = 2.0, b: float = 1.0):
+    """Ellipse x = a cos t, y = b sin t, n points equispaced in arc length.
+
+    Returns (points 2 x n, weight h = L / n, outward unit normals 2 x n,
+    curvature n).  Arc length from the Fourier series of the speed
+    |x'(t)| = sqrt(a^2 sin^2 t + b^2 cos^2 t) (4096-node periodic trapezoid),
+    nodes by Newton's method as for the starfish; the normal is
+    (b cos t, a sin t) / |x'(t)| and the curvature a b / |x'(t)|^3.
+    """
+    nodes = 4096
+    th = 2.0 * np.pi * np.arange(nodes) / nodes
+    c = np.fft.rfft(np.sqrt((a * np.sin(th)) ** 2 + (b * np.cos(th)) ** 2)) / nodes
+    keep = len(c)
+    small = np.abs(c) < 1e-15 * abs(c[0])
+    for m in range(len(c)):
+        if small[m:].all():
+            keep = m
+            break
+    c = c[:keep]
+    length = 2.0 * np.pi * c[0].real
+
+    def s_of(t):
+        e1 = np.exp(1j * t)
+        em = np.ones_like(e1)
+        acc = np.zeros_like(t)
+        for m in range(1, len(c)):
+            em = em * e1
+            acc += np.real(c[m] * (em - 1.0) / (1j * m))
+        return c[0].real * t + 2.0 * acc
+
+    def speed(t):
+        return np.sqrt((a * np.sin(t)) ** 2 + (b * np.cos(t)) ** 2)
+
+    target = length * np.arange(n) / n
+    t = 2.0 * np.pi * np.arange(n) / n
+    for _ in range(20):
+        step = (s_of(t) - target) / speed(t)
+        t = t - step
+        if np.max(np.abs(step)) < 1e-14:
+            break
+    sp = speed(t)
+    pts = np.vstack([a * np.cos(t), b * np.sin(t)])
+    nrm = np.vstack([b * np.cos(t), a * np.sin(t)]) / sp
+    curv = a * b / sp ** 3
+    return pts, length / n, nrm, curv
+
+
 def fibonacci_sphere(n: int):
     """Fibonacci points on the unit sphere.  Returns (points 3 x n, 4 pi / n)."""
     i = np.arange(n, dtype=np.float64)
@@ -187,4 +237,6 @@ def geometry(name: str, n: int, **kw):
         return starfish(n, **kw)
     if name == "sphere":
         return fibonacci_sphere(n)
+    if name == "ellipse":
+        return ellipse(n, **kw)[:2]
     raise ValueError(name)

@@ -108,7 +108,7 @@ def test_randomized_id_on_kernel_matrix():
     lv = F.tree.levels[L]
     active = [F._active(L, b) for b in range(lv.nbox)]
     for b in (0, lv.nbox // 2, lv.nbox - 1):
-        M = F._compress_matrix(L, b, active[b], active)
+        M = F._compress_matrix(L, b, active[b][1], active)
         sk, rd, T = interp.interp_decomp_randomized(M, 1e-10, 8, seed=1)
         P = interp.projection(sk, rd, T, M.shape[1])
         assert np.linalg.norm(M - M[:, sk] @ P, 2) <= 100 * 1e-10 * np.linalg.norm(M, 2)
