@@ -557,7 +557,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t) / e2e_steps
 
-    serve = others = fwd = None
+    serve = others = fwd = dlr = None
     if not args.no_serve and rank == 0:
         try:
             serve = serving(rs, torch, H, n, 1e6 / plain_us, args.serve_window, stream)
@@ -571,6 +571,10 @@ def run_ours(args, ws, rank, local):
             fwd = forward_apply(rs, torch, stream)
         except Exception as e:
             fwd = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            dlr = double_layer(rs, torch, stream)
+        except Exception as e:
+            dlr = {"error": f"{type(e).__name__}: {e}"}
     H.free()
 
     # roofline of the dominant kernel category in the timed region
@@ -640,6 +644,7 @@ def run_ours(args, ws, rank, local):
         "kernels": kernels,
         "other_configs": others,
         "forward_apply": fwd,
+        "double_layer": dlr,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -753,6 +758,64 @@ def other_configs(rs, torch, stream):
                      "relres_max": float(np.max(rel))}
         H.free()
     return out
+
+
+# The paper's 2D Laplace solver table (Sec. 6.2, Table solve-lap-2d: the
+# double-layer interior Dirichlet problem on the ellipse, eps 1e-9, one CPU
+# core at 2.66 GHz) at N = 131072: compression + factorization seconds,
+# solve seconds, the interior error E and the storage in MB.
+PAPER_DL_131072 = {"t_build_s": 4.6 + 3.7, "t_solve_s": 7.5e-2, "E": 8.5e-11, "M_MB": 220.0}
+
+
+def double_layer(rs, torch, stream):
+    """The non-symmetric double layer (two-sided IDs, Sec. 3.1) on the paper's
+    ellipse at N = 131072: build time, the FP64 one-RHS solve, a refined
+    256-column solve, and E, the error of the double-layer potential of the
+    solved density at interior points against the exterior point source's
+    field (the measurement of Sec. 6.2; evaluated here with numpy on 4
+    points, outside the timed work)."""
+    name = "laplace2d_dl_ellipse_131072"
+    wl = ri.WORKLOADS[name]
+    n = wl["n"]
+    p, h, nrm, kap = ri.ellipse(n)
+    w = -2.0 * h
+    H = rs.rs_build(p, wl["kernel"], w, wl["eps"], wl["leaf"], wl["nproxy"], normals=nrm, curvature=kap,
+                    stream=stream)
+    st = H.stats()
+    src = np.array([3.0, 2.0])
+    xin = np.array([[0.5, -1.2, 1.6, 0.0], [0.2, -0.3, 0.1, 0.6]])
+    f = -np.log(np.hypot(*(p - src[:, None]))) / (2 * np.pi)
+    b = torch.from_numpy(-2.0 * f).cuda()[:, None]
+    x = torch.zeros_like(b)
+    rs.rs_solve(H, b, x, stream=stream)   # warm-up
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        rs.rs_solve(H, b, x, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solve_us = e0.elapsed_time(e1) / 10 * 1e3
+    sig = x[:, 0].cpu().numpy()
+    d = xin[:, :, None] - p[:, None, :]
+    kern = np.einsum("dij,dj->ij", d, nrm) / (2 * np.pi * np.einsum("dij,dij->ij", d, d))
+    u = h * (kern @ sig)
+    ex = -np.log(np.hypot(*(xin - src[:, None]))) / (2 * np.pi)
+    E = float(np.max(np.abs(u - ex) / np.abs(ex)))
+    B = torch.from_numpy(ri.rhs(n, 256, seed=302)).cuda().t().contiguous().t()
+    X = torch.zeros_like(B)
+    rs.rs_solve_refined(H, B, X, tol=1e-10, max_it=8, stream=stream)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    its, rel = rs.rs_solve_refined(H, B, X, tol=1e-10, max_it=8, stream=stream)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t) * 1e3
+    H.free()
+    return {name: {"build_ms": st["build_ms"], "depth": st["depth"], "top_skeletons": st["top_skeletons"],
+                   "factor_bytes": st["factor_bytes"], "fp64_solve_us": solve_us, "E_interior": E,
+                   "refined_256_ms": ms, "refined_rhs_per_s": 256 / (ms / 1e3), "refine_iterations": its,
+                   "relres_max": float(np.max(rel)), "paper_one_cpu_core": PAPER_DL_131072}}
 
 
 def profile_step():

@@ -13,7 +13,9 @@
  *   - factorization: block elimination of the sparse embedding
  *     (eq. compressed-inverse, eq. multilevel-inverse, Sec. 3.4);
  *   - solve: the telescoping inverse applied level by level (Sec. 4.3).
- * Green's functions: eq. 2d-laplace, eq. 3d-laplace, eq. 2d-helmholtz.
+ * Green's functions: eq. 2d-laplace, eq. 3d-laplace, eq. 2d-helmholtz,
+ * eq. 3d-helmholtz, and the 2D double-layer kernel of eq. double-layer
+ * (non-symmetric: separate row and column skeletons, Sec. 3.1).
  *
  * Conventions (all entry points):
  *   - Return value: RS_OK (0) or a negative RS_ERR_* code.  On error no
@@ -55,7 +57,10 @@ enum rs_kernel {
   RS_LAPLACE2D = 0,   /* G = -(1/2 pi) log r          (eq. 2d-laplace)   */
   RS_HELMHOLTZ2D = 1, /* G = (i/4) H0^(1)(k r)         (eq. 2d-helmholtz) */
   RS_LAPLACE3D = 2,   /* G = 1 / (4 pi r)              (eq. 3d-laplace)   */
-  RS_HELMHOLTZ3D = 3  /* G = e^{i k r} / (4 pi r)      (eq. 3d-helmholtz) */
+  RS_HELMHOLTZ3D = 3, /* G = e^{i k r} / (4 pi r)      (eq. 3d-helmholtz) */
+  RS_LAPLACE2D_DL = 4 /* K = dG/dnu_y = (1/2 pi) (x - y).nu_y / r^2, the 2D
+                         double layer (eq. double-layer, Sec. 6.2); needs
+                         rs_params.normals and .curvature; K_ii = -kappa_i/(4 pi) */
 };
 
 enum rs_precision {
@@ -90,15 +95,30 @@ enum rs_id_arith {
  * Needs id_arith = RS_ID_FP64 and every box's n + p <= 1024; p = 0 keeps the
  * deterministic ID.  The paper samples with a structured random transform;
  * the Gaussian sample is the plain form of the same scheme. */
+/* Non-symmetric kernels (RS_LAPLACE2D_DL).  Every box gets a column ID of
+ * its off-diagonal block column (outgoing skeletons; proxy rows: the kernel
+ * at the proxy points as targets) and a row ID of its off-diagonal block row
+ * (incoming skeletons; proxy rows: single-layer charges on the proxy circle
+ * and a constant as sources), both at the rank max(row rank, column rank)
+ * (Sec. 3.1, in the equal-dimension form of Sec. 3.4's block elimination).
+ * The second-kind equation -sigma/2 + D sigma = f of eq. 2k-integral-eqn is
+ * A sigma = -2 f with weight w = -2 h.  normals: 2 x N column-major outward
+ * unit normals (point i at normals[2 i], normals[2 i + 1]); curvature: N
+ * values; both host or device, in the caller's point order, copied at build;
+ * ignored (may be NULL) for the other kernels.  These builds take the
+ * one-CTA-per-box ID and the general block elimination; the randomized ID
+ * and the double-float ID are not available for them. */
 typedef struct {
   int kernel_id;      /* enum rs_kernel */
   double k_wave;      /* Helmholtz wavenumber k > 0 (ignored otherwise) */
-  double weight;      /* w > 0 */
+  double weight;      /* w: > 0, or any finite nonzero value for RS_LAPLACE2D_DL */
   int proxy_n;        /* > 0; 3D needs 6 g^2 */
   double proxy_ratio; /* > 1 */
   int id_arith;       /* enum rs_id_arith */
   int id_oversample;  /* randomized ID oversampling p (0: deterministic CPQR), 0..512 */
   uint64_t id_seed;   /* seed of the randomized ID's sample */
+  const double* normals;    /* RS_LAPLACE2D_DL: 2 x N outward unit normals */
+  const double* curvature;  /* RS_LAPLACE2D_DL: N curvatures */
 } rs_params;
 
 /* Summary of a built handle (Table solve-lap-2d fields plus timings). */
@@ -176,7 +196,11 @@ int rs_solve_refined(rs_handle h, const void* B, int64_t ldb, int nrhs, void* X,
 int rs_matvec(rs_handle h, const void* X, int64_t ldx, int nrhs, void* Y,
               int64_t ldy, void* stream);
 
-/* Fill *out with the handle's summary. */
+/* Fill *out with the handle's summary: N, the tree depth, K at the top and
+ * the stored-factor size are the quantities the paper's tables list per run
+ * (Tables apply-lap-2ds to solve-lap-3d: N, K_row = K_col, M), the build
+ * time their T_cm + T_lu; the box maxima have no counterpart in the paper.
+ * Errors: RS_ERR_ARG (null handle or output). */
 int rs_stats(rs_handle h, rs_stats_t* out);
 
 /* Tree export for bit-exact comparison (host buffers, caller allocated).
@@ -288,7 +312,9 @@ int rs_server_add_handle(rs_server s, rs_handle h, int* handle_id);
 /* Queue a solve of ncols columns (tol: relative residual target). */
 int rs_server_submit_solve(rs_server s, int handle_id, const void* B, int64_t ldb, int ncols,
                            void* X, int64_t ldx, double tol, int64_t* ticket);
-/* Queue a build; on success the request's result is the new handle id. */
+/* Queue a build; on success the request's result is the new handle id.
+ * pts (and, for RS_LAPLACE2D_DL, params->normals and params->curvature) are
+ * host arrays copied at submission. */
 int rs_server_submit_build(rs_server s, const double* pts, int64_t n, int dim,
                            const rs_params* params, double eps, int leaf, int64_t* ticket);
 /* Wait (up to timeout_s; <= 0 waits indefinitely) for a request; status is
@@ -336,7 +362,7 @@ int rs_set_fault(const char* spec);
  *             (1..200); precondition: 0 runs plain GMRES (for comparison)
  *   its_out, relres_out (host, may be NULL): iterations used, final relative
  *             residual.  Returns RS_OK even when tol was not met.
- * Errors: RS_ERR_ARG (null or inconsistent arguments), RS_ERR_OOM,
+ * Errors: RS_ERR_ARG (null or inconsistent arguments, the double layer), RS_ERR_OOM,
  * RS_ERR_CUDA, RS_ERR_TIMEOUT (a block solve's bounded wait ran out). */
 int rs_gmres_patches(int npatch, const rs_handle* patches, const double* pts, const void* B, void* X,
                      double tol, int max_it, int restart, int precondition, int* its_out,
@@ -375,13 +401,18 @@ int rs_gmres_patches(int npatch, const rs_handle* patches, const double* pts, co
 int rs_set_path(const char* spec);
 int rs_path_counts(int64_t* counts, int cap, int reset);
 
-/* Release every resource of the handle.  NULL is accepted. */
+/* Release every resource of the handle (device memory, workspaces, solve
+ * plans) after the work queued on it has finished.  NULL is accepted.  Resource
+ * management with no counterpart in the paper.  Returns RS_OK. */
 int rs_free(rs_handle h);
 
-/* Message of the calling thread's last error ("" if none). */
+/* Message of the calling thread's last error ("" if none); the string is the
+ * library's (do not free), valid until the thread's next library call.  Error
+ * reporting with no counterpart in the paper. */
 const char* rs_last_error(void);
 
-/* Library version string. */
+/* Library version string (static storage), e.g. "rs-gb300 0.1 (sm_103a)".
+ * No counterpart in the paper. */
 const char* rs_version(void);
 
 /* The Green's function exactly as the library evaluates it (eqs. 2d-laplace,

@@ -15,10 +15,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librs.so")
 
-RS_LAPLACE2D, RS_HELMHOLTZ2D, RS_LAPLACE3D, RS_HELMHOLTZ3D = 0, 1, 2, 3
+RS_LAPLACE2D, RS_HELMHOLTZ2D, RS_LAPLACE3D, RS_HELMHOLTZ3D, RS_LAPLACE2D_DL = 0, 1, 2, 3, 4
 RS_PREC_FP64, RS_PREC_FP32 = 0, 1
 KERNELS = {"laplace2d": RS_LAPLACE2D, "helmholtz2d": RS_HELMHOLTZ2D, "laplace3d": RS_LAPLACE3D,
-           "helmholtz3d": RS_HELMHOLTZ3D}
+           "helmholtz3d": RS_HELMHOLTZ3D, "laplace2d_dl": RS_LAPLACE2D_DL}
 COMPLEX_KERNELS = ("helmholtz2d", "helmholtz3d")
 STATUS = {0: "RS_OK", -1: "RS_ERR_ARG", -2: "RS_ERR_OOM", -3: "RS_ERR_CUDA", -4: "RS_ERR_SINGULAR",
           -5: "RS_ERR_TIMEOUT", -6: "RS_ERR_NAN", -7: "RS_ERR_STATE"}
@@ -33,7 +33,18 @@ class RSError(RuntimeError):
 class rs_params(ctypes.Structure):
     _fields_ = [("kernel_id", ctypes.c_int), ("k_wave", ctypes.c_double), ("weight", ctypes.c_double),
                 ("proxy_n", ctypes.c_int), ("proxy_ratio", ctypes.c_double), ("id_arith", ctypes.c_int),
-                ("id_oversample", ctypes.c_int), ("id_seed", ctypes.c_uint64)]
+                ("id_oversample", ctypes.c_int), ("id_seed", ctypes.c_uint64),
+                ("normals", ctypes.c_void_p), ("curvature", ctypes.c_void_p)]
+
+
+def _dlayer(normals, curvature):
+    """Point-major normals (2N doubles) and curvatures (N) for the double layer,
+    or (None, None); returns the arrays to keep alive and their addresses."""
+    if normals is None:
+        return (), None, None
+    nrm = np.ascontiguousarray(np.asarray(normals, dtype=np.float64).T)   # (N, 2): point-major
+    kap = np.ascontiguousarray(np.asarray(curvature, dtype=np.float64))
+    return (nrm, kap), nrm.ctypes.data, kap.ctypes.data
 
 
 class rs_stats_t(ctypes.Structure):
@@ -180,10 +191,11 @@ ID_ARITH = {"fp64": 0, "dfloat": 1}
 
 def rs_build(points, kernel: str, weight: float, eps: float, leaf: int, proxy_n: int,
              proxy_ratio: float = 1.5, k_wave: float = 0.0, stream=None, id_arith: str = "fp64",
-             id_oversample: int = 0, id_seed: int = 0) -> Handle:
+             id_oversample: int = 0, id_seed: int = 0, normals=None, curvature=None) -> Handle:
     """points: (dim, N) array (any order numpy, or a column-major torch tensor).
     id_arith: "fp64" or "dfloat" (arithmetic of the ID's pivoted QR, rs_id_arith).
-    id_oversample > 0: randomized ID with n + id_oversample sample rows (seed id_seed)."""
+    id_oversample > 0: randomized ID with n + id_oversample sample rows (seed id_seed).
+    normals (2, N) and curvature (N,): the double-layer kernel's geometry (host arrays)."""
     load()
     if hasattr(points, "data_ptr"):
         dim, n = points.shape
@@ -195,11 +207,12 @@ def rs_build(points, kernel: str, weight: float, eps: float, leaf: int, proxy_n:
         dim, n = pts.shape
         ptr = pts.ctypes.data
         keep = pts
+    keep_dl, pn, pk = _dlayer(normals, curvature)
     p = rs_params(KERNELS[kernel], float(k_wave), float(weight), int(proxy_n), float(proxy_ratio),
-                  ID_ARITH[id_arith], int(id_oversample), int(id_seed))
+                  ID_ARITH[id_arith], int(id_oversample), int(id_seed), pn, pk)
     out = ctypes.c_void_p()
     rc = _lib.rs_build(ptr, n, dim, ctypes.byref(p), float(eps), int(leaf), _stream(stream), ctypes.byref(out))
-    del keep
+    del keep, keep_dl
     _check(rc)
     return Handle(out.value, n, kernel in COMPLEX_KERNELS)
 
@@ -391,11 +404,13 @@ class Server:
         return t.value
 
     def submit_build(self, points, kernel: str, weight: float, eps: float, leaf: int, proxy_n: int,
-                     proxy_ratio: float = 1.5, k_wave: float = 0.0, id_arith: str = "fp64") -> int:
+                     proxy_ratio: float = 1.5, k_wave: float = 0.0, id_arith: str = "fp64", normals=None,
+                     curvature=None) -> int:
         pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).T)   # point-major
         n, dim = pts.shape
+        keep_dl, pn, pk = _dlayer(normals, curvature)   # copied by the library at submission
         p = rs_params(KERNELS[kernel], float(k_wave), float(weight), int(proxy_n), float(proxy_ratio),
-                      ID_ARITH[id_arith], 0, 0)
+                      ID_ARITH[id_arith], 0, 0, pn, pk)
         t = ctypes.c_int64()
         _check(_lib.rs_server_submit_build(self._s, pts.ctypes.data, n, dim, ctypes.byref(p), float(eps), int(leaf),
                                            ctypes.byref(t)))

@@ -215,6 +215,38 @@ static void release(Staged* s, cudaStream_t st) {
   s->d = nullptr;
 }
 
+// The double layer's normals (2 x N, point-major) and curvatures (N) in
+// tree order: dlg = [normal x | normal y | curvature], N each.
+__global__ void k_permute_dlayer(const double* nrm, const double* kap, const int* perm, int64_t n, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t src = perm[i];
+  out[i] = nrm[2 * src];
+  out[n + i] = nrm[2 * src + 1];
+  out[2 * n + i] = kap[src];
+}
+
+static int load_dlayer(Handle* h, const double* nrm, const double* kap, cudaStream_t st) {
+  const int64_t n = h->N;
+  const double* dn = nrm;
+  const double* dk = kap;
+  double *tn = nullptr, *tk = nullptr;
+  if (!is_device_ptr(nrm)) {
+    RS_TRY(dalloc_t(h, &tn, (size_t)2 * n));
+    RS_CUDA(cudaMemcpyAsync(tn, nrm, sizeof(double) * 2 * n, cudaMemcpyHostToDevice, st));
+    dn = tn;
+  }
+  if (!is_device_ptr(kap)) {
+    RS_TRY(dalloc_t(h, &tk, (size_t)n));
+    RS_CUDA(cudaMemcpyAsync(tk, kap, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    dk = tk;
+  }
+  RS_TRY(dalloc_t(h, &h->dlg, (size_t)3 * n));
+  k_permute_dlayer<<<div_up(n, 256), 256, 0, st>>>(dn, dk, h->perm, n, h->dlg);
+  RS_CHECK_LAUNCH();
+  return RS_OK;
+}
+
 static int check_handle(rs_handle h) {
   if (!h) return fail(RS_ERR_ARG, "null handle");
   return RS_OK;
@@ -267,14 +299,24 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
   if (!pts || !params) return fail(RS_ERR_ARG, "rs_build: null pointer argument");
   if (n < 1 || n > (int64_t)1 << 30) return fail(RS_ERR_ARG, "rs_build: N=%lld out of range", (long long)n);
   if (dim != 2 && dim != 3) return fail(RS_ERR_ARG, "rs_build: dim must be 2 or 3");
-  if (params->kernel_id < RS_LAPLACE2D || params->kernel_id > RS_HELMHOLTZ3D)
+  if (params->kernel_id < RS_LAPLACE2D || params->kernel_id > RS_LAPLACE2D_DL)
     return fail(RS_ERR_ARG, "rs_build: unknown kernel_id %d", params->kernel_id);
   const bool helm = params->kernel_id == RS_HELMHOLTZ2D || params->kernel_id == RS_HELMHOLTZ3D;
+  const bool dl = params->kernel_id == RS_LAPLACE2D_DL;
   if ((params->kernel_id == RS_LAPLACE3D || params->kernel_id == RS_HELMHOLTZ3D) != (dim == 3))
     return fail(RS_ERR_ARG, "rs_build: kernel %d does not match dim %d", params->kernel_id, dim);
   if (!(eps > 0.0 && eps < 1.0)) return fail(RS_ERR_ARG, "rs_build: eps must be in (0, 1)");
   if (leaf < 1) return fail(RS_ERR_ARG, "rs_build: leaf must be >= 1");
-  if (!(params->weight > 0.0) || !std::isfinite(params->weight)) return fail(RS_ERR_ARG, "rs_build: weight must be > 0");
+  if (dl) {
+    if (!(params->weight != 0.0) || !std::isfinite(params->weight))
+      return fail(RS_ERR_ARG, "rs_build: the double layer needs a finite nonzero weight");
+    if (!params->normals || !params->curvature)
+      return fail(RS_ERR_ARG, "rs_build: the double layer needs normals and curvature");
+    if (params->id_oversample > 0 || params->id_arith != RS_ID_FP64)
+      return fail(RS_ERR_ARG, "rs_build: the double layer runs the deterministic FP64 ID");
+  } else if (!(params->weight > 0.0) || !std::isfinite(params->weight)) {
+    return fail(RS_ERR_ARG, "rs_build: weight must be > 0");
+  }
   if (params->proxy_n < 1) return fail(RS_ERR_ARG, "rs_build: proxy_n must be >= 1");
   if (!(params->proxy_ratio > 1.0)) return fail(RS_ERR_ARG, "rs_build: proxy_ratio must be > 1");
   if (params->id_arith != RS_ID_FP64 && params->id_arith != RS_ID_DFLOAT)
@@ -321,6 +363,7 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
     }
   }
   h->cplx = helm;
+  h->nonsym = dl;
   h->nproxy = params->proxy_n;
   h->ratio = params->proxy_ratio;
   h->id_df = params->id_arith == RS_ID_DFLOAT;
@@ -362,6 +405,7 @@ int rs_build(const double* pts, int64_t n, int dim, const rs_params* params, dou
       dp = tmp;
     }
     if ((rc = build_tree(h, dp, st)) != RS_OK) break;
+    if (dl && (rc = load_dlayer(h, params->normals, params->curvature, st)) != RS_OK) break;
     // is and fs start after everything queued on st so far (tree, status
     // words); allocations are ordered on is from here on
     if (cudaEventRecord(ej, st) != cudaSuccess || cudaStreamWaitEvent(fs, ej, 0) != cudaSuccess ||
@@ -663,6 +707,7 @@ int rs_gmres_patches(int npatch, const rs_handle* patches, const double* pts, co
     const Handle* b = hs[i];
     if (b->kp.kind != a->kp.kind || b->kp.kwave != a->kp.kwave || b->dim != a->dim || b->cplx != a->cplx)
       return fail(RS_ERR_ARG, "rs_gmres_patches: patches must share the kernel, wavenumber and dimension");
+    if (b->nonsym) return fail(RS_ERR_ARG, "rs_gmres_patches: the coupled apply takes the Green's functions only");
     n += b->N;
   }
   cudaStream_t st = (cudaStream_t)stream;

@@ -60,21 +60,33 @@ template <> __device__ __forceinline__ void put_hi<c128>(void* p, int64_t i, c12
   static_cast<cdfloat*>(p)[i] = cdfloat(f64_to_df(v.re), f64_to_df(v.im));
 }
 
+// FU's projection rows from the column ID (R_i = P_i), FL from the row ID
+// (L_i = Q_i^T; Q = P for symmetric kernels).
 template <class S>
-__global__ void k_fwd_factors(FwdTab t, const S* T, const int64_t* uoff, const int64_t* loff, void* FUlo, void* FUhi,
-                              void* FLlo, void* FLhi) {
-  extern __shared__ int inv[];   // position within I -> index in the ID order
+__global__ void k_fwd_factors(FwdTab t, const S* T, const int* lperm_r, const S* Tr, const int64_t* uoff,
+                              const int64_t* loff, void* FUlo, void* FUhi, void* FLlo, void* FLhi) {
+  extern __shared__ int inv[];   // position within I -> index in the ID order (column ID, then row ID)
   const int b = blockIdx.x;
   const int n = t.n[b], k = t.k ? t.k[b] : 0, rows = n + k;
   if (k == 0) return;
   const int64_t off = t.off[b];
   const int* lp = t.lperm + off;
+  const int* lpr = lperm_r + off;
   const S* Tb = T + t.toff[b];
-  for (int q = threadIdx.x; q < n; q += blockDim.x) inv[lp[q]] = q;
+  const S* Tbr = Tr + t.toff[b];
+  int* invr = inv + n;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    inv[lp[q]] = q;
+    invr[lpr[q]] = q;
+  }
   __syncthreads();
   auto pval = [&](int a, int c) -> S {   // P[a, c]
     int q = inv[c];
     return q < k ? S(q == a ? 1.0 : 0.0) : Tb[a + (size_t)(q - k) * k];
+  };
+  auto qval = [&](int a, int c) -> S {   // Q[a, c]
+    int q = invr[c];
+    return q < k ? S(q == a ? 1.0 : 0.0) : Tbr[a + (size_t)(q - k) * k];
   };
   const int64_t ub = uoff[b], lb = loff[b];
   for (int64_t e = threadIdx.x; e < (int64_t)k * n; e += blockDim.x) {
@@ -86,7 +98,7 @@ __global__ void k_fwd_factors(FwdTab t, const S* T, const int64_t* uoff, const i
   }
   for (int64_t e = threadIdx.x; e < (int64_t)n * k; e += blockDim.x) {
     const int r = (int)(e % n), a = (int)(e / n);
-    const S v = pval(a, r);
+    const S v = qval(a, r);
     put_lo<S>(FLlo, lb + e, v);
     put_hi<S>(FLhi, lb + e, v);
   }
@@ -101,10 +113,11 @@ int fwd_blocks(Handle* h, cudaStream_t st) {
   for (int d = 1; d <= h->L; ++d) {
     Level& lv = h->lv[d];
     FwdTab t{lv.n, lv.k, lv.off, lv.skoff, lv.lperm, lv.toff};
-    const size_t smem = sizeof(int) * (size_t)std::max(1, lv.maxn);
+    const size_t smem = 2 * sizeof(int) * (size_t)std::max(1, lv.maxn);
     RS_CUDA(cudaFuncSetAttribute(k_fwd_factors<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_fwd_factors<S><<<lv.nbox, 256, smem, st>>>(t, (const S*)lv.T, lv.uoff, lv.loff, lv.FU32, lv.FUdf, lv.FL32,
-                                                 lv.FLdf);
+    k_fwd_factors<S><<<lv.nbox, 256, smem, st>>>(t, (const S*)lv.T, lv.lperm_r ? lv.lperm_r : lv.lperm,
+                                                 (const S*)(lv.T_r ? lv.T_r : lv.T), lv.uoff, lv.loff, lv.FU32,
+                                                 lv.FUdf, lv.FL32, lv.FLdf);
     RS_CHECK_LAUNCH();
   }
   return RS_OK;

@@ -118,6 +118,10 @@ struct Pts {
   const double* x;
   const double* y;
   const double* z;  // null in 2D
+  // outward unit normals and curvature (double-layer kernel only, else null)
+  const double* nx;
+  const double* ny;
+  const double* kap;
 };
 
 __device__ inline double dist2(const Pts& p, int i, int j) {
@@ -188,18 +192,26 @@ __device__ inline c128 green_cplx(int kind, double kwave, double r) {
   }
   return c128(-0.25 * y0(kr), 0.25 * j0(kr));   // (i/4)(J0 + i Y0)
 }
-// w G(x_i, x_j) for distinct points.
+// Double-layer kernel dG/dnu_y (x, y) for the 2D Laplace G (eq. double-layer):
+// (1/2 pi) (x - y) . nu_y / |x - y|^2, target x = (tx, ty), source j.
+__device__ inline double dlayer_at(const Pts& p, double tx, double ty, int j) {
+  const double dx = tx - p.x[j], dy = ty - p.y[j];
+  return (dx * p.nx[j] + dy * p.ny[j]) / (2.0 * M_PI * (dx * dx + dy * dy));
+}
+// w K(x_i, x_j) for distinct points: target i, source j.
 template <class S> __device__ inline S offdiag_entry(const KParams& kp, const Pts& p, int i, int j);
 template <> __device__ inline double offdiag_entry<double>(const KParams& kp, const Pts& p, int i, int j) {
+  if (kp.kind == RS_LAPLACE2D_DL) return kp.w * dlayer_at(p, p.x[i], p.y[i], j);
   return kp.w * green_real_s2(kp, dist2(p, i, j));
 }
 template <> __device__ inline c128 offdiag_entry<c128>(const KParams& kp, const Pts& p, int i, int j) {
   c128 g = green_cplx(kp.kind, kp.kwave, dist(p, i, j));
   return c128(kp.w * g.re, kp.w * g.im);
 }
-// A_ij = delta_ij + w G(x_i, x_j) with K_ii = 0.
+// A_ij = delta_ij + w K(x_i, x_j) with K_ii = 0; for the double layer K_ii
+// is the kernel's limit on a smooth curve, -kappa_i / (4 pi).
 template <class S> __device__ inline S system_entry(const KParams& kp, const Pts& p, int i, int j) {
-  if (i == j) return S(1.0);
+  if (i == j) return kp.kind == RS_LAPLACE2D_DL ? S(1.0 - kp.w * p.kap[i] * (0.25 / M_PI)) : S(1.0);
   return offdiag_entry<S>(kp, p, i, j);
 }
 

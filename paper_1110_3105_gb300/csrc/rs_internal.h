@@ -97,6 +97,12 @@ struct Level {
   void* FL32 = nullptr;
   void* FUdf = nullptr;
   void* FLdf = nullptr;
+  // row side of a non-symmetric kernel (row active set, row ID's column
+  // order and T, at the same offsets as the column side); for symmetric
+  // kernels these alias act, lperm and T
+  int* act_r = nullptr;
+  int* lperm_r = nullptr;
+  void* T_r = nullptr;
   int64_t ksum = 0;            // sum of k (size of depth-1 active vector)
   int64_t usz = 0, lsz = 0, lamsz = 0, tsz = 0;  // scalars in the pools
   int maxn = 0, maxm = 0, maxk = 0;
@@ -124,6 +130,8 @@ struct Handle {
   double center[3] = {0, 0, 0};
   double half = 1.0;           // root half-width a
   double* pts = nullptr;       // 3 * N (x, y, z blocks)
+  double* dlg = nullptr;       // double layer: 3 * N (normal x, normal y, curvature), tree order
+  bool nonsym = false;         // non-symmetric kernel: two-sided IDs
   int* perm = nullptr;
   std::vector<Level> lv;       // index = depth
   std::vector<void*> allocs;   // pool blocks owned by the handle (freed by rs_free)

@@ -50,6 +50,7 @@ struct Request {
   double tol = 1e-10;
   // build
   std::vector<double> pts;
+  std::vector<double> nrm, kap;   // double layer: host copies of the normals and curvatures
   int64_t n = 0;
   int dim = 2;
   rs_params params{};
@@ -396,6 +397,14 @@ int rs_server_submit_build(rs_server s, const double* pts, int64_t n, int dim, c
   r->n = n;
   r->dim = dim;
   r->params = *params;
+  if (params->kernel_id == RS_LAPLACE2D_DL) {   // copied like the points; the build reads the copies
+    if (!params->normals || !params->curvature || dim != 2)
+      return rs::fail(RS_ERR_ARG, "rs_server_submit_build: the double layer needs 2D points, normals and curvature");
+    r->nrm.assign(params->normals, params->normals + (size_t)2 * n);
+    r->kap.assign(params->curvature, params->curvature + (size_t)n);
+    r->params.normals = r->nrm.data();
+    r->params.curvature = r->kap.data();
+  }
   r->eps = eps;
   r->leaf = leaf;
   r->t_submit = Clock::now();

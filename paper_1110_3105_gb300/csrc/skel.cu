@@ -95,7 +95,8 @@ __device__ inline double dist2_to(const Pts& p, int i, const double* q) {
 }
 
 // Column-pivoted Householder QR of M (m x n, column-major, leading dim ld),
-// stopped at relative precision eps.  On return piv holds the column order,
+// stopped at relative precision eps but not before kmin steps (unless the
+// trailing matrix is exactly zero).  On return piv holds the column order,
 // M[0:k, 0:n] the triangular factor; returns k.
 //
 // The trailing column norms that choose the pivots are downdated after each
@@ -106,7 +107,7 @@ __device__ inline double dist2_to(const Pts& p, int i, const double* q) {
 // norm, which sets R_jj, the reflector and the stopping test, is always
 // recomputed exactly.  nrm holds 2 n doubles (current | last exact).
 template <class S, int NT>
-__device__ int cpqr(S* M, int m, int n, int ld, double eps, int* piv, double* nrm, S* u) {
+__device__ int cpqr(S* M, int m, int n, int ld, double eps, int* piv, double* nrm, S* u, int kmin = 0) {
   __shared__ int s_p, s_stop;
   __shared__ double s_rjj, s_r00;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -168,7 +169,7 @@ __device__ int cpqr(S* M, int m, int n, int ld, double eps, int* piv, double* nr
         if (j == 0) {
           s_r00 = rjj;
           if (!(rjj > 0.0)) stop = 1;
-        } else if (rjj <= eps * s_r00) {
+        } else if (rjj <= eps * s_r00 && (j >= kmin || !(rjj > 0.0))) {
           stop = 1;
         }
         s_rjj = rjj;
@@ -269,7 +270,8 @@ __device__ __forceinline__ void df_fma_n(dfloat& s, dfloat a, dfloat b) {
 }
 
 template <int NT>
-__device__ int cpqr_df(dfloat* M, int m, int n, int ld, double eps, int* piv, double* nrm, dfloat* u) {
+__device__ int cpqr_df(dfloat* M, int m, int n, int ld, double eps, int* piv, double* nrm, dfloat* u,
+                       int kmin = 0) {
   __shared__ int s_p, s_stop;
   __shared__ double s_rjj, s_r00;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -329,7 +331,7 @@ __device__ int cpqr_df(dfloat* M, int m, int n, int ld, double eps, int* piv, do
         if (j == 0) {
           s_r00 = rjj;
           if (!(rjj > 0.0)) stop = 1;
-        } else if (rjj <= eps * s_r00) {
+        } else if (rjj <= eps * s_r00 && (j >= kmin || !(rjj > 0.0))) {
           stop = 1;
         }
         s_rjj = rjj;
@@ -411,6 +413,15 @@ struct IdArgs {
   const int64_t* toff;
   int* kout;
   int* lperm;
+  // two-sided IDs (non-symmetric kernels): act_near = the colleagues' point
+  // ids that make the near-field rows (the row active set for the column
+  // ID, the column active set for the row ID; = act for symmetric kernels);
+  // row_side = 1: the transposed row ID (entries K(box point, near point),
+  // proxy rows from single-layer charges on the proxy circle, a constant
+  // row); kmin: per-box minimum rank (null: none)
+  const int* act_near;
+  int row_side;
+  const int* kmin;
   // near-field blocks shared by colleague pairs (k_near_pairs): for box b's
   // colleague slot s, the block G(I_j, I_b) starts at pair_base[27 b + s] of
   // pairs, stored for the lower-numbered box of the pair (n_j x n_b
@@ -497,7 +508,7 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
     while (cstart[j + 1] <= r) ++j;
     int c = a.coll[b * 27 + j];
     const int q = r - cstart[j];
-    rowid[r] = a.act[a.off[c] + q];
+    rowid[r] = a.act_near[a.off[c] + q];
     rstride[r] = 0;   // 0: evaluate the entry
     if (pairs) {      // row q of colleague c in the shared block of the pair
       const int64_t base = a.pair_base[b * 27 + j];
@@ -520,11 +531,15 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
     int pc = a.act[off + c];
     S v;
     if (r < nnear) {
-      v = rstride[r] ? pairs[rbase[r] + (int64_t)c * rstride[r]] : offdiag_entry<S>(a.kp, a.pts, rowid[r], pc);
+      v = rstride[r] ? pairs[rbase[r] + (int64_t)c * rstride[r]]
+          : a.row_side ? offdiag_entry<S>(a.kp, a.pts, pc, rowid[r]) : offdiag_entry<S>(a.kp, a.pts, rowid[r], pc);
     } else if (r < nnear + a.geo.nproxy) {
-      v = green_at_s2<S>(a.kp, dist2_to(a.pts, pc, pxy + 3 * (r - nnear)));
-    } else {
-      v = S(a.kp.w);
+      const double* pp = pxy + 3 * (r - nnear);
+      if (a.kp.kind != RS_LAPLACE2D_DL) v = green_at_s2<S>(a.kp, dist2_to(a.pts, pc, pp));
+      else if (a.row_side) v = S(-a.kp.w * (0.25 / M_PI) * log_tab(a.kp.logtab, dist2_to(a.pts, pc, pp)));
+      else v = S(a.kp.w * dlayer_at(a.pts, pp[0], pp[1], pc));
+    } else {   // the constant row (2D Laplace near radius 1; the double layer's row ID)
+      v = (a.kp.kind != RS_LAPLACE2D_DL || a.row_side) ? S(a.kp.w) : S(0.0);
     }
     if constexpr (std::is_same<S, double>::value)
       if (a.qr_df) {
@@ -560,7 +575,7 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
   if constexpr (std::is_same<S, double>::value)
     if (a.qr_df) {   // the fill stored the matrix as double-float
       dfloat* Md = reinterpret_cast<dfloat*>(M);
-      k = cpqr_df<NT>(Md, m, n, ld, a.eps, piv, nrm, reinterpret_cast<dfloat*>(u));
+      k = cpqr_df<NT>(Md, m, n, ld, a.eps, piv, nrm, reinterpret_cast<dfloat*>(u), a.kmin ? a.kmin[b] : 0);
       __syncthreads();
       back_substitute_df<NT>(Md, k, n, ld);
       __syncthreads();
@@ -572,7 +587,7 @@ __global__ void __launch_bounds__(NT) k_id(IdArgs a, S* Mws, S* Tpool) {
       done = true;
     }
   if (!done) {
-    k = cpqr<S, NT>(M, mq, n, ld, a.eps, piv, nrm, u);
+    k = cpqr<S, NT>(M, mq, n, ld, a.eps, piv, nrm, u, a.kmin ? a.kmin[b] : 0);
     __syncthreads();
     back_substitute<S, NT>(M, k, n, ld);
     __syncthreads();
@@ -1160,6 +1175,12 @@ struct FaArgs {
   // same slots
   float* fu32;
   dfloat* fudf;
+  // non-symmetric kernels (general = 1, k_factor only): rows of D from the
+  // row active set, L = Q^T from the row ID (lperm_r, Tr at toff)
+  int general;
+  const int* act_r;
+  const int* lperm_r;
+  const void* Tr;
 };
 
 // The forward operator's D block shares the assembled block's entries: the
@@ -1195,11 +1216,15 @@ __global__ void __launch_bounds__(NT) k_factor(FaArgs a, const S* Tpool, const S
   S* Aug = ws + a.wsoff[b];
   S* X = Aug + (size_t)2 * n * n;
   S* Y = X + (size_t)n * k;
+  S* Yr = Y + (size_t)2 * k * k;   // general: P D^-1 (k x n)
+  const int* lpr = a.general ? a.lperm_r + off : lp;
+  const S* Tq = a.general ? reinterpret_cast<const S*>(a.Tr) + (a.toff ? a.toff[b] : 0) : T;
+  const int* act_rows = a.general ? a.act_r : a.act;
 
   // D (left half) and I (right half)
   for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
     int r = (int)(e % n), c = (int)(e / n);
-    int pr = a.act[off + r], pc = a.act[off + c];
+    int pr = act_rows[off + r], pc = a.act[off + c];
     S v;
     if (a.leaf_level) {
       v = system_entry<S>(a.kp, a.pts, pr, pc);
@@ -1229,13 +1254,21 @@ __global__ void __launch_bounds__(NT) k_factor(FaArgs a, const S* Tpool, const S
     }
     return;
   }
-  // X = D^-1 P^T : X[:, i] = Dinv[:, sk_i] + sum_e T[i, e] Dinv[:, rd_e]
+  // X = D^-1 L = D^-1 Q^T : X[:, i] = Dinv[:, sk_i] + sum_e T[i, e] Dinv[:, rd_e]
+  // (the row ID's skeletons and T; Q = P for symmetric kernels)
   for (int64_t e = tid; e < (int64_t)n * k; e += NT) {
     int r = (int)(e % n), i = (int)(e / n);
-    S s = Dinv[r + (size_t)lp[i] * n];
-    for (int q = 0; q < nr; ++q) s += T[i + (size_t)q * k] * Dinv[r + (size_t)lp[k + q] * n];
+    S s = Dinv[r + (size_t)lpr[i] * n];
+    for (int q = 0; q < nr; ++q) s += Tq[i + (size_t)q * k] * Dinv[r + (size_t)lpr[k + q] * n];
     X[r + (size_t)i * n] = s;
   }
+  if (a.general)   // Yr = R D^-1 = P D^-1 : Yr[i, c] = Dinv[sk_i, c] + sum_e T[i, e] Dinv[rd_e, c]
+    for (int64_t e = tid; e < (int64_t)k * n; e += NT) {
+      int i = (int)(e % k), c = (int)(e / k);
+      S s = Dinv[lp[i] + (size_t)c * n];
+      for (int q = 0; q < nr; ++q) s += T[i + (size_t)q * k] * Dinv[lp[k + q] + (size_t)c * n];
+      Yr[i + (size_t)c * k] = s;
+    }
   __syncthreads();
   // [P X | I] : (P X)[i, c] = X[sk_i, c] + sum_e T[i, e] X[rd_e, c]
   for (int64_t e = tid; e < (int64_t)k * k; e += NT) {
@@ -1258,19 +1291,26 @@ __global__ void __launch_bounds__(NT) k_factor(FaArgs a, const S* Tpool, const S
     for (int q = 0; q < k; ++q) s += X[r + (size_t)q * n] * Lam[q + (size_t)c * k];
     Lf[r + (size_t)c * n] = s;
   }
-  // calR = Lambda X^T  (k x n) -> rows n.. of U
+  // calR = Lambda R D^-1 (k x n) -> rows n.. of U: R D^-1 = X^T for a
+  // symmetric D and Q = P, else Yr
   for (int64_t e = tid; e < (int64_t)k * n; e += NT) {
     int i = (int)(e % k), c = (int)(e / k);
     S s = S(0.0);
-    for (int q = 0; q < k; ++q) s += Lam[i + (size_t)q * k] * X[c + (size_t)q * n];
+    if (a.general)
+      for (int q = 0; q < k; ++q) s += Lam[i + (size_t)q * k] * Yr[q + (size_t)c * k];
+    else
+      for (int q = 0; q < k; ++q) s += Lam[i + (size_t)q * k] * X[c + (size_t)q * n];
     U[n + i + (size_t)c * ldu] = s;
   }
   __syncthreads();
-  // calD = Dinv - calL X^T  (n x n) -> rows 0..n-1 of U
+  // calD = Dinv - calL R D^-1  (n x n) -> rows 0..n-1 of U
   for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
     int r = (int)(e % n), c = (int)(e / n);
     S s = Dinv[r + (size_t)c * n];
-    for (int q = 0; q < k; ++q) s -= Lf[r + (size_t)q * n] * X[c + (size_t)q * n];
+    if (a.general)
+      for (int q = 0; q < k; ++q) s -= Lf[r + (size_t)q * n] * Yr[q + (size_t)c * k];
+    else
+      for (int q = 0; q < k; ++q) s -= Lf[r + (size_t)q * n] * X[c + (size_t)q * n];
     U[r + (size_t)c * ldu] = s;
   }
 }
@@ -2216,6 +2256,9 @@ Geo make_geo(const Handle* h, int depth) {
     double rho = h->ratio * (std::sqrt(2.0) / 2.0) * g.side;
     g.constrow = std::fabs(std::log(rho)) < 0.1 ? 1 : 0;
   }
+  // the double layer's row ID always has the constant row (the column ID
+  // fills it with zeros, so both sides share one row count)
+  if (h->kp.kind == RS_LAPLACE2D_DL) g.constrow = 1;
   return g;
 }
 
@@ -2224,6 +2267,9 @@ Pts make_pts(const Handle* h) {
   p.x = h->pts;
   p.y = h->pts + h->N;
   p.z = h->dim == 3 ? h->pts + 2 * h->N : nullptr;
+  p.nx = h->dlg;
+  p.ny = h->dlg ? h->dlg + h->N : nullptr;
+  p.kap = h->dlg ? h->dlg + 2 * h->N : nullptr;
   return p;
 }
 
@@ -2529,7 +2575,7 @@ int run_id_big(Handle* h, Level& lv, IdArgs a, const std::vector<int>& mrows_in,
 }
 
 template <class S>
-int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows, int64_t msum,
+int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows, int64_t msum, S* Tout,
            cudaStream_t st) {
   IdArgs a = a0;
   size_t sb = sizeof(S);
@@ -2543,8 +2589,10 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
   S* Mws = nullptr;
   a.smem_path = (mbytes + extra <= limit) ? 1 : 0;
   // boxes too large for one CTA: several CTAs per box
-  const bool big_ok =
-      a.geo.nproxy <= 256 && sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax <= 200 * 1024;
+  // (non-symmetric kernels keep one CTA per box, with M in global memory
+  // when it does not fit shared memory)
+  const bool big_ok = !h->nonsym && a.geo.nproxy <= 256 &&
+                      sizeof(S) * (size_t)a.mmax + sizeof(int) * (size_t)a.nmax <= 200 * 1024;
   if (big_ok && (!a.smem_path || (path_force() & PF_ID_BIG))) return run_id_big<S>(h, lv, a, mrows, st);
   size_t smem = a.smem_path ? mbytes + extra : extra;
   if (smem > 227 * 1024) return fail(RS_ERR_ARG, "box too large for shared staging (m=%d n=%d)", a.mmax, a.nmax);
@@ -2577,7 +2625,7 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
     }
   S* pairs = nullptr;
   prof_begin(P_ID, st);
-  if (!pi.empty()) {
+  if (!pi.empty() && !h->nonsym) {
     int *dpi, *dpj;
     int64_t *dpb, *dsb;
     RS_TRY(upload(h, &dpi, pi, st));
@@ -2590,7 +2638,7 @@ int run_id(Handle* h, Level& lv, const IdArgs& a0, const std::vector<int>& mrows
     a.pair_base = dsb;
     a.pairs = pairs;
   }
-  k_id<S, ID_NT><<<lv.nbox, ID_NT, smem, st>>>(a, Mws, (S*)lv.T);
+  k_id<S, ID_NT><<<lv.nbox, ID_NT, smem, st>>>(a, Mws, Tout);
   RS_CHECK_LAUNCH();
   path_count(PATH_ID_CTA);
   prof_end(P_ID, st, 0.0, 0.0);
@@ -2760,13 +2808,14 @@ int run_factor_big(Handle* h, Level& lv, FaArgs a, const Level* child, double by
 
 template <class S>
 int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t st) {
-  // workspace: [D | I] (2 n^2) + X (n k) + [PX | I] (2 k^2)
+  // workspace: [D | I] (2 n^2) + X (n k) + [PX | I] (2 k^2) (+ P D^-1 (k n),
+  // non-symmetric kernels)
   std::vector<int64_t> wsoff(lv.nbox);
   int64_t acc = 0;
   for (int b = 0; b < lv.nbox; ++b) {
     int64_t n = lv.h_n[b], k = lv.h_k[b];
     wsoff[b] = acc;
-    acc += 2 * n * n + n * k + 2 * k * k;
+    acc += 2 * n * n + n * k + 2 * k * k + (h->nonsym ? k * n : 0);
   }
   // shared-memory path when every box's D, X and Lambda fit
   size_t sm_need = 0;
@@ -2777,7 +2826,8 @@ int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t 
   // one CTA per box in shared memory when the boxes fit and are enough to
   // spread over the SMs; a few large boxes take several CTAs each
   const bool few = 2 * lv.nbox < num_sms() && lv.maxn >= 64 && sizeof(S) * (size_t)lv.maxn <= 200 * 1024;
-  const bool smem_path = sm_need <= 200 * 1024 && !few && !(path_force() & PF_FACTOR_BIG);
+  // (non-symmetric kernels: the general one-CTA-per-box elimination below)
+  const bool smem_path = sm_need <= 200 * 1024 && !few && !(path_force() & PF_FACTOR_BIG) && !h->nonsym;
   double fl0 = 0.0, by0 = 0.0;
   for (int b = 0; b < lv.nbox; ++b) {
     double n = lv.h_n[b], k = lv.h_k[b];
@@ -2797,7 +2847,7 @@ int run_factor(Handle* h, Level& lv, FaArgs a, const Level* child, cudaStream_t 
     prof_end(P_FACTOR, st, by0, fl0);
     return RS_OK;
   }
-  if (sizeof(S) * (size_t)lv.maxn <= 200 * 1024) {
+  if (sizeof(S) * (size_t)lv.maxn <= 200 * 1024 && !h->nonsym) {
     path_count(PATH_FAC_BIG);
     return run_factor_big<S>(h, lv, a, child, by0, st);
   }
@@ -2889,7 +2939,7 @@ namespace {
 // The factorization of one depth (or the root, k = 0) on fs, after the
 // skeletonization work queued on st.
 int factor_level(Handle* h, Level& lv, const Level* child, const int* lperm, const int64_t* toff, bool leaf,
-                 cudaStream_t st, cudaStream_t fs) {
+                 cudaStream_t st, cudaStream_t fs, const int* lperm_r = nullptr) {
   FaArgs f{};
   f.kp = h->kp;
   f.pts = make_pts(h);
@@ -2912,6 +2962,12 @@ int factor_level(Handle* h, Level& lv, const Level* child, const int* lperm, con
   f.bad = h->status + 2;
   f.fu32 = (float*)lv.FU32;
   f.fudf = (dfloat*)lv.FUdf;
+  if (h->nonsym) {
+    f.general = 1;
+    f.act_r = lv.act_r;
+    f.lperm_r = lperm_r ? lperm_r : lperm;
+    f.Tr = lv.T_r ? lv.T_r : lv.T;
+  }
   RS_TRY(follow(fs, st));
   if (h->cplx) RS_TRY(run_factor<c128>(h, lv, f, child, fs));
   else RS_TRY(run_factor<double>(h, lv, f, child, fs));
@@ -2965,6 +3021,17 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st, cudaStream_t fs) {
   RS_TRY(dalloc(h, &lv.T, sb * std::max<int64_t>(1, tacc)));
   RS_TRY(dalloc_t(h, &lv.k, nbox));
   RS_TRY(dalloc_t(h, &lv.lperm, std::max<int64_t>(1, lv.ntot)));
+  int* krow = nullptr;   // non-symmetric kernels: the row IDs' ranks
+  if (h->nonsym) {
+    if (!lv.act_r) lv.act_r = lv.act;   // the leaves: rows and columns are the same points
+    RS_TRY(dalloc(h, &lv.T_r, sb * std::max<int64_t>(1, tacc)));
+    RS_TRY(dalloc_t(h, &lv.lperm_r, std::max<int64_t>(1, lv.ntot)));
+    RS_TRY(dalloc_t(h, &krow, nbox));
+  } else {
+    lv.act_r = lv.act;
+    lv.lperm_r = lv.lperm;
+    lv.T_r = lv.T;
+  }
 
   IdArgs a{};
   a.kp = h->kp;
@@ -2974,6 +3041,9 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st, cudaStream_t fs) {
   a.n = lv.n;
   a.off = lv.off;
   a.act = lv.act;
+  a.act_near = lv.act_r;
+  a.row_side = 0;
+  a.kmin = nullptr;
   a.ncoll = lv.ncoll;
   a.coll = lv.coll;
   a.coords = lv.coords;
@@ -3000,18 +3070,42 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st, cudaStream_t fs) {
     a.sketch = h->sketch;
     a.sketch_p = h->id_p;
   }
-  if (h->cplx) RS_TRY(run_id<c128>(h, lv, a, mrows, msum, st));
-  else RS_TRY(run_id<double>(h, lv, a, mrows, msum, st));
+  if (h->cplx) RS_TRY(run_id<c128>(h, lv, a, mrows, msum, (c128*)lv.T, st));
+  else RS_TRY(run_id<double>(h, lv, a, mrows, msum, (double*)lv.T, st));
+  if (h->nonsym) {
+    // Two-sided compression (Sec. 3.1): the row ID of every box (the
+    // transposed block row against the colleagues' column points and the
+    // proxy charges) at no less than the column rank, then the column ID
+    // again at no less than the row rank, so both sides end at
+    // max(row rank, column rank).
+    IdArgs ar = a;
+    ar.act = lv.act_r;
+    ar.act_near = lv.act;
+    ar.row_side = 1;
+    ar.kmin = lv.k;
+    ar.kout = krow;
+    ar.lperm = lv.lperm_r;
+    RS_TRY(run_id<double>(h, lv, ar, mrows, msum, (double*)lv.T_r, st));
+    IdArgs ac = a;
+    ac.kmin = krow;
+    RS_TRY(run_id<double>(h, lv, ac, mrows, msum, (double*)lv.T, st));
+  }
 
   // ranks -> skeleton offsets in the parent depth (one synchronisation for
   // the ranks and the skeletonization's status words)
   lv.h_k.resize(nbox);
   int bad[2] = {0, 0};
+  std::vector<int> hkr(h->nonsym ? nbox : 0);
   RS_CUDA(cudaMemcpyAsync(lv.h_k.data(), lv.k, sizeof(int) * nbox, cudaMemcpyDeviceToHost, st));
+  if (h->nonsym) RS_CUDA(cudaMemcpyAsync(hkr.data(), krow, sizeof(int) * nbox, cudaMemcpyDeviceToHost, st));
   RS_CUDA(cudaMemcpyAsync(bad, h->status, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   RS_CUDA(cudaStreamSynchronize(st));
   if (bad[1]) return fail(RS_ERR_TIMEOUT, "rs_build: a grid barrier wait ran out during skeletonization");
   if (bad[0]) return fail(RS_ERR_SINGULAR, "rs_build: singular block during skeletonization");
+  for (int b = 0; b < (int)hkr.size(); ++b)
+    if (hkr[b] != lv.h_k[b])
+      return fail(RS_ERR_SINGULAR, "rs_build: box %d of depth %d: row rank %d and column rank %d differ", b, depth,
+                  hkr[b], lv.h_k[b]);
   if (prof_on()) {
     double fl = 0.0, by = 0.0;
     for (int b = 0; b < nbox; ++b) {
@@ -3035,7 +3129,7 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st, cudaStream_t fs) {
   // factor (on fs, overlapping the next depths' skeletonization)
   RS_TRY(alloc_factors(h, lv, st));
   const Level* child = depth < h->L ? &h->lv[depth + 1] : nullptr;
-  RS_TRY(factor_level(h, lv, child, lv.lperm, lv.toff, depth == h->L, st, fs));
+  RS_TRY(factor_level(h, lv, child, lv.lperm, lv.toff, depth == h->L, st, fs, lv.lperm_r));
 
   // active sets of depth-1: skeletons of the children, in child order
   Level& up = h->lv[depth - 1];
@@ -3044,6 +3138,13 @@ int skeletonize_level(Handle* h, int depth, cudaStream_t st, cudaStream_t fs) {
   RS_TRY(dalloc_t(h, &up.owner, std::max<int64_t>(1, kacc)));
   k_emit<<<nbox, 64, 0, st>>>(lv.n, lv.k, lv.off, lv.skoff, lv.act, lv.lperm, nbox, up.act, up.owner);
   RS_CHECK_LAUNCH();
+  if (h->nonsym) {   // the row active sets of depth-1: the children's row skeletons
+    RS_TRY(dalloc_t(h, &up.act_r, std::max<int64_t>(1, kacc)));
+    k_emit<<<nbox, 64, 0, st>>>(lv.n, lv.k, lv.off, lv.skoff, lv.act_r, lv.lperm_r, nbox, up.act_r, up.owner);
+    RS_CHECK_LAUNCH();
+  } else {
+    up.act_r = up.act;
+  }
   up.h_n.assign(up.nbox, 0);
   std::vector<int64_t> upoff(up.nbox, -1);
   for (int b = 0; b < nbox; ++b) {
@@ -3070,6 +3171,7 @@ int factor_root(Handle* h, cudaStream_t st, cudaStream_t fs) {
     RS_TRY(upload(h, &lv.off, off, st));
   }
   lv.maxn = lv.h_n[0];
+  if (!lv.act_r) lv.act_r = lv.act;
   lv.h_k.assign(1, 0);
   std::vector<int> k0(1, 0);
   RS_TRY(upload(h, &lv.k, k0, st));

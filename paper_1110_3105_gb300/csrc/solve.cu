@@ -166,6 +166,8 @@ struct FwdView {
   const int* lperm;
   const int64_t* toff;
   int leaf_level;
+  const int* act_r;     // row active set (targets; = act for symmetric kernels)
+  const int* lperm_r;   // row ID's column order (= lperm for symmetric kernels)
 };
 
 // z_parent[skoff + a] = z[sk_a] + sum_e T[a, e] z[rd_e]
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(SV_NT) k_fwd_dblock(FwdView fv, KParams kp, Pt
       S v = S(0.0);
       if (r < rw && q < gw) {
         int pr = off + r0 + r, pq = off + g0 + q;
-        int ir = fv.act[pr], iq = fv.act[pq];
+        int ir = fv.act_r[pr], iq = fv.act[pq];
         if (fv.leaf_level) v = system_entry<S>(kp, pts, ir, iq);
         else if (fv.owner[pr] != fv.owner[pq]) v = offdiag_entry<S>(kp, pts, ir, iq);
       }
@@ -242,12 +244,13 @@ __global__ void __launch_bounds__(SV_NT) k_fwd_dblock(FwdView fv, KParams kp, Pt
 }
 
 // y[sk_a] += w[a], y[rd_e] += sum_a T[a, e] w[a],  w = y_parent[skoff ...]
+// (the row ID's order and T: L_i = Q_i^T)
 template <class S>
 __global__ void k_fwd_down(FwdView fv, const S* T, const S* ypar, S* y, int R) {
   const int b = blockIdx.x;
   const int n = fv.n[b], k = fv.k[b];
   const int64_t off = fv.off[b], sk = fv.skoff[b];
-  const int* lp = fv.lperm + off;
+  const int* lp = fv.lperm_r + off;
   const S* Tb = T + fv.toff[b];
   for (int e = threadIdx.x; e < n * R; e += blockDim.x) {
     int t = e / R, c = e % R;
@@ -402,7 +405,8 @@ int ensure_fwd(Handle* h, int R, cudaStream_t st) {
 
 FwdView fwd_view(const Handle* h, int d) {
   const Level& lv = h->lv[d];
-  return FwdView{lv.n, lv.k, lv.off, lv.skoff, lv.act, lv.owner, lv.lperm, lv.toff, d == h->L};
+  return FwdView{lv.n, lv.k, lv.off, lv.skoff, lv.act, lv.owner, lv.lperm, lv.toff, d == h->L,
+                 lv.act_r ? lv.act_r : lv.act, lv.lperm_r ? lv.lperm_r : lv.lperm};
 }
 
 // y (tree order, point-major, in h->fy[L]) = A_RS z, z given in h->fz[L].
@@ -413,6 +417,9 @@ int forward_tree(Handle* h, int R, cudaStream_t st) {
   pts.x = h->pts;
   pts.y = h->pts + h->N;
   pts.z = h->dim == 3 ? h->pts + 2 * h->N : nullptr;
+  pts.nx = h->dlg;
+  pts.ny = h->dlg ? h->dlg + h->N : nullptr;
+  pts.kap = h->dlg ? h->dlg + 2 * h->N : nullptr;
   const int nct = div_up(R, FD_CT);
   for (int d = L; d >= 0; --d) {
     const Level& lv = h->lv[d];
@@ -438,7 +445,7 @@ int forward_tree(Handle* h, int R, cudaStream_t st) {
   for (int d = 1; d <= L; ++d) {
     const Level& lv = h->lv[d];
     prof_begin(P_FWD_DOWN, st);
-    k_fwd_down<S><<<lv.nbox, 128, 0, st>>>(fwd_view(h, d), (const S*)lv.T, (const S*)h->fy[d - 1],
+    k_fwd_down<S><<<lv.nbox, 128, 0, st>>>(fwd_view(h, d), (const S*)(lv.T_r ? lv.T_r : lv.T), (const S*)h->fy[d - 1],
                                            (S*)h->fy[d], R);
     RS_CHECK_LAUNCH();
     prof_end(P_FWD_DOWN, st, 0.0, 0.0);

@@ -227,6 +227,10 @@ WORKLOADS = {
     # 3D Helmholtz on the unit sphere, k = 10 (omega = k diam / 2 pi = 3.18)
     "helmholtz3d_sphere_8192": dict(geom="sphere", n=8192, kernel="helmholtz3d",
                                     eps=1e-6, leaf=128, nproxy=216, kwave=10.0),
+    # the interior Dirichlet problem on the ellipse a = 2, b = 1 with the
+    # double layer (Sec. 6.2), weight -2 h (A sigma = -2 f)
+    "laplace2d_dl_ellipse_131072": dict(geom="ellipse", n=131072, kernel="laplace2d_dl",
+                                        eps=1e-9, leaf=64, nproxy=64),
 }
 
 

@@ -1,0 +1,152 @@
+"""GPU parity for the non-symmetric double-layer kernel (two-sided IDs,
+Sec. 3.1; the interior Dirichlet problem on the ellipse of aspect ratio 2,
+Sec. 6.2) against the CPU oracle, through the C ABI.
+
+Bars: tree bit-exact; row/column ranks per box within +-2 of the oracle's
+(pivot near-ties); FP64 solve and FP64 forward operator within 10 eps of the
+oracle's per column; the refined solve within 10 eps of the oracle's solve
+with its residual under the oracle's A_RS within 10 eps; the double-layer
+potential of the GPU's density reproduces the exterior point source's field
+inside the ellipse (the paper's error E, ~1e-10 at eps 1e-9), at the oracle
+sizes and at N = 131072 (the largest N of the paper's 2D Laplace solver
+table).
+"""
+import numpy as np
+import pytest
+
+import rs_inputs as ri
+from oracle import dense, rskel
+from oracle.kernels import green_dl, system_block
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SRC = np.array([3.0, 2.0])                                   # exterior point source
+XIN = np.array([[0.5, -1.2, 1.6, 0.0], [0.2, -0.3, 0.1, 0.6]])  # interior evaluation points
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1110_3105_gb300 as rs
+    rs.load()
+
+
+def _rs():
+    import paper_1110_3105_gb300 as rs
+    return rs
+
+
+def _boundary_data(p):
+    """-2 f with f the field of the exterior source on the curve (A sigma = -2 f)."""
+    return -2.0 * (-np.log(np.hypot(*(p - SRC[:, None]))) / (2 * np.pi))
+
+
+def _interior_err(p, h, nrm, sig):
+    u = h * (green_dl(XIN, p, nrm) @ sig)
+    ex = -np.log(np.hypot(*(XIN - SRC[:, None]))) / (2 * np.pi)
+    return np.max(np.abs(u - ex) / np.abs(ex))
+
+
+CASES = [(2048, 1e-9, 64), (8192, 1e-9, 64), (4096, 1e-10, 32)]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: f"ellipse{c[0]}-eps{c[1]:g}-leaf{c[2]}")
+def built(request):
+    rs = _rs()
+    n, eps, leaf = request.param
+    p, h, nrm, kap = ri.ellipse(n)
+    w = -2.0 * h
+    F = rskel.build(p, rskel.Params(kind="laplace2d_dl", w=w, eps=eps, leaf=leaf, nproxy=64, normals=nrm,
+                                    curvature=kap))
+    H = rs.rs_build(p, "laplace2d_dl", w, eps, leaf, 64, normals=nrm, curvature=kap)
+    yield dict(n=n, eps=eps, F=F, H=H, p=p, h=h, w=w, nrm=nrm, kap=kap)
+    H.free()
+
+
+def test_tree_and_ranks(built):
+    rs = _rs()
+    F, H = built["F"], built["H"]
+    T = F.tree
+    assert np.array_equal(rs.rs_tree_perm(H), T.perm)
+    assert H.stats()["depth"] == T.L
+    for d in range(T.L, 0, -1):
+        n, k = rs.rs_box_ranks(H, d, T.levels[d].nbox)
+        on = np.array([f.n for f in F.boxes[d]])
+        ok = np.array([f.k for f in F.boxes[d]])
+        if d == T.L:
+            assert np.array_equal(n, on)
+        assert np.max(np.abs(k - ok)) <= 2 * (T.L - d + 1), d   # near-ties compound up the tree
+
+
+def test_solve_and_matvec_match_oracle(built):
+    rs = _rs()
+    n, eps, F = built["n"], built["eps"], built["F"]
+    B = ri.rhs(n, 3, seed=41)
+    X = np.zeros_like(B)
+    rs.rs_solve(built["H"], B, X)
+    Xo = F.solve(B)
+    err = np.linalg.norm(X - Xo, axis=0) / np.linalg.norm(Xo, axis=0)
+    assert np.all(err <= 10 * eps), err
+    x = ri.rhs(n, 3, seed=42)
+    y = np.zeros_like(x)
+    rs.rs_matvec(built["H"], x, y)
+    yo = F.apply(x)
+    err = np.linalg.norm(y - yo, axis=0) / np.linalg.norm(yo, axis=0)
+    assert np.all(err <= 10 * eps), err
+    if n <= 8192:   # and the dense non-symmetric A (Sec. 5: A_RS within eps of A)
+        A = dense.dense_matrix("laplace2d_dl", built["p"], built["w"], geom=(built["nrm"], built["kap"]))
+        ya = A @ x
+        assert np.linalg.norm(y - ya) / np.linalg.norm(ya) <= 10 * eps
+
+
+def test_refined_matches_oracle(built):
+    rs = _rs()
+    n, eps, F = built["n"], built["eps"], built["F"]
+    B = ri.rhs(n, 4, seed=43)
+    Xr = np.zeros_like(B)
+    its, rel = rs.rs_solve_refined(built["H"], B, Xr, tol=1e-10, max_it=8)
+    assert its >= 1 and np.all(rel <= 1e-10), rel
+    Xo = F.solve(B)
+    err = np.linalg.norm(Xr - Xo, axis=0) / np.linalg.norm(Xo, axis=0)
+    assert np.all(err <= 10 * eps), err
+    r_oracle = np.linalg.norm(F.apply(Xr) - B, axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(r_oracle <= 10 * eps), r_oracle
+
+
+def test_interior_dirichlet_exact(built):
+    """Sec. 6.2's measurement: the field inside from the GPU's density."""
+    rs = _rs()
+    if built["eps"] > 1e-9:
+        pytest.skip("the exact-field bar is set for eps <= 1e-9")
+    b = _boundary_data(built["p"])[:, None].copy(order="F")
+    x = np.zeros_like(b)
+    its, rel = rs.rs_solve_refined(built["H"], b, x, tol=1e-12, max_it=8)
+    assert _interior_err(built["p"], built["h"], built["nrm"], x[:, 0]) <= 1e-9
+
+
+def test_full_size_ellipse():
+    """N = 131072, eps 1e-9 (the largest case of the paper's 2D solver table):
+    the exact interior field, and sampled rows of the true non-symmetric A."""
+    rs = _rs()
+    n, eps = 131072, 1e-9
+    p, h, nrm, kap = ri.ellipse(n)
+    w = -2.0 * h
+    H = rs.rs_build(p, "laplace2d_dl", w, eps, 64, 64, normals=nrm, curvature=kap)
+    try:
+        b = _boundary_data(p)[:, None].copy(order="F")
+        x = np.zeros_like(b)
+        its, rel = rs.rs_solve_refined(H, b, x, tol=1e-12, max_it=8)
+        assert rel[0] <= 1e-12
+        assert _interior_err(p, h, nrm, x[:, 0]) <= 1e-9
+        B = ri.rhs(n, 2, seed=44)
+        X = np.zeros_like(B)
+        rs.rs_solve_refined(H, B, X, tol=1e-10, max_it=8)
+        rows = np.random.default_rng(3).choice(n, 48, replace=False)
+        Ar = system_block("laplace2d_dl", p, rows, np.arange(n), w, geom=(nrm, kap))
+        res = np.linalg.norm(Ar @ X - B[rows], axis=0) / np.linalg.norm(B[rows], axis=0)
+        assert np.all(res <= 10 * eps), res
+    finally:
+        H.free()

@@ -76,6 +76,20 @@ def test_build_parameter_validation(lib):
         rc = _lib._lib.rs_build(q.ctypes.data, 100, dim, ctypes.byref(p), 1e-9, 64, None, ctypes.byref(out))
         assert rc == -1, (kid, dim, kwave)
         assert out.value is None
+    # the double layer: normals and curvature required, 2D only, a nonzero
+    # weight, the deterministic FP64 ID
+    nrm = np.zeros(200)
+    kap = np.zeros(100)
+    for extra, dim in ((dict(), 2), (dict(normals=nrm.ctypes.data), 2),
+                       (dict(normals=nrm.ctypes.data, curvature=kap.ctypes.data, weight=0.0), 2),
+                       (dict(normals=nrm.ctypes.data, curvature=kap.ctypes.data, id_oversample=8), 2),
+                       (dict(normals=nrm.ctypes.data, curvature=kap.ctypes.data, id_arith=1), 2),
+                       (dict(normals=nrm.ctypes.data, curvature=kap.ctypes.data, proxy_n=216), 3)):
+        p = _lib.rs_params(**dict(good, kernel_id=4, **extra))
+        q = np.asfortranarray(np.random.default_rng(1).random((dim, 100)))
+        rc = _lib._lib.rs_build(q.ctypes.data, 100, dim, ctypes.byref(p), 1e-9, 64, None, ctypes.byref(out))
+        assert rc == -1, extra
+        assert out.value is None
 
 
 def test_handle_and_argument_errors(lib):
@@ -96,6 +110,7 @@ def test_handle_and_argument_errors(lib):
     s2 = np.ones(3)
     g = np.zeros(6)
     assert L.rs_green(9, 0.0, s2.ctypes.data, 3, g.ctypes.data) == -1
+    assert L.rs_green(4, 0.0, s2.ctypes.data, 3, g.ctypes.data) == -1   # the double layer needs normals
     assert L.rs_green(0, 0.0, s2.ctypes.data, -1, g.ctypes.data) == -1
     assert L.rs_version().startswith(b"rs-gb300")
 
