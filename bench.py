@@ -785,8 +785,8 @@ def double_layer(rs, torch, stream):
     src = np.array([3.0, 2.0])
     xin = np.array([[0.5, -1.2, 1.6, 0.0], [0.2, -0.3, 0.1, 0.6]])
     f = -np.log(np.hypot(*(p - src[:, None]))) / (2 * np.pi)
-    b = torch.from_numpy(-2.0 * f).cuda()[:, None]
-    x = torch.zeros_like(b)
+    b = torch.from_numpy(-2.0 * f)[None, :].cuda().t()          # N x 1, leading dimension N
+    x = torch.zeros((1, n), dtype=torch.float64, device="cuda").t()
     rs.rs_solve(H, b, x, stream=stream)   # warm-up
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)

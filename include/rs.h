@@ -91,7 +91,7 @@ enum rs_id_arith {
  * having independent N(0,1) entries: entry (i, r) is element r * 1024 + i of
  * the normal stream 77 of id_seed (splitmix64 counters, Box-Muller pairs),
  * the same numbers the package's input module draws.  Boxes compressed by
- * the multi-CTA forms (too large for one CTA) keep the deterministic QR.
+ * the multi-CTA forms (too large for one CTA) are sampled the same way.
  * Needs id_arith = RS_ID_FP64 and every box's n + p <= 1024; p = 0 keeps the
  * deterministic ID.  The paper samples with a structured random transform;
  * the Gaussian sample is the plain form of the same scheme. */
