@@ -422,15 +422,21 @@ __global__ void k_tma_in(const double* B, int64_t ldb, int Rr, int64_t R, const 
 // the depth form one block (row q at offset 32 q), zeros where a row has no
 // entry; src is one box's column-major block of `rows` x `cols`, written from
 // column `shift` on.
+// One CTA per box and 32 source columns (blockIdx.y); consecutive threads
+// take consecutive columns of one row, so their stores fall into one 128-byte
+// chunk row; the column-strided reads of the source block are shared through
+// the cache by the warps of neighbouring rows.
 __global__ void k_tma_factors(const float* src, const int64_t* soff, const int* rows, const int* cols,
                               const int* shift, const int64_t* rb, int64_t nrows, float* hi, float* lo) {
-  const int b = blockIdx.x;
+  const int b = blockIdx.x, c0 = 32 * blockIdx.y;
   const int nr = rows[b], nc = cols[b], sh = shift ? shift[b] : 0;
+  if (c0 >= nc) return;
+  const int cw = min(32, nc - c0);
   const float* s = src + soff[b];
-  for (int e = threadIdx.x; e < nr * nc; e += blockDim.x) {
-    const int r = e % nr, c = e / nr;
+  for (int e = threadIdx.x; e < nr * cw; e += blockDim.x) {
+    const int c = c0 + e % cw, r = e / cw;
     const int64_t k = sh + c;
-    split_store(hi, lo, ((k >> 5) * nrows + rb[b] + r) * 32 + (k & 31), s[e]);
+    split_store(hi, lo, ((k >> 5) * nrows + rb[b] + r) * 32 + (k & 31), s[r + (int64_t)c * nr]);
   }
 }
 
@@ -674,6 +680,7 @@ int get_fac(Handle* h, TCache* c, int mode, cudaStream_t st, TFac** out) {
     const float* Ls = (const float*)(mode == RS_PREC_FP32 ? lv.Lf32 : lv.FL32);
     std::vector<int> ru(lv.nbox), cu(lv.nbox), rdn(lv.nbox), cdn(lv.nbox), sh(lv.nbox), c1(lv.nbox);
     std::vector<int64_t> su(lv.nbox), sd(lv.nbox), bu(lv.nbox), bd(lv.nbox);
+    int cmax_u = 1, cmax_d = 1;
     for (int b = 0; b < lv.nbox; ++b) {
       const int gi = g.gbase[d] + b;
       ru[b] = g.n[gi] + g.k[gi];
@@ -686,6 +693,8 @@ int get_fac(Handle* h, TCache* c, int mode, cudaStream_t st, TFac** out) {
       bd[b] = g.rbd[gi];
       sh[b] = g.delta[gi];
       c1[b] = (int)rup(g.k[gi] + g.delta[gi], 32);
+      cmax_u = std::max(cmax_u, cu[b]);
+      cmax_d = std::max(cmax_d, cdn[b]);
     }
     int *dru, *dcu;
     int64_t *dsu, *dbu;
@@ -693,7 +702,8 @@ int get_fac(Handle* h, TCache* c, int mode, cudaStream_t st, TFac** out) {
     RS_TRY(tup(c, &dcu, cu, st));
     RS_TRY(tup(c, &dsu, su, st));
     RS_TRY(tup(c, &dbu, bu, st));
-    k_tma_factors<<<lv.nbox, 256, 0, st>>>(Us, dsu, dru, dcu, nullptr, dbu, g.rows_up[d], f->ahu[d], f->alu[d]);
+    k_tma_factors<<<dim3(lv.nbox, (cmax_u + 31) / 32), 256, 0, st>>>(Us, dsu, dru, dcu, nullptr, dbu, g.rows_up[d],
+                                                                      f->ahu[d], f->alu[d]);
     RS_CHECK_LAUNCH();
     if (d > 0) {
       int *drd, *dcd, *dsh, *dc1;
@@ -705,7 +715,8 @@ int get_fac(Handle* h, TCache* c, int mode, cudaStream_t st, TFac** out) {
       RS_TRY(tup(c, &dsh, sh, st));
       RS_TRY(tup(c, &dc1, c1, st));
       const int64_t nr = std::max<int64_t>(1, g.rows_dn[d]);
-      k_tma_factors<<<lv.nbox, 256, 0, st>>>(Ls, dsd, drd, dcd, dsh, dbd, nr, f->ahd[d], f->ald[d]);
+      k_tma_factors<<<dim3(lv.nbox, (cmax_d + 31) / 32), 256, 0, st>>>(Ls, dsd, drd, dcd, dsh, dbd, nr, f->ahd[d],
+                                                                        f->ald[d]);
       RS_CHECK_LAUNCH();
       k_tma_ident<<<lv.nbox, 128, 0, st>>>(dbd, drd, dc1, nr, f->ahd[d]);
       RS_CHECK_LAUNCH();

@@ -150,3 +150,32 @@ def test_full_size_ellipse():
         assert np.all(res <= 10 * eps), res
     finally:
         H.free()
+
+
+def test_served_build_and_solve():
+    """A double-layer build queued on the server (which copies the normals and
+    curvatures at submission, so the caller's arrays may go away) serves
+    solves that match a direct build's."""
+    rs = _rs()
+    n = 4096
+    p, h, nrm, kap = ri.ellipse(n)
+    w = -2.0 * h
+    S = rs.Server(max_cols=16)
+    try:
+        nrm_tmp, kap_tmp = nrm.copy(), kap.copy()
+        t = S.submit_build(p, "laplace2d_dl", w, 1e-9, 64, 64, normals=nrm_tmp, curvature=kap_tmp)
+        del nrm_tmp, kap_tmp
+        r = S.wait(t)
+        assert r["status"] == 0
+        B = _boundary_data(p)[:, None].copy(order="F")
+        X = np.zeros_like(B)
+        q = S.wait(S.submit(r["result"], B, X))
+        assert q["status"] == 0 and q["relres"] <= 1e-10
+    finally:
+        S.destroy()
+    H = rs.rs_build(p, "laplace2d_dl", w, 1e-9, 64, 64, normals=nrm, curvature=kap)
+    Xr = np.zeros_like(B)
+    rs.rs_solve(H, B, Xr)
+    H.free()
+    assert np.linalg.norm(X - Xr) / np.linalg.norm(Xr) <= 1e-9
+    assert _interior_err(p, h, nrm, X[:, 0]) <= 1e-9
