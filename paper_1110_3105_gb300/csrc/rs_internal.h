@@ -193,6 +193,21 @@ void path_count(int which);
 // 0 = the warp kernel, else TM * 1000 + TN.
 int solve_tile_force();
 
+// Mapped pinned int flags (a persistent launch's error flag, read by the
+// host after the launch) from a process-wide pool: one cudaHostAlloc costs
+// more than the rest of a solve plan's set-up, and every new handle builds
+// plans.  flag_take gives a zeroed flag's host and device addresses;
+// flag_release returns it to the pool.
+int flag_take(int** host, int** dev);
+void flag_release(int* host);
+
+// Several small host tables staged for one device allocation and one copy.
+struct HostPack {
+  std::vector<unsigned char> buf;
+  size_t add_bytes(const void* p, size_t bytes);
+  template <class T> size_t add(const std::vector<T>& v) { return add_bytes(v.data(), sizeof(T) * v.size()); }
+};
+
 // allocation helper: records in h->allocs
 int dalloc(Handle* h, void** p, size_t bytes);
 template <class T> int dalloc_t(Handle* h, T** p, size_t count) {

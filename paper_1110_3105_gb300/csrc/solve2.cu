@@ -30,6 +30,7 @@
 #include <mutex>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <cuda/atomic>
 #include <vector>
 
@@ -832,6 +833,58 @@ int ct_for(bool cplx, int prec, int R) {
   return cplx ? 16 : 32;
 }
 
+}  // namespace
+
+// Host staging of several small tables for one device block: each at a
+// 256-byte aligned offset.
+size_t HostPack::add_bytes(const void* p, size_t bytes) {
+  const size_t o = (buf.size() + 255) & ~(size_t)255;
+  buf.resize(o + std::max<size_t>(bytes, 1));
+  if (bytes) std::memcpy(buf.data() + o, p, bytes);
+  return o;
+}
+
+// The flag pool: pages of 256 mapped, portable pinned ints, never returned
+// to the driver (a handful of pages serve a process).
+namespace {
+std::mutex g_flag_mu;
+std::vector<int*> g_flag_free;
+}  // namespace
+
+int flag_take(int** host, int** dev) {
+  int* f = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_flag_mu);
+    if (g_flag_free.empty()) {
+      int* page = nullptr;
+      if (cudaHostAlloc((void**)&page, 256 * sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        return fail(RS_ERR_OOM, "pinned flag page allocation failed");
+      }
+      for (int i = 255; i >= 0; --i) g_flag_free.push_back(page + i);
+    }
+    f = g_flag_free.back();
+    g_flag_free.pop_back();
+  }
+  *(volatile int*)f = 0;
+  if (cudaHostGetDevicePointer((void**)dev, f, 0) != cudaSuccess) {
+    cudaGetLastError();
+    flag_release(f);
+    return fail(RS_ERR_CUDA, "pinned flag: no device address");
+  }
+  *host = f;
+  return RS_OK;
+}
+
+void flag_release(int* host) {
+  if (!host) return;
+  std::lock_guard<std::mutex> lk(g_flag_mu);
+  g_flag_free.push_back(host);
+}
+
+namespace {
+
 template <class T>
 int dev_upload(PersPlan* P, T** d, const std::vector<T>& v, cudaStream_t st) {
   RS_CUDA(cudaMalloc((void**)d, sizeof(T) * std::max<size_t>(1, v.size())));
@@ -931,7 +984,7 @@ void free_pers(Handle* h) {
   if (!c) return;
   for (PersPlan* P : c->plans) {
     for (void* m : P->mem) cudaFree(m);
-    if (P->flag_host) cudaFreeHost(P->flag_host);
+    flag_release(P->flag_host);
     delete P;
   }
   delete c;
@@ -1051,26 +1104,33 @@ static int get_plan(Handle* h, int prec, int R, int tile, cudaStream_t st, PersP
   P->ntiles = (int)tiles.size();
   P->h_tiles = tiles;
   P->h_depth = depth;
-  RS_TRY(dev_upload(P, &P->tiles, tiles, st));
-  RS_TRY(dev_upload(P, &P->bt.depth, depth, st));
-  RS_TRY(dev_upload(P, &P->bt.n, n, st));
-  RS_TRY(dev_upload(P, &P->bt.k, k, st));
-  RS_TRY(dev_upload(P, &P->bt.off, off, st));
-  RS_TRY(dev_upload(P, &P->bt.skoff, skoff, st));
-  RS_TRY(dev_upload(P, &P->bt.uoff, uoff, st));
-  RS_TRY(dev_upload(P, &P->bt.loff, loff, st));
-  RS_TRY(dev_upload(P, &P->bt.parent, parent, st));
-  RS_TRY(dev_upload(P, &P->bt.up_need, up_need, st));
-  RS_TRY(dev_upload(P, &P->bt.dn_need, dn_need, st));
   std::vector<int64_t> ldv(L + 1);
   for (int d = 0; d <= L; ++d) ldv[d] = std::max<int64_t>(1, h->lv[d].ntot);
-  RS_TRY(dev_upload(P, &P->ldv, ldv, st));
+  // every table in one device block and one copy (the plan is built on the
+  // first solve of a new handle, where many small allocations and copies
+  // would cost more than the solve's own launches)
+  HostPack pk;
+  const size_t o_tiles = pk.add(tiles), o_depth = pk.add(depth), o_n = pk.add(n), o_k = pk.add(k),
+               o_off = pk.add(off), o_skoff = pk.add(skoff), o_uoff = pk.add(uoff), o_loff = pk.add(loff),
+               o_parent = pk.add(parent), o_up = pk.add(up_need), o_dn = pk.add(dn_need), o_ldv = pk.add(ldv);
+  unsigned char* blk = nullptr;
+  RS_TRY(dev_upload(P, &blk, pk.buf, st));
+  P->tiles = reinterpret_cast<Tile*>(blk + o_tiles);
+  P->bt.depth = reinterpret_cast<int*>(blk + o_depth);
+  P->bt.n = reinterpret_cast<int*>(blk + o_n);
+  P->bt.k = reinterpret_cast<int*>(blk + o_k);
+  P->bt.off = reinterpret_cast<int64_t*>(blk + o_off);
+  P->bt.skoff = reinterpret_cast<int64_t*>(blk + o_skoff);
+  P->bt.uoff = reinterpret_cast<int64_t*>(blk + o_uoff);
+  P->bt.loff = reinterpret_cast<int64_t*>(blk + o_loff);
+  P->bt.parent = reinterpret_cast<int*>(blk + o_parent);
+  P->bt.up_need = reinterpret_cast<int*>(blk + o_up);
+  P->bt.dn_need = reinterpret_cast<int*>(blk + o_dn);
+  P->ldv = reinterpret_cast<int64_t*>(blk + o_ldv);
   std::vector<int> zeros(2 + 2 * (size_t)G, 0);
   RS_TRY(dev_upload(P, &P->counters, zeros, st));
   RS_TRY(refresh_ptrs(h, P, st));
-  RS_CUDA(cudaHostAlloc((void**)&P->flag_host, sizeof(int), cudaHostAllocMapped));
-  *P->flag_host = 0;
-  RS_CUDA(cudaHostGetDevicePointer((void**)&P->flag_dev, P->flag_host, 0));
+  RS_TRY(flag_take(&P->flag_host, &P->flag_dev));
   RS_CUDA(cudaStreamSynchronize(st));
   *out = P;
   return RS_OK;

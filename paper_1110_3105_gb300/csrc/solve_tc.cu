@@ -637,15 +637,22 @@ int get_vec(TCache* c, int R, cudaStream_t st, TVec** out) {
   const int L = g.L;
   v->uh.assign(L + 1, nullptr);
   v->ul = v->vh = v->vl = v->xh = v->xl = v->uh;
+  // every depth's vectors in one zeroed block (ldp is a multiple of 32 rows,
+  // so every array starts 128-byte aligned)
+  size_t total = 0;
+  for (int d = 0; d <= L; ++d) total += (size_t)g.ldp[d] * R * (d < L ? 6 : 4);
+  float* blk = nullptr;
+  RS_TRY(talloc0(c, &blk, total, st));
+  float* q = blk;
   for (int d = 0; d <= L; ++d) {
     const size_t vs = (size_t)g.ldp[d] * R;
-    RS_TRY(talloc0(c, &v->uh[d], vs, st));
-    RS_TRY(talloc0(c, &v->ul[d], vs, st));
-    RS_TRY(talloc0(c, &v->vh[d], vs, st));
-    RS_TRY(talloc0(c, &v->vl[d], vs, st));
+    v->uh[d] = q; q += vs;
+    v->ul[d] = q; q += vs;
+    v->vh[d] = q; q += vs;
+    v->vl[d] = q; q += vs;
     if (d < L) {
-      RS_TRY(talloc0(c, &v->xh[d], vs, st));
-      RS_TRY(talloc0(c, &v->xl[d], vs, st));
+      v->xh[d] = q; q += vs;
+      v->xl[d] = q; q += vs;
     } else {   // never written or read at the leaves
       v->xh[d] = v->vh[d];
       v->xl[d] = v->vl[d];
@@ -668,16 +675,34 @@ int get_fac(Handle* h, TCache* c, int mode, cudaStream_t st, TFac** out) {
   const int L = g.L;
   f->ahu.assign(L + 1, nullptr);
   f->alu = f->ahd = f->ald = f->ahu;
+  // the four factor-row arrays of every depth in one zeroed block
+  std::vector<size_t> szu(L + 1), szd(L + 1);
+  size_t total = 0;
   for (int d = 0; d <= L; ++d) {
-    RS_TRY(talloc0(c, &f->ahu[d], (size_t)g.rows_up[d] * g.kpu[d], st));
-    RS_TRY(talloc0(c, &f->alu[d], (size_t)g.rows_up[d] * g.kpu[d], st));
-    RS_TRY(talloc0(c, &f->ahd[d], (size_t)std::max<int64_t>(1, g.rows_dn[d]) * g.kpd[d], st));
-    RS_TRY(talloc0(c, &f->ald[d], (size_t)std::max<int64_t>(1, g.rows_dn[d]) * g.kpd[d], st));
-    // sources: the FP32 solve's [calD ; calR] and calL, or the float forward
-    // factors [D ; P] and P^T
+    szu[d] = rup((int64_t)g.rows_up[d] * g.kpu[d], 64);
+    szd[d] = rup(std::max<int64_t>(1, g.rows_dn[d]) * g.kpd[d], 64);
+    total += 2 * (szu[d] + szd[d]);
+  }
+  float* blk = nullptr;
+  RS_TRY(talloc0(c, &blk, total, st));
+  {
+    float* q = blk;
+    for (int d = 0; d <= L; ++d) {
+      f->ahu[d] = q; q += szu[d];
+      f->alu[d] = q; q += szu[d];
+      f->ahd[d] = q; q += szd[d];
+      f->ald[d] = q; q += szd[d];
+    }
+  }
+  // per-box tables of every depth, staged together and copied once
+  struct Off {
+    size_t ru, cu, su, bu, rd, cd, sd, bd, sh, c1;
+    int cmax_u, cmax_d;
+  };
+  std::vector<Off> off(L + 1);
+  HostPack pk;
+  for (int d = 0; d <= L; ++d) {
     const Level& lv = h->lv[d];
-    const float* Us = (const float*)(mode == RS_PREC_FP32 ? lv.U32 : lv.FU32);
-    const float* Ls = (const float*)(mode == RS_PREC_FP32 ? lv.Lf32 : lv.FL32);
     std::vector<int> ru(lv.nbox), cu(lv.nbox), rdn(lv.nbox), cdn(lv.nbox), sh(lv.nbox), c1(lv.nbox);
     std::vector<int64_t> su(lv.nbox), sd(lv.nbox), bu(lv.nbox), bd(lv.nbox);
     int cmax_u = 1, cmax_d = 1;
@@ -696,29 +721,34 @@ int get_fac(Handle* h, TCache* c, int mode, cudaStream_t st, TFac** out) {
       cmax_u = std::max(cmax_u, cu[b]);
       cmax_d = std::max(cmax_d, cdn[b]);
     }
-    int *dru, *dcu;
-    int64_t *dsu, *dbu;
-    RS_TRY(tup(c, &dru, ru, st));
-    RS_TRY(tup(c, &dcu, cu, st));
-    RS_TRY(tup(c, &dsu, su, st));
-    RS_TRY(tup(c, &dbu, bu, st));
-    k_tma_factors<<<dim3(lv.nbox, (cmax_u + 31) / 32), 256, 0, st>>>(Us, dsu, dru, dcu, nullptr, dbu, g.rows_up[d],
-                                                                      f->ahu[d], f->alu[d]);
+    Off& o = off[d];
+    o.ru = pk.add(ru); o.cu = pk.add(cu); o.su = pk.add(su); o.bu = pk.add(bu);
+    o.rd = pk.add(rdn); o.cd = pk.add(cdn); o.sd = pk.add(sd); o.bd = pk.add(bd);
+    o.sh = pk.add(sh); o.c1 = pk.add(c1);
+    o.cmax_u = cmax_u;
+    o.cmax_d = cmax_d;
+  }
+  unsigned char* tb = nullptr;
+  RS_TRY(tup(c, &tb, pk.buf, st));
+  for (int d = 0; d <= L; ++d) {
+    // sources: the FP32 solve's [calD ; calR] and calL, or the float forward
+    // factors [D ; P] and Q^T
+    const Level& lv = h->lv[d];
+    const float* Us = (const float*)(mode == RS_PREC_FP32 ? lv.U32 : lv.FU32);
+    const float* Ls = (const float*)(mode == RS_PREC_FP32 ? lv.Lf32 : lv.FL32);
+    const Off& o = off[d];
+    auto I32 = [&](size_t x) { return reinterpret_cast<const int*>(tb + x); };
+    auto I64 = [&](size_t x) { return reinterpret_cast<const int64_t*>(tb + x); };
+    k_tma_factors<<<dim3(lv.nbox, (o.cmax_u + 31) / 32), 256, 0, st>>>(Us, I64(o.su), I32(o.ru), I32(o.cu), nullptr,
+                                                                        I64(o.bu), g.rows_up[d], f->ahu[d], f->alu[d]);
     RS_CHECK_LAUNCH();
     if (d > 0) {
-      int *drd, *dcd, *dsh, *dc1;
-      int64_t *dsd, *dbd;
-      RS_TRY(tup(c, &drd, rdn, st));
-      RS_TRY(tup(c, &dcd, cdn, st));
-      RS_TRY(tup(c, &dsd, sd, st));
-      RS_TRY(tup(c, &dbd, bd, st));
-      RS_TRY(tup(c, &dsh, sh, st));
-      RS_TRY(tup(c, &dc1, c1, st));
       const int64_t nr = std::max<int64_t>(1, g.rows_dn[d]);
-      k_tma_factors<<<dim3(lv.nbox, (cmax_d + 31) / 32), 256, 0, st>>>(Ls, dsd, drd, dcd, dsh, dbd, nr, f->ahd[d],
-                                                                        f->ald[d]);
+      k_tma_factors<<<dim3(lv.nbox, (o.cmax_d + 31) / 32), 256, 0, st>>>(Ls, I64(o.sd), I32(o.rd), I32(o.cd),
+                                                                          I32(o.sh), I64(o.bd), nr, f->ahd[d],
+                                                                          f->ald[d]);
       RS_CHECK_LAUNCH();
-      k_tma_ident<<<lv.nbox, 128, 0, st>>>(dbd, drd, dc1, nr, f->ahd[d]);
+      k_tma_ident<<<lv.nbox, 128, 0, st>>>(I64(o.bd), I32(o.rd), I32(o.c1), nr, f->ahd[d]);
       RS_CHECK_LAUNCH();
     }
   }
@@ -837,14 +867,16 @@ int build_plan(Handle* h, TCache* c, int mode, int R, int TN, cudaStream_t st, T
   P->ntiles = (int)tiles.size();
   P->h_tiles = tiles;
   TDev& v = P->dev;
-  TTile* dt = nullptr;
-  RS_TRY(tup(c, &dt, tiles, st));
-  v.tiles = dt;
   v.ntiles = P->ntiles;
   v.L = L;
   v.R = R;
   v.Rr = R;
   v.perm = h->perm;
+  // the plan's tables (tiles, leaf offsets, tensor maps, vector pointers,
+  // counters) staged together and copied in one piece
+  HostPack pk;
+  const size_t o_tiles = pk.add(tiles);
+  size_t o_lo = 0, o_lp = 0, o_ln = 0;
   {
     const int nl = h->lv[L].nbox;
     std::vector<int64_t> lo(nl), lp(nl);
@@ -854,15 +886,10 @@ int build_plan(Handle* h, TCache* c, int mode, int R, int TN, cudaStream_t st, T
       lp[b] = g.poff[g.gbase[L] + b];
       ln[b] = n[g.gbase[L] + b];
     }
-    int64_t *dlo, *dlp;
-    int* dln;
-    RS_TRY(tup(c, &dlo, lo, st));
-    RS_TRY(tup(c, &dlp, lp, st));
-    RS_TRY(tup(c, &dln, ln, st));
+    o_lo = pk.add(lo);
+    o_lp = pk.add(lp);
+    o_ln = pk.add(ln);
     P->nleaf = nl;
-    P->leaf_off = dlo;
-    P->leaf_poff = dlp;
-    P->leaf_n = dln;
   }
   std::vector<CUtensorMap> maps((size_t)NMAP * (L + 1));
   for (int d = 0; d <= L; ++d) {
@@ -884,39 +911,32 @@ int build_plan(Handle* h, TCache* c, int mode, int R, int TN, cudaStream_t st, T
     RS_TRY(make_map(m + M_U + 1, vec->ul[d], R, ch, TN));
   }
   {
-    CUtensorMap* dm = nullptr;
-    RS_TRY(cache_alloc(c, (void**)&dm, sizeof(CUtensorMap) * maps.size(), st));
-    RS_CUDA(cudaMemcpyAsync(dm, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, st));
-    v.maps = dm;
-    float** p0;
-    RS_TRY(tup(c, &p0, vec->uh, st));
-    v.uh = p0;
-    float** p1;
-    RS_TRY(tup(c, &p1, vec->ul, st));
-    v.ul = p1;
-    float** p2;
-    RS_TRY(tup(c, &p2, vec->xh, st));
-    v.xh = p2;
-    float** p3;
-    RS_TRY(tup(c, &p3, vec->xl, st));
-    v.xl = p3;
-    float** p4;
-    RS_TRY(tup(c, &p4, vec->vh, st));
-    v.vh = p4;
-    float** p5;
-    RS_TRY(tup(c, &p5, vec->vl, st));
-    v.vl = p5;
+    const size_t o_maps = pk.add(maps);
+    const size_t o_p0 = pk.add(vec->uh), o_p1 = pk.add(vec->ul), o_p2 = pk.add(vec->xh), o_p3 = pk.add(vec->xl),
+                 o_p4 = pk.add(vec->vh), o_p5 = pk.add(vec->vl);
+    std::vector<int> zeros(2 + 2 * (size_t)G, 0);
+    const size_t o_cnt = pk.add(zeros);
+    unsigned char* tb = nullptr;
+    RS_TRY(tup(c, &tb, pk.buf, st));
+    v.tiles = reinterpret_cast<const TTile*>(tb + o_tiles);
+    P->leaf_off = reinterpret_cast<int64_t*>(tb + o_lo);
+    P->leaf_poff = reinterpret_cast<int64_t*>(tb + o_lp);
+    P->leaf_n = reinterpret_cast<int*>(tb + o_ln);
+    v.maps = reinterpret_cast<const CUtensorMap*>(tb + o_maps);
+    v.uh = reinterpret_cast<float* const*>(tb + o_p0);
+    v.ul = reinterpret_cast<float* const*>(tb + o_p1);
+    v.xh = reinterpret_cast<float* const*>(tb + o_p2);
+    v.xl = reinterpret_cast<float* const*>(tb + o_p3);
+    v.vh = reinterpret_cast<float* const*>(tb + o_p4);
+    v.vl = reinterpret_cast<float* const*>(tb + o_p5);
+    P->counters = reinterpret_cast<int*>(tb + o_cnt);
   }
-  std::vector<int> zeros(2 + 2 * (size_t)G, 0);
-  RS_TRY(tup(c, &P->counters, zeros, st));
   v.dispatch = P->counters;
   v.dflag = P->counters + 1;
   v.cnt = P->counters;
   v.trace = nullptr;
-  RS_CUDA(cudaHostAlloc((void**)&P->flag_host, sizeof(int), cudaHostAllocMapped));
+  RS_TRY(flag_take(&P->flag_host, &P->flag_dev));
   c->flags.push_back(P->flag_host);
-  *P->flag_host = 0;
-  RS_CUDA(cudaHostGetDevicePointer((void**)&P->flag_dev, P->flag_host, 0));
   // algorithmic work per column: the float factors read once, B read and X
   // written (double), 2 flops per stored scalar
   double fa = 0.0;
@@ -1047,7 +1067,7 @@ void free_tc(Handle* h) {
   TCache* c = (TCache*)h->pers_tc;
   if (!c) return;
   for (void* m : c->mem) cudaFreeAsync(m, 0);
-  for (int* f : c->flags) cudaFreeHost(f);
+  for (int* f : c->flags) flag_release(f);
   for (TPlan* P : c->plans) delete P;
   for (TVec* v : c->vecs) delete v;
   for (TFac* f : c->facs) delete f;
