@@ -9,16 +9,19 @@
 // block product on the tensor cores (tcgen05.mma kind::tf32, accumulator in
 // tensor memory).  Every operand is kept as two tf32 values a = hi + lo and a
 // product is formed as lo*hi + hi*lo + hi*hi (three MMAs per K step), about
-// fp32 accuracy.
+// fp32 accuracy.  The factor rows are stored split; the vectors are stored as
+// plain floats and split on their way in: the TMA copy lands in the hi slot
+// of a stage and two converter warps rewrite it in place as hi and fill the
+// lo slot before the MMAs read the stage.
 //
 // Data layout (per handle, per precision mode and column count):
-//   * per tree depth d, vectors of ldp_d rows x R columns (column-major);
-//     every box's segment starts at a multiple of 32 rows (its padded
-//     offset poff), the gaps stay zero; the input of the upward pass (vh/vl,
-//     hi and lo parts), calD b (u, float) and the result of the downward pass
-//     (xh/xl) at depths above the leaves; the leaves' input is the caller's B
-//     permuted to tree order and split by one streaming kernel, and the
-//     leaves' result goes to the caller's X (double) through the permutation;
+//   * per tree depth d, float vectors of ldp_d rows x R columns; every box's
+//     segment starts at a multiple of 32 rows (its padded offset poff), the
+//     gaps stay zero; the input of the upward pass (v), calD b (u) and the
+//     result of the downward pass (x) at depths above the leaves; the
+//     leaves' input is the caller's B permuted to tree order by one streaming
+//     kernel, and the leaves' result goes to the caller's X (double) through
+//     the permutation;
 //   * factor rows row-major with a 32-multiple row pitch per depth, hi and lo
 //     arrays: the rows of [calD ; calR] (upward operand) and of calL
 //     (downward operand, preceded by delta zero columns, delta = the
@@ -32,10 +35,11 @@
 // The CTA is warp-specialised: warp 0 (one thread) claims tiles in
 // dependency order, waits for their inputs (bounded spin on the per-box
 // counters) and issues the TMA copies of each K chunk into a ring of stages;
-// warp 1 (one thread) issues the MMAs of each full stage and releases it
-// (tcgen05.commit), two tensor-memory accumulators alternating; warps 2-5
-// read a finished accumulator (warp w: lanes 32 (w % 4)..), split and store
-// the results, and publish a tile with one release-add on its counter.
+// warps 10-11 split each landed input chunk into its hi and lo parts; warp 1
+// (one thread) issues the MMAs of each converted stage and releases it
+// (tcgen05.commit), two tensor-memory accumulators alternating; warps 2-9
+// read a finished accumulator (warp w: lanes 32 (w % 4)..), store the
+// results, and publish a tile with one release-add on its counter.
 // Every wait is bounded; past its limit a waiter raises the error flags and
 // all roles drain and leave.
 #include <cuda.h>
@@ -56,7 +60,8 @@ namespace {
 
 constexpr int K_UP = 0, K_ROOT = 1, K_DOWN = 2;
 constexpr int TT_NE = 256;            // 8 epilogue warps: two per tensor-memory lane quarter
-constexpr int TT_NT = 64 + TT_NE;     // + the producer warp and the MMA warp
+constexpr int TT_NC = 64;             // 2 converter warps (warps 10, 11)
+constexpr int TT_NT = 64 + TT_NE + TT_NC;   // + the producer warp and the MMA warp
 constexpr int TT_TM = 128, TT_KC = 32;
 constexpr int TT_POLLS = 1 << 30;
 constexpr long long TT_WAIT_NS = 500000000;   // give up a stage / accumulator wait after 0.5 s
@@ -181,9 +186,11 @@ __global__ void __launch_bounds__(TT_NT, 1) k_solve_tma(TDev p, const double* B,
   constexpr int NS = C::NS;
   extern __shared__ unsigned char tt_raw[];
   __shared__ uint32_t s_taddr;
-  __shared__ __align__(8) uint64_t s_full[NS], s_empty[NS], s_accf[2], s_acce[2];
+  __shared__ __align__(8) uint64_t s_full[NS], s_conv[NS], s_empty[NS], s_accf[2], s_acce[2];
   __shared__ TUnit s_unit[TT_UQ];
   __shared__ int s_eok[2];
+  __shared__ int s_end[NS];   // 1: the stage carries the producer's end marker (no copies)
+  __shared__ int s_cok;       // the converters' wait for the current stage succeeded
   const uint32_t raw = tc::smem_u32(tt_raw);
   unsigned char* base = tt_raw + ((1024u - (raw & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -191,6 +198,7 @@ __global__ void __launch_bounds__(TT_NT, 1) k_solve_tma(TDev p, const double* B,
   if (tid == 32) {
     for (int i = 0; i < NS; ++i) {
       tc::mbar_init(&s_full[i], 1);
+      tc::mbar_init(&s_conv[i], 1);
       tc::mbar_init(&s_empty[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -230,7 +238,7 @@ __global__ void __launch_bounds__(TT_NT, 1) k_solve_tma(TDev p, const double* B,
           continue;
         }
         const CUtensorMap* mA = p.maps + tl.mapA;
-        const uint32_t tx = 2u * (uint32_t)tl.ah * 128u + 2u * C::b_bytes;
+        const uint32_t tx = 2u * (uint32_t)tl.ah * 128u + C::b_bytes;
         for (int c0 = tl.c0; c0 < cend && !bad; c0 += TN, ++u) {
           for (int kc = 0; kc < tl.nkc; ++kc, ++s) {
             const int si = s % NS;
@@ -241,6 +249,7 @@ __global__ void __launch_bounds__(TT_NT, 1) k_solve_tma(TDev p, const double* B,
             }
             if (kc == 0) s_unit[u % TT_UQ] = TUnit{t, c0, min(TN, cend - c0), tl.nkc, c0 + TN >= cend ? 1 : 0};
             unsigned char* st = base + (size_t)si * C::stage;
+            s_end[si] = 0;
             mbar_expect_tx(&s_full[si], tx);
             // the first nk1 chunks of the input from one vector, the rest from
             // the second (down tiles: x_parent, then u); both bases are
@@ -251,8 +260,7 @@ __global__ void __launch_bounds__(TT_NT, 1) k_solve_tma(TDev p, const double* B,
             const int zb = first ? (tl.bx >> 5) + kc : (tl.bx2 >> 5) + (kc - tl.nk1);
             tma_load_3d(st, mA, tl.ay, kc, &s_full[si]);
             tma_load_3d(st + C::a_bytes, mA + 1, tl.ay, kc, &s_full[si]);
-            tma_load_3d(st + 2 * C::a_bytes, mB, c0, zb, &s_full[si]);
-            tma_load_3d(st + 2 * C::a_bytes + C::b_bytes, mB + 1, c0, zb, &s_full[si]);
+            tma_load_3d(st + 2 * C::a_bytes, mB, c0, zb, &s_full[si]);   // plain floats into the hi slot
           }
         }
       }
@@ -260,16 +268,53 @@ __global__ void __launch_bounds__(TT_NT, 1) k_solve_tma(TDev p, const double* B,
       const int si = s % NS;
       if (!tc::mbar_wait(&s_empty[si], ((s / NS) & 1) ^ 1, TT_POLLS, TT_WAIT_NS)) raise();
       s_unit[u % TT_UQ] = TUnit{-1, 0, 0, 0, 0};
+      s_end[si] = 1;
       mbar_arrive(&s_full[si]);
     }
     __syncwarp();
+  } else if (warp >= 2 + TT_NE / 32) {
+    // ------------------------------------------------ input split (2 warps)
+    // Each landed stage: the input chunk (TN x 32 floats, 128-byte swizzled;
+    // the split is elementwise, so the layout does not matter) becomes its
+    // tf32 hi part in place and its lo part in the lo slot; then the stage
+    // is handed to the MMA warp.  The end marker is passed on unchanged.
+    const int ct = tid - (64 + TT_NE);
+    for (int s = 0;; ++s) {
+      const int si = s % NS;
+      if (ct == 0) {
+        const bool ok = tc::mbar_wait(&s_full[si], (s / NS) & 1, TT_POLLS, TT_WAIT_NS);
+        if (!ok) raise();
+        s_cok = ok ? 1 : 0;
+      }
+      named_sync(3, TT_NC);   // the landed stage (or the failed wait) is seen by both warps
+      const bool end = !s_cok || s_end[si];
+      if (!end && !*(volatile int*)p.dflag) {
+        float4* bh = reinterpret_cast<float4*>(base + (size_t)si * C::stage + 2 * C::a_bytes);
+        float4* bl = reinterpret_cast<float4*>(base + (size_t)si * C::stage + 2 * C::a_bytes + C::b_bytes);
+#pragma unroll 4
+        for (int i = ct; i < (int)(C::b_bytes / 16); i += TT_NC) {
+          const float4 v = bh[i];
+          float4 h, l;
+          tc::tf32_split(v.x, h.x, l.x);
+          tc::tf32_split(v.y, h.y, l.y);
+          tc::tf32_split(v.z, h.z, l.z);
+          tc::tf32_split(v.w, h.w, l.w);
+          bh[i] = h;
+          bl[i] = l;
+        }
+        tc::fence_smem_to_async();   // generic-proxy writes, read next by the tensor cores
+      }
+      named_sync(3, TT_NC);
+      if (ct == 0) mbar_arrive(&s_conv[si]);
+      if (end) break;
+    }
   } else if (warp == 1) {
     // ------------------------------------------------------------- MMA issue
     if (lane == 0) {
       constexpr uint32_t IDESC = tc::idesc(tc::FMT_TF32, TT_TM, TN);
       int s = 0;
       for (int u = 0;; ++u) {
-        if (!tc::mbar_wait(&s_full[s % NS], (s / NS) & 1, TT_POLLS, TT_WAIT_NS)) {
+        if (!tc::mbar_wait(&s_conv[s % NS], (s / NS) & 1, TT_POLLS, TT_WAIT_NS)) {
           raise();
           break;
         }
@@ -286,7 +331,7 @@ __global__ void __launch_bounds__(TT_NT, 1) k_solve_tma(TDev p, const double* B,
         bool bad = false;
         for (int kc = 0; kc < un.nkc; ++kc, ++s) {
           const int si = s % NS;
-          if (kc > 0 && !tc::mbar_wait(&s_full[si], (s / NS) & 1, TT_POLLS, TT_WAIT_NS)) {
+          if (kc > 0 && !tc::mbar_wait(&s_conv[si], (s / NS) & 1, TT_POLLS, TT_WAIT_NS)) {
             raise();
             bad = true;
             break;
@@ -340,11 +385,8 @@ __global__ void __launch_bounds__(TT_NT, 1) k_solve_tma(TDev p, const double* B,
       const int c0 = un.c0, cw = un.cw;
       const int64_t pos = tl.pos0 + i;
       float* const uhd = p.uh[d];
-      float* const uld = p.ul[d];
       float* const xhd = p.xh[d];
-      float* const xld = p.xl[d];
       float* const vhp = d > 0 ? p.vh[d - 1] : nullptr;
-      float* const vlp = d > 0 ? p.vl[d - 1] : nullptr;
       const int64_t pp = tl.slot + (r - n);
       constexpr int JW = TN / 2 < 32 ? TN / 2 : 32;   // columns per batch
       for (int j0 = jb; j0 < jb + TN / 2; j0 += JW) {
@@ -368,18 +410,18 @@ __global__ void __launch_bounds__(TT_NT, 1) k_solve_tma(TDev p, const double* B,
             for (int q = 0; q < JW; ++q)
               if (q < jn) X[dst + (c + q) * ldx] = f32_to_f64(acc[q]);
           }
-        } else if (down || tl.kind == K_ROOT) {   // x, kept split for the children's copies
+        } else if (down || tl.kind == K_ROOT) {   // x, for the children's copies
 #pragma unroll
           for (int q = 0; q < JW; ++q)
-            if (q < jn) split_store(xhd, xld, vidx(pos, c + q, R), acc[q]);
-        } else if (r < n) {   // u = calD b, split: the down tile reads it as an input
+            if (q < jn) xhd[vidx(pos, c + q, R)] = acc[q];
+        } else if (r < n) {   // u = calD b: the down tile reads it as an input
 #pragma unroll
           for (int q = 0; q < JW; ++q)
-            if (q < jn) split_store(uhd, uld, vidx(pos, c + q, R), acc[q]);
+            if (q < jn) uhd[vidx(pos, c + q, R)] = acc[q];
         } else {   // c = calR b into the parent's input
 #pragma unroll
           for (int q = 0; q < JW; ++q)
-            if (q < jn) split_store(vhp, vlp, vidx(pp, c + q, R), acc[q]);
+            if (q < jn) vhp[vidx(pp, c + q, R)] = acc[q];
         }
       }
       tc::fence_before_sync();
@@ -402,7 +444,7 @@ __global__ void __launch_bounds__(TT_NT, 1) k_solve_tma(TDev p, const double* B,
   if (warp == 0) tc::tmem_free(tmem, C::tmem_cols);
 }
 
-// The caller's B (double, original order) into the leaves' split input
+// The caller's B (double, original order) into the leaves' float input
 // vectors (tree order, padded): one CTA per leaf box and 64 columns.
 __global__ void k_tma_in(const double* B, int64_t ldb, int Rr, int64_t R, const int* perm, const int64_t* off,
                          const int64_t* poff, const int* n, float* vh, float* vl) {
@@ -413,7 +455,8 @@ __global__ void k_tma_in(const double* B, int64_t ldb, int Rr, int64_t R, const 
     const int r = e % nb, c = c0 + e / nb;
     if (c >= Rr) break;
     const double v = B[(int64_t)perm[o + r] + (int64_t)c * ldb];
-    split_store(vh, vl, vidx(po + r, c, R), f64_to_f32_rn(v));
+    vh[vidx(po + r, c, R)] = f64_to_f32_rn(v);
+    (void)vl;
   }
 }
 
@@ -638,25 +681,25 @@ int get_vec(TCache* c, int R, cudaStream_t st, TVec** out) {
   v->uh.assign(L + 1, nullptr);
   v->ul = v->vh = v->vl = v->xh = v->xl = v->uh;
   // every depth's vectors in one zeroed block (ldp is a multiple of 32 rows,
-  // so every array starts 128-byte aligned)
+  // so every array starts 128-byte aligned); the vectors are plain floats,
+  // split in shared memory, so the lo arrays are the hi arrays
   size_t total = 0;
-  for (int d = 0; d <= L; ++d) total += (size_t)g.ldp[d] * R * (d < L ? 6 : 4);
+  for (int d = 0; d <= L; ++d) total += (size_t)g.ldp[d] * R * (d < L ? 3 : 2);
   float* blk = nullptr;
   RS_TRY(talloc0(c, &blk, total, st));
   float* q = blk;
   for (int d = 0; d <= L; ++d) {
     const size_t vs = (size_t)g.ldp[d] * R;
     v->uh[d] = q; q += vs;
-    v->ul[d] = q; q += vs;
     v->vh[d] = q; q += vs;
-    v->vl[d] = q; q += vs;
     if (d < L) {
       v->xh[d] = q; q += vs;
-      v->xl[d] = q; q += vs;
     } else {   // never written or read at the leaves
       v->xh[d] = v->vh[d];
-      v->xl[d] = v->vl[d];
     }
+    v->ul[d] = v->uh[d];
+    v->vl[d] = v->vh[d];
+    v->xl[d] = v->xh[d];
   }
   *out = v;
   return RS_OK;
