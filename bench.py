@@ -377,7 +377,7 @@ def serving_session(rs, torch, resident, window_s, rate, seed, build_every_s=5.0
 def serving(rs, torch, H2, n2, plain2, window_s, stream):
     """Configs 2-4 resident (built here besides the benchmark's handle);
     a session at the configuration's rate (2000 requests/s, ~65k RHS/s
-    offered), then one at 70% of the capacity that session measured; and a
+    offered), then one at 50% of the capacity that session measured; and a
     session with the 131072-point factorization alone at the same rate."""
     resident = [(H2, n2, False, 1e-10, plain2)]
     own = []
@@ -390,7 +390,10 @@ def serving(rs, torch, H2, n2, plain2, window_s, stream):
         resident.append((H, wl["n"], cplx, tol, plain_fp64_rate(rs, torch, H, wl["n"], cplx)))
     try:
         sat = serving_session(rs, torch, resident, window_s, 2000.0, seed=7)
-        rate2 = 0.7 * sat["rhs_per_s"] / 32.5
+        # half the saturated rate: served in smaller batches (less efficient per
+        # column than the ~1000-column batches of saturation), so 70% of the
+        # saturated rate was measured to sit at the small-batch capacity
+        rate2 = 0.5 * sat["rhs_per_s"] / 32.5
         below = serving_session(rs, torch, resident, max(10.0, window_s / 3), rate2, seed=8)
         alone = serving_session(rs, torch, resident, max(10.0, window_s / 3), 2000.0, seed=9, only_first=True)
     finally:
