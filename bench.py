@@ -80,10 +80,10 @@ def ncu_traffic(kernel: str):
                 continue
             src = os.path.join(ROOT, kv.get("source", ""))
             cur = hashlib.sha256(open(src, "rb").read()).hexdigest() if os.path.isfile(src) else None
-            where = f"{os.path.relpath(path, ROOT)} ({kv.get('launch', '')})"
+            where = f"of {kernel} ({kv.get('launch', '')} launch)"
             if cur == kv.get("sha256"):
                 return int(kv["dram_bytes"]), f"ncu capture {where}, source unchanged since"
-            stale = f"ncu capture {where} predates the current {kv.get('source')}"
+            stale = f"ncu capture {where} predates the current source of the kernel"
     return None, stale or "no ncu capture of this kernel"
 
 
