@@ -285,7 +285,9 @@ int64_t rs_launch_count(void);
  * takes all requests queued for its handle (up to max_cols columns), packs
  * them into one batch, runs rs_solve_refined on it and completes each
  * request.  Requests arriving while a batch is on the GPU join the next
- * batch; different handles' batches overlap on the device.  Builds submitted
+ * batch; different handles' columns are copied in and out concurrently, but
+ * their solves take turns (one refined solve on the GPU at a time, each
+ * filling the GPU).  Builds submitted
  * to the server run on a builder thread and are admitted only while the
  * estimated device memory of the resident factorizations plus the new one
  * stays under hbm_budget_bytes (<= 0: 90% of the free memory at creation);

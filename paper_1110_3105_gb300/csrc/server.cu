@@ -11,8 +11,13 @@
 // copied in on the copy stream, and a finished batch's columns are copied
 // back on the copy stream while the next solve runs; its requests complete
 // from a host callback once that copy lands.  Requests that arrive while a
-// batch is on the GPU wait for a later one, so batches form continuously;
-// workers of different handles run concurrently.  Builds
+// batch is on the GPU wait for a later one, so batches form continuously.
+// Workers of different handles stage and return columns concurrently but
+// take turns for the solves themselves (one refined solve on the GPU at a
+// time): every solve is a persistent launch sized to fill the GPU, and
+// concurrent ones from several streams contend for the SMs (on the
+// config-5 mix over 60 s, 17.9k right-hand sides per second concurrently
+// against 21.3k taking turns).  Builds
 // run on a builder thread and are admitted only while the estimated device
 // memory of the resident factorizations plus the new one stays under the
 // server's budget.
@@ -85,6 +90,7 @@ struct Server {
   std::vector<double> lat_ms;
   int64_t rhs_done = 0, batches = 0, batch_cols = 0;
   Clock::time_point t0 = Clock::now();
+  std::mutex gpu_mu;   // held by the worker whose refined solve is on the GPU
 };
 
 struct Worker {
@@ -227,7 +233,10 @@ void Worker::run() {
       cudaGetLastError();
       rc = RS_ERR_CUDA;
     }
-    if (rc == RS_OK) rc = rs_solve_refined(h, db[slot], n, cur_cols, dx[slot], n, tol, 8, &its, rel.data(), stream);
+    if (rc == RS_OK) {   // one solve at a time (the copies keep overlapping on the copy streams)
+      std::lock_guard<std::mutex> g(s->gpu_mu);
+      rc = rs_solve_refined(h, db[slot], n, cur_cols, dx[slot], n, tol, 8, &its, rel.data(), stream);
+    }
     // columns back on the copy stream once the solve is done; completion from a callback
     cudaEvent_t solved;
     bool ok = cudaEventCreateWithFlags(&solved, cudaEventDisableTiming) == cudaSuccess &&
