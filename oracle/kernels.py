@@ -31,8 +31,11 @@ kernel is numpy's complex exponential.
 
 Pins: tests/test_oracle_solver.py checks the Laplace 2D kernel through the
 closed-form spectrum of A on the unit circle (eigenvalue 1 - ln(N)/N for the
-constant mode, and its continuum limit 1 + 1/(2m)); the Helmholtz kernel
-through the continuum limit 1 + (i pi / 2) J_m(k) H_m^(1)(k) on the circle;
+constant mode, and its continuum limit 1 + 1/(2m)); the 2D Helmholtz kernel
+through the Helmholtz equation (second differences), the outgoing radiation
+condition and its small-argument limit (the Laplace kernel plus i/4 -
+(log(k/2) + gamma)/(2 pi)), and the continuum limit 1 + (i pi / 2) J_m(k)
+H_m^(1)(k) on the circle;
 the 3D kernel through the single-layer eigenvalue 1 + 1/(2l+1) of the
 spherical harmonics on the sphere; the 3D Helmholtz kernel through the
 Helmholtz equation itself (a finite-difference Laplacian of G plus k^2 G

@@ -157,6 +157,41 @@ def test_helmholtz3d_kernel_pins():
     assert abs(g - ser) < kk**3 * r * r / (4 * np.pi) + 1e-15
 
 
+def test_helmholtz2d_kernel_pins():
+    """G = (i/4) H0^(1)(k r) checked without the Bessel routines it is built
+    from: (Laplacian + k^2) G = 0 off the source (second differences in x and
+    y, O(h^2)); sqrt(r) (dG/dr - i k G) decays like 1/r (outgoing; the
+    incoming wave would leave a term growing like sqrt(r)); and as k r -> 0,
+    G + log(r) / (2 pi) -> i/4 - (log(k/2) + gamma) / (2 pi), the 2D Laplace
+    kernel plus a constant (Euler's gamma)."""
+    k = 7.0
+    y = np.zeros((2, 1))
+    x0 = np.array([0.45, -0.3])
+    for hstep in (1e-2, 5e-3):
+        g0 = green("helmholtz2d", x0[:, None], y, k)[0, 0]
+        lap = 0.0
+        for d in range(2):
+            e = np.zeros(2)
+            e[d] = hstep
+            gp = green("helmholtz2d", (x0 + e)[:, None], y, k)[0, 0]
+            gm = green("helmholtz2d", (x0 - e)[:, None], y, k)[0, 0]
+            lap += (gp - 2 * g0 + gm) / hstep**2
+        assert abs(lap + k * k * g0) < 2.0 * hstep**2 * abs(k**4 * g0) + 1e-9
+    for r in (50.0, 500.0):
+        dr = 1e-5
+        p = lambda t: np.array([[t], [0.0]])
+        g = green("helmholtz2d", p(r), y, k)[0, 0]
+        dg = (green("helmholtz2d", p(r + dr), y, k)[0, 0] - green("helmholtz2d", p(r - dr), y, k)[0, 0]) / (2 * dr)
+        bound = 2.0 * np.sqrt(2.0 / (np.pi * k)) / (8.0 * r)
+        assert abs(np.sqrt(r) * (dg - 1j * k * g)) < bound
+    gamma = 0.5772156649015329
+    for r in (1e-5, 1e-6):
+        kk = 10.0
+        g = green("helmholtz2d", np.array([[r], [0.0]]), y, kk)[0, 0]
+        lim = 0.25j - (np.log(kk / 2) + gamma) / (2 * np.pi)
+        assert abs(g + np.log(r) / (2 * np.pi) - lim) < 1e-6
+
+
 def test_sphere_helmholtz_single_layer_eigenvalue():
     """On the unit sphere the single layer of eq. 3d-helmholtz maps Y_l to
     i k j_l(k) h_l^(1)(k) Y_l; A = I + w K approximates I + S, to the same
