@@ -187,7 +187,10 @@ static int stage_in(const void* p, int64_t ld, int64_t N, int nrhs, size_t sb, c
   RS_CUDA(cudaMallocAsync(&s->d, sb * (size_t)N * nrhs, st));
   s->owned = true;
   s->ld = N;
-  RS_CUDA(cudaMemcpy2DAsync(s->d, sb * N, p, sb * ld, sb * N, nrhs, cudaMemcpyHostToDevice, st));
+  if (ld == N)   // contiguous: one plain copy (the pitched form ran at half the link's rate)
+    RS_CUDA(cudaMemcpyAsync(s->d, p, sb * (size_t)N * nrhs, cudaMemcpyHostToDevice, st));
+  else
+    RS_CUDA(cudaMemcpy2DAsync(s->d, sb * N, p, sb * ld, sb * N, nrhs, cudaMemcpyHostToDevice, st));
   return RS_OK;
 }
 
@@ -205,7 +208,10 @@ static int stage_out_alloc(void* p, int64_t ld, int64_t N, int nrhs, size_t sb, 
 
 static int stage_out_finish(void* p, int64_t ld, int64_t N, int nrhs, size_t sb, cudaStream_t st, Staged* s) {
   if (s->owned) {
-    RS_CUDA(cudaMemcpy2DAsync(p, sb * ld, s->d, sb * N, sb * N, nrhs, cudaMemcpyDeviceToHost, st));
+    if (ld == N)
+      RS_CUDA(cudaMemcpyAsync(p, s->d, sb * (size_t)N * nrhs, cudaMemcpyDeviceToHost, st));
+    else
+      RS_CUDA(cudaMemcpy2DAsync(p, sb * ld, s->d, sb * N, sb * N, nrhs, cudaMemcpyDeviceToHost, st));
   }
   return RS_OK;
 }
