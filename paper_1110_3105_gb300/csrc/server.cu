@@ -169,8 +169,13 @@ int Worker::stage_in(int slot, const std::vector<std::shared_ptr<Request>>& batc
   }
   size_t col = 0;
   for (auto& r : batch) {
-    if (cudaMemcpy2DAsync((char*)db[slot] + col * n * sb, n * sb, r->B, r->ldb * sb, n * sb, r->ncols,
-                          cudaMemcpyHostToDevice, cstream) != cudaSuccess) {
+    // contiguous columns: one plain copy (the pitched form ran at half the link's rate)
+    const cudaError_t e =
+        r->ldb == n ? cudaMemcpyAsync((char*)db[slot] + col * n * sb, r->B, n * sb * r->ncols, cudaMemcpyHostToDevice,
+                                      cstream)
+                    : cudaMemcpy2DAsync((char*)db[slot] + col * n * sb, n * sb, r->B, r->ldb * sb, n * sb, r->ncols,
+                                        cudaMemcpyHostToDevice, cstream);
+    if (e != cudaSuccess) {
       cudaGetLastError();
       return RS_ERR_CUDA;
     }
@@ -249,8 +254,10 @@ void Worker::run() {
     for (auto& r : cur) {
       double worst = 0;
       if (rc == RS_OK &&
-          cudaMemcpy2DAsync(r->X, r->ldx * sb, (const char*)dx[slot] + col * n * sb, n * sb, n * sb, r->ncols,
-                            cudaMemcpyDeviceToHost, cstream) != cudaSuccess) {
+          (r->ldx == n ? cudaMemcpyAsync(r->X, (const char*)dx[slot] + col * n * sb, n * sb * r->ncols,
+                                         cudaMemcpyDeviceToHost, cstream)
+                       : cudaMemcpy2DAsync(r->X, r->ldx * sb, (const char*)dx[slot] + col * n * sb, n * sb, n * sb,
+                                           r->ncols, cudaMemcpyDeviceToHost, cstream)) != cudaSuccess) {
         cudaGetLastError();
         rc = RS_ERR_CUDA;
       }
