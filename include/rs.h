@@ -211,13 +211,16 @@ int rs_stats(rs_handle h, rs_stats_t* out);
  *   ncoll      (nbox) colleague count, or NULL
  *   coll       (nbox * 27) colleague box indices ascending, -1 padded, or NULL
  * rs_tree_perm(h, perm): perm[i] = original index of the point at tree
- * position i (int64, N entries). */
+ * position i (int64, N entries).  The tree is the paper's uniform orthtree
+ * with contiguous boxes (Sec. 2.1, Example 1).  Errors: RS_ERR_ARG for a
+ * null handle, a null perm or a level out of range. */
 int rs_tree_perm(rs_handle h, int64_t* perm);
 int rs_tree_level(rs_handle h, int level, int* nbox_out, int64_t* begin,
                   int* parent, int* ncoll, int* coll);
 
-/* Per-box ranks at depth l (1..depth): n (active size) and k (skeletons),
- * host arrays of nbox entries, either may be NULL. */
+/* Per-box ranks at depth l (1..depth): n (active size) and k (skeletons,
+ * the ID ranks of Sec. 2.2), host arrays of nbox entries, either may be
+ * NULL.  Errors: RS_ERR_ARG for a null handle or a level out of range. */
 int rs_box_ranks(rs_handle h, int level, int* n, int* k);
 
 /* Launch profiler (off by default).  rs_profile_enable(1) clears the record
@@ -274,7 +277,8 @@ int rs_probe_fma_peak(int precision, double* gflops);
  * ran out, RS_ERR_CUDA on a launch error. */
 int rs_tc_selftest(int kind, const float* A, const float* B, float* D, int n);
 
-/* Number of kernels the library has launched in this process so far. */
+/* Number of kernels the library has launched in this process so far
+ * (measurement; no counterpart in the paper). */
 int64_t rs_launch_count(void);
 
 /* ------------------------------------------------------------------ serving
